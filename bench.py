@@ -1,0 +1,336 @@
+"""Benchmark of the Gray-Scott stencil hot path on GB300.
+
+Default workload (one bench step): the plain FP32 stencil on a periodic
+512^3 grid (134M cells, four 0.54 GB field buffers, larger than L2), noise
+0.1 from the counter hash with seed 42, Du=0.2 Dv=0.1 F=0.02 k=0.048 dt=1:
+re-initialise to the centred cube, then 1000 time steps.  Metric: giga
+cell-updates per second (GCUPS) and the fraction of the measured HBM
+roofline (16 B per cell-step in FP32, 32 B in FP64).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas: the plain grid does not shard), and rank 0 prints one JSON line
+with value = total cell updates of all ranks / max time over ranks.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gray-Scott GCUPS & % HBM peak; surrogate/batched vs plain time at fixed error"
+PARAMS = dict(Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0)
+L_MAIN, NSTEPS, NOISE, SEED = 512, 1000, 0.1, 42
+KERNEL_SRC = os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", "gs_stencil.cu")
+PROFILE = os.path.join(ROOT, "profiles", "gs_zmarch_f32_L512.md")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_digest() -> str:
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not b or m.group(1) != kernel_digest():
+        return None
+    return float(b.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(target_s: float = 12.0, L: int = L_MAIN):
+    """Time the FP64 CPU oracle on a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    u, v = oracle.init(L)
+    t0 = time.perf_counter()
+    u, v = oracle.step(u, v, 1, **PARAMS, noise=NOISE, seed=SEED, t0=0)
+    one = time.perf_counter() - t0
+    n = max(1, min(50, int(target_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    u, v = oracle.step(u, v, n, **PARAMS, noise=NOISE, seed=SEED, t0=1)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(u).all()
+    return {"value": L ** 3 * n / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle, L={L}, steps 1..{n} of the noise-0.1 centred-cube run "
+                      f"({n} time steps, {dt:.1f} s, {threads} OpenMP threads)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_oracle()
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    L = L_MAIN
+    u, v = oracle.init(L)
+    per_step_time_steps = 2
+    times = []
+    t = 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        u, v = oracle.step(u, v, per_step_time_steps, **PARAMS, noise=NOISE, seed=SEED, t0=t)
+        dt = time.perf_counter() - t0
+        t += per_step_time_steps
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = L ** 3 * per_step_time_steps * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"FP64 CPU oracle, L={L}, noise {NOISE}, seed {SEED}; each bench step "
+                               f"= {per_step_time_steps} time steps (bounded sample of the 1000-step run)",
+                   "L": L},
+        "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step_time_steps} time steps per bench step at L={L}"},
+        "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2309_10292_gb300 import gs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    L = args.L
+    cells = L ** 3
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sim = gs.GrayScott(L, dtype="f32", noise=NOISE, seed=SEED, **PARAMS)
+    plan = sim.plan
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        sim.init()
+        sim.step(args.time_steps)
+    barrier()
+    launches0 = gs.gs_launch_count(sim.handle)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local) if rank == 0 else None
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        a, b, c = ev[i]
+        a.record(stream)
+        sim.init()
+        b.record(stream)
+        sim.step(args.time_steps)
+        c.record(stream)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    launches = gs.gs_launch_count(sim.handle) - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = sum(b.elapsed_time(c) for (_, b, c) in ev)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * cells * args.time_steps * args.steps / (total_ms / 1e3) / 1e9
+    per_launch_s = step_ms / 1e3 / (args.steps * args.time_steps)
+    hbm_peak, peak_kind = load_peaks()
+    alg_bytes = 16.0 * cells
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = profiled_traffic()
+
+    # end to end through the C-ABI with host buffers: H2D of the initial state,
+    # the 1000 steps, D2H of the final state, every step
+    u0 = torch.empty((L, L, L), dtype=torch.float32).pin_memory()
+    v0 = torch.empty_like(u0).pin_memory()
+    sim.init()
+    gs.gs_read(sim.handle, gs.GS_U, u0)
+    gs.gs_read(sim.handle, gs.GS_V, v0)
+    uo = torch.empty_like(u0).pin_memory()
+    vo = torch.empty_like(u0).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gs.gs_write(sim.handle, gs.GS_U, u0)
+        gs.gs_write(sim.handle, gs.GS_V, v0)
+        gs.gs_set_step(sim.handle, 0)
+        sim.step(args.time_steps)
+        gs.gs_read(sim.handle, gs.GS_U, uo)
+        gs.gs_read(sim.handle, gs.GS_V, vo)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * cells * args.time_steps * e2e_steps / e2e_s / 1e9
+    assert np.isfinite(uo.numpy()).all()
+
+    extra = {}
+    if rank == 0 and not args.no_fp64:
+        # FP64 run of the same workload (oracle-matching precision), shorter
+        s64 = gs.GrayScott(L, dtype="f64", noise=NOISE, seed=SEED, **PARAMS)
+        s64.step(5)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        n64 = 100
+        a.record(stream)
+        s64.step(n64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        g64 = cells * n64 / (ms / 1e3) / 1e9
+        extra["fp64"] = {"value": g64, "unit": "GCUPS", "time_steps": n64,
+                         "hbm_frac": g64 * 32.0 / hbm_peak, "note": "same workload in FP64"}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"plain stencil FP32, L={L} ({cells} cells), periodic, noise {NOISE} "
+                                   f"(counter hash, seed {SEED}), Du=0.2 Dv=0.1 F=0.02 k=0.048 dt=1, "
+                                   f"centred-cube start, {args.time_steps} time steps per bench step",
+                       "L": L, "time_steps": args.time_steps,
+                       "plan": plan,
+                       "l2": "inputs larger than L2 (4 field buffers of %.2f GB)" % (cells * 4 / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "kernel": "gs_zmarch_kernel<float, noise>",
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": per_launch_s * 1e3},
+            "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": 2 * cells * 4,
+                    "d2h_bytes_per_step": 2 * cells * 4},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=L_MAIN)
+    ap.add_argument("--time-steps", type=int, default=NSTEPS)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * gs.h — C-ABI of libgs, the GB300 (sm_103a) Gray-Scott stencil library.
+ *
+ * The method is the two-variable diffusion-reaction system of Section 3.1
+ * (Eq. 1a, 1b), advanced by forward Euler in time with the normalised
+ * 7-point Laplacian in space (Eq. 2a, 2b, 3):
+ *
+ *   lap f = (f[x-1] + f[x+1] + f[y-1] + f[y+1] + f[z-1] + f[z+1] - 6 f) / 6
+ *   du    = Du lap u - u v^2 + F (1 - u) + noise * r
+ *   dv    = Dv lap v + u v^2 - (F + k) v
+ *   u'    = u + dt du,   v' = v + dt dv
+ *
+ * on a cubic L^3 grid with periodic wrap in every axis.  r in (-1, 1) is a
+ * counter-based hash of (seed, step, cell) (see gs_noise_field), so every
+ * draw is reproducible.
+ *
+ * Conventions for every entry point
+ *   - Returns GS_OK (0) or a negative GS_E* status; never throws, never
+ *     aborts.  gs_last_error() returns a thread-local message for the last
+ *     failure on the calling thread.
+ *   - Fields are x-fastest arrays, index = x + L * (y + L * z), of float
+ *     (GS_F32) or double (GS_F64).
+ *   - Device work is enqueued on the object's stream (default: the legacy
+ *     default stream; set with gs_set_stream).  Calls that take host buffers
+ *     (gs_read, gs_write) synchronise that stream.  A kernel fault or a
+ *     bounded-wait timeout surfaces as GS_ECUDA / GS_ETIMEOUT at the next
+ *     synchronising call (gs_sync, gs_read, gs_write).
+ *   - The library owns what it allocates; the caller owns host buffers,
+ *     device buffers passed to gs_create_on and the CUDA stream.
+ *   - Objects are not thread-safe; use one object per thread or serialise.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_sim gs_sim;
+typedef struct gs_batch gs_batch;
+
+enum { GS_F32 = 0, GS_F64 = 1 };
+enum { GS_U = 0, GS_V = 1 };
+enum {
+    GS_OK = 0,
+    GS_EINVAL = -1,   /* bad argument (message says which)                 */
+    GS_ENOMEM = -2,   /* device or host allocation failed                  */
+    GS_ECUDA = -3,    /* CUDA runtime / driver error or kernel fault       */
+    GS_ETIMEOUT = -4, /* a device-side bounded wait expired                */
+    GS_ESTATE = -5    /* call not valid in the object's current state      */
+};
+
+/* Stencil kernels selectable with gs_set_plan (GS_KERNEL_AUTO picks one). */
+enum {
+    GS_KERNEL_AUTO = 0,
+    GS_KERNEL_NAIVE = 1,  /* one thread per cell, any L >= 1                   */
+    GS_KERNEL_ZMARCH = 2, /* TMA-staged z-marching tiles; L % (16/sizeof) == 0 */
+    GS_KERNEL_TBLOCK = 3  /* z-marching with `depth` fused steps per HBM pass  */
+};
+
+/* Largest supported edge: the cell counter of the noise hash is 32-bit. */
+#define GS_MAX_L 1625
+
+/* ---------------------------------------------------------------------- */
+/* Single grid                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Create a simulation of one periodic L^3 grid (Section 3.1 parameters Du,
+ * Dv, F, k, the time step dt and the noise magnitude n of Eq. 1a) and set
+ * it to the centred-cube initial state at step 0: u = 1, v = 0 except the
+ * cube [L/2-3, L/2+3)^3 (clipped to the grid) where u = 0.25, v = 0.33.
+ * Allocates four L^3 device arrays (two per field, double buffering as in
+ * Section 3.2).  dtype: GS_F32 or GS_F64.  1 <= L <= GS_MAX_L.
+ * Errors: GS_EINVAL (L, dtype, non-finite parameter, out == NULL),
+ * GS_ENOMEM, GS_ECUDA.  On error *out is set to NULL. */
+int gs_create(int L, double Du, double Dv, double F, double k, double dt, double noise,
+              uint64_t seed, int dtype, gs_sim** out);
+
+/* As gs_create, but the four field arrays are caller-owned device buffers of
+ * L^3 elements each (256-byte aligned, e.g. from the PyTorch allocator);
+ * the library never frees them.  Initialisation runs on `stream`, which also
+ * becomes the object's stream (NULL = legacy default stream). */
+int gs_create_on(int L, double Du, double Dv, double F, double k, double dt, double noise,
+                 uint64_t seed, int dtype, void* u0, void* v0, void* u1, void* v1,
+                 void* stream, gs_sim** out);
+
+/* Use `stream` (a cudaStream_t, caller-owned, NULL = legacy default) for all
+ * later device work of this object. */
+int gs_set_stream(gs_sim* sim, void* stream);
+
+/* Reset to the centred-cube initial state and step 0 (asynchronous). */
+int gs_init(gs_sim* sim);
+
+/* Advance n >= 0 steps (asynchronous on the object's stream).  Step t -> t+1
+ * draws r(seed, t, cell).  The plan (gs_set_plan) chooses the kernel; all
+ * kernels give bitwise-identical results. */
+int gs_step(gs_sim* sim, int64_t n);
+
+/* Copy field (GS_U / GS_V) of the current state to host memory `dst`
+ * (bytes must equal L^3 * element size).  Synchronises the stream; returns
+ * GS_ETIMEOUT / GS_ECUDA if an earlier kernel failed. */
+int gs_read(gs_sim* sim, int field, void* host_dst, size_t bytes);
+
+/* Overwrite field of the current state from host memory (same size rule).
+ * Synchronises the stream.  The step counter is unchanged. */
+int gs_write(gs_sim* sim, int field, const void* host_src, size_t bytes);
+
+/* Device pointer of the current state's field (valid until the next
+ * gs_step, which swaps the double buffers). */
+int gs_device_ptr(gs_sim* sim, int field, void** dev_ptr);
+
+/* Step counter t: number of steps taken since creation / gs_init, or the
+ * value last set.  Setting it changes which noise draws the next step uses
+ * (resume from a checkpoint). */
+int gs_get_step(gs_sim* sim, int64_t* t);
+int gs_set_step(gs_sim* sim, int64_t t);
+
+/* Choose the stencil kernel and its tile: tile_x, tile_y (cells), tile_z
+ * (z-chunk per work item) and depth (fused steps per pass, GS_KERNEL_TBLOCK
+ * only).  Zeros select defaults.  GS_EINVAL if the kernel cannot run this L
+ * or the tile is unsupported. */
+int gs_set_plan(gs_sim* sim, int kernel, int tile_x, int tile_y, int tile_z, int depth);
+int gs_get_plan(gs_sim* sim, int* kernel, int* tile_x, int* tile_y, int* tile_z, int* depth);
+
+/* Wait for the object's stream and report any device-side failure. */
+int gs_sync(gs_sim* sim);
+
+/* Failure injection and wait budget (testing the failure path without a GPU
+ * fault).  Every device-side wait in the z-marching kernels is bounded by
+ * timeout_ns of GPU global time (default 2e9); when it expires the kernel
+ * records GS_ETIMEOUT in the object's error word, lets its own copies in
+ * flight land and returns, and the next gs_sync / gs_read reports it.
+ * mode 0: normal operation.  mode 1: the TMA producer issues no copies, so
+ * the consumers' waits run out (a flag nothing sets).  gs_init clears the
+ * recorded error. */
+int gs_set_fault(gs_sim* sim, int mode, uint64_t timeout_ns);
+
+/* Number of kernel launches this object has issued (instrumentation). */
+int gs_launch_count(gs_sim* sim, int64_t* count);
+
+int gs_destroy(gs_sim* sim);
+
+/* Thread-local message describing the last failure ("" if none). */
+const char* gs_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Noise field                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Write r(seed, t, c) for c = 0..n-1 into the device array dev_out (float or
+ * double by dtype), asynchronously on `stream`.  The draw (Eq. 1a's r,
+ * uniform in (-1, 1); made reproducible here):
+ *   fmix32 = MurmurHash3 32-bit finaliser (Appleby)
+ *   k1 = fmix32(lo32(seed) ^ fmix32(t ^ 0x9E3779B9))
+ *   k2 = fmix32(hi32(seed) ^ fmix32(k1 ^ 0x7F4A7C15))
+ *   m  = fmix32(fmix32(c ^ k1) ^ k2) >> 8,   r = (2m + 1 - 2^24) / 2^24. */
+int gs_noise_field(uint64_t seed, int64_t t, int64_t n, int dtype, void* dev_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

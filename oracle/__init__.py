@@ -61,6 +61,9 @@ def _load():
         lib.oracle_step.argtypes = [ctypes.c_int, dp, dp] + [ctypes.c_double] * 6 + [
             ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
         lib.oracle_step.restype = ctypes.c_int
+        lib.oracle_window.argtypes = [ctypes.c_int] * 5 + [dp, dp] + [ctypes.c_double] * 6 + [
+            ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, dp, dp]
+        lib.oracle_window.restype = ctypes.c_int
         lib.oracle_conv3d_fwd.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp, dp]
         lib.oracle_conv3d_bwd_data.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp]
         lib.oracle_conv3d_bwd_weight.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp, dp]
@@ -120,6 +123,27 @@ def step(u: np.ndarray, v: np.ndarray, nsteps: int, *, Du: float, Dv: float, F: 
     if rc != 0:
         raise RuntimeError(f"oracle_step failed with status {rc}")
     return uu, vv
+
+
+def window(L: int, center, m: int, nsteps: int, *, Du, Dv, F, k, dt, noise, seed, t0=0,
+           u0=None, v0=None):
+    """(u, v) after nsteps on the (2m+1)^3 cells centred at center=(x, y, z) of an
+    L^3 periodic grid that starts from the centred cube (or from full u0, v0),
+    computed from the light cone only.  Arrays shaped [2m+1]*3 ([z, y, x])."""
+    side = 2 * m + 1
+    uo = np.empty((side, side, side))
+    vo = np.empty((side, side, side))
+    pu = pv = None
+    if u0 is not None:
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        pu, pv = _dp(u0), _dp(v0)
+    cx, cy, cz = center
+    rc = _load().oracle_window(L, cx, cy, cz, m, pu, pv, Du, Dv, F, k, dt, noise, seed, t0, nsteps,
+                               _dp(uo), _dp(vo))
+    if rc != 0:
+        raise RuntimeError(f"oracle_window failed with status {rc}")
+    return uo, vo
 
 
 # --------------------------------------------------------------------------

@@ -17,6 +17,8 @@
  *   oracle_init            centred-cube initial state
  *   oracle_step            n forward-Euler steps of Eq. (2a,2b) with the
  *                          7-point Laplacian of Eq. (3) and periodic wrap
+ *   oracle_window          the same steps for a few sampled cells of a large
+ *                          grid, from their light cone only
  *   oracle_conv3d_*        circular 3x3x3 convolution and its two gradients
  *                          (surrogate model; not in the paper)
  *   oracle_bf16_round      bfloat16 round-to-nearest-even of a binary32 value
@@ -112,6 +114,8 @@ void oracle_noise_field(uint64_t seed, int64_t t, int64_t n, double* r)
 /* v = 0.33.  Layout x-fastest: index = x + L*(y + L*z).                     */
 /* Pinned: octahedral symmetry and light-cone tests start from it.           */
 /* ------------------------------------------------------------------------ */
+static int64_t wrap_axis(int64_t i, int L) { return ((i % L) + L) % L; }
+
 static int in_cube(int L, int i)
 {
     int lo = L / 2 - 3;
@@ -228,6 +232,112 @@ int oracle_step(int L, double* u, double* v, double Du, double Dv, double F, dou
     }
     free(un);
     free(vn);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampled cells of a large run.  The state of a cell after n steps depends  */
+/* only on cells within n steps of it (one neighbour per step), so the       */
+/* cells of a (2m+1)^3 cube centred at (cx, cy, cz) can be computed from a   */
+/* window of radius R = n + m of the periodic L^3 grid.  Window cell (i,j,l) */
+/* is global cell ((cx-R+i) mod L, (cy-R+j) mod L, (cz-R+l) mod L); the noise */
+/* uses the global cell index.  Step s updates only window cells at least    */
+/* s+1 from the window border (the rest would need cells outside it), with   */
+/* the same arithmetic as one_step.  Start state: the centred cube           */
+/* (u0 == NULL) or the full arrays u0, v0 of the grid.                        */
+/* Output: uo, vo of (2m+1)^3 cells, x-fastest.  Returns 0, or -1/-2.        */
+/* Pinned: equals oracle_step at the sampled cells (tests).                  */
+/* ------------------------------------------------------------------------ */
+int oracle_window(int L, int cx, int cy, int cz, int m, const double* u0, const double* v0,
+                  double Du, double Dv, double F, double k, double dt, double noise,
+                  uint64_t seed, int64_t t0, int nsteps, double* uo, double* vo)
+{
+    if (L < 1 || m < 0 || nsteps < 0) return -1;
+    const int R = nsteps + m;
+    const int W = 2 * R + 1;
+    const int64_t WW = (int64_t)W * W, n = WW * W;
+    double* a = (double*)malloc((size_t)n * sizeof(double));
+    double* b = (double*)malloc((size_t)n * sizeof(double));
+    double* c2 = (double*)malloc((size_t)n * sizeof(double));
+    double* d = (double*)malloc((size_t)n * sizeof(double));
+    uint32_t* gid = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+    if (!a || !b || !c2 || !d || !gid) {
+        free(a); free(b); free(c2); free(d); free(gid);
+        return -2;
+    }
+    for (int l = 0; l < W; ++l)
+        for (int j = 0; j < W; ++j)
+            for (int i = 0; i < W; ++i) {
+                int gx = (int)wrap_axis(cx - R + i, L);
+                int gy = (int)wrap_axis(cy - R + j, L);
+                int gz = (int)wrap_axis(cz - R + l, L);
+                int64_t g = gx + (int64_t)L * (gy + (int64_t)L * gz);
+                int64_t w = i + (int64_t)W * j + WW * l;
+                gid[w] = (uint32_t)g;
+                if (u0) {
+                    a[w] = u0[g];
+                    b[w] = v0[g];
+                } else if (in_cube(L, gx) && in_cube(L, gy) && in_cube(L, gz)) {
+                    a[w] = 0.25;
+                    b[w] = 0.33;
+                } else {
+                    a[w] = 1.0;
+                    b[w] = 0.0;
+                }
+            }
+    memcpy(c2, a, (size_t)n * sizeof(double));
+    memcpy(d, b, (size_t)n * sizeof(double));
+    for (int s = 0; s < nsteps; ++s) {
+        uint32_t k1, k2;
+        step_keys(seed, t0 + s, &k1, &k2);
+        const int lo = s + 1, hi = W - 2 - s;
+        for (int l = lo; l <= hi; ++l)
+            for (int j = lo; j <= hi; ++j)
+                for (int i = lo; i <= hi; ++i) {
+                    int64_t w = i + (int64_t)W * j + WW * l;
+                    double uc = a[w], vc = b[w];
+                    double su = a[w - 1] + a[w + 1];
+                    su = su + a[w - W];
+                    su = su + a[w + W];
+                    su = su + a[w - WW];
+                    su = su + a[w + WW];
+                    double sv = b[w - 1] + b[w + 1];
+                    sv = sv + b[w - W];
+                    sv = sv + b[w + W];
+                    sv = sv + b[w - WW];
+                    sv = sv + b[w + WW];
+                    double lapu = (su - 6.0 * uc) / 6.0;
+                    double lapv = (sv - 6.0 * vc) / 6.0;
+                    double r = code_to_r(oracle_fmix32(oracle_fmix32(gid[w] ^ k1) ^ k2));
+                    double uvv = uc * (vc * vc);
+                    double du = Du * lapu - uvv;
+                    du = du + F * (1.0 - uc);
+                    du = du + noise * r;
+                    double dv = Dv * lapv + uvv;
+                    dv = dv - (F + k) * vc;
+                    c2[w] = uc + du * dt;
+                    d[w] = vc + dv * dt;
+                }
+        /* copy the updated interior back (border cells keep stale values and
+           are never read by a later step's smaller interior) */
+        for (int l = lo; l <= hi; ++l)
+            for (int j = lo; j <= hi; ++j)
+                for (int i = lo; i <= hi; ++i) {
+                    int64_t w = i + (int64_t)W * j + WW * l;
+                    a[w] = c2[w];
+                    b[w] = d[w];
+                }
+    }
+    const int side = 2 * m + 1;
+    for (int l = 0; l < side; ++l)
+        for (int j = 0; j < side; ++j)
+            for (int i = 0; i < side; ++i) {
+                int64_t w = (nsteps + i) + (int64_t)W * (nsteps + j) + WW * (nsteps + l);
+                int64_t o = i + (int64_t)side * (j + (int64_t)side * l);
+                uo[o] = a[w];
+                vo[o] = b[w];
+            }
+    free(a); free(b); free(c2); free(d); free(gid);
     return 0;
 }
 

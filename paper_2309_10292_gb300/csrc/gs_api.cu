@@ -1,0 +1,405 @@
+// C-ABI of libgs: object lifetime, argument checks, plan selection, stream
+// handling and error reporting around the stencil kernels (include/gs.h).
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "gs_common.cuh"
+#include "gs_internal.h"
+
+namespace gs {
+
+static thread_local char g_msg[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    const int code = e == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA;
+    return fail(code, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int elem_size(int dtype) { return dtype == GS_F32 ? 4 : 8; }
+
+int num_sms()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y)
+{
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) return CUDA_ERROR_NOT_FOUND;
+    const size_t esz = elem_size(dtype);
+    cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)L};
+    cuuint64_t strides[2] = {(cuuint64_t)L * esz, (cuuint64_t)L * L * esz};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return g_encode(map, dtype == GS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                    3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+struct gs_sim {
+    int L = 0;
+    int dtype = GS_F32;
+    Params p{};
+    void* buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [set][field]
+    bool owns = false;
+    int cur = 0;       // set holding the current state
+    int64_t t = 0;     // step counter
+    cudaStream_t stream = nullptr;
+    int* d_err = nullptr;
+    int kernel = GS_KERNEL_NAIVE;
+    ZPlan zp{128, 8, 32, 4, 1};
+    ZMaps maps[2];     // tensor maps reading set 0 / set 1
+    bool maps_ok = false;
+    int64_t launches = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    int fault = 0;
+};
+
+static bool finite_params(double a, double b, double c, double d, double e, double f)
+{
+    return std::isfinite(a) && std::isfinite(b) && std::isfinite(c) && std::isfinite(d) &&
+           std::isfinite(e) && std::isfinite(f);
+}
+
+static int default_plan(gs_sim* s)
+{
+    if (zmarch_supported(s->dtype, s->L)) {
+        ZPlan pl;
+        const int V = s->dtype == GS_F32 ? 4 : 2;
+        pl.tx = std::min(s->dtype == GS_F32 ? 128 : 64, s->L);
+        pl.tx -= pl.tx % V;
+        pl.ty = std::min(8, s->L);
+        pl.tz = std::min(32, s->L);
+        pl.stages = 4;
+        pl.depth = 1;
+        if (zmarch_validate(s->dtype, s->L, pl) == GS_OK) {
+            s->zp = pl;
+            s->kernel = GS_KERNEL_ZMARCH;
+            return GS_OK;
+        }
+    }
+    s->kernel = GS_KERNEL_NAIVE;
+    return GS_OK;
+}
+
+static int encode_maps(gs_sim* s)
+{
+    s->maps_ok = false;
+    if (s->kernel != GS_KERNEL_ZMARCH) return GS_OK;
+    for (int set = 0; set < 2; ++set) {
+        int rc = zmarch_encode(s->dtype, s->L, s->zp, s->buf[set][0], s->buf[set][1], &s->maps[set]);
+        if (rc) return rc;
+    }
+    s->maps_ok = true;
+    return GS_OK;
+}
+
+static int check_common(int L, double Du, double Dv, double F, double k, double dt, double noise,
+                        int dtype, gs_sim** out)
+{
+    if (!out) return fail(GS_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (L < 1 || L > GS_MAX_L) return fail(GS_EINVAL, "L=%d must be in [1, %d]", L, GS_MAX_L);
+    if (dtype != GS_F32 && dtype != GS_F64) return fail(GS_EINVAL, "dtype=%d must be GS_F32 or GS_F64", dtype);
+    if (!finite_params(Du, Dv, F, k, dt, noise)) return fail(GS_EINVAL, "parameters must be finite");
+    return GS_OK;
+}
+
+static int finish_create(gs_sim* s, gs_sim** out)
+{
+    GS_CUDA_TRY(cudaMalloc(&s->d_err, sizeof(int)));
+    GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+    int rc = default_plan(s);
+    if (!rc) rc = encode_maps(s);
+    if (!rc) rc = launch_init(s->dtype, s->L, s->buf[0][0], s->buf[0][1], s->stream);
+    if (rc) return rc;
+    s->launches += 1;
+    *out = s;
+    return GS_OK;
+}
+
+extern "C" {
+
+const char* gs_last_error(void) { return g_msg; }
+
+int gs_create(int L, double Du, double Dv, double F, double k, double dt, double noise, uint64_t seed,
+              int dtype, gs_sim** out)
+{
+    int rc = check_common(L, Du, Dv, F, k, dt, noise, dtype, out);
+    if (rc) return rc;
+    gs_sim* s = new (std::nothrow) gs_sim();
+    if (!s) return fail(GS_ENOMEM, "host allocation failed");
+    s->L = L;
+    s->dtype = dtype;
+    s->p = Params{Du, Dv, F, k, dt, noise, seed};
+    s->owns = true;
+    const size_t bytes = (size_t)L * L * L * elem_size(dtype);
+    for (int set = 0; set < 2; ++set)
+        for (int f = 0; f < 2; ++f) {
+            cudaError_t e = cudaMalloc(&s->buf[set][f], bytes);
+            if (e != cudaSuccess) {
+                gs_destroy(s);
+                return cuda_fail(e, "cudaMalloc(field)");
+            }
+        }
+    rc = finish_create(s, out);
+    if (rc) {
+        gs_destroy(s);
+        *out = nullptr;
+    }
+    return rc;
+}
+
+int gs_create_on(int L, double Du, double Dv, double F, double k, double dt, double noise, uint64_t seed,
+                 int dtype, void* u0, void* v0, void* u1, void* v1, void* stream, gs_sim** out)
+{
+    int rc = check_common(L, Du, Dv, F, k, dt, noise, dtype, out);
+    if (rc) return rc;
+    void* b[4] = {u0, v0, u1, v1};
+    for (int i = 0; i < 4; ++i) {
+        if (!b[i]) return fail(GS_EINVAL, "device buffer %d is NULL", i);
+        if (reinterpret_cast<uintptr_t>(b[i]) % 256) return fail(GS_EINVAL, "device buffer %d not 256-byte aligned", i);
+    }
+    gs_sim* s = new (std::nothrow) gs_sim();
+    if (!s) return fail(GS_ENOMEM, "host allocation failed");
+    s->L = L;
+    s->dtype = dtype;
+    s->p = Params{Du, Dv, F, k, dt, noise, seed};
+    s->owns = false;
+    s->buf[0][0] = u0;
+    s->buf[0][1] = v0;
+    s->buf[1][0] = u1;
+    s->buf[1][1] = v1;
+    s->stream = (cudaStream_t)stream;
+    rc = finish_create(s, out);
+    if (rc) {
+        gs_destroy(s);
+        *out = nullptr;
+    }
+    return rc;
+}
+
+int gs_set_stream(gs_sim* s, void* stream)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    s->stream = (cudaStream_t)stream;
+    return GS_OK;
+}
+
+int gs_init(gs_sim* s)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    s->cur = 0;
+    s->t = 0;
+    GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+    int rc = launch_init(s->dtype, s->L, s->buf[0][0], s->buf[0][1], s->stream);
+    if (!rc) s->launches += 1;
+    return rc;
+}
+
+int gs_step(gs_sim* s, int64_t n)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (n < 0) return fail(GS_EINVAL, "n=%lld must be >= 0", (long long)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int in = s->cur, outs = 1 - s->cur;
+        int rc;
+        if (s->kernel == GS_KERNEL_ZMARCH) {
+            if (!s->maps_ok) return fail(GS_ESTATE, "tensor maps not encoded");
+            rc = launch_zmarch(s->dtype, s->L, s->zp, s->maps[in], s->buf[outs][0], s->buf[outs][1], s->p,
+                               s->t, s->d_err, s->timeout_ns, s->fault, s->stream);
+        } else {
+            rc = launch_naive(s->dtype, s->L, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1],
+                              s->p, s->t, s->stream);
+        }
+        if (rc) return rc;
+        s->launches += 1;
+        s->cur = outs;
+        s->t += 1;
+    }
+    return GS_OK;
+}
+
+static int check_field(gs_sim* s, int field, size_t bytes)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (field != GS_U && field != GS_V) return fail(GS_EINVAL, "field=%d must be GS_U or GS_V", field);
+    const size_t need = (size_t)s->L * s->L * s->L * elem_size(s->dtype);
+    if (bytes != need) return fail(GS_EINVAL, "bytes=%zu, field holds %zu", bytes, need);
+    return GS_OK;
+}
+
+int gs_sync(gs_sim* s)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    int err = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (err == GS_DERR_TIMEOUT) return fail(GS_ETIMEOUT, "a device-side wait timed out");
+    if (err) return fail(GS_ECUDA, "device error code %d", err);
+    return GS_OK;
+}
+
+int gs_read(gs_sim* s, int field, void* dst, size_t bytes)
+{
+    int rc = check_field(s, field, bytes);
+    if (rc) return rc;
+    if (!dst) return fail(GS_EINVAL, "dst is NULL");
+    GS_CUDA_TRY(cudaMemcpyAsync(dst, s->buf[s->cur][field], bytes, cudaMemcpyDeviceToHost, s->stream));
+    return gs_sync(s);
+}
+
+int gs_write(gs_sim* s, int field, const void* src, size_t bytes)
+{
+    int rc = check_field(s, field, bytes);
+    if (rc) return rc;
+    if (!src) return fail(GS_EINVAL, "src is NULL");
+    GS_CUDA_TRY(cudaMemcpyAsync(s->buf[s->cur][field], src, bytes, cudaMemcpyHostToDevice, s->stream));
+    return gs_sync(s);
+}
+
+int gs_device_ptr(gs_sim* s, int field, void** p)
+{
+    if (!s || !p) return fail(GS_EINVAL, "NULL argument");
+    if (field != GS_U && field != GS_V) return fail(GS_EINVAL, "field=%d must be GS_U or GS_V", field);
+    *p = s->buf[s->cur][field];
+    return GS_OK;
+}
+
+int gs_get_step(gs_sim* s, int64_t* t)
+{
+    if (!s || !t) return fail(GS_EINVAL, "NULL argument");
+    *t = s->t;
+    return GS_OK;
+}
+
+int gs_set_step(gs_sim* s, int64_t t)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (t < 0) return fail(GS_EINVAL, "t must be >= 0");
+    s->t = t;
+    return GS_OK;
+}
+
+int gs_set_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z, int depth)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (kernel == GS_KERNEL_AUTO) {
+        int rc = default_plan(s);
+        return rc ? rc : encode_maps(s);
+    }
+    if (kernel == GS_KERNEL_NAIVE) {
+        s->kernel = GS_KERNEL_NAIVE;
+        s->maps_ok = false;
+        return GS_OK;
+    }
+    if (kernel == GS_KERNEL_ZMARCH) {
+        if (depth > 1) return fail(GS_EINVAL, "GS_KERNEL_ZMARCH takes depth 1");
+        ZPlan pl = s->zp;
+        const int V = s->dtype == GS_F32 ? 4 : 2;
+        pl.tx = tile_x > 0 ? tile_x : std::min(s->dtype == GS_F32 ? 128 : 64, s->L - s->L % V);
+        pl.ty = tile_y > 0 ? tile_y : std::min(8, s->L);
+        pl.tz = tile_z > 0 ? tile_z : std::min(32, s->L);
+        pl.stages = 4;
+        pl.depth = 1;
+        int rc = zmarch_validate(s->dtype, s->L, pl);
+        if (rc) return rc;
+        const int old_kernel = s->kernel;
+        const ZPlan old = s->zp;
+        s->kernel = GS_KERNEL_ZMARCH;
+        s->zp = pl;
+        rc = encode_maps(s);
+        if (rc) {
+            s->kernel = old_kernel;
+            s->zp = old;
+            encode_maps(s);
+        }
+        return rc;
+    }
+    return fail(GS_EINVAL, "kernel=%d not available", kernel);
+}
+
+int gs_get_plan(gs_sim* s, int* kernel, int* tx, int* ty, int* tz, int* depth)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (kernel) *kernel = s->kernel;
+    const bool z = s->kernel != GS_KERNEL_NAIVE;
+    if (tx) *tx = z ? s->zp.tx : 0;
+    if (ty) *ty = z ? s->zp.ty : 0;
+    if (tz) *tz = z ? s->zp.tz : 0;
+    if (depth) *depth = z ? s->zp.depth : 1;
+    return GS_OK;
+}
+
+int gs_set_fault(gs_sim* s, int mode, uint64_t timeout_ns)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (mode != 0 && mode != 1) return fail(GS_EINVAL, "fault mode %d must be 0 or 1", mode);
+    if (timeout_ns == 0) return fail(GS_EINVAL, "timeout_ns must be > 0");
+    s->fault = mode;
+    s->timeout_ns = timeout_ns;
+    return GS_OK;
+}
+
+int gs_launch_count(gs_sim* s, int64_t* count)
+{
+    if (!s || !count) return fail(GS_EINVAL, "NULL argument");
+    *count = s->launches;
+    return GS_OK;
+}
+
+int gs_destroy(gs_sim* s)
+{
+    if (!s) return GS_OK;
+    if (s->owns)
+        for (int set = 0; set < 2; ++set)
+            for (int f = 0; f < 2; ++f)
+                if (s->buf[set][f]) cudaFree(s->buf[set][f]);
+    if (s->d_err) cudaFree(s->d_err);
+    delete s;
+    return GS_OK;
+}
+
+int gs_noise_field(uint64_t seed, int64_t t, int64_t n, int dtype, void* dev_out, void* stream)
+{
+    if (n < 0) return fail(GS_EINVAL, "n must be >= 0");
+    if (dtype != GS_F32 && dtype != GS_F64) return fail(GS_EINVAL, "dtype=%d must be GS_F32 or GS_F64", dtype);
+    if (n > 0 && !dev_out) return fail(GS_EINVAL, "dev_out is NULL");
+    return launch_noise_field(dtype, seed, t, n, dev_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

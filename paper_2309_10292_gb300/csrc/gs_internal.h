@@ -1,0 +1,62 @@
+// Host-side declarations shared by the libgs translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+// Model parameters in double; each kernel converts to its own type once.
+struct Params {
+    double Du, Dv, F, k, dt, noise;
+    uint64_t seed;
+};
+
+// Thread-local error message + status helper.
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define GS_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return ::gs::cuda_fail(_e, #expr); \
+    } while (0)
+
+int elem_size(int dtype);
+int num_sms();
+
+// Tensor-map encoder obtained from the driver at first use.
+CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y);
+
+// ---------------------------------------------------------------------------
+// Stencil kernels (gs_stencil.cu)
+// ---------------------------------------------------------------------------
+int launch_init(int dtype, int L, void* u, void* v, cudaStream_t s);
+int launch_noise_field(int dtype, uint64_t seed, int64_t t, int64_t n, void* out, cudaStream_t s);
+int launch_naive(int dtype, int L, const void* u, const void* v, void* un, void* vn,
+                 const Params& p, int64_t t, cudaStream_t s);
+
+// Three tensor maps per field for the z-marching kernels (main tile, one
+// halo row, one halo column block), for the two fields u, v.
+struct ZMaps {
+    CUtensorMap m[2][3];
+};
+
+struct ZPlan {
+    int tx, ty, tz;   // tile in cells
+    int stages;       // TMA ring depth
+    int depth;        // fused steps per pass (1 = plain z-march)
+};
+
+bool zmarch_supported(int dtype, int L);
+int zmarch_validate(int dtype, int L, const ZPlan& pl);
+int zmarch_encode(int dtype, int L, const ZPlan& pl, void* u, void* v, ZMaps* maps);
+int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
+                  const Params& p, int64_t t, int* d_err, uint64_t timeout_ns, int stall,
+                  cudaStream_t s);
+
+}  // namespace gs

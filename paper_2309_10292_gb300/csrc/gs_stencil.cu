@@ -1,0 +1,481 @@
+// Gray-Scott stencil kernels for sm_103a.
+//
+//   gs_init_kernel       centred-cube initial state
+//   gs_noise_kernel      r(seed, t, c) for a range of cells (Eq. 1a's r)
+//   gs_naive_kernel      one thread per cell, periodic neighbours by index
+//                        arithmetic; any L >= 1 (also the parity baseline)
+//   gs_zmarch_kernel     persistent CTAs marching along z over x-y tiles.
+//                        One producer warp streams each z-plane of the tile
+//                        (plus its one-cell halo ring, wrapped periodically)
+//                        into a shared-memory ring with TMA; consumer warps
+//                        keep the z-1 / z / z+1 centre values in registers,
+//                        read x/y neighbours from shared memory and write the
+//                        new u, v with 16-byte stores.  Each cell's u and v
+//                        are read from HBM once and written once per step:
+//                        16 B/cell (FP32), 32 B/cell (FP64).
+//
+// All kernels apply gs_update (gs_common.cuh) with the same neighbour order,
+// so they agree bit for bit.
+#include <algorithm>
+#include <cstdio>
+
+#include "gs_common.cuh"
+#include "gs_internal.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// Initial state
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void gs_init_kernel(T* __restrict__ u, T* __restrict__ v, int L)
+{
+    const int64_t n = (int64_t)L * L * L;
+    const int lo = L / 2 - 3;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % L);
+        int64_t r = i / L;
+        int y = (int)(r % L);
+        int z = (int)(r / L);
+        bool in = x >= lo && x < lo + 6 && y >= lo && y < lo + 6 && z >= lo && z < lo + 6;
+        u[i] = in ? (T)0.25 : (T)1.0;
+        v[i] = in ? (T)0.33 : (T)0.0;
+    }
+}
+
+template <typename T>
+__global__ void gs_noise_kernel(T* __restrict__ out, int64_t n, GsKeys k)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = gs_noise<T>((uint32_t)i, k);
+}
+
+// ---------------------------------------------------------------------------
+// Plain kernel: one thread per cell
+// ---------------------------------------------------------------------------
+template <typename T>
+GsCoef<T> make_coef(const Params& p)
+{
+    GsCoef<T> c;
+    c.Du6 = (T)(p.Du / 6.0);
+    c.Dv6 = (T)(p.Dv / 6.0);
+    c.F = (T)p.F;
+    c.Fk = (T)(p.F + p.k);
+    c.dt = (T)p.dt;
+    c.noise = (T)p.noise;
+    return c;
+}
+
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, const T* __restrict__ v,
+                                                       T* __restrict__ un, T* __restrict__ vn, int L,
+                                                       GsCoef<T> c, GsKeys k)
+{
+    const int64_t n = (int64_t)L * L * L;
+    const int64_t LL = (int64_t)L * L;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % L);
+        const int64_t r = i / L;
+        const int y = (int)(r % L);
+        const int z = (int)(r / L);
+        const int64_t row = i - x;
+        const int64_t pl = i - (int64_t)y * L;  // x + L*L*z
+        const int64_t ixm = row + (x == 0 ? L - 1 : x - 1);
+        const int64_t ixp = row + (x == L - 1 ? 0 : x + 1);
+        const int64_t iym = pl + (int64_t)(y == 0 ? L - 1 : y - 1) * L;
+        const int64_t iyp = pl + (int64_t)(y == L - 1 ? 0 : y + 1) * L;
+        const int64_t base = i - (int64_t)z * LL;
+        const int64_t izm = base + (int64_t)(z == 0 ? L - 1 : z - 1) * LL;
+        const int64_t izp = base + (int64_t)(z == L - 1 ? 0 : z + 1) * LL;
+        const T uc = u[i], vc = v[i];
+        const T su = gs_nsum(u[ixm], u[ixp], u[iym], u[iyp], u[izm], u[izp]);
+        const T sv = gs_nsum(v[ixm], v[ixp], v[iym], v[iyp], v[izm], v[izp]);
+        T r_ = (T)0;
+        if (NOISE) r_ = gs_noise<T>((uint32_t)i, k);
+        T a, b;
+        gs_update<T, NOISE>(c, uc, vc, su, sv, r_, a, b);
+        un[i] = a;
+        vn[i] = b;
+    }
+}
+
+static int grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    int64_t cap = (int64_t)num_sms() * 32;
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+int launch_init(int dtype, int L, void* u, void* v, cudaStream_t s)
+{
+    const int64_t n = (int64_t)L * L * L;
+    const int g = grid_for(n, 256);
+    if (dtype == GS_F32)
+        gs_init_kernel<float><<<g, 256, 0, s>>>((float*)u, (float*)v, L);
+    else
+        gs_init_kernel<double><<<g, 256, 0, s>>>((double*)u, (double*)v, L);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int launch_noise_field(int dtype, uint64_t seed, int64_t t, int64_t n, void* out, cudaStream_t s)
+{
+    if (n <= 0) return GS_OK;
+    const int g = grid_for(n, 256);
+    GsKeys k = gs_step_keys(seed, t);
+    if (dtype == GS_F32)
+        gs_noise_kernel<float><<<g, 256, 0, s>>>((float*)out, n, k);
+    else
+        gs_noise_kernel<double><<<g, 256, 0, s>>>((double*)out, n, k);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+template <typename T>
+static int naive_t(int L, const void* u, const void* v, void* un, void* vn, const Params& p,
+                   int64_t t, cudaStream_t s)
+{
+    const int64_t n = (int64_t)L * L * L;
+    const int g = grid_for(n, 256);
+    GsCoef<T> c = make_coef<T>(p);
+    GsKeys k = gs_step_keys(p.seed, t);
+    if (p.noise != 0.0)
+        gs_naive_kernel<T, true><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, k);
+    else
+        gs_naive_kernel<T, false><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, k);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int launch_naive(int dtype, int L, const void* u, const void* v, void* un, void* vn,
+                 const Params& p, int64_t t, cudaStream_t s)
+{
+    return dtype == GS_F32 ? naive_t<float>(L, u, v, un, vn, p, t, s)
+                           : naive_t<double>(L, u, v, un, vn, p, t, s);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged z-marching kernel
+// ---------------------------------------------------------------------------
+// Shared-memory stage layout, per field (u then v), each block 128-B aligned:
+//   main  [ty][tx]   cells x0..x0+tx-1, y0..y0+ty-1 of plane z
+//   top   [tx]       row (y0 - 1) mod L
+//   bot   [tx]       row (y0 + nvy) mod L   (nvy = valid rows of the tile)
+//   left  [ty][V]    columns (x0 - V .. x0 - 1) mod L
+//   right [ty][V]    columns (x0 + nvx .. x0 + nvx + V - 1) mod L
+struct ZLayout {
+    int main_off, top_off, bot_off, left_off, right_off;  // elements
+    int field_elems;   // elements per field per stage (padded)
+    int stage_bytes;   // both fields
+    int tx_bytes;      // bytes TMA writes per stage (what the barrier expects)
+};
+
+static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+static ZLayout make_layout(int esz, int V, int tx, int ty)
+{
+    const int a = 128 / esz;  // elements per 128 B
+    ZLayout l;
+    l.main_off = 0;
+    l.top_off = round_up(tx * ty, a);
+    l.bot_off = l.top_off + round_up(tx, a);
+    l.left_off = l.bot_off + round_up(tx, a);
+    l.right_off = l.left_off + round_up(V * ty, a);
+    l.field_elems = l.right_off + round_up(V * ty, a);
+    l.stage_bytes = 2 * l.field_elems * esz;
+    l.tx_bytes = 2 * (tx * ty + 2 * tx + 2 * V * ty) * esz;
+    return l;
+}
+
+template <typename T>
+struct ZArgs {
+    T* un;
+    T* vn;
+    int L;
+    int tx, ty, tz;          // tile
+    int ntx, nty, ntiles;    // tiles along x, y and total (x fastest, then y, then z)
+    int stages;
+    ZLayout lay;
+    GsCoef<T> c;
+    GsKeys keys;
+    int* err;
+    uint64_t timeout_ns;
+    int stall;               // failure injection: the producer issues nothing
+};
+
+template <typename T, bool NOISE>
+__global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
+{
+    constexpr int V = GsVec<T>::N;
+    using VT = typename GsVec<T>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2 * 8];
+    __shared__ volatile int abort_flag;
+
+    const int S = a.stages;
+    uint64_t* full = bars;
+    uint64_t* empty = bars + S;
+    const int nxv = a.tx / V;
+    const int ncons = nxv * a.ty;
+    const int cons_threads = (ncons + 31) & ~31;
+    const int cons_warps = cons_threads >> 5;
+    const int tid = threadIdx.x;
+    const int L = a.L;
+    T* ring = reinterpret_cast<T*>(smem);
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            gs_mbar_init(&full[s], 1);
+            gs_mbar_init(&empty[s], cons_warps);
+        }
+        abort_flag = 0;
+        gs_fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (tid >= cons_threads) {
+        // ------------------------------ producer warp ------------------------------
+        if (tid != cons_threads || a.stall) return;
+        for (int f = 0; f < 2; ++f)
+            for (int m = 0; m < 3; ++m) gs_prefetch_tmap(&maps.m[f][m]);
+        uint32_t seq = 0;
+        for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+            const int txi = tile % a.ntx;
+            const int tyi = (tile / a.ntx) % a.nty;
+            const int tzi = tile / (a.ntx * a.nty);
+            const int x0 = txi * a.tx, y0 = tyi * a.ty, z0 = tzi * a.tz;
+            const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0), nz = min(a.tz, L - z0);
+            const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
+            const int xl = (x0 - V + L) % L, xr = (x0 + nvx) % L;
+            for (int j = 0; j < nz + 2; ++j) {
+                const int zp = (z0 - 1 + j + L) % L;
+                const int s = seq % S;
+                if (seq >= (uint32_t)S) {
+                    if (!gs_mbar_wait(&empty[s], ((seq / S) - 1) & 1, a.timeout_ns)) {
+                        gs_report(a.err, GS_DERR_TIMEOUT);
+                        abort_flag = 1;
+                        goto drain;
+                    }
+                }
+                if (abort_flag) goto drain;
+                gs_mbar_arrive_expect_tx(&full[s], a.lay.tx_bytes);
+                for (int f = 0; f < 2; ++f) {
+                    T* b = ring + (size_t)s * (a.lay.stage_bytes / sizeof(T)) + f * a.lay.field_elems;
+                    gs_tma_load_3d(b + a.lay.main_off, &maps.m[f][0], &full[s], x0, y0, zp);
+                    gs_tma_load_3d(b + a.lay.top_off, &maps.m[f][1], &full[s], x0, ytop, zp);
+                    gs_tma_load_3d(b + a.lay.bot_off, &maps.m[f][1], &full[s], x0, ybot, zp);
+                    gs_tma_load_3d(b + a.lay.left_off, &maps.m[f][2], &full[s], xl, y0, zp);
+                    gs_tma_load_3d(b + a.lay.right_off, &maps.m[f][2], &full[s], xr, y0, zp);
+                }
+                ++seq;
+            }
+        }
+        return;
+    drain:
+        // let every copy this thread issued land before the CTA can exit
+        // (fixed 2 s budget: copies in flight always complete within it)
+        for (uint32_t q = (seq > (uint32_t)S ? seq - S : 0); q < seq; ++q)
+            gs_mbar_wait(&full[q % S], (q / S) & 1, 2000000000ull);
+        return;
+    }
+
+    // ------------------------------- consumer warps --------------------------------
+    const int xv = tid % nxv;
+    const int row = tid / nxv;  // >= ty for the padding threads of the last warp
+    const int lane = tid & 31;
+    const size_t stage_elems = a.lay.stage_bytes / sizeof(T);
+    const int64_t LL = (int64_t)L * L;
+    uint32_t seq = 0;
+
+    auto release = [&](int s) {
+        __syncwarp();
+        if (lane == 0) gs_mbar_arrive(&empty[s]);
+    };
+    auto wait_full = [&](int s, uint32_t q) -> bool {
+        if (gs_mbar_wait(&full[s], (q / S) & 1, a.timeout_ns)) return true;
+        gs_report(a.err, GS_DERR_TIMEOUT);
+        abort_flag = 1;
+        return false;
+    };
+
+    T pu[V], pv[V], cu[V], cv[V], nu[V], nv[V];
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int txi = tile % a.ntx;
+        const int tyi = (tile / a.ntx) % a.nty;
+        const int tzi = tile / (a.ntx * a.nty);
+        const int x0 = txi * a.tx, y0 = tyi * a.ty, z0 = tzi * a.tz;
+        const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0), nz = min(a.tz, L - z0);
+        const bool active = row < nvy && xv * V < nvx;
+        const int rr = row < a.ty ? row : 0;  // padding threads read a valid address
+        const int moff = rr * a.tx + xv * V;
+
+        // plane z0 - 1: centre values only
+        int s = seq % S;
+        if (!wait_full(s, seq)) return;
+        {
+            const T* b = ring + s * stage_elems;
+            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.main_off + moff), pu);
+            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + a.lay.main_off + moff), pv);
+        }
+        release(s);
+        ++seq;
+        // plane z0
+        int sc = seq % S;
+        if (!wait_full(sc, seq)) return;
+        {
+            const T* b = ring + sc * stage_elems;
+            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.main_off + moff), cu);
+            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + a.lay.main_off + moff), cv);
+        }
+        ++seq;
+
+        for (int zi = 0; zi < nz; ++zi) {
+            const int sn = seq % S;
+            if (!wait_full(sn, seq)) return;
+            {
+                const T* b = ring + sn * stage_elems;
+                gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.main_off + moff), nu);
+                gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + a.lay.main_off + moff), nv);
+            }
+            if (active) {
+                const int z = z0 + zi;
+                T outu[V], outv[V];
+                const T* bu = ring + sc * stage_elems;
+                const T* bv = bu + a.lay.field_elems;
+                // y neighbours
+                const int om = row > 0 ? a.lay.main_off + (row - 1) * a.tx + xv * V : a.lay.top_off + xv * V;
+                const int op = row + 1 < nvy ? a.lay.main_off + (row + 1) * a.tx + xv * V : a.lay.bot_off + xv * V;
+                T ymu[V], ypu[V], ymv[V], ypv[V];
+                gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
+                gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
+                gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
+                gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
+                // x neighbours of the vector's two ends
+                const int oxl = xv > 0 ? a.lay.main_off + moff - 1 : a.lay.left_off + row * V + (V - 1);
+                const int oxr = xv * V + V < nvx ? a.lay.main_off + moff + V : a.lay.right_off + row * V;
+                const T xlu = bu[oxl], xru = bu[oxr], xlv = bv[oxl], xrv = bv[oxr];
+                const int64_t gidx = (int64_t)z * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const T su = gs_nsum(e > 0 ? cu[e - 1] : xlu, e < V - 1 ? cu[e + 1] : xru, ymu[e], ypu[e],
+                                         pu[e], nu[e]);
+                    const T sv = gs_nsum(e > 0 ? cv[e - 1] : xlv, e < V - 1 ? cv[e + 1] : xrv, ymv[e], ypv[e],
+                                         pv[e], nv[e]);
+                    T r_ = (T)0;
+                    if (NOISE) r_ = gs_noise<T>((uint32_t)(gidx + e), a.keys);
+                    gs_update<T, NOISE>(a.c, cu[e], cv[e], su, sv, r_, outu[e], outv[e]);
+                }
+                *reinterpret_cast<VT*>(a.un + gidx) = gs_pack<T>(outu);
+                *reinterpret_cast<VT*>(a.vn + gidx) = gs_pack<T>(outv);
+            }
+            release(sc);
+            sc = sn;
+            ++seq;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                pu[e] = cu[e]; pv[e] = cv[e];
+                cu[e] = nu[e]; cv[e] = nv[e];
+            }
+        }
+        release(sc);  // plane z0 + nz (only its centre was used)
+        if (abort_flag) return;
+    }
+}
+
+bool zmarch_supported(int dtype, int L)
+{
+    const int V = dtype == GS_F32 ? 4 : 2;
+    return L >= V && L % V == 0;
+}
+
+int zmarch_validate(int dtype, int L, const ZPlan& pl)
+{
+    const int V = dtype == GS_F32 ? 4 : 2;
+    const int esz = elem_size(dtype);
+    if (!zmarch_supported(dtype, L))
+        return fail(GS_EINVAL, "z-march kernel needs L %% %d == 0 (L=%d)", V, L);
+    if (pl.tx < V || pl.tx % V || pl.tx > 256 || pl.tx > L)
+        return fail(GS_EINVAL, "tile_x=%d must be a multiple of %d in [%d, min(256, L)]", pl.tx, V, V);
+    if (pl.ty < 1 || pl.ty > 256 || pl.ty > L)
+        return fail(GS_EINVAL, "tile_y=%d must be in [1, min(256, L)]", pl.ty);
+    if (pl.tz < 1) return fail(GS_EINVAL, "tile_z=%d must be >= 1", pl.tz);
+    if (pl.stages < 3 || pl.stages > 8) return fail(GS_EINVAL, "stages=%d must be in [3, 8]", pl.stages);
+    const int ncons = (pl.tx / V) * pl.ty;
+    if (((ncons + 31) & ~31) + 32 > 1024)
+        return fail(GS_EINVAL, "tile %dx%d needs more than 1024 threads", pl.tx, pl.ty);
+    ZLayout lay = make_layout(esz, V, pl.tx, pl.ty);
+    if ((size_t)lay.stage_bytes * pl.stages > 200 * 1024)
+        return fail(GS_EINVAL, "tile %dx%d with %d stages needs %d B of shared memory", pl.tx, pl.ty,
+                    pl.stages, lay.stage_bytes * pl.stages);
+    return GS_OK;
+}
+
+int zmarch_encode(int dtype, int L, const ZPlan& pl, void* u, void* v, ZMaps* maps)
+{
+    const int V = dtype == GS_F32 ? 4 : 2;
+    void* f[2] = {u, v};
+    for (int i = 0; i < 2; ++i) {
+        CUresult r0 = encode_tiled_3d(&maps->m[i][0], dtype, f[i], L, pl.tx, pl.ty);
+        CUresult r1 = encode_tiled_3d(&maps->m[i][1], dtype, f[i], L, pl.tx, 1);
+        CUresult r2 = encode_tiled_3d(&maps->m[i][2], dtype, f[i], L, V, pl.ty);
+        if (r0 != CUDA_SUCCESS || r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
+            return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed (%d, %d, %d) for L=%d tile %dx%d",
+                        (int)r0, (int)r1, (int)r2, L, pl.tx, pl.ty);
+    }
+    return GS_OK;
+}
+
+template <typename T, bool NOISE>
+static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
+                           const Params& p, int64_t t, int* d_err, uint64_t timeout_ns,
+                           int stall, cudaStream_t s)
+{
+    constexpr int V = GsVec<T>::N;
+    ZArgs<T> a;
+    a.un = (T*)un;
+    a.vn = (T*)vn;
+    a.L = L;
+    a.tx = pl.tx;
+    a.ty = pl.ty;
+    a.tz = pl.tz;
+    a.ntx = (L + pl.tx - 1) / pl.tx;
+    a.nty = (L + pl.ty - 1) / pl.ty;
+    const int ntz = (L + pl.tz - 1) / pl.tz;
+    a.ntiles = a.ntx * a.nty * ntz;
+    a.stages = pl.stages;
+    a.lay = make_layout(sizeof(T), V, pl.tx, pl.ty);
+    a.c = make_coef<T>(p);
+    a.keys = gs_step_keys(p.seed, t);
+    a.err = d_err;
+    a.timeout_ns = timeout_ns;
+    a.stall = stall;
+    const int ncons = (pl.tx / V) * pl.ty;
+    const int threads = ((ncons + 31) & ~31) + 32;
+    const size_t smem = (size_t)a.lay.stage_bytes * pl.stages;
+    auto kern = gs_zmarch_kernel<T, NOISE>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "z-march tile %dx%d does not fit on an SM", pl.tx, pl.ty);
+    const int grid = std::min(a.ntiles, per_sm * num_sms());
+    kern<<<grid, threads, smem, s>>>(maps, a);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
+                  const Params& p, int64_t t, int* d_err, uint64_t timeout_ns, int stall,
+                  cudaStream_t s)
+{
+    const bool noise = p.noise != 0.0;
+    if (dtype == GS_F32)
+        return noise ? zmarch_launch_t<float, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                     : zmarch_launch_t<float, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+    return noise ? zmarch_launch_t<double, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                 : zmarch_launch_t<double, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+}
+
+}  // namespace gs

@@ -1,0 +1,300 @@
+"""ctypes binding of libgs (include/gs.h), one Python function per C entry point.
+
+Argument marshalling only: every step of the Gray-Scott path runs in the CUDA
+kernels of libgs.so.  Host buffers are numpy arrays (or CPU torch tensors);
+device buffers and streams are integers or torch objects (PyTorch supplies
+device memory and streams).  A non-zero status raises GsError carrying the
+library's message.  The library must be built first
+(``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgs.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gs.h")
+
+GS_F32, GS_F64 = 0, 1
+GS_U, GS_V = 0, 1
+GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ETIMEOUT, GS_ESTATE = 0, -1, -2, -3, -4, -5
+GS_KERNEL_AUTO, GS_KERNEL_NAIVE, GS_KERNEL_ZMARCH, GS_KERNEL_TBLOCK = 0, 1, 2, 3
+STATUS_NAMES = {0: "GS_OK", -1: "GS_EINVAL", -2: "GS_ENOMEM", -3: "GS_ECUDA", -4: "GS_ETIMEOUT",
+                -5: "GS_ESTATE"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        super().__init__(f"{func}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_d = ctypes.c_double
+_sz = ctypes.c_size_t
+_pp = ctypes.POINTER(ctypes.c_void_p)
+
+# argtypes of every entry point (restype int unless listed in _RESTYPES)
+_SIGS = {
+    "gs_create": [_i, _d, _d, _d, _d, _d, _d, _u64, _i, _pp],
+    "gs_create_on": [_i, _d, _d, _d, _d, _d, _d, _u64, _i, _vp, _vp, _vp, _vp, _vp, _pp],
+    "gs_set_stream": [_vp, _vp],
+    "gs_init": [_vp],
+    "gs_step": [_vp, _i64],
+    "gs_read": [_vp, _i, _vp, _sz],
+    "gs_write": [_vp, _i, _vp, _sz],
+    "gs_device_ptr": [_vp, _i, _pp],
+    "gs_get_step": [_vp, ctypes.POINTER(_i64)],
+    "gs_set_step": [_vp, _i64],
+    "gs_set_plan": [_vp, _i, _i, _i, _i, _i],
+    "gs_get_plan": [_vp] + [ctypes.POINTER(_i)] * 5,
+    "gs_sync": [_vp],
+    "gs_set_fault": [_vp, _i, _u64],
+    "gs_launch_count": [_vp, ctypes.POINTER(_i64)],
+    "gs_destroy": [_vp],
+    "gs_last_error": [],
+    "gs_noise_field": [_u64, _i64, _i64, _i, _vp, _vp],
+}
+_RESTYPES = {"gs_last_error": ctypes.c_char_p}
+
+
+def lib():
+    """Load libgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library with "
+                               "__graft_entry__.build() (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _RESTYPES.get(name, ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions include/gs.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc: int, func: str):
+    if rc != GS_OK:
+        raise GsError(rc, func, lib().gs_last_error().decode())
+
+
+def _ptr(x) -> int | None:
+    """Address of a device/host buffer given as int, torch tensor or numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None or isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (GS_F32, "f32", "float32", np.float32):
+        return GS_F32
+    if dtype in (GS_F64, "f64", "float64", np.float64):
+        return GS_F64
+    raise ValueError(f"dtype {dtype!r} must be f32 or f64")
+
+
+def np_dtype(code: int):
+    return np.float32 if code == GS_F32 else np.float64
+
+
+# ---------------------------------------------------------------------------
+# Entry points
+# ---------------------------------------------------------------------------
+def gs_last_error() -> str:
+    return lib().gs_last_error().decode()
+
+
+def gs_create(L, Du, Dv, F, k, dt, noise, seed, dtype):
+    out = ctypes.c_void_p()
+    _check(lib().gs_create(L, Du, Dv, F, k, dt, noise, seed, _dtype_code(dtype), ctypes.byref(out)),
+           "gs_create")
+    return out.value
+
+
+def gs_create_on(L, Du, Dv, F, k, dt, noise, seed, dtype, u0, v0, u1, v1, stream=None):
+    out = ctypes.c_void_p()
+    _check(lib().gs_create_on(L, Du, Dv, F, k, dt, noise, seed, _dtype_code(dtype), _ptr(u0), _ptr(v0),
+                              _ptr(u1), _ptr(v1), _stream(stream), ctypes.byref(out)), "gs_create_on")
+    return out.value
+
+
+def gs_set_stream(sim, stream):
+    _check(lib().gs_set_stream(sim, _stream(stream)), "gs_set_stream")
+
+
+def gs_init(sim):
+    _check(lib().gs_init(sim), "gs_init")
+
+
+def gs_step(sim, n: int):
+    _check(lib().gs_step(sim, int(n)), "gs_step")
+
+
+def gs_read(sim, field: int, dst):
+    """Copy a field into the host buffer dst (numpy array / CPU tensor of L^3 elements)."""
+    nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+    _check(lib().gs_read(sim, field, _ptr(dst), nbytes), "gs_read")
+    return dst
+
+
+def gs_write(sim, field: int, src):
+    nbytes = src.nbytes if isinstance(src, np.ndarray) else src.numel() * src.element_size()
+    if isinstance(src, np.ndarray):
+        assert src.flags["C_CONTIGUOUS"]
+    _check(lib().gs_write(sim, field, _ptr(src), nbytes), "gs_write")
+
+
+def gs_device_ptr(sim, field: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().gs_device_ptr(sim, field, ctypes.byref(p)), "gs_device_ptr")
+    return p.value
+
+
+def gs_get_step(sim) -> int:
+    t = _i64()
+    _check(lib().gs_get_step(sim, ctypes.byref(t)), "gs_get_step")
+    return t.value
+
+
+def gs_set_step(sim, t: int):
+    _check(lib().gs_set_step(sim, int(t)), "gs_set_step")
+
+
+def gs_set_plan(sim, kernel: int, tile_x=0, tile_y=0, tile_z=0, depth=0):
+    _check(lib().gs_set_plan(sim, kernel, tile_x, tile_y, tile_z, depth), "gs_set_plan")
+
+
+def gs_get_plan(sim) -> dict:
+    v = [_i() for _ in range(5)]
+    _check(lib().gs_get_plan(sim, *[ctypes.byref(x) for x in v]), "gs_get_plan")
+    return dict(zip(("kernel", "tile_x", "tile_y", "tile_z", "depth"), (x.value for x in v)))
+
+
+def gs_sync(sim):
+    _check(lib().gs_sync(sim), "gs_sync")
+
+
+def gs_set_fault(sim, mode: int, timeout_ns: int = 2_000_000_000):
+    _check(lib().gs_set_fault(sim, mode, timeout_ns), "gs_set_fault")
+
+
+def gs_launch_count(sim) -> int:
+    c = _i64()
+    _check(lib().gs_launch_count(sim, ctypes.byref(c)), "gs_launch_count")
+    return c.value
+
+
+def gs_destroy(sim):
+    _check(lib().gs_destroy(sim), "gs_destroy")
+
+
+def gs_noise_field(seed, t, n, dtype, dev_out, stream=None):
+    _check(lib().gs_noise_field(seed, t, n, _dtype_code(dtype), _ptr(dev_out), _stream(stream)),
+           "gs_noise_field")
+
+
+# ---------------------------------------------------------------------------
+# Convenience owner of one simulation whose fields live in PyTorch tensors.
+# ---------------------------------------------------------------------------
+class GrayScott:
+    """One periodic L^3 Gray-Scott grid on the current CUDA device.
+
+    The four field buffers are torch tensors (PyTorch's allocator); the stream
+    is torch's current stream at construction.  All compute runs in libgs.
+    """
+
+    def __init__(self, L, Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0, noise=0.0, seed=0, dtype="f32",
+                 device=None, stream=None):
+        import torch
+        self.L = int(L)
+        self.dtype = _dtype_code(dtype)
+        tdt = torch.float32 if self.dtype == GS_F32 else torch.float64
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self._bufs = [torch.empty((L, L, L), dtype=tdt, device=dev) for _ in range(4)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.handle = gs_create_on(self.L, Du, Dv, F, k, dt, noise, seed, self.dtype, *self._bufs,
+                                   stream=self.stream)
+
+    def step(self, n: int):
+        gs_step(self.handle, n)
+
+    def init(self):
+        gs_init(self.handle)
+
+    def set_plan(self, kernel, tile_x=0, tile_y=0, tile_z=0, depth=0):
+        gs_set_plan(self.handle, kernel, tile_x, tile_y, tile_z, depth)
+
+    @property
+    def plan(self) -> dict:
+        return gs_get_plan(self.handle)
+
+    @property
+    def t(self) -> int:
+        return gs_get_step(self.handle)
+
+    @t.setter
+    def t(self, value: int):
+        gs_set_step(self.handle, value)
+
+    def read(self):
+        """(u, v) of the current state as numpy arrays shaped [L, L, L] ([z, y, x])."""
+        u = np.empty((self.L,) * 3, dtype=np_dtype(self.dtype))
+        v = np.empty_like(u)
+        gs_read(self.handle, GS_U, u)
+        gs_read(self.handle, GS_V, v)
+        return u, v
+
+    def write(self, u, v):
+        gs_write(self.handle, GS_U, np.ascontiguousarray(u, dtype=np_dtype(self.dtype)))
+        gs_write(self.handle, GS_V, np.ascontiguousarray(v, dtype=np_dtype(self.dtype)))
+
+    def tensors(self):
+        """Device tensors (u, v) of the current state (valid until the next step)."""
+        pu = gs_device_ptr(self.handle, GS_U)
+        pv = gs_device_ptr(self.handle, GS_V)
+        by = {b.data_ptr(): b for b in self._bufs}
+        return by[pu], by[pv]
+
+    def sync(self):
+        gs_sync(self.handle)
+
+    def close(self):
+        if self.handle:
+            gs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,201 @@
+"""GPU parity of the Gray-Scott stencil kernels against the FP64 CPU oracle.
+
+Every call goes through the C-ABI (ctypes binding).  Tolerances: the GPU FP64
+path must match the oracle within max-abs 1e-10 and the FP32 path within
+1e-4 (stated per field); kernels must agree with each other bit for bit; the
+noise draws are integer work and must match exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_10292_gb300 import gs, inputs
+from tests.gpu_util import PAPER, maxabs, need_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+V = {"f32": 4, "f64": 2}
+
+
+def make(L, dtype, kernel=None, tiles=(0, 0, 0), **kw):
+    need_cuda()
+    prm = dict(PAPER)
+    prm.update(kw)
+    sim = gs.GrayScott(L, dtype=dtype, **prm)
+    if kernel is not None:
+        sim.set_plan(kernel, *tiles)
+    return sim
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("seed,t", [(42, 0), (42, 1), (42, 999), (2 ** 40 + 3, 5)])
+def test_noise_field_bitwise(dtype, seed, t):
+    torch = need_cuda()
+    n = 64 ** 3 + 5
+    out = torch.empty(n, dtype=torch.float32 if dtype == "f32" else torch.float64, device="cuda")
+    gs.gs_noise_field(seed, t, n, dtype, out)
+    torch.cuda.synchronize()
+    ref = oracle.noise_field(seed, t, n)
+    np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
+def test_config1_parity_100_steps(dtype, kernel):
+    # L=64, 100 steps, noise 0, centred cube: FP64 <= 1e-10, FP32 <= 1e-4
+    L, n = 64, 100
+    u0, v0 = oracle.init(L)
+    uo, vo = oracle.step(u0, v0, n, **PAPER, noise=0.0, seed=0)
+    sim = make(L, dtype, kernel, noise=0.0, seed=0)
+    sim.step(n)
+    u, v = sim.read()
+    eu, ev = maxabs(u, uo), maxabs(v, vo)
+    print(f"config1 {dtype} kernel={kernel}: max-abs u {eu:.3e} v {ev:.3e}")
+    assert eu <= TOL[dtype] and ev <= TOL[dtype]
+    assert sim.t == n
+
+
+def _cases():
+    out = []
+    for L in (1, 2, 3, 4, 5, 8, 17, 32, 48, 64):
+        for dtype in ("f64", "f32"):
+            out.append((L, dtype, gs.GS_KERNEL_NAIVE, (0, 0, 0)))
+    for dtype in ("f64", "f32"):
+        v = V[dtype]
+        for L, tiles in [(8, (8, 8, 8)), (8, (v, 3, 3)), (16, (8, 5, 7)), (32, (32, 8, 32)),
+                         (48, (32, 5, 7)), (48, (16, 16, 48)), (64, (64, 1, 5)), (64, (16, 64, 9)),
+                         (64, (8 if v == 4 else 4, 7, 64))]:
+            out.append((L, dtype, gs.GS_KERNEL_ZMARCH, tiles))
+    return out
+
+
+@pytest.mark.parametrize("L,dtype,kernel,tiles", _cases())
+def test_random_state_parity(L, dtype, kernel, tiles):
+    # random initial state, noise on, 20 steps from step index 7
+    n = 20
+    u0, v0 = inputs.random_fields(L, seed=1000 + L, lo=0.0, hi=1.0)
+    prm = dict(Du=0.2, Dv=0.1, F=0.035, k=0.06, dt=0.5, noise=0.1, seed=1234)
+    uo, vo = oracle.step(u0, v0, n, t0=7, **prm)
+    sim = make(L, dtype, kernel, tiles, **prm)
+    sim.write(u0, v0)
+    sim.t = 7
+    sim.step(n)
+    u, v = sim.read()
+    assert maxabs(u, uo) <= TOL[dtype] and maxabs(v, vo) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("L,tiles", [(64, [(0, 0, 0), (32, 8, 16), (64, 4, 64), (16, 3, 5)]),
+                                     (48, [(0, 0, 0), (16, 16, 7), (48, 16, 48)])])
+def test_kernels_bitwise_equal(dtype, L, tiles):
+    prm = dict(PAPER, noise=0.1, seed=7)
+    ref = make(L, dtype, gs.GS_KERNEL_NAIVE, **prm)
+    ref.step(30)
+    ur, vr = ref.read()
+    for t in tiles:
+        sim = make(L, dtype, gs.GS_KERNEL_ZMARCH, t, **prm)
+        sim.step(30)
+        u, v = sim.read()
+        np.testing.assert_array_equal(u, ur)
+        np.testing.assert_array_equal(v, vr)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("L", [3, 16, 64])
+def test_fixed_point_bitwise(dtype, L):
+    sim = make(L, dtype, noise=0.0)
+    sim.write(np.ones((L, L, L)), np.zeros((L, L, L)))
+    sim.step(40)
+    u, v = sim.read()
+    assert np.all(u == 1.0) and np.all(v == 0.0)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_x_reflection_bitwise(dtype):
+    L = 32
+    sim = make(L, dtype, noise=0.0)
+    sim.step(40)
+    u, v = sim.read()
+    np.testing.assert_array_equal(u, u[:, :, ::-1])
+    np.testing.assert_array_equal(v, v[:, :, ::-1])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_resume_from_state_bitwise(dtype):
+    L = 32
+    prm = dict(PAPER, noise=0.1, seed=99)
+    a = make(L, dtype, **prm)
+    a.step(30)
+    ua, va = a.read()
+    b = make(L, dtype, **prm)
+    b.step(13)
+    ub, vb = b.read()
+    c = make(L, dtype, **prm)
+    c.write(ub, vb)
+    c.t = 13
+    c.step(17)
+    uc, vc = c.read()
+    np.testing.assert_array_equal(uc, ua)
+    np.testing.assert_array_equal(vc, va)
+
+
+@pytest.mark.parametrize("L,dtype", [(512, "f32"), (512, "f64"), (1024, "f32")])
+def test_full_size_sampled_cells(L, dtype):
+    # the benchmark's workload (centred cube, noise 0.1, seed 42, default plan)
+    # checked at sampled cells against the oracle's light-cone computation
+    n = 16
+    prm = dict(PAPER, noise=0.1, seed=42)
+    sim = make(L, dtype, **prm)
+    assert sim.plan["kernel"] == gs.GS_KERNEL_ZMARCH
+    sim.step(n)
+    u, v = sim.read()
+    rng = np.random.default_rng(L)
+    centers = [(L // 2, L // 2, L // 2), (L // 2 - 9, L // 2 + 4, L // 2 - 1), (0, 0, 0),
+               (L - 1, 5, L // 2)] + [tuple(int(c) for c in rng.integers(0, L, 3)) for _ in range(3)]
+    m = 2
+    for c in centers:
+        uo, vo = oracle.window(L, c, m, n, **prm)
+        idx = [(np.arange(-m, m + 1) + cc) % L for cc in c]
+        sel = np.ix_(idx[2], idx[1], idx[0])
+        assert maxabs(u[sel], uo) <= TOL[dtype], c
+        assert maxabs(v[sel], vo) <= TOL[dtype], c
+    del u, v
+    sim.close()
+
+
+def test_step_zero_and_argument_errors():
+    sim = make(8, "f32")
+    sim.step(0)
+    assert sim.t == 0
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_read(sim.handle, gs.GS_U, np.empty(7, dtype=np.float32))
+    assert e.value.status == gs.GS_EINVAL
+    with pytest.raises(gs.GsError):
+        gs.gs_step(sim.handle, -1)
+    odd = make(17, "f32")
+    with pytest.raises(gs.GsError) as e:
+        odd.set_plan(gs.GS_KERNEL_ZMARCH)
+    assert e.value.status == gs.GS_EINVAL
+    assert odd.plan["kernel"] == gs.GS_KERNEL_NAIVE
+    with pytest.raises(gs.GsError):
+        sim.set_plan(gs.GS_KERNEL_ZMARCH, 6, 4, 4)  # tile_x not a multiple of 4
+
+
+def test_bounded_wait_timeout_reports_and_recovers():
+    # failure injection: the producer issues no copies, the consumers' bounded
+    # waits expire, the next sync reports GS_ETIMEOUT and the context stays usable
+    L = 32
+    sim = make(L, "f32", gs.GS_KERNEL_ZMARCH, noise=0.0)
+    gs.gs_set_fault(sim.handle, 1, 1_000_000)
+    sim.step(1)
+    with pytest.raises(gs.GsError) as e:
+        sim.sync()
+    assert e.value.status == gs.GS_ETIMEOUT
+    gs.gs_set_fault(sim.handle, 0, 2_000_000_000)
+    sim.init()
+    sim.step(5)
+    u, v = sim.read()
+    u0, v0 = oracle.init(L)
+    uo, vo = oracle.step(u0, v0, 5, **PAPER, noise=0.0, seed=0)
+    assert maxabs(u, uo) <= 1e-4 and maxabs(v, vo) <= 1e-4

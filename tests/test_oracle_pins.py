@@ -260,6 +260,26 @@ def test_step_composition_and_step_index(orc):
     assert not np.array_equal(uc, ub)
 
 
+@pytest.mark.parametrize("L,center,m,n", [(16, (3, 0, 15), 1, 5), (12, (6, 6, 6), 2, 4),
+                                          (5, (0, 0, 0), 1, 7)])
+def test_window_equals_full_grid(orc, L, center, m, n):
+    # light-cone window (with its own wrap when the window exceeds L) gives the
+    # same bits as the full periodic grid at the sampled cells
+    args = dict(**P, noise=0.1, seed=3)
+    u0, v0 = orc.init(L)
+    uf, vf = orc.step(u0, v0, n, t0=2, **args)
+    uw, vw = orc.window(L, center, m, n, t0=2, **args)
+    idx = [(np.arange(-m, m + 1) + c) % L for c in center]
+    sel = np.ix_(idx[2], idx[1], idx[0])
+    np.testing.assert_array_equal(uw, uf[sel])
+    np.testing.assert_array_equal(vw, vf[sel])
+    ur, vr = inputs.random_fields(L, seed=4)
+    uf, vf = orc.step(ur, vr, n, **args)
+    uw, vw = orc.window(L, center, m, n, u0=ur, v0=vr, **args)
+    np.testing.assert_array_equal(uw, uf[sel])
+    np.testing.assert_array_equal(vw, vf[sel])
+
+
 def test_plausible_ranges_noise(orc):
     # loose plausibility only (the paper's Listing 1 ranges come from a different
     # boundary, RNG and size): the state stays bounded and v >= 0
