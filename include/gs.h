@@ -147,6 +147,65 @@ int gs_destroy(gs_sim* sim);
 const char* gs_last_error(void);
 
 /* ---------------------------------------------------------------------- */
+/* Batch: many independent grids of different sizes advanced together     */
+/* ---------------------------------------------------------------------- */
+
+/* Create n independent periodic grids (the Section 3.1 model, one instance
+ * per entry) with edges L[i], feed F[i] and kill k[i], sharing Du, Dv, dt and
+ * the noise magnitude; instance i draws its noise with seed + i (cell index
+ * local to the instance), so each instance evolves exactly as a gs_sim with
+ * those parameters would.  Each L[i] must be a multiple of 16/sizeof(T) in
+ * [16/sizeof(T), 256].  The library allocates one device arena for all
+ * instances' double-buffered fields, the per-instance tables and TMA
+ * descriptors, and a control block (step counter, buffer parity, grid-barrier
+ * counter, error word).  All instances start at the centred cube, step 0.
+ * Errors: GS_EINVAL, GS_ENOMEM, GS_ECUDA. */
+int gs_batch_create(int n, const int* L, const double* F, const double* k, double Du, double Dv,
+                    double dt, double noise, uint64_t seed, int dtype, gs_batch** out);
+
+/* Stream for later device work (caller-owned; NULL = legacy default). */
+int gs_batch_set_stream(gs_batch* b, void* stream);
+
+/* Reset every instance to the centred cube and step 0; clears a recorded
+ * device failure.  Synchronises the stream. */
+int gs_batch_init(gs_batch* b);
+
+/* Advance every instance n steps with ONE launch of a persistent kernel
+ * (captured once per distinct n as a CUDA graph: barrier-counter reset +
+ * kernel).  Between steps all CTAs meet at a bounded grid barrier.
+ * Asynchronous; failures surface at gs_batch_sync / gs_batch_read. */
+int gs_batch_step(gs_batch* b, int64_t n);
+
+/* Baseline: the same n steps as one z-march kernel launch per instance per
+ * step (n * number-of-instances launches).  Bitwise-equal results. */
+int gs_batch_step_sequential(gs_batch* b, int64_t n);
+
+/* Copy / overwrite field of instance i (bytes = L[i]^3 * element size).
+ * Synchronises the stream; reports earlier device failures. */
+int gs_batch_read(gs_batch* b, int i, int field, void* host_dst, size_t bytes);
+int gs_batch_write(gs_batch* b, int i, int field, const void* host_src, size_t bytes);
+
+/* Common step counter of all instances (see gs_get_step / gs_set_step). */
+int gs_batch_get_step(gs_batch* b, int64_t* t);
+int gs_batch_set_step(gs_batch* b, int64_t t);
+
+/* Wait for the stream and report any device-side failure. */
+int gs_batch_sync(gs_batch* b);
+
+/* Failure injection (see gs_set_fault): mode 1 = the TMA producer issues no
+ * copies; mode 2 = CTA 0 never arrives at the grid barrier, so every other
+ * CTA's bounded barrier wait expires.  mode 0 restores normal operation and
+ * clears the recorded error. */
+int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns);
+
+/* Launch shape of the persistent kernel (CTAs, work items per step, whether
+ * the cooperative launch attribute was accepted) and the number of kernel
+ * launches issued so far. */
+int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t* launches);
+
+int gs_batch_destroy(gs_batch* b);
+
+/* ---------------------------------------------------------------------- */
 /* Noise field                                                             */
 /* ---------------------------------------------------------------------- */
 

@@ -1,0 +1,712 @@
+// Batched Gray-Scott: many independent periodic grids of different sizes
+// and (F, k) advanced together by one persistent kernel.
+//
+// Work decomposition.  Instance i (edge L_i, 4 <= L_i <= 256) is cut into
+// full-row tiles: all L_i cells of a row by ty_i = min(L_i, 256 * V / L_i)
+// rows, times a z-chunk of tz planes.  Every work item therefore holds about
+// the same number of cells, and because a tile spans whole rows the x wrap is
+// an index wrap inside shared memory (no x-halo copies).  Work items are
+// numbered instance by instance; CTA b takes items b, b + grid, ...
+//
+// Per item a producer warp streams the planes z0-1 .. z0+nz with TMA (tile
+// box + two wrapped halo rows per field, per-instance tensor maps in global
+// memory) into a shared-memory ring; 256 consumer threads hold z-1/z/z+1 in
+// registers and store u', v' with 16-byte writes, exactly like the single
+// grid z-march kernel and with the same per-cell update, so results are
+// bitwise equal to running each instance alone.
+//
+// Between steps all CTAs meet at a grid barrier in global memory (an
+// arrival counter, reset before every launch).  Every wait is bounded: on
+// expiry the kernel records GS_ETIMEOUT in the control block and all CTAs
+// leave after letting their own copies land.  The n-step run (counter reset +
+// kernel) is captured once per n as a CUDA graph and replayed with one
+// cudaGraphLaunch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "gs_common.cuh"
+#include "gs_internal.h"
+
+namespace gs {
+
+constexpr int kBatchConsumers = 256;
+constexpr int kBatchThreads = kBatchConsumers + 32;
+
+struct BInst {
+    int L, ty, nty, ntz;
+    int item0, nitems;
+    uint32_t seed_lo, seed_hi;
+    double F, Fk;
+    long long off[2][2];  // element offsets of buffer [set][field] in the arena
+};
+
+struct BCtrl {
+    long long t;   // step counter of the current state
+    int cur;       // buffer set holding the current state
+    unsigned bar;  // grid barrier arrivals (reset before every launch)
+    int err;       // device error word
+    int pad[3];
+};
+
+template <typename T>
+struct BArgs {
+    T* arena;
+    const BInst* inst;
+    const int* item_inst;     // work item -> instance
+    const CUtensorMap* maps;  // [inst][set][field][kind]: kind 0 tile box, 1 halo row
+    BCtrl* ctrl;
+    int nitems, tz, stages;
+    int main_elems, row_elems, field_elems;  // shared-memory stage layout (elements)
+    long long nsteps;
+    T Du6, Dv6, dt, noise;
+    uint64_t timeout_ns;
+    int fault;  // 1: the producer issues no copies; 2: CTA 0 never arrives at the grid barrier
+};
+
+GS_D bool wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t timeout_ns, volatile int* abort_flag)
+{
+    if (gs_mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gs_globaltimer();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (gs_mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gs_globaltimer() - t0 > timeout_ns) return false;
+    }
+}
+
+// All threads of the CTA call this.  Returns false once any CTA failed.
+GS_D bool batch_grid_sync(BCtrl* ctrl, unsigned target, uint64_t timeout_ns, bool skip_arrive,
+                          volatile int* s_abort)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = *s_abort == 0;
+        if (ok && !skip_arrive) {
+            __threadfence();
+            gs_atom_add_release_gpu(&ctrl->bar, 1u);
+        }
+        if (ok) {
+            uint64_t t0 = 0;
+            bool timing = false;
+            while (gs_ld_acquire_gpu(&ctrl->bar) < target) {
+                if (gs_ld_relaxed_gpu(&ctrl->err)) {
+                    ok = false;
+                    break;
+                }
+                if (!timing) {
+                    t0 = gs_globaltimer();
+                    timing = true;
+                } else if (gs_globaltimer() - t0 > timeout_ns) {
+                    gs_report(&ctrl->err, GS_DERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (!ok) *s_abort = 1;
+        __threadfence();
+    }
+    __syncthreads();
+    return *s_abort == 0;
+}
+
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_constant__ BArgs<T> a)
+{
+    constexpr int V = GsVec<T>::N;
+    using VT = typename GsVec<T>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[16];
+    __shared__ volatile int s_abort;
+
+    const int S = a.stages;
+    uint64_t* full = bars;
+    uint64_t* empty = bars + S;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    T* ring = reinterpret_cast<T*>(smem);
+    const int stage_elems = 2 * a.field_elems;
+    const int top_off = a.main_elems, bot_off = a.main_elems + a.row_elems;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            gs_mbar_init(&full[s], 1);
+            gs_mbar_init(&empty[s], kBatchConsumers / 32);
+        }
+        s_abort = 0;
+        gs_fence_mbar_init();
+    }
+    __syncthreads();
+
+    const long long t0 = a.ctrl->t;
+    const int cur0 = a.ctrl->cur;
+    uint32_t seq = 0;  // ring sequence, advanced identically by producer and consumers
+    long long s = 0;
+    for (; s < a.nsteps; ++s) {
+        const int in = (cur0 + (int)(s & 1)) & 1, out = in ^ 1;
+        const long long t = t0 + s;
+        if (tid < kBatchConsumers) {
+            // ------------------------------ consumers ------------------------------
+            T pu[V], pv[V], cu[V], cv[V], nu[V], nv[V];
+            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x) {
+                const int ii = a.item_inst[item];
+                const BInst& I = a.inst[ii];
+                const int L = I.L, ty = I.ty, nxv = L / V;
+                const int local = item - I.item0;
+                const int y0 = (local % I.nty) * ty, z0 = (local / I.nty) * a.tz;
+                const int nvy = min(ty, L - y0), nz = min(a.tz, L - z0);
+                const int xv = tid % nxv, row = tid / nxv;
+                const bool active = row < nvy;
+                const int rr = row < ty ? row : 0;
+                const int moff = rr * L + xv * V;
+                const int rowbase = rr * L;
+                GsCoef<T> c;
+                c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise = a.noise;
+                c.F = (T)I.F; c.Fk = (T)I.Fk;
+                const GsKeys keys = gs_step_keys(((uint64_t)I.seed_hi << 32) | I.seed_lo, t);
+                T* un = a.arena + I.off[out][0];
+                T* vn = a.arena + I.off[out][1];
+                const long long LL = (long long)L * L;
+
+                int st = seq % S;
+                if (!wait_or_abort(&full[st], (seq / S) & 1, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
+                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + st * stage_elems + moff), pu);
+                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + st * stage_elems + a.field_elems + moff), pv);
+                __syncwarp();
+                if (lane == 0) gs_mbar_arrive(&empty[st]);
+                ++seq;
+                int sc = seq % S;
+                if (!wait_or_abort(&full[sc], (seq / S) & 1, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
+                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sc * stage_elems + moff), cu);
+                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sc * stage_elems + a.field_elems + moff), cv);
+                ++seq;
+                bool failed = false;
+                for (int zi = 0; zi < nz; ++zi) {
+                    const int sn = seq % S;
+                    if (!wait_or_abort(&full[sn], (seq / S) & 1, a.timeout_ns, &s_abort)) { failed = true; break; }
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sn * stage_elems + moff), nu);
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sn * stage_elems + a.field_elems + moff), nv);
+                    if (active) {
+                        const T* bu = ring + sc * stage_elems;
+                        const T* bv = bu + a.field_elems;
+                        const int om = row > 0 ? moff - L : top_off + xv * V;
+                        const int op = row + 1 < nvy ? moff + L : bot_off + xv * V;
+                        T ymu[V], ypu[V], ymv[V], ypv[V], ou[V], ov[V];
+                        gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
+                        gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
+                        gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
+                        gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
+                        const int oxl = xv > 0 ? moff - 1 : rowbase + L - 1;
+                        const int oxr = xv < nxv - 1 ? moff + V : rowbase;
+                        const T xlu = bu[oxl], xru = bu[oxr], xlv = bv[oxl], xrv = bv[oxr];
+                        const long long g = (long long)(z0 + zi) * LL + (long long)(y0 + row) * L + xv * V;
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const T su = gs_nsum(e > 0 ? cu[e - 1] : xlu, e < V - 1 ? cu[e + 1] : xru, ymu[e], ypu[e],
+                                                 pu[e], nu[e]);
+                            const T sv = gs_nsum(e > 0 ? cv[e - 1] : xlv, e < V - 1 ? cv[e + 1] : xrv, ymv[e], ypv[e],
+                                                 pv[e], nv[e]);
+                            T r_ = (T)0;
+                            if (NOISE) r_ = gs_noise<T>((uint32_t)(g + e), keys);
+                            gs_update<T, NOISE>(c, cu[e], cv[e], su, sv, r_, ou[e], ov[e]);
+                        }
+                        *reinterpret_cast<VT*>(un + g) = gs_pack<T>(ou);
+                        *reinterpret_cast<VT*>(vn + g) = gs_pack<T>(ov);
+                    }
+                    __syncwarp();
+                    if (lane == 0) gs_mbar_arrive(&empty[sc]);
+                    sc = sn;
+                    ++seq;
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        pu[e] = cu[e]; pv[e] = cv[e];
+                        cu[e] = nu[e]; cv[e] = nv[e];
+                    }
+                }
+                if (failed) {
+                    gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                __syncwarp();
+                if (lane == 0) gs_mbar_arrive(&empty[sc]);
+            }
+            gs_fence_proxy_async_global();  // this step's stores before the next step's TMA reads
+        } else if (tid == kBatchConsumers && a.fault != 1) {
+            // ------------------------------ producer -------------------------------
+            gs_fence_proxy_async_global();  // the previous step's stores (acquired at the barrier)
+            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x) {
+                const int ii = a.item_inst[item];
+                const BInst& I = a.inst[ii];
+                const int L = I.L, ty = I.ty;
+                const int local = item - I.item0;
+                const int y0 = (local % I.nty) * ty, z0 = (local / I.nty) * a.tz;
+                const int nvy = min(ty, L - y0), nz = min(a.tz, L - z0);
+                const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
+                const uint32_t bytes = 2u * (uint32_t)(L * ty + 2 * L) * (uint32_t)sizeof(T);
+                const CUtensorMap* mu = a.maps + (((size_t)ii * 2 + in) * 2 + 0) * 2;
+                const CUtensorMap* mv = a.maps + (((size_t)ii * 2 + in) * 2 + 1) * 2;
+                bool failed = false;
+                for (int j = 0; j < nz + 2; ++j) {
+                    const int zp = (z0 - 1 + j + L) % L;
+                    const int sl = seq % S;
+                    if (seq >= (uint32_t)S &&
+                        !wait_or_abort(&empty[sl], ((seq / S) - 1) & 1, a.timeout_ns, &s_abort)) {
+                        failed = true;
+                        break;
+                    }
+                    gs_mbar_arrive_expect_tx(&full[sl], bytes);
+                    T* b = ring + sl * stage_elems;
+                    gs_tma_load_3d(b, &mu[0], &full[sl], 0, y0, zp);
+                    gs_tma_load_3d(b + top_off, &mu[1], &full[sl], 0, ytop, zp);
+                    gs_tma_load_3d(b + bot_off, &mu[1], &full[sl], 0, ybot, zp);
+                    b += a.field_elems;
+                    gs_tma_load_3d(b, &mv[0], &full[sl], 0, y0, zp);
+                    gs_tma_load_3d(b + top_off, &mv[1], &full[sl], 0, ytop, zp);
+                    gs_tma_load_3d(b + bot_off, &mv[1], &full[sl], 0, ybot, zp);
+                    ++seq;
+                }
+                if (failed) {
+                    gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
+                    s_abort = 1;
+                }
+            }
+        }
+        const bool skip = a.fault == 2 && blockIdx.x == 0;
+        if (!batch_grid_sync(a.ctrl, (unsigned)(s + 1) * gridDim.x, a.timeout_ns, skip, &s_abort)) break;
+    }
+    if (tid == kBatchConsumers && s_abort) {
+        // a failure stopped the consumers: let every copy this thread issued
+        // land before the CTA can leave (fixed budget; copies always complete)
+        for (uint32_t q = (seq > (uint32_t)S ? seq - S : 0); q < seq; ++q)
+            gs_mbar_wait(&full[q % S], (q / S) & 1, 2000000000ull);
+    }
+    if (blockIdx.x == 0 && tid == 0 && s == a.nsteps) {
+        a.ctrl->t = t0 + a.nsteps;
+        a.ctrl->cur = (cur0 + (int)(a.nsteps & 1)) & 1;
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+struct gs_batch {
+    int n = 0, dtype = GS_F32;
+    double Du = 0, Dv = 0, dt = 0, noise = 0;
+    uint64_t seed = 0;
+    std::vector<int> L;
+    std::vector<double> F, k;
+    std::vector<BInst> h_inst;
+    void* arena = nullptr;
+    BInst* d_inst = nullptr;
+    int* d_item_inst = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    BCtrl* d_ctrl = nullptr;
+    std::vector<ZPlan> zplan;               // per-instance plan of the sequential path
+    std::vector<ZMaps> zmaps[2];            // per-instance tensor maps of the sequential path
+    int nitems = 0, tz = 32, stages = 4, main_elems = 0, row_elems = 0, field_elems = 0;
+    int grid = 0;
+    int64_t t = 0;
+    int cur = 0;
+    bool ctrl_dirty = true;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    std::map<int64_t, cudaGraphExec_t> graphs;
+    int64_t launches = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    int fault = 0;
+    bool cooperative = true;
+};
+
+static int batch_upload_ctrl(gs_batch* b)
+{
+    BCtrl h{};
+    h.t = b->t;
+    h.cur = b->cur;
+    h.bar = 0;
+    h.err = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&b->d_ctrl->t, &h.t, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    GS_CUDA_TRY(cudaMemcpyAsync(&b->d_ctrl->cur, &h.cur, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->ctrl_dirty = false;
+    return GS_OK;
+}
+
+static void drop_graphs(gs_batch* b)
+{
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+template <typename T, bool NOISE>
+static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
+{
+    BArgs<T> a;
+    a.arena = (T*)b->arena;
+    a.inst = b->d_inst;
+    a.item_inst = b->d_item_inst;
+    a.maps = b->d_maps;
+    a.ctrl = b->d_ctrl;
+    a.nitems = b->nitems;
+    a.tz = b->tz;
+    a.stages = b->stages;
+    a.main_elems = b->main_elems;
+    a.row_elems = b->row_elems;
+    a.field_elems = b->field_elems;
+    a.nsteps = n;
+    GsCoef<T> c = gs_make_coef<T>(b->Du, b->Dv, 0.0, 0.0, b->dt, b->noise);
+    a.Du6 = c.Du6;
+    a.Dv6 = c.Dv6;
+    a.dt = c.dt;
+    a.noise = c.noise;
+    a.timeout_ns = b->timeout_ns;
+    a.fault = b->fault;
+    const size_t smem = (size_t)2 * b->field_elems * sizeof(T) * b->stages;
+    auto kern = gs_batch_kernel<T, NOISE>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "batch kernel does not fit on an SM");
+    b->grid = std::min(per_sm * num_sms(), b->nitems);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        cudaGraph_t g = nullptr;
+        GS_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = cudaMemsetAsync(&b->d_ctrl->bar, 0, sizeof(unsigned), b->cap);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(b->grid);
+        cfg.blockDim = dim3(kBatchThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = b->cap;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = b->cooperative ? 1 : 0;
+        cudaError_t e2 = e1 == cudaSuccess ? cudaLaunchKernelEx(&cfg, kern, a) : e1;
+        cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
+        cudaError_t e4 = cudaErrorUnknown;
+        if (e2 == cudaSuccess && e3 == cudaSuccess) e4 = cudaGraphInstantiate(exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) return GS_OK;
+        cudaGetLastError();
+        if (!b->cooperative) {
+            cudaError_t e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
+            return cuda_fail(e, "capturing the batched persistent launch");
+        }
+        b->cooperative = false;  // retry without the cooperative attribute (grid is sized to be co-resident)
+    }
+    return fail(GS_ECUDA, "capturing the batched persistent launch failed");
+}
+
+static int batch_capture(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
+{
+    const bool noise = b->noise != 0.0;
+    if (b->dtype == GS_F32)
+        return noise ? batch_capture_t<float, true>(b, n, exec) : batch_capture_t<float, false>(b, n, exec);
+    return noise ? batch_capture_t<double, true>(b, n, exec) : batch_capture_t<double, false>(b, n, exec);
+}
+
+static int batch_check_inst(gs_batch* b, int i, int field)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (i < 0 || i >= b->n) return fail(GS_EINVAL, "instance %d out of range [0, %d)", i, b->n);
+    if (field != GS_U && field != GS_V) return fail(GS_EINVAL, "field=%d must be GS_U or GS_V", field);
+    return GS_OK;
+}
+
+extern "C" {
+
+int gs_batch_destroy(gs_batch* b)
+{
+    if (!b) return GS_OK;
+    drop_graphs(b);
+    if (b->arena) cudaFree(b->arena);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_item_inst) cudaFree(b->d_item_inst);
+    if (b->d_maps) cudaFree(b->d_maps);
+    if (b->d_ctrl) cudaFree(b->d_ctrl);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return GS_OK;
+}
+
+int gs_batch_create(int n, const int* L, const double* F, const double* k, double Du, double Dv, double dt,
+                    double noise, uint64_t seed, int dtype, gs_batch** out)
+{
+    if (!out) return fail(GS_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (n < 1) return fail(GS_EINVAL, "n=%d must be >= 1", n);
+    if (!L || !F || !k) return fail(GS_EINVAL, "L, F, k must not be NULL");
+    if (dtype != GS_F32 && dtype != GS_F64) return fail(GS_EINVAL, "dtype=%d must be GS_F32 or GS_F64", dtype);
+    const int V = dtype == GS_F32 ? 4 : 2;
+    const int esz = dtype == GS_F32 ? 4 : 8;
+    int maxL = 0;
+    for (int i = 0; i < n; ++i) {
+        if (L[i] < V || L[i] > 256 || L[i] % V)
+            return fail(GS_EINVAL, "instance %d: L=%d must be a multiple of %d in [%d, 256]", i, L[i], V, V);
+        if (!std::isfinite(F[i]) || !std::isfinite(k[i])) return fail(GS_EINVAL, "instance %d: F, k must be finite", i);
+        maxL = std::max(maxL, L[i]);
+    }
+    if (!std::isfinite(Du) || !std::isfinite(Dv) || !std::isfinite(dt) || !std::isfinite(noise))
+        return fail(GS_EINVAL, "parameters must be finite");
+    gs_batch* b = new (std::nothrow) gs_batch();
+    if (!b) return fail(GS_ENOMEM, "host allocation failed");
+    b->n = n;
+    b->dtype = dtype;
+    b->Du = Du;
+    b->Dv = Dv;
+    b->dt = dt;
+    b->noise = noise;
+    b->seed = seed;
+    b->L.assign(L, L + n);
+    b->F.assign(F, F + n);
+    b->k.assign(k, k + n);
+    // shared-memory layout: the tile box (at most 256 * V elements) then two halo rows
+    const int a128 = 128 / esz;
+    b->main_elems = kBatchConsumers * V;
+    b->row_elems = (maxL + a128 - 1) / a128 * a128;
+    b->field_elems = b->main_elems + 2 * b->row_elems;
+    // instance table, arena offsets, work items
+    std::vector<int> item_inst;
+    long long off = 0;
+    const long long align = 256 / esz;
+    for (int i = 0; i < n; ++i) {
+        BInst I{};
+        I.L = L[i];
+        I.ty = std::min(L[i], kBatchConsumers * V / L[i]);
+        I.nty = (L[i] + I.ty - 1) / I.ty;
+        I.ntz = (L[i] + b->tz - 1) / b->tz;
+        I.item0 = (int)item_inst.size();
+        I.nitems = I.nty * I.ntz;
+        const uint64_t si = seed + (uint64_t)i;
+        I.seed_lo = (uint32_t)si;
+        I.seed_hi = (uint32_t)(si >> 32);
+        I.F = F[i];
+        I.Fk = F[i] + k[i];
+        const long long cells = (long long)L[i] * L[i] * L[i];
+        for (int s = 0; s < 2; ++s)
+            for (int f = 0; f < 2; ++f) {
+                I.off[s][f] = off;
+                off += (cells + align - 1) / align * align;
+            }
+        for (int j = 0; j < I.nitems; ++j) item_inst.push_back(i);
+        b->h_inst.push_back(I);
+    }
+    b->nitems = (int)item_inst.size();
+    int rc = GS_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->arena, (size_t)off * esz)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_inst, sizeof(BInst) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_item_inst, sizeof(int) * b->nitems)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * (size_t)n * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_ctrl, sizeof(BCtrl))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+        rc = cuda_fail(e, "allocating the batch");
+        gs_batch_destroy(b);
+        return rc;
+    }
+    // tensor maps: persistent kernel (full-row boxes) and the sequential baseline (z-march plans)
+    std::vector<CUtensorMap> maps((size_t)n * 8);
+    b->zplan.resize(n);
+    b->zmaps[0].resize(n);
+    b->zmaps[1].resize(n);
+    for (int i = 0; i < n && rc == GS_OK; ++i) {
+        const BInst& I = b->h_inst[i];
+        for (int s = 0; s < 2 && rc == GS_OK; ++s)
+            for (int f = 0; f < 2 && rc == GS_OK; ++f) {
+                void* base = (char*)b->arena + (size_t)I.off[s][f] * esz;
+                CUtensorMap* m = &maps[((size_t)i * 2 + s) * 2 * 2 + f * 2];
+                if (encode_tiled_3d(&m[0], dtype, base, I.L, I.L, I.ty) != CUDA_SUCCESS ||
+                    encode_tiled_3d(&m[1], dtype, base, I.L, I.L, 1) != CUDA_SUCCESS)
+                    rc = fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for instance %d (L=%d)", i, I.L);
+            }
+        ZPlan pl;
+        pl.tx = std::min(dtype == GS_F32 ? 128 : 64, I.L);
+        pl.ty = std::min(8, I.L);
+        pl.tz = std::min(32, I.L);
+        pl.stages = 4;
+        pl.depth = 1;
+        if (rc == GS_OK) rc = zmarch_validate(dtype, I.L, pl);
+        b->zplan[i] = pl;
+        for (int s = 0; s < 2 && rc == GS_OK; ++s)
+            rc = zmarch_encode(dtype, I.L, pl, (char*)b->arena + (size_t)I.off[s][0] * esz,
+                               (char*)b->arena + (size_t)I.off[s][1] * esz, &b->zmaps[s][i]);
+    }
+    if (rc == GS_OK) {
+        if ((e = cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->d_item_inst, item_inst.data(), sizeof(int) * b->nitems, cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemset(b->d_ctrl, 0, sizeof(BCtrl))) != cudaSuccess)
+            rc = cuda_fail(e, "uploading the batch tables");
+    }
+    if (rc == GS_OK) rc = gs_batch_init(b);
+    if (rc != GS_OK) {
+        gs_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return GS_OK;
+}
+
+int gs_batch_set_stream(gs_batch* b, void* stream)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    b->stream = (cudaStream_t)stream;
+    return GS_OK;
+}
+
+int gs_batch_init(gs_batch* b)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    const int esz = elem_size(b->dtype);
+    for (int i = 0; i < b->n; ++i) {
+        const BInst& I = b->h_inst[i];
+        int rc = launch_init(b->dtype, I.L, (char*)b->arena + (size_t)I.off[0][0] * esz,
+                             (char*)b->arena + (size_t)I.off[0][1] * esz, b->stream);
+        if (rc) return rc;
+        b->launches += 1;
+    }
+    b->t = 0;
+    b->cur = 0;
+    GS_CUDA_TRY(cudaMemsetAsync(&b->d_ctrl->err, 0, sizeof(int), b->stream));
+    return batch_upload_ctrl(b);
+}
+
+int gs_batch_step(gs_batch* b, int64_t n)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (n < 0) return fail(GS_EINVAL, "n must be >= 0");
+    if (n == 0) return GS_OK;
+    if (b->ctrl_dirty) {
+        int rc = batch_upload_ctrl(b);
+        if (rc) return rc;
+    }
+    auto it = b->graphs.find(n);
+    cudaGraphExec_t exec = nullptr;
+    if (it == b->graphs.end()) {
+        int rc = batch_capture(b, n, &exec);
+        if (rc) return rc;
+        b->graphs[n] = exec;
+    } else {
+        exec = it->second;
+    }
+    GS_CUDA_TRY(cudaGraphLaunch(exec, b->stream));
+    b->launches += 1;
+    b->t += n;
+    b->cur = (b->cur + (int)(n & 1)) & 1;
+    return GS_OK;
+}
+
+int gs_batch_step_sequential(gs_batch* b, int64_t n)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (n < 0) return fail(GS_EINVAL, "n must be >= 0");
+    const int esz = elem_size(b->dtype);
+    for (int64_t s = 0; s < n; ++s) {
+        const int in = b->cur, out = 1 - b->cur;
+        for (int i = 0; i < b->n; ++i) {
+            const BInst& I = b->h_inst[i];
+            Params p{b->Du, b->Dv, b->F[i], b->k[i], b->dt, b->noise, b->seed + (uint64_t)i};
+            int rc = launch_zmarch(b->dtype, I.L, b->zplan[i], b->zmaps[in][i],
+                                   (char*)b->arena + (size_t)I.off[out][0] * esz,
+                                   (char*)b->arena + (size_t)I.off[out][1] * esz, p, b->t, &b->d_ctrl->err,
+                                   b->timeout_ns, 0, b->stream);
+            if (rc) return rc;
+            b->launches += 1;
+        }
+        b->cur = out;
+        b->t += 1;
+    }
+    b->ctrl_dirty = true;
+    return GS_OK;
+}
+
+int gs_batch_sync(gs_batch* b)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    int err = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&err, &b->d_ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (err == GS_DERR_TIMEOUT) return fail(GS_ETIMEOUT, "a device-side wait timed out");
+    if (err) return fail(GS_ECUDA, "device error code %d", err);
+    return GS_OK;
+}
+
+int gs_batch_read(gs_batch* b, int i, int field, void* dst, size_t bytes)
+{
+    int rc = batch_check_inst(b, i, field);
+    if (rc) return rc;
+    const BInst& I = b->h_inst[i];
+    const size_t need = (size_t)I.L * I.L * I.L * elem_size(b->dtype);
+    if (bytes != need) return fail(GS_EINVAL, "bytes=%zu, instance %d field holds %zu", bytes, i, need);
+    if (!dst) return fail(GS_EINVAL, "dst is NULL");
+    GS_CUDA_TRY(cudaMemcpyAsync(dst, (char*)b->arena + (size_t)I.off[b->cur][field] * elem_size(b->dtype), bytes,
+                                cudaMemcpyDeviceToHost, b->stream));
+    return gs_batch_sync(b);
+}
+
+int gs_batch_write(gs_batch* b, int i, int field, const void* src, size_t bytes)
+{
+    int rc = batch_check_inst(b, i, field);
+    if (rc) return rc;
+    const BInst& I = b->h_inst[i];
+    const size_t need = (size_t)I.L * I.L * I.L * elem_size(b->dtype);
+    if (bytes != need) return fail(GS_EINVAL, "bytes=%zu, instance %d field holds %zu", bytes, i, need);
+    if (!src) return fail(GS_EINVAL, "src is NULL");
+    GS_CUDA_TRY(cudaMemcpyAsync((char*)b->arena + (size_t)I.off[b->cur][field] * elem_size(b->dtype), src, bytes,
+                                cudaMemcpyHostToDevice, b->stream));
+    return gs_batch_sync(b);
+}
+
+int gs_batch_get_step(gs_batch* b, int64_t* t)
+{
+    if (!b || !t) return fail(GS_EINVAL, "NULL argument");
+    *t = b->t;
+    return GS_OK;
+}
+
+int gs_batch_set_step(gs_batch* b, int64_t t)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (t < 0) return fail(GS_EINVAL, "t must be >= 0");
+    b->t = t;
+    b->ctrl_dirty = true;
+    return GS_OK;
+}
+
+int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (mode < 0 || mode > 2) return fail(GS_EINVAL, "fault mode %d must be 0, 1 or 2", mode);
+    if (timeout_ns == 0) return fail(GS_EINVAL, "timeout_ns must be > 0");
+    if (mode != b->fault || timeout_ns != b->timeout_ns) drop_graphs(b);
+    b->fault = mode;
+    b->timeout_ns = timeout_ns;
+    if (mode == 0) {
+        // clear a recorded failure so the batch can be used again
+        GS_CUDA_TRY(cudaMemsetAsync(&b->d_ctrl->err, 0, sizeof(int), b->stream));
+    }
+    return GS_OK;
+}
+
+int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t* launches)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (grid) *grid = b->grid;
+    if (items) *items = b->nitems;
+    if (cooperative) *cooperative = b->cooperative ? 1 : 0;
+    if (launches) *launches = b->launches;
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -68,6 +68,20 @@ struct GsCoef {
     T dt, noise;
 };
 
+// Kernel-side coefficients from the model parameters (host).
+template <typename T>
+inline GsCoef<T> gs_make_coef(double Du, double Dv, double F, double k, double dt, double noise)
+{
+    GsCoef<T> c;
+    c.Du6 = (T)(Du / 6.0);
+    c.Dv6 = (T)(Dv / 6.0);
+    c.F = (T)F;
+    c.Fk = (T)(F + k);
+    c.dt = (T)dt;
+    c.noise = (T)noise;
+    return c;
+}
+
 GS_D float gs_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 GS_D double gs_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 GS_D float gs_mul(float a, float b) { return __fmul_rn(a, b); }
@@ -233,3 +247,32 @@ template <>
 GS_D float4 gs_pack<float>(const float* a) { return make_float4(a[0], a[1], a[2], a[3]); }
 template <>
 GS_D double2 gs_pack<double>(const double* a) { return make_double2(a[0], a[1]); }
+
+// ---------------------------------------------------------------------------
+// Grid-scope ordering for persistent kernels.
+// ---------------------------------------------------------------------------
+GS_D void gs_fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+GS_D unsigned gs_atom_add_release_gpu(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+GS_D unsigned gs_ld_acquire_gpu(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+GS_D int gs_ld_relaxed_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}

@@ -56,16 +56,9 @@ __global__ void gs_noise_kernel(T* __restrict__ out, int64_t n, GsKeys k)
 // Plain kernel: one thread per cell
 // ---------------------------------------------------------------------------
 template <typename T>
-GsCoef<T> make_coef(const Params& p)
+static GsCoef<T> make_coef(const Params& p)
 {
-    GsCoef<T> c;
-    c.Du6 = (T)(p.Du / 6.0);
-    c.Dv6 = (T)(p.Dv / 6.0);
-    c.F = (T)p.F;
-    c.Fk = (T)(p.F + p.k);
-    c.dt = (T)p.dt;
-    c.noise = (T)p.noise;
-    return c;
+    return gs_make_coef<T>(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
 }
 
 template <typename T, bool NOISE>

@@ -64,6 +64,20 @@ _SIGS = {
     "gs_destroy": [_vp],
     "gs_last_error": [],
     "gs_noise_field": [_u64, _i64, _i64, _i, _vp, _vp],
+    "gs_batch_create": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _pp],
+    "gs_batch_set_stream": [_vp, _vp],
+    "gs_batch_init": [_vp],
+    "gs_batch_step": [_vp, _i64],
+    "gs_batch_step_sequential": [_vp, _i64],
+    "gs_batch_read": [_vp, _i, _i, _vp, _sz],
+    "gs_batch_write": [_vp, _i, _i, _vp, _sz],
+    "gs_batch_get_step": [_vp, ctypes.POINTER(_i64)],
+    "gs_batch_set_step": [_vp, _i64],
+    "gs_batch_sync": [_vp],
+    "gs_batch_set_fault": [_vp, _i, _u64],
+    "gs_batch_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                      ctypes.POINTER(_i64)],
+    "gs_batch_destroy": [_vp],
 }
 _RESTYPES = {"gs_last_error": ctypes.c_char_p}
 
@@ -221,6 +235,132 @@ def gs_destroy(sim):
 def gs_noise_field(seed, t, n, dtype, dev_out, stream=None):
     _check(lib().gs_noise_field(seed, t, n, _dtype_code(dtype), _ptr(dev_out), _stream(stream)),
            "gs_noise_field")
+
+
+def gs_batch_create(L, F, k, Du, Dv, dt, noise, seed, dtype):
+    n = len(L)
+    La = (ctypes.c_int * n)(*[int(x) for x in L])
+    Fa = (ctypes.c_double * n)(*[float(x) for x in F])
+    ka = (ctypes.c_double * n)(*[float(x) for x in k])
+    out = ctypes.c_void_p()
+    _check(lib().gs_batch_create(n, La, Fa, ka, Du, Dv, dt, noise, seed, _dtype_code(dtype),
+                                 ctypes.byref(out)), "gs_batch_create")
+    return out.value
+
+
+def gs_batch_set_stream(b, stream):
+    _check(lib().gs_batch_set_stream(b, _stream(stream)), "gs_batch_set_stream")
+
+
+def gs_batch_init(b):
+    _check(lib().gs_batch_init(b), "gs_batch_init")
+
+
+def gs_batch_step(b, n: int):
+    _check(lib().gs_batch_step(b, int(n)), "gs_batch_step")
+
+
+def gs_batch_step_sequential(b, n: int):
+    _check(lib().gs_batch_step_sequential(b, int(n)), "gs_batch_step_sequential")
+
+
+def gs_batch_read(b, i: int, field: int, dst):
+    nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+    _check(lib().gs_batch_read(b, i, field, _ptr(dst), nbytes), "gs_batch_read")
+    return dst
+
+
+def gs_batch_write(b, i: int, field: int, src):
+    nbytes = src.nbytes if isinstance(src, np.ndarray) else src.numel() * src.element_size()
+    _check(lib().gs_batch_write(b, i, field, _ptr(src), nbytes), "gs_batch_write")
+
+
+def gs_batch_get_step(b) -> int:
+    t = _i64()
+    _check(lib().gs_batch_get_step(b, ctypes.byref(t)), "gs_batch_get_step")
+    return t.value
+
+
+def gs_batch_set_step(b, t: int):
+    _check(lib().gs_batch_set_step(b, int(t)), "gs_batch_set_step")
+
+
+def gs_batch_sync(b):
+    _check(lib().gs_batch_sync(b), "gs_batch_sync")
+
+
+def gs_batch_set_fault(b, mode: int, timeout_ns: int = 2_000_000_000):
+    _check(lib().gs_batch_set_fault(b, mode, timeout_ns), "gs_batch_set_fault")
+
+
+def gs_batch_info(b) -> dict:
+    g, it, co, la = _i(), _i(), _i(), _i64()
+    _check(lib().gs_batch_info(b, ctypes.byref(g), ctypes.byref(it), ctypes.byref(co), ctypes.byref(la)),
+           "gs_batch_info")
+    return {"grid": g.value, "items": it.value, "cooperative": bool(co.value), "launches": la.value}
+
+
+def gs_batch_destroy(b):
+    _check(lib().gs_batch_destroy(b), "gs_batch_destroy")
+
+
+class GrayScottBatch:
+    """Many independent grids (edges L[i], feed F[i], kill k[i]) on the current device."""
+
+    def __init__(self, L, F, k, Du=0.2, Dv=0.1, dt=1.0, noise=0.0, seed=0, dtype="f32", stream=None):
+        import torch
+        self.L = [int(x) for x in L]
+        self.dtype = _dtype_code(dtype)
+        self.handle = gs_batch_create(self.L, F, k, Du, Dv, dt, noise, seed, self.dtype)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        gs_batch_set_stream(self.handle, self.stream)
+
+    def step(self, n: int):
+        gs_batch_step(self.handle, n)
+
+    def step_sequential(self, n: int):
+        gs_batch_step_sequential(self.handle, n)
+
+    def init(self):
+        gs_batch_init(self.handle)
+
+    @property
+    def t(self) -> int:
+        return gs_batch_get_step(self.handle)
+
+    @t.setter
+    def t(self, value: int):
+        gs_batch_set_step(self.handle, value)
+
+    def read(self, i: int):
+        L = self.L[i]
+        u = np.empty((L, L, L), dtype=np_dtype(self.dtype))
+        v = np.empty_like(u)
+        gs_batch_read(self.handle, i, GS_U, u)
+        gs_batch_read(self.handle, i, GS_V, v)
+        return u, v
+
+    def write(self, i: int, u, v):
+        gs_batch_write(self.handle, i, GS_U, np.ascontiguousarray(u, dtype=np_dtype(self.dtype)))
+        gs_batch_write(self.handle, i, GS_V, np.ascontiguousarray(v, dtype=np_dtype(self.dtype)))
+
+    def sync(self):
+        gs_batch_sync(self.handle)
+
+    @property
+    def info(self) -> dict:
+        return gs_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            gs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------
