@@ -147,8 +147,9 @@ def test_batch_argument_errors():
     with pytest.raises(gs.GsError):
         gs.GrayScottBatch([512], [0.02], [0.05], dtype="f32")
     b = gs.GrayScottBatch([8], [0.02], [0.05], dtype="f32")
-    with pytest.raises(gs.GsError):
-        b.read(1)
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_batch_read(b.handle, 1, gs.GS_U, np.empty(8 ** 3, dtype=np.float32))
+    assert e.value.status == gs.GS_EINVAL
     with pytest.raises(gs.GsError):
         gs.gs_batch_read(b.handle, 0, gs.GS_U, np.empty(5, dtype=np.float32))
     b.close()
