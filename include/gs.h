@@ -205,6 +205,41 @@ int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t*
 
 int gs_batch_destroy(gs_batch* b);
 
+/* Allocation-free batched step.  (The paper has no counterpart: this entry
+ * point exists for callers of this library, not for the method.)
+ *
+ * Some callers cannot call cudaMalloc on their hot path: a framework whose
+ * caching allocator already holds the device's free memory, a service that
+ * forbids allocation after start-up because cudaMalloc can synchronise the
+ * device and stall other streams, or code that must not fail with
+ * out-of-memory halfway through a run.  This call advances a batch like
+ * gs_batch_step but creates no object and allocates no device memory: the
+ * control block, instance and work-item tables and TMA descriptors live in
+ * one fixed file-scope device array of about 309 KB (enough for 256
+ * instances and 8192 work items), which every GPU that loads the library
+ * holds until the process exits.  Larger batches are rejected with
+ * GS_EINVAL and a message naming the limit.
+ *
+ * Arguments as in gs_batch_create, plus:
+ *   arena   caller-owned device memory (256-byte aligned) holding every
+ *           instance's four fields in instance order u0, v0, u1, v1, each
+ *           L[i]^3 elements rounded up to a multiple of 256 bytes;
+ *   t, cur  step counter of the current state and the buffer set holding it
+ *           (0: u0/v0, 1: u1/v1); after the call the state is in set
+ *           (cur + nsteps) % 2 with step counter t + nsteps;
+ *   stream  the caller's stream (NULL = legacy default).
+ * The call synchronises `stream` before returning and reports a device-side
+ * timeout as GS_ETIMEOUT.  The first call on each device looks up the
+ * array's device address there (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the one array and leaves the last call's tables in it (the call
+ * resets the barrier counter and error word it needs); calls that overlap on
+ * the GPU (other streams, other host threads on the same device) race on it
+ * and must be serialised by the caller. */
+int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k, double Du,
+                          double Dv, double dt, double noise, uint64_t seed, int dtype, void* arena,
+                          int64_t t, int cur, int64_t nsteps, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Noise field                                                             */
 /* ---------------------------------------------------------------------- */

@@ -24,7 +24,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -710,3 +712,189 @@ int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t*
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free batched step.
+//
+// Everything gs_batch_create would allocate besides the fields (control
+// block, instance table, work-item table, TMA descriptors) lives instead in
+// one file-scope device array of fixed size, which the driver reserves on
+// every GPU that loads this library for as long as the process runs.  The
+// caller supplies the field arena and the step state; nothing is allocated
+// per call.
+// ===========================================================================
+namespace gs {
+
+constexpr int kNoAllocMaxInst = 256;
+constexpr int kNoAllocMaxItems = 8192;
+constexpr size_t kNaCtrlOff = 0;
+constexpr size_t kNaInstOff = 256;
+constexpr size_t kNaItemOff = kNaInstOff + (kNoAllocMaxInst * sizeof(BInst) + 255) / 256 * 256;
+constexpr size_t kNaMapOff = kNaItemOff + (kNoAllocMaxItems * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kNaBytes = kNaMapOff + (size_t)kNoAllocMaxInst * 8 * sizeof(CUtensorMap);
+constexpr int kNaMaxDevices = 64;
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// symbol: the device address comes from cudaGetSymbolAddress, per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+static std::mutex g_na_mutex;
+static void* g_na_addr[kNaMaxDevices] = {};
+static BInst g_na_inst[kNoAllocMaxInst];
+static int g_na_items[kNoAllocMaxItems];
+static CUtensorMap g_na_maps[(size_t)kNoAllocMaxInst * 8];
+
+template <typename T, bool NOISE>
+static int noalloc_launch_t(char* scratch, void* arena, int n, int nitems, int main_elems, int row_elems,
+                            double Du, double Dv, double dt, double noise, int64_t nsteps, cudaStream_t s)
+{
+    BArgs<T> a;
+    a.arena = (T*)arena;
+    a.inst = (const BInst*)(scratch + kNaInstOff);
+    a.item_inst = (const int*)(scratch + kNaItemOff);
+    a.maps = (const CUtensorMap*)(scratch + kNaMapOff);
+    a.ctrl = (BCtrl*)(scratch + kNaCtrlOff);
+    a.nitems = nitems;
+    a.tz = 32;
+    a.stages = 4;
+    a.main_elems = main_elems;
+    a.row_elems = row_elems;
+    a.field_elems = main_elems + 2 * row_elems;
+    a.nsteps = nsteps;
+    GsCoef<T> c = gs_make_coef<T>(Du, Dv, 0.0, 0.0, dt, noise);
+    a.Du6 = c.Du6;
+    a.Dv6 = c.Dv6;
+    a.dt = c.dt;
+    a.noise = c.noise;
+    a.timeout_ns = 2000000000ull;
+    a.fault = 0;
+    (void)n;
+    const size_t smem = (size_t)2 * a.field_elems * sizeof(T) * a.stages;
+    auto kern = gs_batch_kernel<T, NOISE>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "batch kernel does not fit on an SM");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::min(per_sm * num_sms(), nitems));
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, a) != cudaSuccess) {
+        cudaGetLastError();
+        cfg.numAttrs = 0;  // the grid is sized to be co-resident; the barrier waits are bounded
+        GS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
+    }
+    return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k, double Du,
+                                     double Dv, double dt, double noise, uint64_t seed, int dtype, void* arena,
+                                     int64_t t, int cur, int64_t nsteps, void* stream)
+{
+    if (n < 1 || n > kNoAllocMaxInst)
+        return fail(GS_EINVAL, "n=%d instances: the allocation-free step takes 1 to %d", n, kNoAllocMaxInst);
+    if (!L || !F || !k) return fail(GS_EINVAL, "L, F, k must not be NULL");
+    if (dtype != GS_F32 && dtype != GS_F64) return fail(GS_EINVAL, "dtype=%d must be GS_F32 or GS_F64", dtype);
+    if (!arena || reinterpret_cast<uintptr_t>(arena) % 256) return fail(GS_EINVAL, "arena must be a 256-byte aligned device pointer");
+    if (t < 0 || (cur != 0 && cur != 1) || nsteps < 0) return fail(GS_EINVAL, "need t >= 0, cur in {0, 1}, nsteps >= 0");
+    if (!std::isfinite(Du) || !std::isfinite(Dv) || !std::isfinite(dt) || !std::isfinite(noise))
+        return fail(GS_EINVAL, "parameters must be finite");
+    const int V = dtype == GS_F32 ? 4 : 2;
+    const int esz = dtype == GS_F32 ? 4 : 8;
+    int maxL = 0;
+    long long items = 0;
+    for (int i = 0; i < n; ++i) {
+        if (L[i] < V || L[i] > 256 || L[i] % V)
+            return fail(GS_EINVAL, "instance %d: L=%d must be a multiple of %d in [%d, 256]", i, L[i], V, V);
+        if (!std::isfinite(F[i]) || !std::isfinite(k[i])) return fail(GS_EINVAL, "instance %d: F, k must be finite", i);
+        maxL = std::max(maxL, L[i]);
+        const int ty = std::min(L[i], kBatchConsumers * V / L[i]);
+        items += (long long)((L[i] + ty - 1) / ty) * ((L[i] + 31) / 32);
+    }
+    if (items > kNoAllocMaxItems)
+        return fail(GS_EINVAL, "%lld work items: the allocation-free step takes at most %d", items, kNoAllocMaxItems);
+    if (nsteps == 0) return GS_OK;
+
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    int dev = 0;
+    GS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNaMaxDevices) return fail(GS_EINVAL, "device %d beyond the supported %d", dev, kNaMaxDevices);
+    if (!g_na_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(allocation-free scratch)");
+        g_na_addr[dev] = p;
+    }
+    char* scratch = (char*)g_na_addr[dev];
+
+    // same tables as gs_batch_create, built in static host staging
+    const int a128 = 128 / esz;
+    const int main_elems = kBatchConsumers * V;
+    const int row_elems = (maxL + a128 - 1) / a128 * a128;
+    const long long align = 256 / esz;
+    long long off = 0;
+    int nit = 0;
+    for (int i = 0; i < n; ++i) {
+        BInst I{};
+        I.L = L[i];
+        I.ty = std::min(L[i], kBatchConsumers * V / L[i]);
+        I.nty = (L[i] + I.ty - 1) / I.ty;
+        I.ntz = (L[i] + 31) / 32;
+        I.item0 = nit;
+        I.nitems = I.nty * I.ntz;
+        const uint64_t si = seed + (uint64_t)i;
+        I.seed_lo = (uint32_t)si;
+        I.seed_hi = (uint32_t)(si >> 32);
+        I.F = F[i];
+        I.Fk = F[i] + k[i];
+        const long long cells = (long long)L[i] * L[i] * L[i];
+        for (int s = 0; s < 2; ++s)
+            for (int f = 0; f < 2; ++f) {
+                I.off[s][f] = off;
+                off += (cells + align - 1) / align * align;
+            }
+        for (int j = 0; j < I.nitems; ++j) g_na_items[nit++] = i;
+        g_na_inst[i] = I;
+        for (int s = 0; s < 2; ++s)
+            for (int f = 0; f < 2; ++f) {
+                void* base = (char*)arena + (size_t)I.off[s][f] * esz;
+                CUtensorMap* m = &g_na_maps[((size_t)i * 2 + s) * 2 * 2 + f * 2];
+                if (encode_tiled_3d(&m[0], dtype, base, I.L, I.L, I.ty) != CUDA_SUCCESS ||
+                    encode_tiled_3d(&m[1], dtype, base, I.L, I.L, 1) != CUDA_SUCCESS)
+                    return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for instance %d (L=%d)", i, I.L);
+            }
+    }
+    BCtrl h{};
+    h.t = t;
+    h.cur = cur;
+    cudaStream_t s = (cudaStream_t)stream;
+    GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaCtrlOff, &h, sizeof(BCtrl), cudaMemcpyHostToDevice, s));
+    GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaInstOff, g_na_inst, sizeof(BInst) * n, cudaMemcpyHostToDevice, s));
+    GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaItemOff, g_na_items, sizeof(int) * nit, cudaMemcpyHostToDevice, s));
+    GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaMapOff, g_na_maps, sizeof(CUtensorMap) * (size_t)n * 8,
+                                cudaMemcpyHostToDevice, s));
+    const bool nz = noise != 0.0;
+    int rc;
+    if (dtype == GS_F32)
+        rc = nz ? noalloc_launch_t<float, true>(scratch, arena, n, nit, main_elems, row_elems, Du, Dv, dt, noise, nsteps, s)
+                : noalloc_launch_t<float, false>(scratch, arena, n, nit, main_elems, row_elems, Du, Dv, dt, noise, nsteps, s);
+    else
+        rc = nz ? noalloc_launch_t<double, true>(scratch, arena, n, nit, main_elems, row_elems, Du, Dv, dt, noise, nsteps, s)
+                : noalloc_launch_t<double, false>(scratch, arena, n, nit, main_elems, row_elems, Du, Dv, dt, noise, nsteps, s);
+    if (rc) return rc;
+    int err = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&err, scratch + kNaCtrlOff + offsetof(BCtrl, err), sizeof(int),
+                                cudaMemcpyDeviceToHost, s));
+    GS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err == GS_DERR_TIMEOUT) return fail(GS_ETIMEOUT, "a device-side wait timed out");
+    if (err) return fail(GS_ECUDA, "device error code %d", err);
+    return GS_OK;
+}

@@ -78,6 +78,7 @@ _SIGS = {
     "gs_batch_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                       ctypes.POINTER(_i64)],
     "gs_batch_destroy": [_vp],
+    "gs_batch_step_noalloc": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _vp, _i64, _i, _i64, _vp],
 }
 _RESTYPES = {"gs_last_error": ctypes.c_char_p}
 
@@ -302,6 +303,33 @@ def gs_batch_info(b) -> dict:
 
 def gs_batch_destroy(b):
     _check(lib().gs_batch_destroy(b), "gs_batch_destroy")
+
+
+def gs_batch_step_noalloc(L, F, k, Du, Dv, dt, noise, seed, dtype, arena, t, cur, nsteps, stream=None):
+    """Allocation-free batched step on a caller-owned arena (see include/gs.h)."""
+    n = len(L)
+    La = (ctypes.c_int * n)(*[int(x) for x in L])
+    Fa = (ctypes.c_double * n)(*[float(x) for x in F])
+    ka = (ctypes.c_double * n)(*[float(x) for x in k])
+    _check(lib().gs_batch_step_noalloc(n, La, Fa, ka, Du, Dv, dt, noise, seed, _dtype_code(dtype),
+                                       _ptr(arena), int(t), int(cur), int(nsteps), _stream(stream)),
+           "gs_batch_step_noalloc")
+
+
+def noalloc_arena_offsets(L, dtype) -> tuple[list, int]:
+    """Element offsets (u0, v0, u1, v1) of each instance in an allocation-free arena,
+    and the arena's total length in elements."""
+    esz = 4 if _dtype_code(dtype) == GS_F32 else 8
+    align = 256 // esz
+    off, out = 0, []
+    for x in L:
+        cells = int(x) ** 3
+        o = []
+        for _ in range(4):
+            o.append(off)
+            off += (cells + align - 1) // align * align
+        out.append(o)
+    return out, off
 
 
 class GrayScottBatch:
