@@ -226,6 +226,39 @@ def bench_batched(args, stream, hbm_peak):
             "cooperative_attribute": info["cooperative"], "graph_launches": 1}
 
 
+def bench_large(args, stream, hbm_peak):
+    """L=1024 FP32 (four 4.3 GB fields), noise 0.1, plan autotuned over the plain,
+    z-march and temporally blocked (depth 2-4) kernels, 500 steps."""
+    import torch
+
+    from paper_2309_10292_gb300 import gs
+    L, n = 1024, args.large_steps
+    sim = gs.GrayScott(L, dtype="f32", noise=NOISE, seed=SEED, **PARAMS)
+    best, trials = sim.autotune(steps_per_trial=12)
+    by_depth = {}
+    for r in trials:
+        d = r["depth"] if r["kernel"] == gs.GS_KERNEL_TBLOCK else 1
+        if d not in by_depth or r["us_per_step"] < by_depth[d]["us_per_step"]:
+            by_depth[d] = r
+    sim.step(4)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.step(n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    s = a.elapsed_time(b) / 1e3
+    g = L ** 3 * n / s / 1e9
+    depth = best["depth"] if best["kernel"] == gs.GS_KERNEL_TBLOCK else 1
+    sim.close()
+    return {"workload": f"plain stencil FP32, L={L}, noise {NOISE}, {n} steps, autotuned plan",
+            "value": g, "unit": "GCUPS", "time_s": s, "plan": best,
+            "hbm_frac_per_pass": g * 16.0 / depth / hbm_peak,
+            "best_gcups_by_depth": {str(d): L ** 3 / r["us_per_step"] / 1e3 for d, r in sorted(by_depth.items())},
+            "tuned_candidates": len(trials)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -248,6 +281,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sim = gs.GrayScott(L, dtype="f32", noise=NOISE, seed=SEED, **PARAMS)
+    tune_best, tune_trials = sim.autotune(steps_per_trial=24)
     plan = sim.plan
     # warm-up (untimed)
     for _ in range(args.warmup):
@@ -273,6 +307,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop() if clocks else None
     launches = gs.gs_launch_count(sim.handle) - launches0
+    stencil_launches = launches - args.steps  # one init launch per bench step
     total_ms = t_start.elapsed_time(t_end)
     step_ms = sum(b.elapsed_time(c) for (_, b, c) in ev)
     if ws > 1:
@@ -280,11 +315,13 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = ws * cells * args.time_steps * args.steps / (total_ms / 1e3) / 1e9
-    per_launch_s = step_ms / 1e3 / (args.steps * args.time_steps)
+    per_launch_s = step_ms / 1e3 / stencil_launches
     hbm_peak, peak_kind = load_peaks()
-    alg_bytes = 16.0 * cells
+    alg_bytes = 16.0 * cells  # one read and one write of u and v per pass
     achieved = alg_bytes / per_launch_s / 1e9
-    traffic = profiled_traffic()
+    kname = {gs.GS_KERNEL_NAIVE: "gs_naive_kernel<float, noise>", gs.GS_KERNEL_ZMARCH: "gs_zmarch_kernel<float, noise>",
+             gs.GS_KERNEL_TBLOCK: f"gs_tblock_kernel<noise, {plan['depth']}>"}[plan["kernel"]]
+    traffic = profiled_traffic() if plan["kernel"] == gs.GS_KERNEL_ZMARCH else None
 
     # end to end through the C-ABI with host buffers: H2D of the initial state,
     # the 1000 steps, D2H of the final state, every step
@@ -335,6 +372,8 @@ def run_ours(args):
 
     if rank == 0 and not args.no_batch:
         extra["batched"] = bench_batched(args, stream, hbm_peak)
+    if rank == 0 and not args.no_large:
+        extra["l1024"] = bench_large(args, stream, hbm_peak)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -350,11 +389,13 @@ def run_ours(args):
                                    f"centred-cube start, {args.time_steps} time steps per bench step",
                        "L": L, "time_steps": args.time_steps,
                        "plan": plan,
+                       "autotune": {"candidates": len(tune_trials), "best_us_per_step": tune_best["us_per_step"]},
                        "l2": "inputs larger than L2 (4 field buffers of %.2f GB)" % (cells * 4 / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic,
-                         "kernel": "gs_zmarch_kernel<float, noise>",
+                         "kernel": kname, "launches": stencil_launches,
+                         "steps_per_launch": plan["depth"] if plan["kernel"] == gs.GS_KERNEL_TBLOCK else 1,
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": alg_bytes,
@@ -384,6 +425,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances measurement")
     ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--no-large", action="store_true", help="skip the L=1024 measurement")
+    ap.add_argument("--large-steps", type=int, default=500)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -125,6 +125,28 @@ int gs_set_step(gs_sim* sim, int64_t t);
 int gs_set_plan(gs_sim* sim, int kernel, int tile_x, int tile_y, int tile_z, int depth);
 int gs_get_plan(gs_sim* sim, int* kernel, int* tile_x, int* tile_y, int* tile_z, int* depth);
 
+/* A complete plan: kernel, tile, fused depth and TMA ring depth (`stages`,
+ * z-march only, 3..8); us_per_step is filled in by gs_autotune. */
+typedef struct gs_plan {
+    int kernel, tile_x, tile_y, tile_z, depth, stages;
+    double us_per_step;
+} gs_plan;
+
+/* Set every field of a plan (stages 0 = default).  GS_EINVAL as gs_set_plan. */
+int gs_set_plan_full(gs_sim* sim, const gs_plan* plan);
+
+/* Autotuner: time every candidate plan valid for this grid — the plain
+ * kernel; z-march tiles x z-chunks x ring depths; for FP32, temporal
+ * blocking at depths 2-4 with several tiles — over `steps_per_trial` steps
+ * each (rounded up to a multiple of 12 so every depth runs whole passes;
+ * CUDA events on the object's stream, after two warm-up launches), keep the
+ * fastest plan set, and restore the simulation's fields and step counter
+ * exactly (the fields are copied to two temporary L^3 device buffers for the
+ * duration).  `results` (may be NULL) receives up to max_results trials in
+ * order, *n_results their count, *best the chosen plan.  Synchronous. */
+int gs_autotune(gs_sim* sim, int steps_per_trial, gs_plan* results, int max_results, int* n_results,
+                gs_plan* best);
+
 /* Wait for the object's stream and report any device-side failure. */
 int gs_sync(gs_sim* sim);
 

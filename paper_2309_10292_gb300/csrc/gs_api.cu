@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "gs_common.cuh"
 #include "gs_internal.h"
@@ -81,7 +82,8 @@ struct gs_sim {
     cudaStream_t stream = nullptr;
     int* d_err = nullptr;
     int kernel = GS_KERNEL_NAIVE;
-    ZPlan zp{128, 8, 32, 4, 1};
+    ZPlan zp{128, 8, 32, 4, 1};   // z-march plan (also runs the steps a blocked pass leaves over)
+    ZPlan tp{64, 16, 64, 5, 2};   // temporal-blocking plan (kernel GS_KERNEL_TBLOCK)
     ZMaps maps[2];     // tensor maps reading set 0 / set 1
     bool maps_ok = false;
     int64_t launches = 0;
@@ -119,7 +121,7 @@ static int default_plan(gs_sim* s)
 static int encode_maps(gs_sim* s)
 {
     s->maps_ok = false;
-    if (s->kernel != GS_KERNEL_ZMARCH) return GS_OK;
+    if (s->kernel == GS_KERNEL_NAIVE || !zmarch_supported(s->dtype, s->L)) return GS_OK;
     for (int set = 0; set < 2; ++set) {
         int rc = zmarch_encode(s->dtype, s->L, s->zp, s->buf[set][0], s->buf[set][1], &s->maps[set]);
         if (rc) return rc;
@@ -235,10 +237,23 @@ int gs_step(gs_sim* s, int64_t n)
 {
     if (!s) return fail(GS_EINVAL, "sim is NULL");
     if (n < 0) return fail(GS_EINVAL, "n=%lld must be >= 0", (long long)n);
-    for (int64_t i = 0; i < n; ++i) {
+    int64_t i = 0;
+    if (s->kernel == GS_KERNEL_TBLOCK) {
+        const int D = s->tp.depth;
+        for (; i + D <= n; i += D) {
+            const int in = s->cur, outs = 1 - s->cur;
+            int rc = launch_tblock(s->L, s->tp, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1],
+                                   s->p, s->t, s->stream);
+            if (rc) return rc;
+            s->launches += 1;
+            s->cur = outs;
+            s->t += D;
+        }
+    }
+    for (; i < n; ++i) {
         const int in = s->cur, outs = 1 - s->cur;
         int rc;
-        if (s->kernel == GS_KERNEL_ZMARCH) {
+        if (s->kernel != GS_KERNEL_NAIVE) {
             if (!s->maps_ok) return fail(GS_ESTATE, "tensor maps not encoded");
             rc = launch_zmarch(s->dtype, s->L, s->zp, s->maps[in], s->buf[outs][0], s->buf[outs][1], s->p,
                                s->t, s->d_err, s->timeout_ns, s->fault, s->stream);
@@ -315,9 +330,8 @@ int gs_set_step(gs_sim* s, int64_t t)
     return GS_OK;
 }
 
-int gs_set_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z, int depth)
+static int apply_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z, int depth, int stages)
 {
-    if (!s) return fail(GS_EINVAL, "sim is NULL");
     if (kernel == GS_KERNEL_AUTO) {
         int rc = default_plan(s);
         return rc ? rc : encode_maps(s);
@@ -334,7 +348,7 @@ int gs_set_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z, int d
         pl.tx = tile_x > 0 ? tile_x : std::min(s->dtype == GS_F32 ? 128 : 64, s->L - s->L % V);
         pl.ty = tile_y > 0 ? tile_y : std::min(8, s->L);
         pl.tz = tile_z > 0 ? tile_z : std::min(32, s->L);
-        pl.stages = 4;
+        pl.stages = stages > 0 ? stages : 4;
         pl.depth = 1;
         int rc = zmarch_validate(s->dtype, s->L, pl);
         if (rc) return rc;
@@ -350,7 +364,135 @@ int gs_set_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z, int d
         }
         return rc;
     }
+    if (kernel == GS_KERNEL_TBLOCK) {
+        ZPlan pl = s->tp;
+        pl.tx = tile_x > 0 ? tile_x : 64;
+        pl.ty = tile_y > 0 ? tile_y : 16;
+        pl.tz = tile_z > 0 ? tile_z : 64;
+        pl.depth = depth > 0 ? depth : 2;
+        pl.stages = 5;
+        int rc = tblock_validate(s->dtype, s->L, pl);
+        if (rc) return rc;
+        if (!zmarch_supported(s->dtype, s->L)) return fail(GS_EINVAL, "L=%d not supported by the z-march kernel", s->L);
+        const int old_kernel = s->kernel;
+        s->kernel = GS_KERNEL_TBLOCK;
+        s->tp = pl;
+        if (!s->maps_ok) {
+            rc = encode_maps(s);
+            if (rc) {
+                s->kernel = old_kernel;
+                return rc;
+            }
+        }
+        return GS_OK;
+    }
     return fail(GS_EINVAL, "kernel=%d not available", kernel);
+}
+
+int gs_set_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z, int depth)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    return apply_plan(s, kernel, tile_x, tile_y, tile_z, depth, 0);
+}
+
+int gs_set_plan_full(gs_sim* s, const gs_plan* p)
+{
+    if (!s || !p) return fail(GS_EINVAL, "NULL argument");
+    return apply_plan(s, p->kernel, p->tile_x, p->tile_y, p->tile_z, p->depth, p->stages);
+}
+
+static gs_plan current_plan(gs_sim* s)
+{
+    gs_plan p{};
+    p.kernel = s->kernel;
+    if (s->kernel == GS_KERNEL_ZMARCH) {
+        p.tile_x = s->zp.tx; p.tile_y = s->zp.ty; p.tile_z = s->zp.tz; p.depth = 1; p.stages = s->zp.stages;
+    } else if (s->kernel == GS_KERNEL_TBLOCK) {
+        p.tile_x = s->tp.tx; p.tile_y = s->tp.ty; p.tile_z = s->tp.tz; p.depth = s->tp.depth; p.stages = s->tp.stages;
+    } else {
+        p.depth = 1;
+    }
+    return p;
+}
+
+int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_results, int* n_results, gs_plan* best)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (steps_per_trial < 1) return fail(GS_EINVAL, "steps_per_trial must be >= 1");
+    if (max_results < 0 || (max_results > 0 && !results)) return fail(GS_EINVAL, "bad results buffer");
+    const int n = (steps_per_trial + 11) / 12 * 12;
+    // candidate plans
+    std::vector<gs_plan> cand;
+    cand.push_back(gs_plan{GS_KERNEL_NAIVE, 0, 0, 0, 1, 0, 0.0});
+    const int zt[][2] = {{128, 8}, {256, 4}, {64, 16}, {128, 4}, {64, 8}, {256, 8}, {128, 16}, {32, 16}};
+    for (auto& t : zt)
+        for (int tz : {32, 64, 128})
+            for (int st : {4, 6}) cand.push_back(gs_plan{GS_KERNEL_ZMARCH, t[0], t[1], tz, 1, st, 0.0});
+    const int bt[][2] = {{64, 16}, {128, 16}, {64, 32}, {128, 8}, {64, 8}, {32, 16}};
+    for (int d = 2; d <= 4; ++d)
+        for (auto& t : bt)
+            for (int tz : {64, 128}) cand.push_back(gs_plan{GS_KERNEL_TBLOCK, t[0], t[1], tz, d, 5, 0.0});
+    // save the state
+    const size_t bytes = (size_t)s->L * s->L * s->L * elem_size(s->dtype);
+    const gs_plan saved_plan = current_plan(s);
+    const int64_t t0 = s->t;
+    const int cur0 = s->cur;
+    void* bu = nullptr;
+    void* bv = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = GS_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&bu, bytes)) != cudaSuccess || (e = cudaMalloc(&bv, bytes)) != cudaSuccess ||
+        (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        rc = cuda_fail(e, "autotune set-up");
+    }
+    if (!rc) {
+        if ((e = cudaMemcpyAsync(bu, s->buf[cur0][0], bytes, cudaMemcpyDeviceToDevice, s->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(bv, s->buf[cur0][1], bytes, cudaMemcpyDeviceToDevice, s->stream)) != cudaSuccess)
+            rc = cuda_fail(e, "autotune save");
+    }
+    gs_plan win{};
+    win.us_per_step = -1.0;
+    int count = 0;
+    for (size_t i = 0; i < cand.size() && !rc; ++i) {
+        gs_plan& c = cand[i];
+        if (apply_plan(s, c.kernel, c.tile_x, c.tile_y, c.tile_z, c.depth, c.stages) != GS_OK) continue;
+        c = current_plan(s);
+        int r = gs_step(s, c.kernel == GS_KERNEL_TBLOCK ? 2 * c.depth : 2);
+        if (!r && (e = cudaEventRecord(e0, s->stream)) != cudaSuccess) r = cuda_fail(e, "event");
+        if (!r) r = gs_step(s, n);
+        if (!r && (e = cudaEventRecord(e1, s->stream)) != cudaSuccess) r = cuda_fail(e, "event");
+        if (!r) r = gs_sync(s);
+        float ms = 0.f;
+        if (!r && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) r = cuda_fail(e, "event");
+        if (r) {
+            rc = r;
+            break;
+        }
+        c.us_per_step = 1e3 * ms / n;
+        if (results && count < max_results) results[count] = c;
+        ++count;
+        if (win.us_per_step < 0 || c.us_per_step < win.us_per_step) win = c;
+    }
+    // restore the state and keep the winner (or the previous plan on failure)
+    if (bu && bv) {
+        cudaMemcpyAsync(s->buf[cur0][0], bu, bytes, cudaMemcpyDeviceToDevice, s->stream);
+        cudaMemcpyAsync(s->buf[cur0][1], bv, bytes, cudaMemcpyDeviceToDevice, s->stream);
+        cudaStreamSynchronize(s->stream);
+    }
+    s->cur = cur0;
+    s->t = t0;
+    const gs_plan keep = (!rc && win.us_per_step >= 0) ? win : saved_plan;
+    int rc2 = apply_plan(s, keep.kernel, keep.tile_x, keep.tile_y, keep.tile_z, keep.depth, keep.stages);
+    if (bu) cudaFree(bu);
+    if (bv) cudaFree(bv);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (n_results) *n_results = count;
+    if (best) *best = keep;
+    return GS_OK;
 }
 
 int gs_get_plan(gs_sim* s, int* kernel, int* tx, int* ty, int* tz, int* depth)
@@ -358,10 +500,11 @@ int gs_get_plan(gs_sim* s, int* kernel, int* tx, int* ty, int* tz, int* depth)
     if (!s) return fail(GS_EINVAL, "sim is NULL");
     if (kernel) *kernel = s->kernel;
     const bool z = s->kernel != GS_KERNEL_NAIVE;
-    if (tx) *tx = z ? s->zp.tx : 0;
-    if (ty) *ty = z ? s->zp.ty : 0;
-    if (tz) *tz = z ? s->zp.tz : 0;
-    if (depth) *depth = z ? s->zp.depth : 1;
+    const ZPlan& pl = s->kernel == GS_KERNEL_TBLOCK ? s->tp : s->zp;
+    if (tx) *tx = z ? pl.tx : 0;
+    if (ty) *ty = z ? pl.ty : 0;
+    if (tz) *tz = z ? pl.tz : 0;
+    if (depth) *depth = z ? pl.depth : 1;
     return GS_OK;
 }
 

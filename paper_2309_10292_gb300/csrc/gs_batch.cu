@@ -64,7 +64,7 @@ struct BArgs {
     int nitems, tz, stages;
     int main_elems, row_elems, field_elems;  // shared-memory stage layout (elements)
     long long nsteps;
-    T Du6, Dv6, dt, noise;
+    T Du6, Dv6, dt, noise24;
     uint64_t timeout_ns;
     int fault;  // 1: the producer issues no copies; 2: CTA 0 never arrives at the grid barrier
 };
@@ -170,9 +170,10 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                 const int moff = rr * L + xv * V;
                 const int rowbase = rr * L;
                 GsCoef<T> c;
-                c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise = a.noise;
+                c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise24 = a.noise24;
                 c.F = (T)I.F; c.Fk = (T)I.Fk;
                 const GsKeys keys = gs_step_keys(((uint64_t)I.seed_hi << 32) | I.seed_lo, t);
+                const uint32_t kk2 = gs_kk2(keys);
                 T* un = a.arena + I.off[out][0];
                 T* vn = a.arena + I.off[out][1];
                 const long long LL = (long long)L * L;
@@ -209,16 +210,9 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                         const int oxr = xv < nxv - 1 ? moff + V : rowbase;
                         const T xlu = bu[oxl], xru = bu[oxr], xlv = bv[oxl], xrv = bv[oxr];
                         const long long g = (long long)(z0 + zi) * LL + (long long)(y0 + row) * L + xv * V;
-#pragma unroll
-                        for (int e = 0; e < V; ++e) {
-                            const T su = gs_nsum(e > 0 ? cu[e - 1] : xlu, e < V - 1 ? cu[e + 1] : xru, ymu[e], ypu[e],
-                                                 pu[e], nu[e]);
-                            const T sv = gs_nsum(e > 0 ? cv[e - 1] : xlv, e < V - 1 ? cv[e + 1] : xrv, ymv[e], ypv[e],
-                                                 pv[e], nv[e]);
-                            T r_ = (T)0;
-                            if (NOISE) r_ = gs_noise<T>((uint32_t)(g + e), keys);
-                            gs_update<T, NOISE>(c, cu[e], cv[e], su, sv, r_, ou[e], ov[e]);
-                        }
+                        const uint32_t pre = NOISE ? gs_group_pre((uint32_t)g, keys) : 0u;
+                        gs_update_group<T, NOISE>(c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
+                                                  xru, xlv, xrv, ou, ov);
                         *reinterpret_cast<VT*>(un + g) = gs_pack<T>(ou);
                         *reinterpret_cast<VT*>(vn + g) = gs_pack<T>(ov);
                     }
@@ -368,7 +362,7 @@ static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
     a.Du6 = c.Du6;
     a.Dv6 = c.Dv6;
     a.dt = c.dt;
-    a.noise = c.noise;
+    a.noise24 = c.noise24;
     a.timeout_ns = b->timeout_ns;
     a.fault = b->fault;
     const size_t smem = (size_t)2 * b->field_elems * sizeof(T) * b->stages;
@@ -765,7 +759,7 @@ static int noalloc_launch_t(char* scratch, void* arena, int n, int nitems, int m
     a.Du6 = c.Du6;
     a.Dv6 = c.Dv6;
     a.dt = c.dt;
-    a.noise = c.noise;
+    a.noise24 = c.noise24;
     a.timeout_ns = 2000000000ull;
     a.fault = 0;
     (void)n;

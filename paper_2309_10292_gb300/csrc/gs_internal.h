@@ -59,4 +59,9 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
                   const Params& p, int64_t t, int* d_err, uint64_t timeout_ns, int stall,
                   cudaStream_t s);
 
+// Temporally blocked kernel (gs_tblock.cu): `depth` steps per pass, FP32.
+int tblock_validate(int dtype, int L, const ZPlan& pl);
+int launch_tblock(int L, const ZPlan& pl, const void* u, const void* v, void* un, void* vn, const Params& p,
+                  int64_t t, cudaStream_t s);
+
 }  // namespace gs

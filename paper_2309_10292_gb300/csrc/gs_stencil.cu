@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, 
         const T uc = u[i], vc = v[i];
         const T su = gs_nsum(u[ixm], u[ixp], u[iym], u[iyp], u[izm], u[izp]);
         const T sv = gs_nsum(v[ixm], v[ixp], v[iym], v[iyp], v[izm], v[izp]);
-        T r_ = (T)0;
-        if (NOISE) r_ = gs_noise<T>((uint32_t)i, k);
+        T rn = (T)0;
+        if (NOISE) rn = (T)gs_noise_num((uint32_t)i, k);
         T a, b;
-        gs_update<T, NOISE>(c, uc, vc, su, sv, r_, a, b);
+        gs_update<T, NOISE>(c, uc, vc, su, sv, rn, a, b);
         un[i] = a;
         vn[i] = b;
     }
@@ -281,6 +281,7 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
     const int lane = tid & 31;
     const size_t stage_elems = a.lay.stage_bytes / sizeof(T);
     const int64_t LL = (int64_t)L * L;
+    const uint32_t kk2 = gs_kk2(a.keys);
     uint32_t seq = 0;
 
     auto release = [&](int s) {
@@ -351,16 +352,9 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                 const int oxr = xv * V + V < nvx ? a.lay.main_off + moff + V : a.lay.right_off + row * V;
                 const T xlu = bu[oxl], xru = bu[oxr], xlv = bv[oxl], xrv = bv[oxr];
                 const int64_t gidx = (int64_t)z * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    const T su = gs_nsum(e > 0 ? cu[e - 1] : xlu, e < V - 1 ? cu[e + 1] : xru, ymu[e], ypu[e],
-                                         pu[e], nu[e]);
-                    const T sv = gs_nsum(e > 0 ? cv[e - 1] : xlv, e < V - 1 ? cv[e + 1] : xrv, ymv[e], ypv[e],
-                                         pv[e], nv[e]);
-                    T r_ = (T)0;
-                    if (NOISE) r_ = gs_noise<T>((uint32_t)(gidx + e), a.keys);
-                    gs_update<T, NOISE>(a.c, cu[e], cv[e], su, sv, r_, outu[e], outv[e]);
-                }
+                const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
+                gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
+                                          xlv, xrv, outu, outv);
                 *reinterpret_cast<VT*>(a.un + gidx) = gs_pack<T>(outu);
                 *reinterpret_cast<VT*>(a.vn + gidx) = gs_pack<T>(outv);
             }

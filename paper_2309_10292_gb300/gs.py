@@ -59,6 +59,8 @@ _SIGS = {
     "gs_set_plan": [_vp, _i, _i, _i, _i, _i],
     "gs_get_plan": [_vp] + [ctypes.POINTER(_i)] * 5,
     "gs_sync": [_vp],
+    "gs_set_plan_full": [_vp, _vp],
+    "gs_autotune": [_vp, _i, _vp, _i, ctypes.POINTER(_i), _vp],
     "gs_set_fault": [_vp, _i, _u64],
     "gs_launch_count": [_vp, ctypes.POINTER(_i64)],
     "gs_destroy": [_vp],
@@ -213,6 +215,31 @@ def gs_get_plan(sim) -> dict:
     v = [_i() for _ in range(5)]
     _check(lib().gs_get_plan(sim, *[ctypes.byref(x) for x in v]), "gs_get_plan")
     return dict(zip(("kernel", "tile_x", "tile_y", "tile_z", "depth"), (x.value for x in v)))
+
+
+class GsPlan(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("tile_z", ctypes.c_int), ("depth", ctypes.c_int), ("stages", ctypes.c_int),
+                ("us_per_step", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def gs_set_plan_full(sim, plan: dict):
+    p = GsPlan(**{k: plan[k] for k in ("kernel", "tile_x", "tile_y", "tile_z", "depth", "stages")
+                  if k in plan})
+    _check(lib().gs_set_plan_full(sim, ctypes.byref(p)), "gs_set_plan_full")
+
+
+def gs_autotune(sim, steps_per_trial: int = 12, max_results: int = 256):
+    """Run the native autotuner; returns (best plan, list of trials) as dicts."""
+    res = (GsPlan * max_results)()
+    n = _i()
+    best = GsPlan()
+    _check(lib().gs_autotune(sim, steps_per_trial, res, max_results, ctypes.byref(n), ctypes.byref(best)),
+           "gs_autotune")
+    return best.as_dict(), [res[i].as_dict() for i in range(min(n.value, max_results))]
 
 
 def gs_sync(sim):
@@ -425,6 +452,10 @@ class GrayScott:
     @property
     def plan(self) -> dict:
         return gs_get_plan(self.handle)
+
+    def autotune(self, steps_per_trial: int = 12):
+        """Pick the fastest plan for this grid (state is left unchanged)."""
+        return gs_autotune(self.handle, steps_per_trial)
 
     @property
     def t(self) -> int:

@@ -199,3 +199,94 @@ def test_bounded_wait_timeout_reports_and_recovers():
     u0, v0 = oracle.init(L)
     uo, vo = oracle.step(u0, v0, 5, **PAPER, noise=0.0, seed=0)
     assert maxabs(u, uo) <= 1e-4 and maxabs(v, vo) <= 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Temporal blocking: `depth` fused steps per HBM pass (FP32)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("L,tiles,depth,n", [(32, (16, 8, 32), 2, 9), (32, (8, 4, 5), 3, 10),
+                                             (48, (16, 8, 7), 4, 11), (64, (64, 16, 64), 2, 6),
+                                             (64, (32, 8, 13), 4, 8), (16, (4, 2, 3), 2, 5)])
+def test_tblock_bitwise_equal_to_plain(L, tiles, depth, n):
+    prm = dict(PAPER, noise=0.1, seed=3)
+    ref = make(L, "f32", gs.GS_KERNEL_NAIVE, **prm)
+    ref.step(n)
+    ur, vr = ref.read()
+    sim = make(L, "f32", **prm)
+    sim.set_plan(gs.GS_KERNEL_TBLOCK, *tiles, depth)
+    assert sim.plan["kernel"] == gs.GS_KERNEL_TBLOCK and sim.plan["depth"] == depth
+    sim.step(n)  # n // depth blocked passes, the rest single steps
+    u, v = sim.read()
+    np.testing.assert_array_equal(u, ur)
+    np.testing.assert_array_equal(v, vr)
+    assert sim.t == n
+
+
+def test_tblock_config1_parity():
+    L, n = 64, 100
+    u0, v0 = oracle.init(L)
+    uo, vo = oracle.step(u0, v0, n, **PAPER, noise=0.0, seed=0)
+    sim = make(L, "f32", noise=0.0, seed=0)
+    sim.set_plan(gs.GS_KERNEL_TBLOCK, 32, 8, 32, 4)
+    sim.step(n)
+    u, v = sim.read()
+    assert maxabs(u, uo) <= 1e-4 and maxabs(v, vo) <= 1e-4
+
+
+@pytest.mark.parametrize("depth", [2, 4])
+def test_tblock_full_size_sampled_cells(depth):
+    # the L=1024 FP32 workload with temporal blocking, sampled against the oracle
+    L, n = 1024, 16
+    prm = dict(PAPER, noise=0.1, seed=42)
+    sim = make(L, "f32", **prm)
+    sim.set_plan(gs.GS_KERNEL_TBLOCK, 64, 16 if depth == 2 else 8, 64, depth)
+    sim.step(n)
+    u, v = sim.read()
+    m = 2
+    for c in [(L // 2, L // 2, L // 2), (0, 0, 0), (L - 1, 63, 64), (64, 15, L - 1), (300, 700, 5)]:
+        uo, vo = oracle.window(L, c, m, n, **prm)
+        idx = [(np.arange(-m, m + 1) + cc) % L for cc in c]
+        sel = np.ix_(idx[2], idx[1], idx[0])
+        assert maxabs(u[sel], uo) <= 1e-4 and maxabs(v[sel], vo) <= 1e-4, c
+    sim.close()
+
+
+def test_tblock_rejects_unsupported_plans():
+    sim = make(64, "f64")
+    with pytest.raises(gs.GsError) as e:
+        sim.set_plan(gs.GS_KERNEL_TBLOCK, 32, 8, 32, 2)
+    assert e.value.status == gs.GS_EINVAL
+    s32 = make(48, "f32")
+    for bad in [(32, 8, 8, 2), (16, 7, 8, 2), (16, 8, 8, 5), (16, 8, 8, 1)]:
+        with pytest.raises(gs.GsError):
+            s32.set_plan(gs.GS_KERNEL_TBLOCK, *bad)
+    assert s32.plan["kernel"] == gs.GS_KERNEL_ZMARCH
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_autotune_restores_state_and_keeps_fastest_plan(dtype):
+    L = 64
+    prm = dict(PAPER, noise=0.1, seed=8)
+    a = make(L, dtype, **prm)
+    a.step(7)
+    u0, v0 = a.read()
+    best, trials = a.autotune(steps_per_trial=12)
+    assert a.t == 7
+    u1, v1 = a.read()
+    np.testing.assert_array_equal(u0, u1)
+    np.testing.assert_array_equal(v0, v1)
+    assert len(trials) > 3
+    fastest = min(trials, key=lambda r: r["us_per_step"])
+    assert best["us_per_step"] == fastest["us_per_step"]
+    assert a.plan["kernel"] == best["kernel"]
+    kinds = {r["kernel"] for r in trials}
+    assert gs.GS_KERNEL_NAIVE in kinds and gs.GS_KERNEL_ZMARCH in kinds
+    if dtype == "f32":
+        assert gs.GS_KERNEL_TBLOCK in kinds
+    a.step(13)
+    ref = make(L, dtype, gs.GS_KERNEL_NAIVE, **prm)
+    ref.step(20)
+    ua, va = a.read()
+    ur, vr = ref.read()
+    np.testing.assert_array_equal(ua, ur)
+    np.testing.assert_array_equal(va, vr)
