@@ -41,6 +41,7 @@ extern "C" {
 
 typedef struct gs_sim gs_sim;
 typedef struct gs_batch gs_batch;
+typedef struct gs_surr gs_surr;
 
 enum { GS_F32 = 0, GS_F64 = 1 };
 enum { GS_U = 0, GS_V = 1 };
@@ -90,6 +91,10 @@ int gs_create_on(int L, double Du, double Dv, double F, double k, double dt, dou
 /* Use `stream` (a cudaStream_t, caller-owned, NULL = legacy default) for all
  * later device work of this object. */
 int gs_set_stream(gs_sim* sim, void* stream);
+
+/* The object's stream and grid: edge L and dtype. */
+int gs_get_stream(gs_sim* sim, void** stream);
+int gs_sim_shape(gs_sim* sim, int* L, int* dtype);
 
 /* Reset to the centred-cube initial state and step 0 (asynchronous). */
 int gs_init(gs_sim* sim);
@@ -261,6 +266,73 @@ int gs_batch_destroy(gs_batch* b);
 int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k, double Du,
                           double Dv, double dt, double noise, uint64_t seed, int dtype, void* arena,
                           int64_t t, int cur, int64_t nsteps, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Learned surrogate (not in the paper): a network that advances a grid by  */
+/* K = 16 steps, trained on trajectories of the stencil itself             */
+/* ---------------------------------------------------------------------- */
+/*
+ * Network (6 layers, circular 3x3x3 convolutions, weights [27][Cin][Cout] with
+ * tap = 9 (dz+1) + 3 (dy+1) + (dx+1), biases [Cout]):
+ *   x0  = (u - 1, v, 20 F, 20 k)                  rounded to bfloat16
+ *   h1  = relu(conv0(x0))                         4 -> 32 channels
+ *   h_l = h_{l-1} + relu(conv_l(h_{l-1}))         32 -> 32, l = 2..5
+ *   out = (u, v) + conv5(h5)                      32 -> 2, = state after 16 steps
+ * Activations and weights are bfloat16, every product is accumulated in
+ * FP32 on the tensor cores.  Parameters are one flat FP32 array: for each
+ * layer its weights then its biases (gs_surr_param_count entries).  Grids:
+ * L a multiple of 16 (of 128 above 128); fields are FP32 device arrays of
+ * N x L^3 cells (N grids back to back, x-fastest), F and k host arrays of N.
+ */
+typedef struct gs_surr_report {
+    int64_t surrogate_applications; /* network applications (16 steps each) kept  */
+    int64_t surrogate_steps;        /* steps advanced by the network                */
+    int64_t stencil_steps;          /* steps advanced by the stencil                */
+    int64_t checks;                 /* number of network-vs-stencil checks          */
+    int64_t fallbacks;              /* checks whose error exceeded tol              */
+    double max_check_error;         /* largest max-abs check error (u and v)        */
+    double last_check_error;
+} gs_surr_report;
+
+int gs_surr_param_count(size_t* count);
+/* Allocates parameters (zero), Adam moments and bf16 weight copies. */
+int gs_surr_create(gs_surr** out);
+int gs_surr_set_stream(gs_surr* s, void* stream);
+/* Host FP32 parameter array in / out (count must equal gs_surr_param_count);
+ * setting parameters resets the Adam moments.  Synchronous. */
+int gs_surr_set_params(gs_surr* s, const float* host, size_t count);
+int gs_surr_get_params(gs_surr* s, float* host, size_t count);
+/* Gradients of the last gs_surr_grad / gs_surr_train_step, same layout. */
+int gs_surr_get_grads(gs_surr* s, float* host, size_t count);
+/* Apply the network: (u_out, v_out) = prediction of the state 16 steps after
+ * (u, v) for N grids (device arrays; outputs may not alias inputs). */
+int gs_surr_forward(gs_surr* s, int N, int L, const float* u, const float* v, const double* F,
+                    const double* k, float* u_out, float* v_out);
+/* Loss = mean over all cells and both fields of (prediction - target)^2; its
+ * gradient w.r.t. every parameter into the internal gradient buffer; *loss
+ * (host) receives the loss.  Synchronous. */
+int gs_surr_grad(gs_surr* s, int N, int L, const float* u, const float* v, const double* F,
+                 const double* k, const float* u_tgt, const float* v_tgt, double* loss);
+/* One Adam step (Kingma & Ba 2015) on the FP32 master parameters. */
+int gs_surr_adam(gs_surr* s, double lr, double beta1, double beta2, double eps);
+/* gs_surr_grad followed by gs_surr_adam(lr, 0.9, 0.999, 1e-8). */
+int gs_surr_train_step(gs_surr* s, int N, int L, const float* u, const float* v, const double* F,
+                       const double* k, const float* u_tgt, const float* v_tgt, double lr, double* loss);
+/* max |a - b| and root-mean-square difference of n device floats. */
+int gs_surr_diff(gs_surr* s, const float* a, const float* b, int64_t n, double* maxabs, double* rms);
+/* Advance an FP32 simulation (noise 0 expected; the network cannot predict
+ * noise) nsteps with the network, judged by the stencil: each segment of
+ * check_every steps (a multiple of 16) applies the network check_every/16 - 1
+ * times, then compares one more application against 16 stencil steps from
+ * the same state and keeps the stencil's state.  A check error (max-abs over
+ * u and v) above tol makes the next segment a plain stencil segment
+ * (fallback).  F, k are the simulation's feed and kill rates.  Uses the
+ * simulation's stream; synchronous; temporary device buffers for one grid
+ * are allocated for the duration. */
+int gs_surr_run(gs_surr* s, gs_sim* sim, double F, double k, int64_t nsteps, int check_every,
+                double tol, gs_surr_report* report);
+int gs_surr_launch_count(gs_surr* s, int64_t* count);
+int gs_surr_destroy(gs_surr* s);
 
 /* ---------------------------------------------------------------------- */
 /* Noise field                                                             */

@@ -194,7 +194,9 @@ def bf16_round(a: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Surrogate network (not in the paper), FP64 with optional bf16 emulation at
 # the points where the GPU path stores bf16 values.
-#   x0 = (u, v, F*FK_SCALE, k*FK_SCALE)                       [N, L, L, L, 4]
+#   x0 = (u - 1, v, F*FK_SCALE, k*FK_SCALE)                   [N, L, L, L, 4]
+#        (u - 1 is zero on the u = 1 background, so bfloat16 keeps small
+#        deviations at full relative precision)
 #   h1 = relu(conv1(x0))                                      4 -> 32
 #   h_l = h_{l-1} + relu(conv_l(h_{l-1})),  l = 2..5          32 -> 32
 #   d  = conv6(h5)                                            32 -> 2
@@ -217,7 +219,7 @@ def surrogate_forward(params, u, v, F, k, *, emulate_bf16: bool = False):
     """
     N, L = u.shape[0], u.shape[1]
     x0 = np.empty((N, L, L, L, 4), dtype=np.float64)
-    x0[..., 0] = u
+    x0[..., 0] = np.asarray(u, dtype=np.float64) - 1.0
     x0[..., 1] = v
     x0[..., 2] = (np.asarray(F, dtype=np.float64) * FK_SCALE)[:, None, None, None]
     x0[..., 3] = (np.asarray(k, dtype=np.float64) * FK_SCALE)[:, None, None, None]

@@ -222,6 +222,21 @@ int gs_set_stream(gs_sim* s, void* stream)
     return GS_OK;
 }
 
+int gs_get_stream(gs_sim* s, void** stream)
+{
+    if (!s || !stream) return fail(GS_EINVAL, "NULL argument");
+    *stream = (void*)s->stream;
+    return GS_OK;
+}
+
+int gs_sim_shape(gs_sim* s, int* L, int* dtype)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (L) *L = s->L;
+    if (dtype) *dtype = s->dtype;
+    return GS_OK;
+}
+
 int gs_init(gs_sim* s)
 {
     if (!s) return fail(GS_EINVAL, "sim is NULL");

@@ -1,0 +1,1063 @@
+// Learned surrogate of the Gray-Scott stencil (not in the paper): a 6-layer
+// 3D residual convolution network advancing (u, v) by K = 16 steps.
+//
+//   x0  = bf16(u - 1, v, 20 F, 20 k)             4 channels (padded to 16)
+//   h1  = relu(conv0(x0))                        4 -> 32
+//   h_l = h_{l-1} + relu(conv_l(h_{l-1}))        32 -> 32, l = 2..5
+//   out = (u, v) + conv5(h5)                     32 -> 2 (padded to 8)
+//
+// conv = circular 3x3x3 convolution with bias, weights [tap][Cin][Cout],
+// tap = 9 (dz+1) + 3 (dy+1) + (dx+1).  Activations are bf16, channels-last
+// [n][z][y][x][c]; every contraction runs on the tensor cores (bf16 x bf16 ->
+// fp32, mma.sync m16n8k16) as an implicit GEMM over M = cells, N = output
+// channels, K = 27 taps x input channels:
+//
+//   gs_conv_kernel    forward (epilogues: first / residual hidden / final
+//                     state update) and data gradient (the same convolution
+//                     with tap-flipped, transposed weights; epilogue adds the
+//                     residual-path gradient and applies the ReLU mask of the
+//                     layer below)
+//   gs_wgrad_kernel   weight gradient: per tap, [Cin x cells] x [cells x Cout]
+//   + packing, bias-gradient, MSE-loss, Adam and weight-layout kernels.
+//
+// A CTA stages 4 output rows (y0..y0+3) of a 128-cell x segment: 6 x 3 input
+// rows with a one-cell periodic halo, and the layer's weights, in shared
+// memory with a 16-byte XOR swizzle so every ldmatrix is conflict-free.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gs_common.cuh"
+#include "gs_internal.h"
+
+namespace gs {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kSurrLayers = 6;
+constexpr int kChan[kSurrLayers + 1] = {4, 32, 32, 32, 32, 32, 2};
+constexpr int kCinP[kSurrLayers] = {16, 32, 32, 32, 32, 32};
+constexpr int kCoutP[kSurrLayers] = {32, 32, 32, 32, 32, 8};
+constexpr float kFkScale = 20.f;
+constexpr int kRows = 4;          // output rows per CTA work item
+constexpr int kConvThreads = 512; // 16 warps: 4 rows x 4 segments of 32 cells
+
+enum { EPI_FIRST = 0, EPI_HIDDEN = 1, EPI_LAST = 2, EPI_DGRAD = 3 };
+
+// byte offset of 16-byte chunk j of row `r` in a swizzled [rows][nch * 16 B] buffer
+GS_D uint32_t swz(int r, int j, int nch)
+{
+    const int x = nch >= 4 ? ((r >> 1) & 3) : (nch == 2 ? ((r >> 2) & 1) : 0);
+    return (uint32_t)(r * nch * 16 + ((j ^ x) * 16));
+}
+
+GS_D void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+GS_D void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+GS_D void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+GS_D void ldsm_x2_t(uint32_t addr, uint32_t& r0, uint32_t& r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+GS_D void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+GS_D void cp16(uint32_t smem, const void* g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem), "l"(g) : "memory");
+}
+GS_D void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+struct ConvArgs {
+    const bf16* in;     // [N][L^3][CINP]
+    const bf16* w;      // [27][COUTP][CINP] (n-major rows of k)
+    const float* bias;  // [COUTP] or null
+    int N, L;
+    const bf16* res;    // EPI_HIDDEN: residual h_in [..][32]
+    bf16* out;          // EPI_FIRST / EPI_HIDDEN: h_out [..][32]
+    bf16* zout;         // forward: pre-activation z [..][32] (or null)
+    const float* su;    // EPI_LAST: state in, u and v planes [N][L^3]
+    const float* sv;
+    float* ou;          // EPI_LAST: state out
+    float* ov;
+    float* gh;          // EPI_DGRAD: residual-path gradient [..][32], fp32, in / out
+    int gh_acc;         // EPI_DGRAD: 1 -> gh += acc, 0 -> gh = acc
+    const bf16* zprev;  // EPI_DGRAD: z of the layer below (ReLU mask) or null
+    bf16* gz;           // EPI_DGRAD: gz = gh * (zprev > 0)
+};
+
+// Work item: (n, z, y-group of 4 rows, x segment).
+template <int CINP, int COUTP, int EPI>
+__global__ void __launch_bounds__(kConvThreads, 1) gs_conv_kernel(const ConvArgs a)
+{
+    constexpr int NCH = CINP / 8;  // 16-byte chunks per input cell
+    constexpr int NT = COUTP / 8;  // n8 tiles
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int L = a.L;
+    const int SEG = L < 128 ? L : 128;
+    const int HC = SEG + 2;
+    const int nseg = L / SEG;
+    const long long L3 = (long long)L * L * L;
+    unsigned char* wsm = smem;                                      // weights
+    unsigned char* hsm = smem + 27 * COUTP * CINP * 2;              // halo [18 rows][HC cells]
+    const uint32_t wbase = gs_smem_addr(wsm), hbase = gs_smem_addr(hsm);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // weights once per CTA
+    for (int i = tid; i < 27 * COUTP * NCH; i += kConvThreads) {
+        const int r = i / NCH, j = i % NCH;
+        cp16(wbase + swz(r, j, NCH), a.w + (size_t)r * CINP + j * 8);
+    }
+
+    const int wrow = warp >> 2;           // output row within the item
+    const int wseg = (warp & 3) * 32;     // first cell of this warp's 32
+    const bool wact = wseg < SEG;
+    const int nmt = SEG - wseg >= 32 ? 2 : 1;  // m16 tiles of this warp
+    const int g = lane >> 2, t = lane & 3;
+
+    const long long items = (long long)a.N * L * (L / kRows) * nseg;
+    for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+        const int seg = (int)(item % nseg);
+        long long r = item / nseg;
+        const int yg = (int)(r % (L / kRows));
+        r /= (L / kRows);
+        const int z = (int)(r % L);
+        const int n = (int)(r / L);
+        const int x0 = seg * SEG, y0 = yg * kRows;
+        __syncthreads();  // previous item's reads of the halo are done
+        // halo rows: yi = 0..5 -> y0 - 1 + yi, zi = 0..2 -> z - 1 + zi
+        const int hchunks = 18 * HC * NCH;
+        for (int i = tid; i < hchunks; i += kConvThreads) {
+            const int j = i % NCH;
+            const int c = (i / NCH) % HC;
+            const int hr = i / (NCH * HC);
+            const int yy = (y0 - 1 + hr % 6 + L) % L;
+            const int zz = (z - 1 + hr / 6 + L) % L;
+            const int xx = (x0 + c - 1 + L) % L;
+            const bf16* src = a.in + ((size_t)n * L3 + ((size_t)zz * L + yy) * L + xx) * CINP + j * 8;
+            cp16(hbase + swz(hr * HC + c, j, NCH), src);
+        }
+        cp_wait_all();
+        __syncthreads();
+        if (!wact) continue;
+
+        float acc[2][NT][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            const int hr = (wrow + 1 + dy) + 6 * (1 + dz);
+#pragma unroll
+            for (int kc = 0; kc < CINP / 16; ++kc) {
+                uint32_t b[NT][2];
+                if constexpr (NT == 1) {
+                    const int m = (lane >> 3) & 1;
+                    const int co = lane & 7;
+                    ldsm_x2(wbase + swz(tap * COUTP + co, kc * 2 + m, NCH), b[0][0], b[0][1]);
+                } else {
+#pragma unroll
+                    for (int np = 0; np < NT; np += 2) {
+                        const int m = lane >> 3;
+                        const int co = (np + (m >> 1)) * 8 + (lane & 7);
+                        ldsm_x4(wbase + swz(tap * COUTP + co, kc * 2 + (m & 1), NCH), b[np][0], b[np][1],
+                                b[np + 1][0], b[np + 1][1]);
+                    }
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    if (mt >= nmt) break;
+                    const int m = lane >> 3;
+                    const int cell = wseg + mt * 16 + (lane & 7) + (m & 1) * 8;
+                    uint32_t af[4];
+                    ldsm_x4(hbase + swz(hr * HC + 1 + dx + cell, kc * 2 + (m >> 1), NCH), af[0], af[1], af[2], af[3]);
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], af, b[nt][0], b[nt][1]);
+                }
+            }
+        }
+
+        // epilogue
+        const int y = y0 + wrow;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            if (mt >= nmt) break;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int x = x0 + wseg + mt * 16 + g + hh * 8;
+                const size_t cell = (size_t)n * L3 + ((size_t)z * L + y) * L + x;
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int ch = nt * 8 + 2 * t;
+                    float v0 = acc[mt][nt][2 * hh], v1 = acc[mt][nt][2 * hh + 1];
+                    if constexpr (EPI == EPI_FIRST || EPI == EPI_HIDDEN) {
+                        v0 += a.bias[ch];
+                        v1 += a.bias[ch + 1];
+                        if (a.zout) *reinterpret_cast<__nv_bfloat162*>(a.zout + cell * 32 + ch) = __floats2bfloat162_rn(v0, v1);
+                        float h0 = fmaxf(v0, 0.f), h1 = fmaxf(v1, 0.f);
+                        if constexpr (EPI == EPI_HIDDEN) {
+                            const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(a.res + cell * 32 + ch);
+                            h0 = __bfloat162float(rr.x) + h0;
+                            h1 = __bfloat162float(rr.y) + h1;
+                        }
+                        *reinterpret_cast<__nv_bfloat162*>(a.out + cell * 32 + ch) = __floats2bfloat162_rn(h0, h1);
+                    } else if constexpr (EPI == EPI_LAST) {
+                        if (ch == 0) {
+                            a.ou[cell] = a.su[cell] + (v0 + a.bias[0]);
+                            a.ov[cell] = a.sv[cell] + (v1 + a.bias[1]);
+                        }
+                    } else {  // EPI_DGRAD
+                        float* gp = a.gh + cell * 32 + ch;
+                        if (a.gh_acc) {
+                            v0 += gp[0];
+                            v1 += gp[1];
+                        }
+                        gp[0] = v0;
+                        gp[1] = v1;
+                        if (a.gz) {
+                            const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162*>(a.zprev + cell * 32 + ch);
+                            const float m0 = __bfloat162float(zz.x) > 0.f ? v0 : 0.f;
+                            const float m1 = __bfloat162float(zz.y) > 0.f ? v1 : 0.f;
+                            *reinterpret_cast<__nv_bfloat162*>(a.gz + cell * 32 + ch) = __floats2bfloat162_rn(m0, m1);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    cp_wait_all();
+}
+
+// Weight gradient: dW[tap][ci][co] += sum over cells of in[cell + d(tap)][ci] * g[cell][co]
+struct WgArgs {
+    const bf16* in;  // [N][L^3][CINP]
+    const bf16* g;   // [N][L^3][GST] (first NP channels used)
+    float* dw;       // [27][cin][cout] (fp32, accumulated with atomics)
+    int N, L, GST, cin, cout;
+};
+
+constexpr int kWgThreads = 288;  // 9 warps x 3 taps
+
+template <int CINP, int NP>
+__global__ void __launch_bounds__(kWgThreads, 1) gs_wgrad_kernel(const WgArgs a)
+{
+    constexpr int NCH = CINP / 8, GCH = NP / 8;
+    constexpr int MT = CINP / 16, NT = NP / 8;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int L = a.L;
+    const int SEG = L < 128 ? L : 128;
+    const int HC = SEG + 2;
+    const int nseg = L / SEG;
+    const long long L3 = (long long)L * L * L;
+    unsigned char* hsm = smem;                      // 18 halo rows of `in`
+    unsigned char* gsm = smem + 18 * HC * CINP * 2; // 4 rows of g
+    const uint32_t hbase = gs_smem_addr(hsm), gbase = gs_smem_addr(gsm);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g8 = lane >> 2, t4 = lane & 3;
+
+    float acc[3][MT][NT][4];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[q][mt][nt][i] = 0.f;
+
+    const long long items = (long long)a.N * L * (L / kRows) * nseg;
+    for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+        const int seg = (int)(item % nseg);
+        long long r = item / nseg;
+        const int yg = (int)(r % (L / kRows));
+        r /= (L / kRows);
+        const int z = (int)(r % L);
+        const int n = (int)(r / L);
+        const int x0 = seg * SEG, y0 = yg * kRows;
+        __syncthreads();
+        for (int i = tid; i < 18 * HC * NCH; i += kWgThreads) {
+            const int j = i % NCH;
+            const int c = (i / NCH) % HC;
+            const int hr = i / (NCH * HC);
+            const int yy = (y0 - 1 + hr % 6 + L) % L;
+            const int zz = (z - 1 + hr / 6 + L) % L;
+            const int xx = (x0 + c - 1 + L) % L;
+            cp16(hbase + swz(hr * HC + c, j, NCH), a.in + ((size_t)n * L3 + ((size_t)zz * L + yy) * L + xx) * CINP + j * 8);
+        }
+        for (int i = tid; i < kRows * SEG * GCH; i += kWgThreads) {
+            const int j = i % GCH;
+            const int c = (i / GCH) % SEG;
+            const int rr = i / (GCH * SEG);
+            cp16(gbase + swz(rr * SEG + c, j, GCH),
+                 a.g + ((size_t)n * L3 + ((size_t)z * L + (y0 + rr)) * L + x0 + c) * a.GST + j * 8);
+        }
+        cp_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int tap = warp * 3 + q;
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+#pragma unroll 1
+            for (int rr = 0; rr < kRows; ++rr) {
+                const int hr = (rr + 1 + dy) + 6 * (1 + dz);
+                for (int k0 = 0; k0 < SEG; k0 += 16) {
+                    // B (cells x co) from g, transposed load
+                    uint32_t b[NT][2];
+                    if constexpr (NT == 1) {
+                        const int m = (lane >> 3) & 1;
+                        const int cell = k0 + (lane & 7) + m * 8;
+                        ldsm_x2_t(gbase + swz(rr * SEG + cell, 0, GCH), b[0][0], b[0][1]);
+                    } else {
+#pragma unroll
+                        for (int np = 0; np < NT; np += 2) {
+                            const int m = lane >> 3;
+                            const int cell = k0 + (lane & 7) + (m & 1) * 8;
+                            ldsm_x4_t(gbase + swz(rr * SEG + cell, np + (m >> 1), GCH), b[np][0], b[np][1],
+                                      b[np + 1][0], b[np + 1][1]);
+                        }
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        // A (ci x cells) from the shifted input row, transposed load
+                        const int m = lane >> 3;
+                        const int cell = k0 + (lane & 7) + (m >> 1) * 8;
+                        uint32_t af[4];
+                        ldsm_x4_t(hbase + swz(hr * HC + 1 + dx + cell, mt * 2 + (m & 1), NCH), af[0], af[1], af[2],
+                                  af[3]);
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[q][mt][nt], af, b[nt][0], b[nt][1]);
+                    }
+                }
+            }
+        }
+    }
+    // accumulate this CTA's partial sums
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int tap = warp * 3 + q;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int ci = mt * 16 + g8 + (i >= 2 ? 8 : 0);
+                    const int co = nt * 8 + 2 * t4 + (i & 1);
+                    if (ci < a.cin && co < a.cout) atomicAdd(a.dw + ((size_t)tap * a.cin + ci) * a.cout + co, acc[q][mt][nt][i]);
+                }
+    }
+}
+
+// x0 = bf16(u - 1, v, 20 F, 20 k, 0, ...) : [N][L^3][16]
+__global__ void gs_pack_kernel(const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ Fk,
+                               bf16* __restrict__ x0, long long L3, int N)
+{
+    const long long total = L3 * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(i / L3);
+        __align__(16) bf16 c[16];
+        c[0] = __float2bfloat16_rn(u[i] - 1.f);  // zero on the u = 1 background
+        c[1] = __float2bfloat16_rn(v[i]);
+        c[2] = __float2bfloat16_rn(Fk[2 * n] * kFkScale);
+        c[3] = __float2bfloat16_rn(Fk[2 * n + 1] * kFkScale);
+        for (int j = 4; j < 16; ++j) c[j] = __float2bfloat16_rn(0.f);
+        uint4* dst = reinterpret_cast<uint4*>(x0 + i * 16);
+        dst[0] = reinterpret_cast<const uint4*>(c)[0];
+        dst[1] = reinterpret_cast<const uint4*>(c)[1];
+    }
+}
+
+// fp32 master weights [27][cin][cout] -> bf16 forward layout [27][COUTP][CINP]
+// (and, for dgrad, [27][cin][COUTP'] with taps flipped: entry (tap, ci, co) =
+// W[26 - tap][ci][co], i.e. the forward layout of the transposed conv).
+__global__ void gs_wprep_kernel(const float* __restrict__ w, int cin, int cout, bf16* __restrict__ wf, int coutp,
+                                int cinp, bf16* __restrict__ wd, int dcoutp_k)
+{
+    const int total = 27 * coutp * cinp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int ci = i % cinp, co = (i / cinp) % coutp, tap = i / (cinp * coutp);
+        const float val = (ci < cin && co < cout) ? w[((size_t)tap * cin + ci) * cout + co] : 0.f;
+        wf[i] = __float2bfloat16_rn(val);
+    }
+    if (!wd) return;
+    // dgrad layout: rows n = ci (cin, = 32), k = co (padded to dcoutp_k)
+    const int total2 = 27 * cin * dcoutp_k;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total2; i += gridDim.x * blockDim.x) {
+        const int co = i % dcoutp_k, ci = (i / dcoutp_k) % cin, tap = i / (dcoutp_k * cin);
+        const float val = co < cout ? w[((size_t)(26 - tap) * cin + ci) * cout + co] : 0.f;
+        wd[i] = __float2bfloat16_rn(val);
+    }
+}
+
+// loss = sum (out - tgt)^2 / count;  gd[cell][0..1] = 2 (out - tgt) / count, rest 0
+__global__ void gs_mse_kernel(const float* __restrict__ ou, const float* __restrict__ ov, const float* __restrict__ tu,
+                              const float* __restrict__ tv, long long total, double inv_count, bf16* __restrict__ gd,
+                              double* __restrict__ loss)
+{
+    double local = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const float du = ou[i] - tu[i], dv = ov[i] - tv[i];
+        local += (double)du * du + (double)dv * dv;
+        __align__(16) bf16 c[16];
+        c[0] = __float2bfloat16_rn((float)(2.0 * du * inv_count));
+        c[1] = __float2bfloat16_rn((float)(2.0 * dv * inv_count));
+        for (int j = 2; j < 16; ++j) c[j] = __float2bfloat16_rn(0.f);
+        uint4* dst = reinterpret_cast<uint4*>(gd + i * 16);
+        dst[0] = reinterpret_cast<const uint4*>(c)[0];
+        dst[1] = reinterpret_cast<const uint4*>(c)[1];
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(loss, s * inv_count);
+    }
+}
+
+// db[co] += sum over cells of g[cell][co] (co < cout)
+__global__ void gs_bias_grad_kernel(const bf16* __restrict__ g, long long cells, int gst, int cout, float* __restrict__ db)
+{
+    __shared__ float part[32];
+    if (threadIdx.x < 32) part[threadIdx.x] = 0.f;
+    __syncthreads();
+    const int co = threadIdx.x % 32;
+    float s = 0.f;
+    if (co < cout)
+        for (long long i = blockIdx.x * (long long)(blockDim.x / 32) + threadIdx.x / 32; i < cells;
+             i += (long long)gridDim.x * (blockDim.x / 32))
+            s += __bfloat162float(g[i * gst + co]);
+    atomicAdd(&part[co], s);
+    __syncthreads();
+    if (threadIdx.x < cout) atomicAdd(db + threadIdx.x, part[threadIdx.x]);
+}
+
+// Adam (Kingma & Ba 2015, Algorithm 1) on fp32 master parameters.
+__global__ void gs_adam_kernel(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m,
+                               float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                               float c2)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float g = gr[i];
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// max |a - b| and sum (a - b)^2 over n values
+__global__ void gs_diff_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                               unsigned int* __restrict__ maxbits, double* __restrict__ sumsq)
+{
+    float mx = 0.f;
+    double ss = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float d = fabsf(a[i] - b[i]);
+        if (!(d <= 3.402823466e38f)) d = __int_as_float(0x7f800000);  // NaN or inf counts as +inf
+        mx = fmaxf(mx, d);
+        ss += (double)d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(maxbits, __float_as_uint(mx));  // non-negative floats order like their bits
+        atomicAdd(sumsq, ss);
+    }
+}
+
+}  // namespace gs
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+using namespace gs;
+
+struct gs_surr {
+    float* params = nullptr;  // fp32 master: per layer W [27][cin][cout] then b [cout]
+    float* grads = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    size_t np = 0;
+    size_t woff[kSurrLayers] = {}, boff[kSurrLayers] = {};
+    bf16* wf[kSurrLayers] = {};  // forward layout
+    bf16* wd[kSurrLayers] = {};  // data-gradient layout (layers 1..5)
+    bool wdirty = true;
+    // workspace
+    int N = 0, L = 0;
+    bool train_ws = false;
+    bf16* x0 = nullptr;
+    bf16* h[kSurrLayers] = {};  // h[1..5] (training) / h[1], h[2] ping-pong (inference)
+    bf16* z[kSurrLayers - 1] = {};
+    float* gh = nullptr;
+    bf16* gz[2] = {};
+    bf16* gd = nullptr;
+    float* ou = nullptr;
+    float* ov = nullptr;
+    float* fk = nullptr;
+    double* d_loss = nullptr;
+    unsigned* d_max = nullptr;
+    double* d_ss = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t adam_t = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+int surr_valid_L(int L)
+{
+    if (L < 16 || L % 16 || (L > 128 && L % 128))
+        return fail(GS_EINVAL, "surrogate grid L=%d must be a multiple of 16 (and of 128 above 128)", L);
+    return GS_OK;
+}
+
+void free_ws(gs_surr* s)
+{
+    cudaFree(s->x0);
+    for (auto& p : s->h) { cudaFree(p); p = nullptr; }
+    for (auto& p : s->z) { cudaFree(p); p = nullptr; }
+    cudaFree(s->gh);
+    cudaFree(s->gz[0]);
+    cudaFree(s->gz[1]);
+    cudaFree(s->gd);
+    cudaFree(s->ou);
+    cudaFree(s->ov);
+    cudaFree(s->fk);
+    s->x0 = nullptr; s->gh = nullptr; s->gz[0] = s->gz[1] = nullptr; s->gd = nullptr;
+    s->ou = s->ov = nullptr; s->fk = nullptr;
+    s->N = s->L = 0;
+}
+
+int ensure_ws(gs_surr* s, int N, int L, bool train)
+{
+    if (s->N == N && s->L == L && (s->train_ws || !train)) return GS_OK;
+    free_ws(s);
+    const size_t cells = (size_t)N * L * L * L;
+    cudaError_t e;
+#define ALLOC(p, bytes) if ((e = cudaMalloc(&(p), (bytes))) != cudaSuccess) { free_ws(s); return cuda_fail(e, "surrogate workspace"); }
+    ALLOC(s->x0, cells * 16 * sizeof(bf16));
+    ALLOC(s->fk, (size_t)N * 2 * sizeof(float));
+    const int nh = train ? 5 : 2;
+    for (int l = 1; l <= nh; ++l) ALLOC(s->h[l], cells * 32 * sizeof(bf16));
+    if (train) {
+        for (int l = 0; l < 5; ++l) ALLOC(s->z[l], cells * 32 * sizeof(bf16));
+        ALLOC(s->gh, cells * 32 * sizeof(float));
+        ALLOC(s->gz[0], cells * 32 * sizeof(bf16));
+        ALLOC(s->gz[1], cells * 32 * sizeof(bf16));
+        ALLOC(s->gd, cells * 16 * sizeof(bf16));
+        ALLOC(s->ou, cells * sizeof(float));
+        ALLOC(s->ov, cells * sizeof(float));
+    }
+#undef ALLOC
+    s->N = N;
+    s->L = L;
+    s->train_ws = train;
+    return GS_OK;
+}
+
+template <int CINP, int COUTP, int EPI>
+int conv_launch(gs_surr* s, ConvArgs a)
+{
+    const int SEG = a.L < 128 ? a.L : 128;
+    const size_t smem = (size_t)27 * COUTP * CINP * 2 + (size_t)18 * (SEG + 2) * CINP * 2;
+    auto k = gs_conv_kernel<CINP, COUTP, EPI>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kConvThreads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "convolution tile does not fit on an SM");
+    const long long items = (long long)a.N * a.L * (a.L / kRows) * (a.L / SEG);
+    const int grid = (int)std::min<long long>(items, (long long)per_sm * num_sms());
+    k<<<grid, kConvThreads, smem, s->stream>>>(a);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+    return GS_OK;
+}
+
+template <int CINP, int NP>
+int wgrad_launch(gs_surr* s, WgArgs a)
+{
+    const int SEG = a.L < 128 ? a.L : 128;
+    const size_t smem = (size_t)18 * (SEG + 2) * CINP * 2 + (size_t)kRows * SEG * NP * 2;
+    auto k = gs_wgrad_kernel<CINP, NP>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWgThreads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "weight-gradient tile does not fit on an SM");
+    const long long items = (long long)a.N * a.L * (a.L / kRows) * (a.L / SEG);
+    const int grid = (int)std::min<long long>(items, (long long)per_sm * num_sms());
+    k<<<grid, kWgThreads, smem, s->stream>>>(a);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+    return GS_OK;
+}
+
+int grid1d(long long n, int block) { return (int)std::max<long long>(1, std::min<long long>((n + block - 1) / block, 8LL * num_sms())); }
+
+int prep_weights(gs_surr* s)
+{
+    if (!s->wdirty) return GS_OK;
+    for (int l = 0; l < kSurrLayers; ++l) {
+        const int cin = kChan[l], cout = kChan[l + 1];
+        const int dk = l == 5 ? 16 : 32;
+        gs_wprep_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, s->wf[l], kCoutP[l], kCinP[l],
+                                                  l >= 1 ? s->wd[l] : nullptr, dk);
+        GS_CUDA_TRY(cudaGetLastError());
+        s->launches += 1;
+    }
+    s->wdirty = false;
+    return GS_OK;
+}
+
+int upload_fk(gs_surr* s, int N, const double* F, const double* k)
+{
+    std::vector<float> h((size_t)N * 2);
+    for (int n = 0; n < N; ++n) {
+        h[2 * n] = (float)F[n];
+        h[2 * n + 1] = (float)k[n];
+    }
+    GS_CUDA_TRY(cudaMemcpyAsync(s->fk, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    return GS_OK;
+}
+
+// forward pass; train: keep h1..h5 and z0..z4, write (ou, ov); else ping-pong
+int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo, float* vo, bool train)
+{
+    int rc = prep_weights(s);
+    if (rc) return rc;
+    const long long cells = (long long)N * L * L * L;
+    gs_pack_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(u, v, s->fk, s->x0, (long long)L * L * L, N);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+    ConvArgs a{};
+    a.N = N;
+    a.L = L;
+    // layer 0
+    a.in = s->x0;
+    a.w = s->wf[0];
+    a.bias = s->params + s->boff[0];
+    a.out = s->h[1];
+    a.zout = train ? s->z[0] : nullptr;
+    if ((rc = conv_launch<16, 32, EPI_FIRST>(s, a))) return rc;
+    // layers 1..4
+    for (int l = 1; l <= 4; ++l) {
+        bf16* hin = train ? s->h[l] : s->h[1 + ((l - 1) & 1)];
+        bf16* hout = train ? s->h[l + 1] : s->h[1 + (l & 1)];
+        a.in = hin;
+        a.res = hin;
+        a.w = s->wf[l];
+        a.bias = s->params + s->boff[l];
+        a.out = hout;
+        a.zout = train ? s->z[l] : nullptr;
+        if ((rc = conv_launch<32, 32, EPI_HIDDEN>(s, a))) return rc;
+    }
+    // layer 5: state update
+    ConvArgs b{};
+    b.N = N;
+    b.L = L;
+    b.in = train ? s->h[5] : s->h[1];
+    b.w = s->wf[5];
+    b.bias = s->params + s->boff[5];
+    b.su = u;
+    b.sv = v;
+    b.ou = uo;
+    b.ov = vo;
+    return conv_launch<32, 8, EPI_LAST>(s, b);
+}
+
+// gradients of the MSE loss into s->grads (zeroed first); loss into *loss
+int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double* loss)
+{
+    const long long cells = (long long)N * L * L * L;
+    GS_CUDA_TRY(cudaMemsetAsync(s->grads, 0, s->np * sizeof(float), s->stream));
+    GS_CUDA_TRY(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
+    gs_mse_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(s->ou, s->ov, tu, tv, cells, 1.0 / (2.0 * cells), s->gd,
+                                                            s->d_loss);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+    int rc;
+    auto bias_grad = [&](const bf16* g, int gst, int cout, float* db) -> int {
+        gs_bias_grad_kernel<<<grid1d(cells, 32), 256, 0, s->stream>>>(g, cells, gst, cout, db);
+        GS_CUDA_TRY(cudaGetLastError());
+        s->launches += 1;
+        return GS_OK;
+    };
+    // layer 5
+    WgArgs w{};
+    w.N = N;
+    w.L = L;
+    w.in = s->h[5];
+    w.g = s->gd;
+    w.GST = 16;
+    w.cin = 32;
+    w.cout = 2;
+    w.dw = s->grads + s->woff[5];
+    if ((rc = wgrad_launch<32, 8>(s, w))) return rc;
+    if ((rc = bias_grad(s->gd, 16, 2, s->grads + s->boff[5]))) return rc;
+    ConvArgs d{};
+    d.N = N;
+    d.L = L;
+    d.in = s->gd;
+    d.w = s->wd[5];
+    d.gh = s->gh;
+    d.gh_acc = 0;
+    d.zprev = s->z[4];
+    d.gz = s->gz[0];
+    if ((rc = conv_launch<16, 32, EPI_DGRAD>(s, d))) return rc;
+    int cur = 0;
+    for (int l = 4; l >= 1; --l) {
+        w.in = s->h[l];
+        w.g = s->gz[cur];
+        w.GST = 32;
+        w.cin = 32;
+        w.cout = 32;
+        w.dw = s->grads + s->woff[l];
+        if ((rc = wgrad_launch<32, 32>(s, w))) return rc;
+        if ((rc = bias_grad(s->gz[cur], 32, 32, s->grads + s->boff[l]))) return rc;
+        d.in = s->gz[cur];
+        d.w = s->wd[l];
+        d.gh_acc = 1;
+        d.zprev = s->z[l - 1];
+        d.gz = s->gz[cur ^ 1];
+        if ((rc = conv_launch<32, 32, EPI_DGRAD>(s, d))) return rc;
+        cur ^= 1;
+    }
+    // layer 0
+    w.in = s->x0;
+    w.g = s->gz[cur];
+    w.GST = 32;
+    w.cin = 4;
+    w.cout = 32;
+    w.dw = s->grads + s->woff[0];
+    if ((rc = wgrad_launch<16, 32>(s, w))) return rc;
+    if ((rc = bias_grad(s->gz[cur], 32, 32, s->grads + s->boff[0]))) return rc;
+    if (loss) {
+        GS_CUDA_TRY(cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    }
+    return GS_OK;
+}
+
+int diff(gs_surr* s, const float* a, const float* b, long long n, double* maxabs, double* rms)
+{
+    GS_CUDA_TRY(cudaMemsetAsync(s->d_max, 0, sizeof(unsigned), s->stream));
+    GS_CUDA_TRY(cudaMemsetAsync(s->d_ss, 0, sizeof(double), s->stream));
+    gs_diff_kernel<<<grid1d(n, 256), 256, 0, s->stream>>>(a, b, n, s->d_max, s->d_ss);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+    unsigned mb = 0;
+    double ss = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&mb, s->d_max, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+    GS_CUDA_TRY(cudaMemcpyAsync(&ss, s->d_ss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    float mx;
+    memcpy(&mx, &mb, sizeof(float));
+    if (maxabs) *maxabs = mx;
+    if (rms) *rms = sqrt(ss / (double)n);
+    return GS_OK;
+}
+
+int check_fields(int N, int L, const void* u, const void* v)
+{
+    if (N < 1) return fail(GS_EINVAL, "N=%d must be >= 1", N);
+    int rc = surr_valid_L(L);
+    if (rc) return rc;
+    if (!u || !v) return fail(GS_EINVAL, "field pointers must not be NULL");
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gs_surr_param_count(size_t* count)
+{
+    if (!count) return fail(GS_EINVAL, "count is NULL");
+    size_t n = 0;
+    for (int l = 0; l < kSurrLayers; ++l) n += (size_t)27 * kChan[l] * kChan[l + 1] + kChan[l + 1];
+    *count = n;
+    return GS_OK;
+}
+
+int gs_surr_destroy(gs_surr* s)
+{
+    if (!s) return GS_OK;
+    free_ws(s);
+    cudaFree(s->params);
+    cudaFree(s->grads);
+    cudaFree(s->m);
+    cudaFree(s->v);
+    for (int l = 0; l < kSurrLayers; ++l) {
+        cudaFree(s->wf[l]);
+        cudaFree(s->wd[l]);
+    }
+    cudaFree(s->d_loss);
+    cudaFree(s->d_max);
+    cudaFree(s->d_ss);
+    delete s;
+    return GS_OK;
+}
+
+int gs_surr_create(gs_surr** out)
+{
+    if (!out) return fail(GS_EINVAL, "out is NULL");
+    *out = nullptr;
+    gs_surr* s = new (std::nothrow) gs_surr();
+    if (!s) return fail(GS_ENOMEM, "host allocation failed");
+    size_t off = 0;
+    for (int l = 0; l < kSurrLayers; ++l) {
+        s->woff[l] = off;
+        off += (size_t)27 * kChan[l] * kChan[l + 1];
+        s->boff[l] = off;
+        off += kChan[l + 1];
+    }
+    s->np = off;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&s->params, off * 4)) != cudaSuccess || (e = cudaMalloc(&s->grads, off * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&s->m, off * 4)) != cudaSuccess || (e = cudaMalloc(&s->v, off * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_loss, sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_max, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_ss, sizeof(double))) != cudaSuccess) {
+        int rc = cuda_fail(e, "surrogate allocation");
+        gs_surr_destroy(s);
+        return rc;
+    }
+    for (int l = 0; l < kSurrLayers && e == cudaSuccess; ++l) {
+        e = cudaMalloc(&s->wf[l], (size_t)27 * kCoutP[l] * kCinP[l] * sizeof(bf16));
+        if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wd[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
+    }
+    if (e != cudaSuccess || (e = cudaMemset(s->params, 0, off * 4)) != cudaSuccess ||
+        (e = cudaMemset(s->m, 0, off * 4)) != cudaSuccess || (e = cudaMemset(s->v, 0, off * 4)) != cudaSuccess) {
+        int rc = cuda_fail(e, "surrogate allocation");
+        gs_surr_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return GS_OK;
+}
+
+int gs_surr_set_stream(gs_surr* s, void* stream)
+{
+    if (!s) return fail(GS_EINVAL, "surrogate is NULL");
+    s->stream = (cudaStream_t)stream;
+    return GS_OK;
+}
+
+int gs_surr_set_params(gs_surr* s, const float* host, size_t count)
+{
+    if (!s || !host) return fail(GS_EINVAL, "NULL argument");
+    if (count != s->np) return fail(GS_EINVAL, "count=%zu, the network has %zu parameters", count, s->np);
+    GS_CUDA_TRY(cudaMemcpyAsync(s->params, host, count * 4, cudaMemcpyHostToDevice, s->stream));
+    GS_CUDA_TRY(cudaMemsetAsync(s->m, 0, count * 4, s->stream));
+    GS_CUDA_TRY(cudaMemsetAsync(s->v, 0, count * 4, s->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->adam_t = 0;
+    s->wdirty = true;
+    return GS_OK;
+}
+
+int gs_surr_get_params(gs_surr* s, float* host, size_t count)
+{
+    if (!s || !host) return fail(GS_EINVAL, "NULL argument");
+    if (count != s->np) return fail(GS_EINVAL, "count=%zu, the network has %zu parameters", count, s->np);
+    GS_CUDA_TRY(cudaMemcpyAsync(host, s->params, count * 4, cudaMemcpyDeviceToHost, s->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return GS_OK;
+}
+
+int gs_surr_get_grads(gs_surr* s, float* host, size_t count)
+{
+    if (!s || !host) return fail(GS_EINVAL, "NULL argument");
+    if (count != s->np) return fail(GS_EINVAL, "count=%zu, the network has %zu parameters", count, s->np);
+    GS_CUDA_TRY(cudaMemcpyAsync(host, s->grads, count * 4, cudaMemcpyDeviceToHost, s->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return GS_OK;
+}
+
+int gs_surr_forward(gs_surr* s, int N, int L, const float* u, const float* v, const double* F, const double* k,
+                    float* u_out, float* v_out)
+{
+    if (!s || !F || !k || !u_out || !v_out) return fail(GS_EINVAL, "NULL argument");
+    int rc = check_fields(N, L, u, v);
+    if (rc) return rc;
+    if ((rc = ensure_ws(s, N, L, false))) return rc;
+    if ((rc = upload_fk(s, N, F, k))) return rc;
+    return forward(s, N, L, u, v, u_out, v_out, false);
+}
+
+int gs_surr_grad(gs_surr* s, int N, int L, const float* u, const float* v, const double* F, const double* k,
+                 const float* u_tgt, const float* v_tgt, double* loss)
+{
+    if (!s || !F || !k || !u_tgt || !v_tgt) return fail(GS_EINVAL, "NULL argument");
+    int rc = check_fields(N, L, u, v);
+    if (rc) return rc;
+    if ((rc = ensure_ws(s, N, L, true))) return rc;
+    if ((rc = upload_fk(s, N, F, k))) return rc;
+    if ((rc = forward(s, N, L, u, v, s->ou, s->ov, true))) return rc;
+    return backward(s, N, L, u_tgt, v_tgt, loss);
+}
+
+int gs_surr_adam(gs_surr* s, double lr, double beta1, double beta2, double eps)
+{
+    if (!s) return fail(GS_EINVAL, "surrogate is NULL");
+    if (!(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+        return fail(GS_EINVAL, "bad Adam hyper-parameters");
+    s->adam_t += 1;
+    const float c1 = (float)(1.0 - pow(beta1, (double)s->adam_t));
+    const float c2 = (float)(1.0 - pow(beta2, (double)s->adam_t));
+    gs_adam_kernel<<<grid1d((long long)s->np, 256), 256, 0, s->stream>>>(s->params, s->grads, s->m, s->v,
+                                                                         (long long)s->np, (float)lr, (float)beta1,
+                                                                         (float)beta2, (float)eps, c1, c2);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+    s->wdirty = true;
+    return GS_OK;
+}
+
+int gs_surr_train_step(gs_surr* s, int N, int L, const float* u, const float* v, const double* F, const double* k,
+                       const float* u_tgt, const float* v_tgt, double lr, double* loss)
+{
+    int rc = gs_surr_grad(s, N, L, u, v, F, k, u_tgt, v_tgt, loss);
+    if (rc) return rc;
+    return gs_surr_adam(s, lr, 0.9, 0.999, 1e-8);
+}
+
+int gs_surr_diff(gs_surr* s, const float* a, const float* b, int64_t n, double* maxabs, double* rms)
+{
+    if (!s || !a || !b || n < 1) return fail(GS_EINVAL, "bad argument");
+    return diff(s, a, b, n, maxabs, rms);
+}
+
+int gs_surr_run(gs_surr* s, gs_sim* sim, double F, double k, int64_t nsteps, int check_every, double tol,
+                gs_surr_report* rep)
+{
+    if (!s || !sim) return fail(GS_EINVAL, "NULL argument");
+    if (nsteps < 0 || check_every < 16 || check_every % 16) return fail(GS_EINVAL, "check_every must be a positive multiple of 16");
+    if (!(tol > 0)) return fail(GS_EINVAL, "tol must be > 0");
+    int kernel = 0;
+    int rc = gs_get_plan(sim, &kernel, nullptr, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    int L = 0, dtype = 0;
+    if ((rc = gs_sim_shape(sim, &L, &dtype))) return rc;
+    if (dtype != GS_F32) return fail(GS_EINVAL, "the surrogate runs on FP32 simulations");
+    if ((rc = surr_valid_L(L))) return rc;
+    // run the network on the simulation's stream so both stay ordered
+    void* sim_stream = nullptr;
+    if ((rc = gs_get_stream(sim, &sim_stream))) return rc;
+    cudaStream_t saved_stream = s->stream;
+    s->stream = (cudaStream_t)sim_stream;
+    if ((rc = ensure_ws(s, 1, L, false)) || (rc = upload_fk(s, 1, &F, &k))) {
+        s->stream = saved_stream;
+        return rc;
+    }
+    const size_t cells = (size_t)L * L * L;
+    float* tu = nullptr;
+    float* tv = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&tu, cells * 4)) != cudaSuccess || (e = cudaMalloc(&tv, cells * 4)) != cudaSuccess) {
+        cudaFree(tu);
+        s->stream = saved_stream;
+        return cuda_fail(e, "surrogate run buffers");
+    }
+    gs_surr_report r{};
+    bool fallback = false;
+    int64_t done = 0;
+    while (done < nsteps && !rc) {
+        const int64_t seg = std::min<int64_t>(check_every, nsteps - done);
+        if (fallback || seg < 16) {
+            rc = gs_step(sim, seg);
+            r.stencil_steps += seg;
+            done += seg;
+            fallback = false;  // try the surrogate again on the next segment
+            continue;
+        }
+        // surrogate for all but the last 16 steps of the segment
+        const int64_t napp = seg / 16 - 1;
+        for (int64_t a = 0; a < napp && !rc; ++a) {
+            void* cu;
+            void* cv;
+            gs_device_ptr(sim, GS_U, &cu);
+            gs_device_ptr(sim, GS_V, &cv);
+            rc = forward(s, 1, L, (const float*)cu, (const float*)cv, tu, tv, false);
+            if (!rc) {
+                cudaMemcpyAsync(cu, tu, cells * 4, cudaMemcpyDeviceToDevice, s->stream);
+                cudaMemcpyAsync(cv, tv, cells * 4, cudaMemcpyDeviceToDevice, s->stream);
+                int64_t t;
+                gs_get_step(sim, &t);
+                gs_set_step(sim, t + 16);
+                r.surrogate_applications += 1;
+                r.surrogate_steps += 16;
+            }
+        }
+        if (rc) break;
+        // check: one application against 16 stencil steps from the same state; keep the stencil's
+        void* cu;
+        void* cv;
+        gs_device_ptr(sim, GS_U, &cu);
+        gs_device_ptr(sim, GS_V, &cv);
+        if ((rc = forward(s, 1, L, (const float*)cu, (const float*)cv, tu, tv, false))) break;
+        if ((rc = gs_step(sim, 16))) break;
+        r.stencil_steps += 16;
+        gs_device_ptr(sim, GS_U, &cu);
+        gs_device_ptr(sim, GS_V, &cv);
+        double mu = 0, ru = 0, mv = 0, rv = 0;
+        if ((rc = diff(s, tu, (const float*)cu, (long long)cells, &mu, &ru))) break;
+        if ((rc = diff(s, tv, (const float*)cv, (long long)cells, &mv, &rv))) break;
+        const double err = (std::isnan(mu) || std::isnan(mv)) ? INFINITY : std::max(mu, mv);
+        r.checks += 1;
+        r.max_check_error = std::max(r.max_check_error, err);
+        r.last_check_error = err;
+        if (err > tol) {
+            r.fallbacks += 1;
+            fallback = true;
+        }
+        done += seg;
+    }
+    cudaStreamSynchronize(s->stream);
+    cudaFree(tu);
+    cudaFree(tv);
+    s->stream = saved_stream;
+    if (rep) *rep = r;
+    return rc;
+}
+
+int gs_surr_launch_count(gs_surr* s, int64_t* count)
+{
+    if (!s || !count) return fail(GS_EINVAL, "NULL argument");
+    *count = s->launches;
+    return GS_OK;
+}
+
+}  // extern "C"

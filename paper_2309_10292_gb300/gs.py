@@ -80,6 +80,22 @@ _SIGS = {
     "gs_batch_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                       ctypes.POINTER(_i64)],
     "gs_batch_destroy": [_vp],
+    "gs_get_stream": [_vp, _pp],
+    "gs_sim_shape": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)],
+    "gs_surr_param_count": [ctypes.POINTER(_sz)],
+    "gs_surr_create": [_pp],
+    "gs_surr_set_stream": [_vp, _vp],
+    "gs_surr_set_params": [_vp, _vp, _sz],
+    "gs_surr_get_params": [_vp, _vp, _sz],
+    "gs_surr_get_grads": [_vp, _vp, _sz],
+    "gs_surr_forward": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+    "gs_surr_grad": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)],
+    "gs_surr_adam": [_vp, _d, _d, _d, _d],
+    "gs_surr_train_step": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(_d)],
+    "gs_surr_diff": [_vp, _vp, _vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d)],
+    "gs_surr_run": [_vp, _vp, _d, _d, _i64, _i, _d, _vp],
+    "gs_surr_launch_count": [_vp, ctypes.POINTER(_i64)],
+    "gs_surr_destroy": [_vp],
     "gs_batch_step_noalloc": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _vp, _i64, _i, _i64, _vp],
 }
 _RESTYPES = {"gs_last_error": ctypes.c_char_p}
@@ -357,6 +373,183 @@ def noalloc_arena_offsets(L, dtype) -> tuple[list, int]:
             off += (cells + align - 1) // align * align
         out.append(o)
     return out, off
+
+
+def gs_get_stream(sim) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().gs_get_stream(sim, ctypes.byref(p)), "gs_get_stream")
+    return p.value or 0
+
+
+def gs_sim_shape(sim):
+    L, dt = _i(), _i()
+    _check(lib().gs_sim_shape(sim, ctypes.byref(L), ctypes.byref(dt)), "gs_sim_shape")
+    return L.value, dt.value
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate
+# ---------------------------------------------------------------------------
+class GsSurrReport(ctypes.Structure):
+    _fields_ = [("surrogate_applications", ctypes.c_int64), ("surrogate_steps", ctypes.c_int64),
+                ("stencil_steps", ctypes.c_int64), ("checks", ctypes.c_int64), ("fallbacks", ctypes.c_int64),
+                ("max_check_error", ctypes.c_double), ("last_check_error", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _f64_array(x):
+    x = [float(v) for v in x]
+    return (ctypes.c_double * len(x))(*x)
+
+
+def gs_surr_param_count() -> int:
+    n = _sz()
+    _check(lib().gs_surr_param_count(ctypes.byref(n)), "gs_surr_param_count")
+    return n.value
+
+
+def gs_surr_create():
+    out = ctypes.c_void_p()
+    _check(lib().gs_surr_create(ctypes.byref(out)), "gs_surr_create")
+    return out.value
+
+
+def gs_surr_set_stream(s, stream):
+    _check(lib().gs_surr_set_stream(s, _stream(stream)), "gs_surr_set_stream")
+
+
+def gs_surr_set_params(s, flat: np.ndarray):
+    flat = np.ascontiguousarray(flat, dtype=np.float32)
+    _check(lib().gs_surr_set_params(s, flat.ctypes.data, flat.size), "gs_surr_set_params")
+
+
+def gs_surr_get_params(s) -> np.ndarray:
+    out = np.empty(gs_surr_param_count(), dtype=np.float32)
+    _check(lib().gs_surr_get_params(s, out.ctypes.data, out.size), "gs_surr_get_params")
+    return out
+
+
+def gs_surr_get_grads(s) -> np.ndarray:
+    out = np.empty(gs_surr_param_count(), dtype=np.float32)
+    _check(lib().gs_surr_get_grads(s, out.ctypes.data, out.size), "gs_surr_get_grads")
+    return out
+
+
+def gs_surr_forward(s, N, L, u, v, F, k, u_out, v_out):
+    _check(lib().gs_surr_forward(s, N, L, _ptr(u), _ptr(v), _f64_array(F), _f64_array(k), _ptr(u_out),
+                                 _ptr(v_out)), "gs_surr_forward")
+
+
+def gs_surr_grad(s, N, L, u, v, F, k, u_tgt, v_tgt) -> float:
+    loss = _d()
+    _check(lib().gs_surr_grad(s, N, L, _ptr(u), _ptr(v), _f64_array(F), _f64_array(k), _ptr(u_tgt),
+                              _ptr(v_tgt), ctypes.byref(loss)), "gs_surr_grad")
+    return loss.value
+
+
+def gs_surr_adam(s, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(lib().gs_surr_adam(s, lr, beta1, beta2, eps), "gs_surr_adam")
+
+
+def gs_surr_train_step(s, N, L, u, v, F, k, u_tgt, v_tgt, lr) -> float:
+    loss = _d()
+    _check(lib().gs_surr_train_step(s, N, L, _ptr(u), _ptr(v), _f64_array(F), _f64_array(k), _ptr(u_tgt),
+                                    _ptr(v_tgt), lr, ctypes.byref(loss)), "gs_surr_train_step")
+    return loss.value
+
+
+def gs_surr_diff(s, a, b, n):
+    mx, rms = _d(), _d()
+    _check(lib().gs_surr_diff(s, _ptr(a), _ptr(b), int(n), ctypes.byref(mx), ctypes.byref(rms)), "gs_surr_diff")
+    return mx.value, rms.value
+
+
+def gs_surr_run(s, sim, F, k, nsteps, check_every=64, tol=0.05) -> dict:
+    rep = GsSurrReport()
+    _check(lib().gs_surr_run(s, sim, F, k, int(nsteps), int(check_every), tol, ctypes.byref(rep)), "gs_surr_run")
+    return rep.as_dict()
+
+
+def gs_surr_launch_count(s) -> int:
+    c = _i64()
+    _check(lib().gs_surr_launch_count(s, ctypes.byref(c)), "gs_surr_launch_count")
+    return c.value
+
+
+def gs_surr_destroy(s):
+    _check(lib().gs_surr_destroy(s), "gs_surr_destroy")
+
+
+SURR_CHANNELS = (4, 32, 32, 32, 32, 32, 2)
+
+
+def surr_flatten(params) -> np.ndarray:
+    """[(w [27, cin, cout], b [cout]), ...] -> the flat FP32 layout of gs_surr_set_params."""
+    return np.concatenate([np.concatenate([np.asarray(w, dtype=np.float32).ravel(),
+                                           np.asarray(b, dtype=np.float32).ravel()]) for w, b in params])
+
+
+def surr_unflatten(flat) -> list:
+    out, o = [], 0
+    for l in range(6):
+        cin, cout = SURR_CHANNELS[l], SURR_CHANNELS[l + 1]
+        nw = 27 * cin * cout
+        out.append((np.asarray(flat[o:o + nw], dtype=np.float64).reshape(27, cin, cout),
+                    np.asarray(flat[o + nw:o + nw + cout], dtype=np.float64)))
+        o += nw + cout
+    return out
+
+
+class Surrogate:
+    """The 16-step surrogate network with its FP32 master parameters on the GPU."""
+
+    def __init__(self, params=None, stream=None):
+        import torch
+        self.handle = gs_surr_create()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        gs_surr_set_stream(self.handle, self.stream)
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        flat = params if isinstance(params, np.ndarray) else surr_flatten(params)
+        gs_surr_set_params(self.handle, flat)
+
+    def params(self):
+        return surr_unflatten(gs_surr_get_params(self.handle))
+
+    def grads(self):
+        return surr_unflatten(gs_surr_get_grads(self.handle))
+
+    def forward(self, u, v, F, k):
+        """u, v: torch float32 CUDA tensors [N, L, L, L]; returns predicted (u, v) after 16 steps."""
+        import torch
+        N, L = u.shape[0], u.shape[1]
+        uo, vo = torch.empty_like(u), torch.empty_like(v)
+        gs_surr_forward(self.handle, N, L, u, v, F, k, uo, vo)
+        return uo, vo
+
+    def grad(self, u, v, F, k, ut, vt) -> float:
+        return gs_surr_grad(self.handle, u.shape[0], u.shape[1], u, v, F, k, ut, vt)
+
+    def train_step(self, u, v, F, k, ut, vt, lr) -> float:
+        return gs_surr_train_step(self.handle, u.shape[0], u.shape[1], u, v, F, k, ut, vt, lr)
+
+    def run(self, sim, F, k, nsteps, check_every=64, tol=0.05) -> dict:
+        return gs_surr_run(self.handle, sim.handle, F, k, nsteps, check_every, tol)
+
+    def close(self):
+        if self.handle:
+            gs_surr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class GrayScottBatch:

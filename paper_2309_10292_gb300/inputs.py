@@ -38,11 +38,11 @@ def batch_instances(n: int = 256, seed: int = 0, sizes=BATCH_SIZES):
 
 
 def surrogate_init_params(seed: int = 0, channels=(4, 32, 32, 32, 32, 32, 2),
-                          last_scale: float = 0.1):
+                          last_scale: float = 0.0):
     """He-uniform weights [27, Cin, Cout] and zero biases for each layer.
 
-    The last layer is scaled down so an untrained network starts close to the
-    identity map of the residual output.
+    The last layer is scaled by last_scale: 0 (the default) makes an untrained
+    network exactly the identity map of its residual output ("no change").
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     params = []
