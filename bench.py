@@ -259,6 +259,81 @@ def bench_large(args, stream, hbm_peak):
             "tuned_candidates": len(trials)}
 
 
+def bench_surrogate(args, stream):
+    """Surrogate: train on L=128 stencil trajectories, then advance an L=256 FP32
+    grid (noise 0) by N steps with the checked surrogate run and compare its
+    time-to-state and error with the plain FP32 stencil and the FP64 stencil."""
+    import numpy as np
+    import torch
+
+    from paper_2309_10292_gb300 import gs, inputs, surrogate
+    p = dict(PARAMS)
+    F, k = p.pop("F"), p.pop("k")
+    # training
+    pool = surrogate.TrajectoryPool(L=128, n=8, seed=11, warm=(200, 1500))
+    net = gs.Surrogate(inputs.surrogate_init_params(seed=0))
+    losses, t_train = surrogate.train(net, pool, iters=args.surr_iters, lr=1e-3, batch=1, warmup=50)
+    ev = surrogate.evaluate(net, pool, pairs=4)
+    pool.close()
+    L, n, warm = 256, args.surr_steps, 300
+    # forward throughput at L=256
+    x = torch.rand((1, L, L, L), device="cuda")
+    y = torch.rand((1, L, L, L), device="cuda") * 0.3
+    net.forward(x, y, [F], [k])
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        net.forward(x, y, [F], [k])
+    b.record(stream)
+    torch.cuda.synchronize()
+    fwd_s = a.elapsed_time(b) / 3e3
+    flop = 2 * 27 * (4 * 32 + 4 * 32 * 32 + 32 * 2) * L ** 3
+    del x, y
+    # time-to-state: plain FP32 stencil (autotuned plan), surrogate run, FP64 stencil
+    def fresh(dtype):
+        sim = gs.GrayScott(L, F=F, k=k, noise=0.0, seed=0, dtype=dtype, **p)
+        sim.step(warm)
+        return sim
+    plain = fresh("f32")
+    plain.autotune(steps_per_trial=12)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain.step(n)
+    plain.sync()
+    t_plain = time.perf_counter() - t0
+    up, vp = plain.read()
+    plain.close()
+    s32 = fresh("f32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = net.run(s32, F, k, n, check_every=64, tol=args.surr_tol)
+    t_surr = time.perf_counter() - t0
+    us, vs = s32.read()
+    s32.close()
+    s64 = fresh("f64")
+    s64.step(n)
+    u64, v64 = s64.read()
+    s64.close()
+    net.close()
+    err = lambda a, b: float(max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()))
+    return {"workload": f"surrogate trained on {args.surr_iters} pairs of L=128 stencil trajectories "
+                        f"(F, k as the batched workload, noise 0); run on L={L} FP32 from step {warm}, "
+                        f"{n} steps, check every 64 steps against 16 stencil steps, tol {args.surr_tol}",
+            "train_time_s": t_train, "train_loss_first": float(np.mean(losses[:10])),
+            "train_loss_last": float(np.mean(losses[-10:])),
+            "heldout_rms_network": ev["rms_network"], "heldout_rms_no_change": ev["rms_persistence"],
+            "forward_ms_L256": fwd_s * 1e3,
+            "forward_tflops": flop / fwd_s / 1e12,
+            "time_to_state_s": {"surrogate_run": t_surr, "plain_fp32": t_plain},
+            "speedup_vs_plain": t_plain / t_surr,
+            "report": rep,
+            "max_abs_error_vs_fp32_stencil": err((us, vs), (up, vp)),
+            "max_abs_error_vs_fp64_stencil": err((us, vs), (u64, v64)),
+            "fp32_stencil_vs_fp64_stencil": err((up, vp), (u64, v64))}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -281,7 +356,17 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sim = gs.GrayScott(L, dtype="f32", noise=NOISE, seed=SEED, **PARAMS)
-    tune_best, tune_trials = sim.autotune(steps_per_trial=24)
+    if args.plan:
+        # explicit plan (profiling runs): kernel name, tile_x, tile_y, tile_z, depth/stages
+        kind, *nums = args.plan.split(",")
+        kern = {"naive": gs.GS_KERNEL_NAIVE, "zmarch": gs.GS_KERNEL_ZMARCH, "tblock": gs.GS_KERNEL_TBLOCK}[kind]
+        tx, ty, tz, last = (int(x) for x in nums)
+        gs.gs_set_plan_full(sim.handle, dict(kernel=kern, tile_x=tx, tile_y=ty, tile_z=tz,
+                                             depth=last if kern == gs.GS_KERNEL_TBLOCK else 1,
+                                             stages=last if kern == gs.GS_KERNEL_ZMARCH else 0))
+        tune_best, tune_trials = {"us_per_step": None}, []
+    else:
+        tune_best, tune_trials = sim.autotune(steps_per_trial=24)
     plan = sim.plan
     # warm-up (untimed)
     for _ in range(args.warmup):
@@ -374,6 +459,8 @@ def run_ours(args):
         extra["batched"] = bench_batched(args, stream, hbm_peak)
     if rank == 0 and not args.no_large:
         extra["l1024"] = bench_large(args, stream, hbm_peak)
+    if rank == 0 and not args.no_surrogate:
+        extra["surrogate"] = bench_surrogate(args, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -427,6 +514,11 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--no-large", action="store_true", help="skip the L=1024 measurement")
     ap.add_argument("--large-steps", type=int, default=500)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
+    ap.add_argument("--plan", default="", help="fixed plan instead of autotuning, e.g. zmarch,128,8,64,6")
+    ap.add_argument("--surr-iters", type=int, default=2000)
+    ap.add_argument("--surr-steps", type=int, default=1024)
+    ap.add_argument("--surr-tol", type=float, default=0.05)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

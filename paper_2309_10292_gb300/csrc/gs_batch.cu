@@ -196,6 +196,10 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                     if (!wait_or_abort(&full[sn], (seq / S) & 1, a.timeout_ns, &s_abort)) { failed = true; break; }
                     gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sn * stage_elems + moff), nu);
                     gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sn * stage_elems + a.field_elems + moff), nv);
+                    const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
+                    const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
+                    const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
+                    const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
                     if (active) {
                         const T* bu = ring + sc * stage_elems;
                         const T* bv = bu + a.field_elems;
@@ -206,9 +210,17 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                         gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
                         gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
                         gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
-                        const int oxl = xv > 0 ? moff - 1 : rowbase + L - 1;
-                        const int oxr = xv < nxv - 1 ? moff + V : rowbase;
-                        const T xlu = bu[oxl], xru = bu[oxr], xlv = bv[oxl], xrv = bv[oxr];
+                        T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
+                        if (xv == 0 || lane == 0) {
+                            const int oxl = xv > 0 ? moff - 1 : rowbase + L - 1;  // periodic in x
+                            xlu = bu[oxl];
+                            xlv = bv[oxl];
+                        }
+                        if (xv == nxv - 1 || lane == 31) {
+                            const int oxr = xv < nxv - 1 ? moff + V : rowbase;
+                            xru = bu[oxr];
+                            xrv = bv[oxr];
+                        }
                         const long long g = (long long)(z0 + zi) * LL + (long long)(y0 + row) * L + xv * V;
                         const uint32_t pre = NOISE ? gs_group_pre((uint32_t)g, keys) : 0u;
                         gs_update_group<T, NOISE>(c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,

@@ -334,6 +334,13 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                 gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.main_off + moff), nu);
                 gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + a.lay.main_off + moff), nv);
             }
+            // x neighbours of the group's end cells: from the adjacent lanes when
+            // they hold the same row's neighbouring groups (conflict-free), else
+            // from shared memory (halo columns, or a group in another warp)
+            const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
+            const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
+            const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
+            const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
             if (active) {
                 const int z = z0 + zi;
                 T outu[V], outv[V];
@@ -347,10 +354,18 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
-                // x neighbours of the vector's two ends
-                const int oxl = xv > 0 ? a.lay.main_off + moff - 1 : a.lay.left_off + row * V + (V - 1);
-                const int oxr = xv * V + V < nvx ? a.lay.main_off + moff + V : a.lay.right_off + row * V;
-                const T xlu = bu[oxl], xru = bu[oxr], xlv = bv[oxl], xrv = bv[oxr];
+                const bool has_r = xv * V + V < nvx;
+                T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
+                if (xv == 0 || lane == 0) {
+                    const int oxl = xv > 0 ? a.lay.main_off + moff - 1 : a.lay.left_off + row * V + (V - 1);
+                    xlu = bu[oxl];
+                    xlv = bv[oxl];
+                }
+                if (!has_r || lane == 31) {
+                    const int oxr = has_r ? a.lay.main_off + moff + V : a.lay.right_off + row * V;
+                    xru = bu[oxr];
+                    xrv = bv[oxr];
+                }
                 const int64_t gidx = (int64_t)z * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
                 const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
                 gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
