@@ -331,6 +331,14 @@ int gs_surr_diff(gs_surr* s, const float* a, const float* b, int64_t n, double* 
  * are allocated for the duration. */
 int gs_surr_run(gs_surr* s, gs_sim* sim, double F, double k, int64_t nsteps, int check_every,
                 double tol, gs_surr_report* report);
+/* Convolution path: 0 = automatic (5th-generation tensor cores, tcgen05 with
+ * TMEM accumulators, when L % 128 == 0; else mma.sync), 1 = mma.sync only,
+ * 2 = tcgen05 only (GS_EINVAL for other L).  Both give the same values up to
+ * FP32 accumulation order. */
+int gs_surr_set_backend(gs_surr* s, int backend);
+/* Wait for the surrogate's stream; GS_ETIMEOUT if a bounded device wait of a
+ * tcgen05 convolution expired. */
+int gs_surr_sync(gs_surr* s);
 int gs_surr_launch_count(gs_surr* s, int64_t* count);
 int gs_surr_destroy(gs_surr* s);
 

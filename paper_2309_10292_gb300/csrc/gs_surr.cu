@@ -500,6 +500,356 @@ __global__ void gs_diff_kernel(const float* __restrict__ a, const float* __restr
 
 }  // namespace gs
 
+namespace gs {
+
+// ===========================================================================
+// 5th-generation tensor-core forward convolution (tcgen05, TMEM accumulators)
+// ===========================================================================
+//
+// One 4-warp CTA per SM.  A work unit is a column of 4 output rows (y0..y0+3)
+// by 128 cells (x0..x0+127) of one grid, marched over a z-chunk.  The input
+// planes z-1, z, z+1 (each: 6 rows y0-1..y0+4 by 130 cells x0-1..x0+128,
+// periodic) sit in a 3-slab shared ring in the canonical K-major layout
+// without swizzle: slab[chunk j][row][cell][8 channels], one 16-byte core
+// matrix row per cell and chunk.  The A operand of tap (dz, dy, dx) for
+// output row r is then 128 consecutive cells starting at (row r+1+dy, cell
+// 1+dx) of the dz slab: a descriptor offset, no data movement (LBO = one
+// chunk plane, SBO = 8 cells).  Weights (B, K-major [tap][chunk][n][8]) stay
+// in shared memory.  Thread 0 issues tcgen05.mma (M=128, N=32/16, K=16) into
+// 4 TMEM accumulators (one per output row), commits once after the dz=-1
+// taps (that slab is then refilled with plane z+2 by cp.async while the rest
+// of the MMAs run) and once at the end; the 4 warps read their 32 TMEM lanes
+// each (tcgen05.ld) and apply the epilogue.  Every wait is bounded; on a
+// timeout the CTA records it, lets its own MMAs and copies finish and frees
+// its TMEM.
+
+constexpr int kTcThreads = 128;
+constexpr int kTcRows = 4;
+constexpr int kTcCells = 128;
+constexpr int kTcHC = kTcCells + 2;       // cells per slab row (with halo)
+constexpr int kTcSlabRows = kTcRows + 2;  // rows per slab
+constexpr int kTcZChunk = 16;
+
+struct ConvTcArgs {
+    const bf16* in;     // [N][L^3][CINP]
+    const bf16* w;      // [27][CINP/8][NT][8]
+    const float* bias;  // [>= NT] fp32 (padded with zeros)
+    int N, L;
+    const bf16* res;    // unused (the residual comes from the centre slab)
+    bf16* out;
+    bf16* zout;
+    const float* su;
+    const float* sv;
+    float* ou;
+    float* ov;
+    int* err;
+    uint64_t timeout_ns;
+};
+
+GS_D uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    // shared-memory matrix descriptor, no swizzle: start, LBO, SBO (all >> 4),
+    // bits 46-48 = 0b001, base offset 0, layout type 0
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+GS_HD uint32_t tc_idesc(int n)
+{
+    // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
+    // B bf16 (10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+GS_D void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+GS_D void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     gs_smem_addr(bar))
+                 : "memory");
+}
+
+GS_D void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+GS_D void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int NCOL>
+GS_D void tc_ld(uint32_t taddr, float (&v)[NCOL]);
+
+template <>
+GS_D void tc_ld<32>(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+GS_D void tc_ld<16>(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CINP, int NT, int EPI>
+__global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcArgs a)
+{
+    constexpr int NCH = CINP / 8;
+    constexpr uint32_t PLANE = kTcSlabRows * kTcHC * 16;  // bytes of one chunk plane of a slab
+    constexpr uint32_t SLAB = NCH * PLANE;
+    constexpr uint32_t WBYTES = 27 * NCH * NT * 16;
+    constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
+    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256);
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    __shared__ __align__(8) uint64_t bar_slab, bar_done[2];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int L = a.L;
+    const long long L3 = (long long)L * L * L;
+    const uint32_t sbase = gs_smem_addr(smem_tc);
+    const uint32_t wbase = sbase + 3 * SLAB;
+    const uint32_t idesc = tc_idesc(NT);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gs_smem_addr(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        gs_mbar_init(&bar_slab, 1);
+        gs_mbar_init(&bar_done[0], 1);
+        gs_mbar_init(&bar_done[1], 1);
+        abort_s = 0;
+        gs_fence_mbar_init();
+    }
+    for (uint32_t i = tid; i < WBYTES / 16; i += kTcThreads) cp16(wbase + i * 16, a.w + (size_t)i * 8);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    const int nseg = L / kTcCells;
+    const int nyg = L / kTcRows;
+    const int nzc = (L + kTcZChunk - 1) / kTcZChunk;
+    const long long units = (long long)a.N * nyg * nseg * nzc;
+    uint32_t ph_slab = 0, ph_done[2] = {0, 0};  // completed phases seen, per barrier
+    int pending = 0;                            // accumulator sets committed but not yet consumed (0..2)
+    bool failed = false;
+
+    auto load_slab = [&](int slot, int n, int zz, int y0, int x0) {
+        const uint32_t dst0 = sbase + slot * SLAB;
+        const int zw = (zz % L + L) % L;
+        for (int i = tid; i < kTcSlabRows * kTcHC * NCH; i += kTcThreads) {
+            const int j = i % NCH;
+            const int c = (i / NCH) % kTcHC;
+            const int yi = i / (NCH * kTcHC);
+            const int yy = (y0 - 1 + yi + L) % L;
+            const int xx = (x0 - 1 + c + L) % L;
+            const bf16* src = a.in + ((size_t)n * L3 + ((size_t)zw * L + yy) * L + xx) * CINP + j * 8;
+            cp16(dst0 + j * PLANE + (uint32_t)(yi * kTcHC + c) * 16, src);
+        }
+    };
+
+    // epilogue of one finished item: accumulator set `set`, centre plane in slot `cslot`
+    auto epilogue = [&](int set, int cslot, int n, int z, int y0, int x0) {
+        const int x = x0 + tid;
+#pragma unroll 1
+        for (int r = 0; r < kTcRows; ++r) {
+            float acc[NT];
+            tc_ld<NT>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(set * ACC_COLS + r * NT), acc);
+            const int y = y0 + r;
+            const size_t cell = (size_t)n * L3 + ((size_t)z * L + y) * L + x;
+            if constexpr (EPI == EPI_LAST) {
+                a.ou[cell] = a.su[cell] + (acc[0] + a.bias[0]);
+                a.ov[cell] = a.sv[cell] + (acc[1] + a.bias[1]);
+            } else {
+                const unsigned char* ctr = smem_tc + cslot * SLAB + (uint32_t)((r + 1) * kTcHC + 1 + tid) * 16;
+#pragma unroll
+                for (int j = 0; j < NT / 8; ++j) {
+                    float h[8], zv[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        zv[e] = acc[j * 8 + e] + a.bias[j * 8 + e];
+                        h[e] = fmaxf(zv[e], 0.f);
+                    }
+                    if constexpr (EPI == EPI_HIDDEN) {
+                        const uint4 rv = *reinterpret_cast<const uint4*>(ctr + j * PLANE);
+                        const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            h[2 * e] = __bfloat162float(rb[e].x) + h[2 * e];
+                            h[2 * e + 1] = __bfloat162float(rb[e].y) + h[2 * e + 1];
+                        }
+                    }
+                    uint4 ho, zo;
+                    __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(&ho);
+                    __nv_bfloat162* zb = reinterpret_cast<__nv_bfloat162*>(&zo);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        hb[e] = __floats2bfloat162_rn(h[2 * e], h[2 * e + 1]);
+                        zb[e] = __floats2bfloat162_rn(zv[2 * e], zv[2 * e + 1]);
+                    }
+                    *reinterpret_cast<uint4*>(a.out + cell * 32 + j * 8) = ho;
+                    if (a.zout) *reinterpret_cast<uint4*>(a.zout + cell * 32 + j * 8) = zo;
+                }
+            }
+        }
+    };
+
+    // uniform bounded wait on an accumulator set's completion
+    auto wait_done = [&](int set) -> bool {
+        const int to = __syncthreads_or(!gs_mbar_wait(&bar_done[set], ph_done[set] & 1, a.timeout_ns));
+        if (to) return false;
+        ph_done[set] += 1;
+        --pending;
+        tc_fence_after();
+        return true;
+    };
+
+    int it = 0;  // items issued by this CTA (accumulator set = it & 1)
+    for (long long unit = blockIdx.x; unit < units && !failed; unit += gridDim.x) {
+        const int zc = (int)(unit % nzc);
+        long long r0 = unit / nzc;
+        const int seg = (int)(r0 % nseg);
+        r0 /= nseg;
+        const int yg = (int)(r0 % nyg);
+        const int n = (int)(r0 / nyg);
+        const int x0 = seg * kTcCells, y0 = yg * kTcRows;
+        const int z0 = zc * kTcZChunk;
+        const int nz = min(kTcZChunk, L - z0);
+        load_slab(0, n, z0 - 1, y0, x0);
+        load_slab(1, n, z0, y0, x0);
+        load_slab(2, n, z0 + 1, y0, x0);
+        for (int q = 0; q < nz; ++q, ++it) {
+            const int z = z0 + q;
+            const int set = it & 1;
+            cp_wait_all();
+            gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
+            tc_fence_before();
+            __syncthreads();
+            const int sm1 = q % 3, s0 = (q + 1) % 3, sp1 = (q + 2) % 3;
+            if (tid == 0) {
+                tc_fence_after();
+                // descriptors: the start-address field is the low 14 bits, so a
+                // descriptor plus (byte offset >> 4) addresses the shifted operand
+                const uint64_t bdesc0 = tc_desc(wbase, NT * 16, 128);
+                const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
+#pragma unroll 1
+                for (int dzi = 0; dzi < 3; ++dzi) {
+                    const int slot = dzi == 0 ? sm1 : (dzi == 1 ? s0 : sp1);
+                    const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
+#pragma unroll 1
+                    for (int r = 0; r < kTcRows; ++r) {
+                        const uint64_t ar = adz + (uint64_t)(r * kTcHC);  // (r * HC * 16 B) >> 4
+                        const uint32_t d = dset + (uint32_t)(r * NT);
+#pragma unroll
+                        for (int dyi = 0; dyi < 3; ++dyi)
+#pragma unroll
+                            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                                for (int kk = 0; kk < CINP / 16; ++kk) {
+                                    const int tap = dzi * 9 + dyi * 3 + dxi;
+                                    const uint64_t ad = ar + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(dyi * kTcHC + dxi);
+                                    const uint64_t bd = bdesc0 + (uint64_t)(((tap * NCH + 2 * kk) * NT * 16) >> 4);
+                                    tc_mma(d, ad, bd, idesc, (dzi | dyi | dxi | kk) ? 1u : 0u);
+                                }
+                    }
+                    if (dzi == 0) tc_commit(&bar_slab);
+                }
+                tc_commit(&bar_done[set]);
+            }
+            ++pending;
+            // meanwhile: the epilogue of the previous item (other accumulator set)
+            if (q > 0) {
+                if (!wait_done(set ^ 1)) {
+                    failed = true;
+                    break;
+                }
+                epilogue(set ^ 1, q % 3, n, z - 1, y0, x0);  // centre of item q-1 = plane z-1 = slot q % 3
+            }
+            // the dz=-1 slab of this item is free once its MMAs are done (and the
+            // epilogue above has read its centre cells): refill it with plane z+2
+            const int to = __syncthreads_or(!gs_mbar_wait(&bar_slab, ph_slab & 1, a.timeout_ns));
+            if (to) {
+                failed = true;
+                break;
+            }
+            ph_slab += 1;
+            if (q + 1 < nz) load_slab(sm1, n, z + 2, y0, x0);
+            tc_fence_before();
+            __syncthreads();  // TMEM reads of the epilogue done before the next MMAs reuse that set
+        }
+        if (failed) break;
+        // the last item of the unit
+        if (!wait_done((it - 1) & 1)) {
+            failed = true;
+            break;
+        }
+        epilogue((it - 1) & 1, (nz - 1 + 1) % 3, n, z0 + nz - 1, y0, x0);
+        tc_fence_before();
+        __syncthreads();
+    }
+    // nothing of this CTA may be in flight when its TMEM and shared memory go
+    cp_wait_all();
+    if (failed && tid == 0) {
+        gs_report(a.err, GS_DERR_TIMEOUT);
+        for (int s2 = 0; s2 < 2; ++s2)
+            if (pending > 0) gs_mbar_wait(&bar_done[s2], ph_done[s2] & 1, 2000000000ull);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// fp32 master weights [27][cin][cout] -> tcgen05 B layout [27][CINP/8][NT][8] (zero padded)
+__global__ void gs_wprep_tc_kernel(const float* __restrict__ w, int cin, int cout, int cinp, int nt, bf16* __restrict__ wt)
+{
+    const int total = 27 * cinp * nt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i % 8;
+        const int co = (i / 8) % nt;
+        const int j = (i / (8 * nt)) % (cinp / 8);
+        const int tap = i / (8 * nt * (cinp / 8));
+        const int ci = j * 8 + e;
+        const float val = (ci < cin && co < cout) ? w[((size_t)tap * cin + ci) * cout + co] : 0.f;
+        wt[i] = __float2bfloat16_rn(val);
+    }
+}
+
+}  // namespace gs
+
 // ===========================================================================
 // Host side
 // ===========================================================================
@@ -514,7 +864,10 @@ struct gs_surr {
     size_t woff[kSurrLayers] = {}, boff[kSurrLayers] = {};
     bf16* wf[kSurrLayers] = {};  // forward layout
     bf16* wd[kSurrLayers] = {};  // data-gradient layout (layers 1..5)
+    bf16* wt[kSurrLayers] = {};  // tcgen05 B layout [27][CINP/8][NT][8]
     bool wdirty = true;
+    int backend = 0;             // 0 auto (tcgen05 when L % 128 == 0), 1 mma.sync, 2 tcgen05
+    int* d_err = nullptr;
     // workspace
     int N = 0, L = 0;
     bool train_ws = false;
@@ -624,6 +977,27 @@ int wgrad_launch(gs_surr* s, WgArgs a)
     return GS_OK;
 }
 
+template <int CINP, int NT, int EPI>
+int tc_launch(gs_surr* s, ConvTcArgs a)
+{
+    constexpr uint32_t SLAB = (CINP / 8) * kTcSlabRows * kTcHC * 16;
+    const size_t smem = 3 * (size_t)SLAB + (size_t)27 * (CINP / 8) * NT * 16;
+    auto k = gs_conv_tc_kernel<CINP, NT, EPI>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "tensor-core convolution does not fit on an SM");
+    per_sm = std::min(per_sm, 2);  // TMEM: at most 2 x 128 columns per SM
+    a.err = s->d_err;
+    a.timeout_ns = 2000000000ull;
+    const long long units = (long long)a.N * (a.L / kTcRows) * (a.L / kTcCells) * ((a.L + kTcZChunk - 1) / kTcZChunk);
+    const int grid = (int)std::min<long long>(units, (long long)per_sm * num_sms());
+    k<<<grid, kTcThreads, smem, s->stream>>>(a);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+    return GS_OK;
+}
+
 int grid1d(long long n, int block) { return (int)std::max<long long>(1, std::min<long long>((n + block - 1) / block, 8LL * num_sms())); }
 
 int prep_weights(gs_surr* s)
@@ -635,7 +1009,10 @@ int prep_weights(gs_surr* s)
         gs_wprep_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, s->wf[l], kCoutP[l], kCinP[l],
                                                   l >= 1 ? s->wd[l] : nullptr, dk);
         GS_CUDA_TRY(cudaGetLastError());
-        s->launches += 1;
+        gs_wprep_tc_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, kCinP[l], l == 5 ? 16 : 32,
+                                                     s->wt[l]);
+        GS_CUDA_TRY(cudaGetLastError());
+        s->launches += 2;
     }
     s->wdirty = false;
     return GS_OK;
@@ -661,6 +1038,38 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
     gs_pack_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(u, v, s->fk, s->x0, (long long)L * L * L, N);
     GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
+    const bool tc = s->backend != 1 && L % kTcCells == 0;
+    if (s->backend == 2 && !tc) return fail(GS_EINVAL, "the tcgen05 path needs L %% 128 == 0 (L=%d)", L);
+    if (tc) {
+        ConvTcArgs t{};
+        t.N = N;
+        t.L = L;
+        t.in = s->x0;
+        t.w = s->wt[0];
+        t.bias = s->params + s->boff[0];
+        t.out = s->h[1];
+        t.zout = train ? s->z[0] : nullptr;
+        if ((rc = tc_launch<16, 32, EPI_FIRST>(s, t))) return rc;
+        for (int l = 1; l <= 4; ++l) {
+            t.in = train ? s->h[l] : s->h[1 + ((l - 1) & 1)];
+            t.out = train ? s->h[l + 1] : s->h[1 + (l & 1)];
+            t.w = s->wt[l];
+            t.bias = s->params + s->boff[l];
+            t.zout = train ? s->z[l] : nullptr;
+            if ((rc = tc_launch<32, 32, EPI_HIDDEN>(s, t))) return rc;
+        }
+        ConvTcArgs b{};
+        b.N = N;
+        b.L = L;
+        b.in = train ? s->h[5] : s->h[1];
+        b.w = s->wt[5];
+        b.bias = s->params + s->boff[5];
+        b.su = u;
+        b.sv = v;
+        b.ou = uo;
+        b.ov = vo;
+        return tc_launch<32, 16, EPI_LAST>(s, b);
+    }
     ConvArgs a{};
     a.N = N;
     a.L = L;
@@ -763,11 +1172,8 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     w.dw = s->grads + s->woff[0];
     if ((rc = wgrad_launch<16, 32>(s, w))) return rc;
     if ((rc = bias_grad(s->gz[cur], 32, 32, s->grads + s->boff[0]))) return rc;
-    if (loss) {
-        GS_CUDA_TRY(cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-        GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    }
-    return GS_OK;
+    if (loss) GS_CUDA_TRY(cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    return gs_surr_sync(s);
 }
 
 int diff(gs_surr* s, const float* a, const float* b, long long n, double* maxabs, double* rms)
@@ -822,7 +1228,9 @@ int gs_surr_destroy(gs_surr* s)
     for (int l = 0; l < kSurrLayers; ++l) {
         cudaFree(s->wf[l]);
         cudaFree(s->wd[l]);
+        cudaFree(s->wt[l]);
     }
+    cudaFree(s->d_err);
     cudaFree(s->d_loss);
     cudaFree(s->d_max);
     cudaFree(s->d_ss);
@@ -849,13 +1257,15 @@ int gs_surr_create(gs_surr** out)
         (e = cudaMalloc(&s->m, off * 4)) != cudaSuccess || (e = cudaMalloc(&s->v, off * 4)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_loss, sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&s->d_max, sizeof(unsigned))) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_ss, sizeof(double))) != cudaSuccess) {
+        (e = cudaMalloc(&s->d_ss, sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(s->d_err, 0, sizeof(int))) != cudaSuccess) {
         int rc = cuda_fail(e, "surrogate allocation");
         gs_surr_destroy(s);
         return rc;
     }
     for (int l = 0; l < kSurrLayers && e == cudaSuccess; ++l) {
         e = cudaMalloc(&s->wf[l], (size_t)27 * kCoutP[l] * kCinP[l] * sizeof(bf16));
+        if (e == cudaSuccess) e = cudaMalloc(&s->wt[l], (size_t)27 * kCinP[l] * (l == 5 ? 16 : 32) * sizeof(bf16));
         if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wd[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
     }
     if (e != cudaSuccess || (e = cudaMemset(s->params, 0, off * 4)) != cudaSuccess ||
@@ -1035,6 +1445,7 @@ int gs_surr_run(gs_surr* s, gs_sim* sim, double F, double k, int64_t nsteps, int
         double mu = 0, ru = 0, mv = 0, rv = 0;
         if ((rc = diff(s, tu, (const float*)cu, (long long)cells, &mu, &ru))) break;
         if ((rc = diff(s, tv, (const float*)cv, (long long)cells, &mv, &rv))) break;
+        if ((rc = gs_surr_sync(s))) break;
         const double err = (std::isnan(mu) || std::isnan(mv)) ? INFINITY : std::max(mu, mv);
         r.checks += 1;
         r.max_check_error = std::max(r.max_check_error, err);
@@ -1051,6 +1462,25 @@ int gs_surr_run(gs_surr* s, gs_sim* sim, double F, double k, int64_t nsteps, int
     s->stream = saved_stream;
     if (rep) *rep = r;
     return rc;
+}
+
+int gs_surr_set_backend(gs_surr* s, int backend)
+{
+    if (!s) return fail(GS_EINVAL, "surrogate is NULL");
+    if (backend < 0 || backend > 2) return fail(GS_EINVAL, "backend=%d must be 0, 1 or 2", backend);
+    s->backend = backend;
+    return GS_OK;
+}
+
+int gs_surr_sync(gs_surr* s)
+{
+    if (!s) return fail(GS_EINVAL, "surrogate is NULL");
+    int err = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (err == GS_DERR_TIMEOUT) return fail(GS_ETIMEOUT, "a device-side wait timed out");
+    if (err) return fail(GS_ECUDA, "device error code %d", err);
+    return GS_OK;
 }
 
 int gs_surr_launch_count(gs_surr* s, int64_t* count)

@@ -94,6 +94,8 @@ _SIGS = {
     "gs_surr_train_step": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(_d)],
     "gs_surr_diff": [_vp, _vp, _vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "gs_surr_run": [_vp, _vp, _d, _d, _i64, _i, _d, _vp],
+    "gs_surr_set_backend": [_vp, _i],
+    "gs_surr_sync": [_vp],
     "gs_surr_launch_count": [_vp, ctypes.POINTER(_i64)],
     "gs_surr_destroy": [_vp],
     "gs_batch_step_noalloc": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _vp, _i64, _i, _i64, _vp],
@@ -470,6 +472,17 @@ def gs_surr_run(s, sim, F, k, nsteps, check_every=64, tol=0.05) -> dict:
     rep = GsSurrReport()
     _check(lib().gs_surr_run(s, sim, F, k, int(nsteps), int(check_every), tol, ctypes.byref(rep)), "gs_surr_run")
     return rep.as_dict()
+
+
+GS_SURR_AUTO, GS_SURR_MMA, GS_SURR_TCGEN05 = 0, 1, 2
+
+
+def gs_surr_set_backend(s, backend: int):
+    _check(lib().gs_surr_set_backend(s, backend), "gs_surr_set_backend")
+
+
+def gs_surr_sync(s):
+    _check(lib().gs_surr_sync(s), "gs_surr_sync")
 
 
 def gs_surr_launch_count(s) -> int:

@@ -168,3 +168,66 @@ def test_surrogate_argument_errors():
     with pytest.raises(gs.GsError):
         s.run(sim, 0.02, 0.048, 64)
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# 5th-generation tensor-core (tcgen05) forward path, L % 128 == 0
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [1, 2])
+def test_tcgen05_forward_matches_mma_path_and_oracle(N):
+    torch = need_cuda()
+    L = 128
+    params = inputs.surrogate_init_params(seed=21, last_scale=1.0)
+    rng = np.random.default_rng(N)
+    u = rng.uniform(0, 1, (N, L, L, L)).astype(np.float32)
+    v = rng.uniform(0, 0.5, (N, L, L, L)).astype(np.float32)
+    F, k = [0.03, 0.045][:N], [0.055, 0.062][:N]
+    s = gs.Surrogate(params)
+    gs.gs_surr_set_backend(s.handle, gs.GS_SURR_TCGEN05)
+    tu, tv = s.forward(_dev(torch, u), _dev(torch, v), F, k)
+    gs.gs_surr_sync(s.handle)
+    gs.gs_surr_set_backend(s.handle, gs.GS_SURR_MMA)
+    mu, mv = s.forward(_dev(torch, u), _dev(torch, v), F, k)
+    tu, tv, mu, mv = (t.cpu().numpy() for t in (tu, tv, mu, mv))
+    d_t = np.stack([tu - u, tv - v])
+    d_m = np.stack([mu - u, mv - v])
+    scale = np.abs(d_m).max()
+    err = np.abs(d_t - d_m)
+    print(f"tcgen05 vs mma.sync: max |d| {scale:.3e} max err {err.max():.3e} mean {err.mean():.3e}")
+    assert err.max() <= 2e-2 * scale and err.mean() <= 1e-3 * scale
+    for n in range(N):
+        for c in [(0, 0, 0), (127, 5, 64), (64, 127, 127)]:
+            idx = [(np.arange(-6, 7) + cc) % L for cc in c]
+            sel = np.ix_(idx[2], idx[1], idx[0])
+            wu, wv = u[n][sel][None].astype(np.float64), v[n][sel][None].astype(np.float64)
+            out, _ = oracle.surrogate_forward(params, wu, wv, [F[n]], [k[n]], emulate_bf16=True)
+            x, y, z = c
+            for ch, (tt, base) in enumerate(((tu, u), (tv, v))):
+                d_o = out[0, 6, 6, 6, ch] - base[n, z, y, x]
+                d_g = tt[n, z, y, x] - base[n, z, y, x]
+                assert abs(d_g - d_o) <= 2e-2 * max(abs(d_o), 1e-3), (n, c, ch, d_g, d_o)
+    s.close()
+
+
+def test_tcgen05_training_gradients_match_mma_path():
+    torch = need_cuda()
+    L = 128
+    params = inputs.surrogate_init_params(seed=4, last_scale=1.0)
+    rng = np.random.default_rng(7)
+    u = _dev(torch, rng.uniform(0, 1, (1, L, L, L)))
+    v = _dev(torch, rng.uniform(0, 0.5, (1, L, L, L)))
+    ut = _dev(torch, rng.uniform(0, 1, (1, L, L, L)))
+    vt = _dev(torch, rng.uniform(0, 0.5, (1, L, L, L)))
+    s = gs.Surrogate(params)
+    gs.gs_surr_set_backend(s.handle, gs.GS_SURR_TCGEN05)
+    lt = s.grad(u, v, [0.03], [0.05], ut, vt)
+    gt = s.grads()
+    gs.gs_surr_set_backend(s.handle, gs.GS_SURR_MMA)
+    lm = s.grad(u, v, [0.03], [0.05], ut, vt)
+    gm = s.grads()
+    assert abs(lt - lm) <= 1e-3 * lm
+    for l in range(6):
+        for j in range(2):
+            rel = np.linalg.norm(gt[l][j] - gm[l][j]) / np.linalg.norm(gm[l][j])
+            assert rel <= 1e-2, (l, j, rel)
+    s.close()
