@@ -37,6 +37,22 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", "gs_stencil.cu
 PROFILE = os.path.join(ROOT, "profiles", "gs_zmarch_f32_L512.md")
 
 
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """Largest value of x over all ranks (x itself when running alone)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: float, seconds_max: float) -> float:
+    """Aggregate throughput: units processed by all ranks over the slowest rank's time."""
+    return ws * units_per_rank / seconds_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -393,13 +409,9 @@ def run_ours(args):
     clk = clocks.stop() if clocks else None
     launches = gs.gs_launch_count(sim.handle) - launches0
     stencil_launches = launches - args.steps  # one init launch per bench step
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), ws, dev)
     step_ms = sum(b.elapsed_time(c) for (_, b, c) in ev)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * cells * args.time_steps * args.steps / (total_ms / 1e3) / 1e9
+    value = whole_job_rate(ws, cells * args.time_steps * args.steps, total_ms / 1e3) / 1e9
     per_launch_s = step_ms / 1e3 / stencil_launches
     hbm_peak, peak_kind = load_peaks()
     alg_bytes = 16.0 * cells  # one read and one write of u and v per pass
@@ -428,12 +440,8 @@ def run_ours(args):
         gs.gs_read(sim.handle, gs.GS_U, uo)
         gs.gs_read(sim.handle, gs.GS_V, vo)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * cells * args.time_steps * e2e_steps / e2e_s / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    e2e_value = whole_job_rate(ws, cells * args.time_steps * e2e_steps, e2e_s) / 1e9
     assert np.isfinite(uo.numpy()).all()
 
     extra = {}
