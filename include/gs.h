@@ -225,6 +225,11 @@ int gs_batch_sync(gs_batch* b);
  * clears the recorded error. */
 int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns);
 
+/* Work decomposition of the persistent kernel: z-chunk per work item
+ * (1..256, default 32) and TMA ring depth (3..8, default 8).  Synchronous;
+ * drops the captured graphs. */
+int gs_batch_set_plan(gs_batch* b, int tile_z, int stages);
+
 /* Launch shape of the persistent kernel (CTAs, work items per step, whether
  * the cooperative launch attribute was accepted) and the number of kernel
  * launches issued so far. */

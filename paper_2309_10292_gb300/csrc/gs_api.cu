@@ -442,8 +442,8 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
     const int zt[][2] = {{128, 8}, {256, 4}, {64, 16}, {128, 4}, {64, 8}, {256, 8}, {128, 16}, {32, 16}};
     for (auto& t : zt)
         for (int tz : {32, 64, 128})
-            for (int st : {4, 6}) cand.push_back(gs_plan{GS_KERNEL_ZMARCH, t[0], t[1], tz, 1, st, 0.0});
-    const int bt[][2] = {{64, 16}, {128, 16}, {64, 32}, {128, 8}, {64, 8}, {32, 16}};
+            for (int st : {4, 6, 8}) cand.push_back(gs_plan{GS_KERNEL_ZMARCH, t[0], t[1], tz, 1, st, 0.0});
+    const int bt[][2] = {{64, 16}, {128, 8}, {64, 8}, {32, 16}, {128, 4}, {32, 32}};
     for (int d = 2; d <= 4; ++d)
         for (auto& t : bt)
             for (int tz : {64, 128}) cand.push_back(gs_plan{GS_KERNEL_TBLOCK, t[0], t[1], tz, d, 5, 0.0});

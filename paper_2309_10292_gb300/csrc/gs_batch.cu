@@ -149,14 +149,23 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
 
     const long long t0 = a.ctrl->t;
     const int cur0 = a.ctrl->cur;
-    uint32_t seq = 0;  // ring sequence, advanced identically by producer and consumers
+    // ring position, advanced identically by producer and consumers: stage
+    // index and the parity of its current round (no runtime division)
+    int cs = 0;
+    uint32_t cph = 0;
+    uint32_t seq = 0;      // planes issued by the producer (for its drain)
+    bool wrapped = false;  // producer: every stage used once
+    auto advance = [&]() {
+        if (++cs == S) { cs = 0; cph ^= 1u; wrapped = true; }
+    };
     long long s = 0;
     for (; s < a.nsteps; ++s) {
         const int in = (cur0 + (int)(s & 1)) & 1, out = in ^ 1;
         const long long t = t0 + s;
         if (tid < kBatchConsumers) {
             // ------------------------------ consumers ------------------------------
-            T pu[V], pv[V], cu[V], cv[V], nu[V], nv[V];
+            // planes z-1, z, z+1 in three register sets rotated by renaming
+            T qu[3][V], qv[3][V];
             for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x) {
                 const int ii = a.item_inst[item];
                 const BInst& I = a.inst[ii];
@@ -177,25 +186,24 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                 T* un = a.arena + I.off[out][0];
                 T* vn = a.arena + I.off[out][1];
                 const long long LL = (long long)L * L;
+                const int om = row > 0 ? moff - L : top_off + xv * V;
+                const int op = row + 1 < nvy ? moff + L : bot_off + xv * V;
+                const bool l_smem = xv == 0 || lane == 0;
+                const bool r_smem = xv == nxv - 1 || lane == 31;
+                const int oxl = xv > 0 ? moff - 1 : rowbase + L - 1;  // periodic in x
+                const int oxr = xv < nxv - 1 ? moff + V : rowbase;
+                long long g = (long long)z0 * LL + (long long)(y0 + row) * L + xv * V;
 
-                int st = seq % S;
-                if (!wait_or_abort(&full[st], (seq / S) & 1, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
-                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + st * stage_elems + moff), pu);
-                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + st * stage_elems + a.field_elems + moff), pv);
-                __syncwarp();
-                if (lane == 0) gs_mbar_arrive(&empty[st]);
-                ++seq;
-                int sc = seq % S;
-                if (!wait_or_abort(&full[sc], (seq / S) & 1, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
-                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sc * stage_elems + moff), cu);
-                gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sc * stage_elems + a.field_elems + moff), cv);
-                ++seq;
-                bool failed = false;
-                for (int zi = 0; zi < nz; ++zi) {
-                    const int sn = seq % S;
-                    if (!wait_or_abort(&full[sn], (seq / S) & 1, a.timeout_ns, &s_abort)) { failed = true; break; }
-                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sn * stage_elems + moff), nu);
-                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + sn * stage_elems + a.field_elems + moff), nv);
+                auto load = [&](T (&u)[V], T (&v)[V]) {
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + cs * stage_elems + moff), u);
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + cs * stage_elems + a.field_elems + moff), v);
+                };
+                int sc = 0;
+                // one plane: P, C, N are planes z-1, z, z+1 (N loaded here)
+                auto plane = [&](T (&pu)[V], T (&pv)[V], T (&cu)[V], T (&cv)[V], T (&nu)[V], T (&nv)[V]) -> bool {
+                    const int sn = cs;
+                    if (!wait_or_abort(&full[sn], cph, a.timeout_ns, &s_abort)) return false;
+                    load(nu, nv);
                     const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
                     const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
                     const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
@@ -203,25 +211,14 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                     if (active) {
                         const T* bu = ring + sc * stage_elems;
                         const T* bv = bu + a.field_elems;
-                        const int om = row > 0 ? moff - L : top_off + xv * V;
-                        const int op = row + 1 < nvy ? moff + L : bot_off + xv * V;
                         T ymu[V], ypu[V], ymv[V], ypv[V], ou[V], ov[V];
                         gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
                         gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
                         gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
                         gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
                         T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
-                        if (xv == 0 || lane == 0) {
-                            const int oxl = xv > 0 ? moff - 1 : rowbase + L - 1;  // periodic in x
-                            xlu = bu[oxl];
-                            xlv = bv[oxl];
-                        }
-                        if (xv == nxv - 1 || lane == 31) {
-                            const int oxr = xv < nxv - 1 ? moff + V : rowbase;
-                            xru = bu[oxr];
-                            xrv = bv[oxr];
-                        }
-                        const long long g = (long long)(z0 + zi) * LL + (long long)(y0 + row) * L + xv * V;
+                        if (l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
+                        if (r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
                         const uint32_t pre = NOISE ? gs_group_pre((uint32_t)g, keys) : 0u;
                         gs_update_group<T, NOISE>(c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
                                                   xru, xlv, xrv, ou, ov);
@@ -231,14 +228,31 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                     __syncwarp();
                     if (lane == 0) gs_mbar_arrive(&empty[sc]);
                     sc = sn;
-                    ++seq;
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        pu[e] = cu[e]; pv[e] = cv[e];
-                        cu[e] = nu[e]; cv[e] = nv[e];
-                    }
+                    advance();
+                    g += LL;
+                    return true;
+                };
+
+                if (!wait_or_abort(&full[cs], cph, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
+                load(qu[0], qv[0]);
+                __syncwarp();
+                if (lane == 0) gs_mbar_arrive(&empty[cs]);
+                advance();
+                sc = cs;
+                if (!wait_or_abort(&full[cs], cph, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
+                load(qu[1], qv[1]);
+                advance();
+                bool ok = true;
+                int zi = 0;
+                for (; ok && zi + 3 <= nz; zi += 3) {
+                    ok = plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2]) &&
+                         plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0]) &&
+                         plane(qu[2], qv[2], qu[0], qv[0], qu[1], qv[1]);
                 }
-                if (failed) {
+                // remainder (each item reloads its first two planes into q0, q1)
+                if (ok && zi < nz) ok = plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2]);
+                if (ok && zi + 1 < nz) ok = plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0]);
+                if (!ok) {
                     gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
                     s_abort = 1;
                     break;
@@ -262,11 +276,10 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                 const CUtensorMap* mu = a.maps + (((size_t)ii * 2 + in) * 2 + 0) * 2;
                 const CUtensorMap* mv = a.maps + (((size_t)ii * 2 + in) * 2 + 1) * 2;
                 bool failed = false;
+                int zp = (z0 - 1 + L) % L;
                 for (int j = 0; j < nz + 2; ++j) {
-                    const int zp = (z0 - 1 + j + L) % L;
-                    const int sl = seq % S;
-                    if (seq >= (uint32_t)S &&
-                        !wait_or_abort(&empty[sl], ((seq / S) - 1) & 1, a.timeout_ns, &s_abort)) {
+                    const int sl = cs;
+                    if (wrapped && !wait_or_abort(&empty[sl], cph ^ 1u, a.timeout_ns, &s_abort)) {
                         failed = true;
                         break;
                     }
@@ -280,6 +293,8 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                     gs_tma_load_3d(b + top_off, &mv[1], &full[sl], 0, ytop, zp);
                     gs_tma_load_3d(b + bot_off, &mv[1], &full[sl], 0, ybot, zp);
                     ++seq;
+                    advance();
+                    zp = zp + 1 == L ? 0 : zp + 1;
                 }
                 if (failed) {
                     gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
@@ -320,7 +335,7 @@ struct gs_batch {
     BCtrl* d_ctrl = nullptr;
     std::vector<ZPlan> zplan;               // per-instance plan of the sequential path
     std::vector<ZMaps> zmaps[2];            // per-instance tensor maps of the sequential path
-    int nitems = 0, tz = 32, stages = 4, main_elems = 0, row_elems = 0, field_elems = 0;
+    int nitems = 0, tz = 32, stages = 8, main_elems = 0, row_elems = 0, field_elems = 0;
     int grid = 0;
     int64_t t = 0;
     int cur = 0;
@@ -704,6 +719,37 @@ int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns)
         // clear a recorded failure so the batch can be used again
         GS_CUDA_TRY(cudaMemsetAsync(&b->d_ctrl->err, 0, sizeof(int), b->stream));
     }
+    return GS_OK;
+}
+
+int gs_batch_set_plan(gs_batch* b, int tile_z, int stages)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (tile_z < 1 || tile_z > 256) return fail(GS_EINVAL, "tile_z=%d must be in [1, 256]", tile_z);
+    if (stages < 3 || stages > 8) return fail(GS_EINVAL, "stages=%d must be in [3, 8]", stages);
+    const size_t esz = elem_size(b->dtype);
+    if ((size_t)2 * b->field_elems * esz * stages > 200 * 1024) return fail(GS_EINVAL, "ring too large");
+    // rebuild the work-item tables for the new z-chunk
+    std::vector<int> item_inst;
+    for (int i = 0; i < b->n; ++i) {
+        BInst& I = b->h_inst[i];
+        I.ntz = (I.L + tile_z - 1) / tile_z;
+        I.item0 = (int)item_inst.size();
+        I.nitems = I.nty * I.ntz;
+        for (int j = 0; j < I.nitems; ++j) item_inst.push_back(i);
+    }
+    if ((int)item_inst.size() != b->nitems) {
+        int* d = nullptr;
+        GS_CUDA_TRY(cudaMalloc(&d, sizeof(int) * item_inst.size()));
+        cudaFree(b->d_item_inst);
+        b->d_item_inst = d;
+        b->nitems = (int)item_inst.size();
+    }
+    GS_CUDA_TRY(cudaMemcpy(b->d_item_inst, item_inst.data(), sizeof(int) * item_inst.size(), cudaMemcpyHostToDevice));
+    GS_CUDA_TRY(cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(BInst) * b->n, cudaMemcpyHostToDevice));
+    b->tz = tile_z;
+    b->stages = stages;
+    drop_graphs(b);
     return GS_OK;
 }
 

@@ -61,9 +61,11 @@ GS_D T gs_noise(uint32_t c, GsKeys k)
 // The same numerators for the V consecutive cells g + e (e < V) of one
 // 16-byte group, g a multiple of V (V <= 4).  Because g + e = g ^ e and e
 // only touches the two low bits, the first xor-shift of fmix32(c ^ k1) is
-// pre ^ e with pre = x ^ (x >> 16), x = g ^ k1, computed once per group; the
-// first xor-shift of the second round folds k2 into kk2 = k2 ^ (k2 >> 16).
-// Bit for bit equal to gs_noise_num(g + e, k).
+// pre ^ e with pre = x ^ (x >> 16), x = g ^ k1, computed once per group.
+// The xor-shift by 16 is its own inverse (y ^ (y >> 16) ^ ((y ^ (y >> 16))
+// >> 16) = y for 32-bit y), so the last xor-shift of the first round and the
+// first xor-shift of the second, with k2 xored in between, reduce to one xor
+// with kk2 = k2 ^ (k2 >> 16).  Bit for bit equal to gs_noise_num(g + e, k).
 GS_HD uint32_t gs_group_pre(uint32_t g, GsKeys k)
 {
     const uint32_t x = g ^ k.k1;
@@ -78,8 +80,7 @@ GS_HD int32_t gs_group_num(uint32_t pre, uint32_t e, uint32_t kk2)
     h *= 0x85ebca6bu;
     h ^= h >> 13;
     h *= 0xc2b2ae35u;
-    h ^= h >> 16;
-    h = h ^ (h >> 16) ^ kk2;
+    h ^= kk2;  // = (y ^ (y >> 16) ^ k2) xor-shifted by 16, y = h before it
     h *= 0x85ebca6bu;
     h ^= h >> 13;
     h *= 0xc2b2ae35u;

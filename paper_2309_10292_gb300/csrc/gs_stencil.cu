@@ -234,7 +234,10 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         if (tid != cons_threads || a.stall) return;
         for (int f = 0; f < 2; ++f)
             for (int m = 0; m < 3; ++m) gs_prefetch_tmap(&maps.m[f][m]);
-        uint32_t seq = 0;
+        uint32_t seq = 0;           // planes issued (for the drain)
+        int ps = 0;                 // stage of the next plane
+        uint32_t pph = 0;           // its round's parity
+        bool wrapped = false;       // every stage used once: wait for the consumers' release
         for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
             const int txi = tile % a.ntx;
             const int tyi = (tile / a.ntx) % a.nty;
@@ -243,27 +246,28 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
             const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0), nz = min(a.tz, L - z0);
             const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
             const int xl = (x0 - V + L) % L, xr = (x0 + nvx) % L;
+            int zp = (z0 - 1 + L) % L;
             for (int j = 0; j < nz + 2; ++j) {
-                const int zp = (z0 - 1 + j + L) % L;
-                const int s = seq % S;
-                if (seq >= (uint32_t)S) {
-                    if (!gs_mbar_wait(&empty[s], ((seq / S) - 1) & 1, a.timeout_ns)) {
+                if (wrapped) {
+                    if (!gs_mbar_wait(&empty[ps], pph ^ 1u, a.timeout_ns)) {
                         gs_report(a.err, GS_DERR_TIMEOUT);
                         abort_flag = 1;
                         goto drain;
                     }
                 }
                 if (abort_flag) goto drain;
-                gs_mbar_arrive_expect_tx(&full[s], a.lay.tx_bytes);
+                gs_mbar_arrive_expect_tx(&full[ps], a.lay.tx_bytes);
                 for (int f = 0; f < 2; ++f) {
-                    T* b = ring + (size_t)s * (a.lay.stage_bytes / sizeof(T)) + f * a.lay.field_elems;
-                    gs_tma_load_3d(b + a.lay.main_off, &maps.m[f][0], &full[s], x0, y0, zp);
-                    gs_tma_load_3d(b + a.lay.top_off, &maps.m[f][1], &full[s], x0, ytop, zp);
-                    gs_tma_load_3d(b + a.lay.bot_off, &maps.m[f][1], &full[s], x0, ybot, zp);
-                    gs_tma_load_3d(b + a.lay.left_off, &maps.m[f][2], &full[s], xl, y0, zp);
-                    gs_tma_load_3d(b + a.lay.right_off, &maps.m[f][2], &full[s], xr, y0, zp);
+                    T* b = ring + (size_t)ps * (a.lay.stage_bytes / sizeof(T)) + f * a.lay.field_elems;
+                    gs_tma_load_3d(b + a.lay.main_off, &maps.m[f][0], &full[ps], x0, y0, zp);
+                    gs_tma_load_3d(b + a.lay.top_off, &maps.m[f][1], &full[ps], x0, ytop, zp);
+                    gs_tma_load_3d(b + a.lay.bot_off, &maps.m[f][1], &full[ps], x0, ybot, zp);
+                    gs_tma_load_3d(b + a.lay.left_off, &maps.m[f][2], &full[ps], xl, y0, zp);
+                    gs_tma_load_3d(b + a.lay.right_off, &maps.m[f][2], &full[ps], xr, y0, zp);
                 }
                 ++seq;
+                if (++ps == S) { ps = 0; pph ^= 1u; wrapped = true; }
+                zp = zp + 1 == L ? 0 : zp + 1;
             }
         }
         return;
@@ -282,20 +286,26 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
     const size_t stage_elems = a.lay.stage_bytes / sizeof(T);
     const int64_t LL = (int64_t)L * L;
     const uint32_t kk2 = gs_kk2(a.keys);
-    uint32_t seq = 0;
+    int cs = 0;        // stage of the next plane to consume
+    uint32_t cph = 0;  // its round's parity
 
+    auto advance = [&]() {
+        if (++cs == S) { cs = 0; cph ^= 1u; }
+    };
     auto release = [&](int s) {
         __syncwarp();
         if (lane == 0) gs_mbar_arrive(&empty[s]);
     };
-    auto wait_full = [&](int s, uint32_t q) -> bool {
-        if (gs_mbar_wait(&full[s], (q / S) & 1, a.timeout_ns)) return true;
+    auto wait_full = [&]() -> bool {
+        if (gs_mbar_wait(&full[cs], cph, a.timeout_ns)) return true;
         gs_report(a.err, GS_DERR_TIMEOUT);
         abort_flag = 1;
         return false;
     };
 
-    T pu[V], pv[V], cu[V], cv[V], nu[V], nv[V];
+    // planes z-1, z, z+1 of this thread's group in three register sets that
+    // rotate by renaming (the loop below is unrolled by 3)
+    T qu[3][V], qv[3][V];
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const int txi = tile % a.ntx;
         const int tyi = (tile / a.ntx) % a.nty;
@@ -304,69 +314,48 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0), nz = min(a.tz, L - z0);
         const bool active = row < nvy && xv * V < nvx;
         const int rr = row < a.ty ? row : 0;  // padding threads read a valid address
-        const int moff = rr * a.tx + xv * V;
+        const int moff = a.lay.main_off + rr * a.tx + xv * V;
+        // y neighbours (top / bottom halo rows at the tile's edges)
+        const int om = row > 0 ? a.lay.main_off + (row - 1) * a.tx + xv * V : a.lay.top_off + xv * V;
+        const int op = row + 1 < nvy ? a.lay.main_off + (row + 1) * a.tx + xv * V : a.lay.bot_off + xv * V;
+        // x neighbours of the group's end cells: from the adjacent lanes when
+        // they hold the same row's neighbouring groups (conflict-free), else
+        // from shared memory (halo columns, or a group in another warp)
+        const bool has_r = xv * V + V < nvx;
+        const bool l_smem = xv == 0 || lane == 0;
+        const bool r_smem = !has_r || lane == 31;
+        const int oxl = xv > 0 ? moff - 1 : a.lay.left_off + rr * V + (V - 1);
+        const int oxr = has_r ? moff + V : a.lay.right_off + rr * V;
+        int64_t gidx = (int64_t)z0 * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
 
-        // plane z0 - 1: centre values only
-        int s = seq % S;
-        if (!wait_full(s, seq)) return;
-        {
-            const T* b = ring + s * stage_elems;
-            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.main_off + moff), pu);
-            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + a.lay.main_off + moff), pv);
-        }
-        release(s);
-        ++seq;
-        // plane z0
-        int sc = seq % S;
-        if (!wait_full(sc, seq)) return;
-        {
-            const T* b = ring + sc * stage_elems;
-            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.main_off + moff), cu);
-            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + a.lay.main_off + moff), cv);
-        }
-        ++seq;
-
-        for (int zi = 0; zi < nz; ++zi) {
-            const int sn = seq % S;
-            if (!wait_full(sn, seq)) return;
-            {
-                const T* b = ring + sn * stage_elems;
-                gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.main_off + moff), nu);
-                gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + a.lay.main_off + moff), nv);
-            }
-            // x neighbours of the group's end cells: from the adjacent lanes when
-            // they hold the same row's neighbouring groups (conflict-free), else
-            // from shared memory (halo columns, or a group in another warp)
+        auto load_centre = [&](T (&u)[V], T (&v)[V]) {
+            const T* b = ring + cs * stage_elems;
+            gs_unpack<T>(*reinterpret_cast<const VT*>(b + moff), u);
+            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + moff), v);
+        };
+        // one plane: P, C, N are planes z-1, z, z+1 (N is loaded here); the
+        // centre plane's stage is released afterwards
+        int sc = 0;
+        auto plane = [&](T (&pu)[V], T (&pv)[V], T (&cu)[V], T (&cv)[V], T (&nu)[V], T (&nv)[V]) -> bool {
+            const int sn = cs;
+            if (!wait_full()) return false;
+            load_centre(nu, nv);
             const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
             const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
             const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
             const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
             if (active) {
-                const int z = z0 + zi;
                 T outu[V], outv[V];
                 const T* bu = ring + sc * stage_elems;
                 const T* bv = bu + a.lay.field_elems;
-                // y neighbours
-                const int om = row > 0 ? a.lay.main_off + (row - 1) * a.tx + xv * V : a.lay.top_off + xv * V;
-                const int op = row + 1 < nvy ? a.lay.main_off + (row + 1) * a.tx + xv * V : a.lay.bot_off + xv * V;
                 T ymu[V], ypu[V], ymv[V], ypv[V];
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
-                const bool has_r = xv * V + V < nvx;
                 T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
-                if (xv == 0 || lane == 0) {
-                    const int oxl = xv > 0 ? a.lay.main_off + moff - 1 : a.lay.left_off + row * V + (V - 1);
-                    xlu = bu[oxl];
-                    xlv = bv[oxl];
-                }
-                if (!has_r || lane == 31) {
-                    const int oxr = has_r ? a.lay.main_off + moff + V : a.lay.right_off + row * V;
-                    xru = bu[oxr];
-                    xrv = bv[oxr];
-                }
-                const int64_t gidx = (int64_t)z * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
+                if (l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
+                if (r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
                 const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
                 gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
                                           xlv, xrv, outu, outv);
@@ -375,13 +364,31 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
             }
             release(sc);
             sc = sn;
-            ++seq;
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                pu[e] = cu[e]; pv[e] = cv[e];
-                cu[e] = nu[e]; cv[e] = nv[e];
-            }
+            advance();
+            gidx += LL;
+            return true;
+        };
+
+        // plane z0 - 1: centre values only
+        if (!wait_full()) return;
+        load_centre(qu[0], qv[0]);
+        release(cs);
+        advance();
+        // plane z0
+        sc = cs;
+        if (!wait_full()) return;
+        load_centre(qu[1], qv[1]);
+        advance();
+
+        int zi = 0;
+        for (; zi + 3 <= nz; zi += 3) {
+            if (!plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2])) return;
+            if (!plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0])) return;
+            if (!plane(qu[2], qv[2], qu[0], qv[0], qu[1], qv[1])) return;
         }
+        // remainder (each tile reloads planes z0 - 1 and z0 into q0, q1)
+        if (zi < nz && !plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2])) return;
+        if (zi + 1 < nz && !plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0])) return;
         release(sc);  // plane z0 + nz (only its centre was used)
         if (abort_flag) return;
     }

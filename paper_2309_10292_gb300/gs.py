@@ -77,6 +77,7 @@ _SIGS = {
     "gs_batch_set_step": [_vp, _i64],
     "gs_batch_sync": [_vp],
     "gs_batch_set_fault": [_vp, _i, _u64],
+    "gs_batch_set_plan": [_vp, _i, _i],
     "gs_batch_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                       ctypes.POINTER(_i64)],
     "gs_batch_destroy": [_vp],
@@ -337,6 +338,10 @@ def gs_batch_sync(b):
 
 def gs_batch_set_fault(b, mode: int, timeout_ns: int = 2_000_000_000):
     _check(lib().gs_batch_set_fault(b, mode, timeout_ns), "gs_batch_set_fault")
+
+
+def gs_batch_set_plan(b, tile_z: int, stages: int):
+    _check(lib().gs_batch_set_plan(b, tile_z, stages), "gs_batch_set_plan")
 
 
 def gs_batch_info(b) -> dict:

@@ -153,3 +153,24 @@ def test_batch_argument_errors():
     with pytest.raises(gs.GsError):
         gs.gs_batch_read(b.handle, 0, gs.GS_U, np.empty(5, dtype=np.float32))
     b.close()
+
+
+@pytest.mark.parametrize("tz,stages", [(3, 3), (16, 4), (64, 6), (256, 8)])
+def test_batch_plan_changes_no_bits(tz, stages):
+    """Any z-chunk / ring depth evolves every instance bit for bit like the default plan."""
+    ref, Ls, _, _ = small_batch("f32")
+    ref.step(13)
+    b, _, _, _ = small_batch("f32")
+    gs.gs_batch_set_plan(b.handle, tz, stages)
+    b.step(13)
+    for i in range(len(Ls)):
+        ur, vr = ref.read(i)
+        ub, vb = b.read(i)
+        np.testing.assert_array_equal(ub, ur)
+        np.testing.assert_array_equal(vb, vr)
+    for bad in [(0, 6), (257, 6), (32, 2), (32, 9)]:
+        with pytest.raises(gs.GsError):
+            gs.gs_batch_set_plan(b.handle, *bad)
+    b.step(2)  # still usable after the rejected plans
+    ref.close()
+    b.close()
