@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Gray-Scott GCUPS & % HBM peak; surrogate/batched vs plain time at fixed error"
 PARAMS = dict(Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0)
 L_MAIN, NSTEPS, NOISE, SEED = 512, 1000, 0.1, 42
-KERNEL_SRC = os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", "gs_stencil.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", f) for f in ("gs_stencil.cu", "gs_common.cuh")]
 PROFILE = os.path.join(ROOT, "profiles", "gs_zmarch_f32_L512.md")
 
 
@@ -69,7 +69,10 @@ def load_peaks():
 
 
 def kernel_digest() -> str:
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():

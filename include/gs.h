@@ -140,6 +140,11 @@ typedef struct gs_plan {
 /* Set every field of a plan (stages 0 = default).  GS_EINVAL as gs_set_plan. */
 int gs_set_plan_full(gs_sim* sim, const gs_plan* plan);
 
+/* The current plan, every field (stages 0 for kernels without a TMA ring;
+ * us_per_step is the tuner's time for it, or 0 if it was set by hand).
+ * GS_EINVAL if sim or out is NULL. */
+int gs_get_plan_full(gs_sim* sim, gs_plan* out);
+
 /* Autotuner: time every candidate plan valid for this grid — the plain
  * kernel; z-march tiles x z-chunks x ring depths; for FP32, temporal
  * blocking at depths 2-4 with several tiles — over `steps_per_trial` steps

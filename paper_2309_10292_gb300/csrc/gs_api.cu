@@ -89,6 +89,7 @@ struct gs_sim {
     int64_t launches = 0;
     uint64_t timeout_ns = 2000000000ull;
     int fault = 0;
+    double plan_us = 0.0;  // the tuner's time for the current plan (0: set by hand)
 };
 
 static bool finite_params(double a, double b, double c, double d, double e, double f)
@@ -407,13 +408,17 @@ static int apply_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z,
 int gs_set_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z, int depth)
 {
     if (!s) return fail(GS_EINVAL, "sim is NULL");
-    return apply_plan(s, kernel, tile_x, tile_y, tile_z, depth, 0);
+    const int rc = apply_plan(s, kernel, tile_x, tile_y, tile_z, depth, 0);
+    if (!rc) s->plan_us = 0.0;
+    return rc;
 }
 
 int gs_set_plan_full(gs_sim* s, const gs_plan* p)
 {
     if (!s || !p) return fail(GS_EINVAL, "NULL argument");
-    return apply_plan(s, p->kernel, p->tile_x, p->tile_y, p->tile_z, p->depth, p->stages);
+    const int rc = apply_plan(s, p->kernel, p->tile_x, p->tile_y, p->tile_z, p->depth, p->stages);
+    if (!rc) s->plan_us = 0.0;
+    return rc;
 }
 
 static gs_plan current_plan(gs_sim* s)
@@ -499,6 +504,7 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
     s->t = t0;
     const gs_plan keep = (!rc && win.us_per_step >= 0) ? win : saved_plan;
     int rc2 = apply_plan(s, keep.kernel, keep.tile_x, keep.tile_y, keep.tile_z, keep.depth, keep.stages);
+    if (!rc && !rc2) s->plan_us = keep.us_per_step;
     if (bu) cudaFree(bu);
     if (bv) cudaFree(bv);
     if (e0) cudaEventDestroy(e0);
@@ -520,6 +526,14 @@ int gs_get_plan(gs_sim* s, int* kernel, int* tx, int* ty, int* tz, int* depth)
     if (ty) *ty = z ? pl.ty : 0;
     if (tz) *tz = z ? pl.tz : 0;
     if (depth) *depth = z ? pl.depth : 1;
+    return GS_OK;
+}
+
+int gs_get_plan_full(gs_sim* s, gs_plan* out)
+{
+    if (!s || !out) return fail(GS_EINVAL, "sim or out is NULL");
+    *out = current_plan(s);
+    out->us_per_step = s->plan_us;
     return GS_OK;
 }
 

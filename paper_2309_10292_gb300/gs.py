@@ -58,6 +58,7 @@ _SIGS = {
     "gs_set_step": [_vp, _i64],
     "gs_set_plan": [_vp, _i, _i, _i, _i, _i],
     "gs_get_plan": [_vp] + [ctypes.POINTER(_i)] * 5,
+    "gs_get_plan_full": [_vp, _vp],
     "gs_sync": [_vp],
     "gs_set_plan_full": [_vp, _vp],
     "gs_autotune": [_vp, _i, _vp, _i, ctypes.POINTER(_i), _vp],
@@ -249,6 +250,12 @@ def gs_set_plan_full(sim, plan: dict):
     p = GsPlan(**{k: plan[k] for k in ("kernel", "tile_x", "tile_y", "tile_z", "depth", "stages")
                   if k in plan})
     _check(lib().gs_set_plan_full(sim, ctypes.byref(p)), "gs_set_plan_full")
+
+
+def gs_get_plan_full(sim) -> dict:
+    p = GsPlan()
+    _check(lib().gs_get_plan_full(sim, ctypes.byref(p)), "gs_get_plan_full")
+    return p.as_dict()
 
 
 def gs_autotune(sim, steps_per_trial: int = 12, max_results: int = 256):
@@ -662,7 +669,8 @@ class GrayScott:
 
     @property
     def plan(self) -> dict:
-        return gs_get_plan(self.handle)
+        """Every field of the current plan (gs_get_plan_full)."""
+        return gs_get_plan_full(self.handle)
 
     def autotune(self, steps_per_trial: int = 12):
         """Pick the fastest plan for this grid (state is left unchanged)."""

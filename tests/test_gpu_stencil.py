@@ -278,7 +278,7 @@ def test_autotune_restores_state_and_keeps_fastest_plan(dtype):
     assert len(trials) > 3
     fastest = min(trials, key=lambda r: r["us_per_step"])
     assert best["us_per_step"] == fastest["us_per_step"]
-    assert a.plan["kernel"] == best["kernel"]
+    assert a.plan == best  # every field, the tuner's time included
     kinds = {r["kernel"] for r in trials}
     assert gs.GS_KERNEL_NAIVE in kinds and gs.GS_KERNEL_ZMARCH in kinds
     if dtype == "f32":
@@ -290,3 +290,5 @@ def test_autotune_restores_state_and_keeps_fastest_plan(dtype):
     ur, vr = ref.read()
     np.testing.assert_array_equal(ua, ur)
     np.testing.assert_array_equal(va, vr)
+    a.set_plan(best["kernel"], best["tile_x"], best["tile_y"], best["tile_z"], best["depth"])
+    assert a.plan["us_per_step"] == 0.0  # a plan set by hand carries no tuner time
