@@ -514,14 +514,20 @@ namespace gs {
 // matrix row per cell and chunk.  The A operand of tap (dz, dy, dx) for
 // output row r is then 128 consecutive cells starting at (row r+1+dy, cell
 // 1+dx) of the dz slab: a descriptor offset, no data movement (LBO = one
-// chunk plane, SBO = 8 cells).  Weights (B, K-major [tap][chunk][n][8]) stay
-// in shared memory.  Thread 0 issues tcgen05.mma (M=128, N=32/16, K=16) into
-// 4 TMEM accumulators (one per output row), commits once after the dz=-1
-// taps (that slab is then refilled with plane z+2 by cp.async while the rest
-// of the MMAs run) and once at the end; the 4 warps read their 32 TMEM lanes
-// each (tcgen05.ld) and apply the epilogue.  Every wait is bounded; on a
-// timeout the CTA records it, lets its own MMAs and copies finish and frees
-// its TMEM.
+// chunk plane, SBO = 8 cells).  Weights (B) stay in shared memory, K-major
+// [dz][dx][chunk][n][8] with n = (2 - (dy + 1)) * NT + cout: for a fixed
+// (dz, dx) the three dy taps sit side by side along N.  One input slab row
+// feeds output rows row-2 (dy = +1), row-1 (dy = 0) and row (dy = -1), whose
+// accumulators are adjacent in TMEM (one per output row), so a single MMA
+// with N = 3 NT (fewer at the slab's edge rows) covers all three: half the
+// MMAs and half the A-operand reads of one MMA per (row, tap).  Thread 0
+// issues tcgen05.mma (M=128, N=NT..3NT, K=16); the first MMAs into a fresh
+// accumulator set (slab rows 5 and 2, which together touch every row once)
+// overwrite, the rest accumulate.  It commits once after the dz=-1 taps (that
+// slab is then refilled with plane z+2 by cp.async while the rest of the MMAs
+// run) and once at the end; the 4 warps read their 32 TMEM lanes each
+// (tcgen05.ld) and apply the epilogue.  Every wait is bounded; on a timeout
+// the CTA records it, lets its own MMAs and copies finish and frees its TMEM.
 
 constexpr int kTcThreads = 128;
 constexpr int kTcRows = 4;
@@ -532,7 +538,7 @@ constexpr int kTcZChunk = 16;
 
 struct ConvTcArgs {
     const bf16* in;     // [N][L^3][CINP]
-    const bf16* w;      // [27][CINP/8][NT][8]
+    const bf16* w;      // [3 dz][3 dx][CINP/8][3 NT][8] (see gs_wprep_tc_kernel)
     const float* bias;  // [>= NT] fp32 (padded with zeros)
     int N, L;
     const bf16* res;    // unused (the residual comes from the centre slab)
@@ -627,16 +633,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
     constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256);
     extern __shared__ __align__(128) unsigned char smem_tc[];
-    __shared__ __align__(8) uint64_t bar_slab, bar_done[2];
+    __shared__ __align__(8) uint64_t bar_slab, bar_done[2], bar_fin;
     __shared__ uint32_t tmem_base_s;
-    __shared__ volatile int abort_s;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int L = a.L;
     const long long L3 = (long long)L * L * L;
     const uint32_t sbase = gs_smem_addr(smem_tc);
     const uint32_t wbase = sbase + 3 * SLAB;
-    const uint32_t idesc = tc_idesc(NT);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gs_smem_addr(&tmem_base_s)),
@@ -648,7 +652,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
         gs_mbar_init(&bar_slab, 1);
         gs_mbar_init(&bar_done[0], 1);
         gs_mbar_init(&bar_done[1], 1);
-        abort_s = 0;
+        gs_mbar_init(&bar_fin, 1);
         gs_fence_mbar_init();
     }
     for (uint32_t i = tid; i < WBYTES / 16; i += kTcThreads) cp16(wbase + i * 16, a.w + (size_t)i * 8);
@@ -662,7 +666,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
     const int nzc = (L + kTcZChunk - 1) / kTcZChunk;
     const long long units = (long long)a.N * nyg * nseg * nzc;
     uint32_t ph_slab = 0, ph_done[2] = {0, 0};  // completed phases seen, per barrier
-    int pending = 0;                            // accumulator sets committed but not yet consumed (0..2)
     bool failed = false;
 
     auto load_slab = [&](int slot, int n, int zz, int y0, int x0) {
@@ -725,17 +728,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
         }
     };
 
-    // uniform bounded wait on an accumulator set's completion
-    auto wait_done = [&](int set) -> bool {
-        const int to = __syncthreads_or(!gs_mbar_wait(&bar_done[set], ph_done[set] & 1, a.timeout_ns));
-        if (to) return false;
-        ph_done[set] += 1;
-        --pending;
-        tc_fence_after();
-        return true;
+    // bounded wait, decided uniformly by the whole CTA (also a barrier)
+    auto wait_uniform = [&](uint64_t* bar, uint32_t parity) -> bool {
+        return !__syncthreads_or(!gs_mbar_wait(bar, parity, a.timeout_ns));
     };
 
-    int it = 0;  // items issued by this CTA (accumulator set = it & 1)
+    // thread 0: the MMAs of one dz group of an item into accumulator set
+    // `set`, operand A from the slab in `slot`
+    auto issue_group = [&](int set, int dzi, int slot) {
+        // descriptors: the start-address field is the low 14 bits, so a
+        // descriptor plus (byte offset >> 4) addresses the shifted operand
+        constexpr uint32_t WCH = 3 * NT * 16;  // bytes of one weight chunk plane
+        constexpr int kOrder[kTcSlabRows] = {5, 2, 0, 1, 3, 4};
+        const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
+        const uint32_t idn[3] = {tc_idesc(NT), tc_idesc(2 * NT), tc_idesc(3 * NT)};
+        const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
+#pragma unroll
+        for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+            for (int kk = 0; kk < CINP / 16; ++kk) {
+                const uint64_t bk = tc_desc(wbase + (uint32_t)((dzi * 3 + dxi) * NCH + 2 * kk) * WCH, WCH, 128);
+                const uint64_t ak = adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)dxi;
+                // slab rows 5 and 2 first: together they touch every output row once
+#pragma unroll
+                for (int q = 0; q < kTcSlabRows; ++q) {
+                    const int sr = kOrder[q];
+                    const int rlo = sr - 2 > 0 ? sr - 2 : 0;
+                    const int rhi = sr < kTcRows - 1 ? sr : kTcRows - 1;
+                    const int b0 = 2 - sr + rlo;  // first dy block (dy = +1 - block)
+                    const bool fresh = dzi == 0 && dxi == 0 && kk == 0 && q < 2;
+                    tc_mma(dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * kTcHC),
+                           bk + (uint64_t)((b0 * NT * 16) >> 4), idn[rhi - rlo], fresh ? 0u : 1u);
+                }
+            }
+    };
+
+    // Software pipeline over the items of a unit (item q = output plane
+    // z0 + q; plane z0 - 1 + i lives in slab slot i % 3).  Item q+1's taps on
+    // planes z and z+1 (resident) are issued as soon as the accumulator set
+    // of item q-1 has been drained; only its dz=+1 taps wait for plane z+2,
+    // whose load starts when item q's dz=-1 taps (the slot's last reader) are
+    // done.  The tensor pipe thus always holds more than an item of work
+    // while the CTA runs epilogues and loads.  Each barrier has at most one
+    // phase outstanding when it is waited on.
+    int it = 0;  // items started by this CTA before the current unit (set = item & 1)
     for (long long unit = blockIdx.x; unit < units && !failed; unit += gridDim.x) {
         const int zc = (int)(unit % nzc);
         long long r0 = unit / nzc;
@@ -749,81 +785,79 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
         load_slab(0, n, z0 - 1, y0, x0);
         load_slab(1, n, z0, y0, x0);
         load_slab(2, n, z0 + 1, y0, x0);
-        for (int q = 0; q < nz; ++q, ++it) {
+        cp_wait_all();
+        gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_group(it & 1, 0, 0);
+            if (nz > 1) tc_commit(&bar_slab);
+            issue_group(it & 1, 1, 1);
+            issue_group(it & 1, 2, 2);
+            tc_commit(&bar_done[it & 1]);
+        }
+        for (int q = 0; q < nz; ++q) {
             const int z = z0 + q;
-            const int set = it & 1;
-            cp_wait_all();
-            gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
-            tc_fence_before();
-            __syncthreads();
-            const int sm1 = q % 3, s0 = (q + 1) % 3, sp1 = (q + 2) % 3;
-            if (tid == 0) {
-                tc_fence_after();
-                // descriptors: the start-address field is the low 14 bits, so a
-                // descriptor plus (byte offset >> 4) addresses the shifted operand
-                const uint64_t bdesc0 = tc_desc(wbase, NT * 16, 128);
-                const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
-#pragma unroll 1
-                for (int dzi = 0; dzi < 3; ++dzi) {
-                    const int slot = dzi == 0 ? sm1 : (dzi == 1 ? s0 : sp1);
-                    const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
-#pragma unroll 1
-                    for (int r = 0; r < kTcRows; ++r) {
-                        const uint64_t ar = adz + (uint64_t)(r * kTcHC);  // (r * HC * 16 B) >> 4
-                        const uint32_t d = dset + (uint32_t)(r * NT);
-#pragma unroll
-                        for (int dyi = 0; dyi < 3; ++dyi)
-#pragma unroll
-                            for (int dxi = 0; dxi < 3; ++dxi)
-#pragma unroll
-                                for (int kk = 0; kk < CINP / 16; ++kk) {
-                                    const int tap = dzi * 9 + dyi * 3 + dxi;
-                                    const uint64_t ad = ar + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(dyi * kTcHC + dxi);
-                                    const uint64_t bd = bdesc0 + (uint64_t)(((tap * NCH + 2 * kk) * NT * 16) >> 4);
-                                    tc_mma(d, ad, bd, idesc, (dzi | dyi | dxi | kk) ? 1u : 0u);
-                                }
-                    }
-                    if (dzi == 0) tc_commit(&bar_slab);
-                }
-                tc_commit(&bar_done[set]);
-            }
-            ++pending;
-            // meanwhile: the epilogue of the previous item (other accumulator set)
+            const int set = (it + q) & 1;
             if (q > 0) {
-                if (!wait_done(set ^ 1)) {
+                // drain item q-1 (centre plane z-1 in slot q % 3)
+                if (!wait_uniform(&bar_done[set ^ 1], ph_done[set ^ 1] & 1)) {
                     failed = true;
                     break;
                 }
-                epilogue(set ^ 1, q % 3, n, z - 1, y0, x0);  // centre of item q-1 = plane z-1 = slot q % 3
+                ph_done[set ^ 1] += 1;
+                tc_fence_after();
+                epilogue(set ^ 1, q % 3, n, z - 1, y0, x0);
             }
-            // the dz=-1 slab of this item is free once its MMAs are done (and the
-            // epilogue above has read its centre cells): refill it with plane z+2
-            const int to = __syncthreads_or(!gs_mbar_wait(&bar_slab, ph_slab & 1, a.timeout_ns));
-            if (to) {
+            tc_fence_before();
+            __syncthreads();  // set ^ 1 drained; slot q % 3 no longer read by the epilogue
+            if (q + 1 >= nz) break;
+            // plane z+2 into slot q % 3 once item q's dz=-1 taps are done
+            if (!wait_uniform(&bar_slab, ph_slab & 1)) {
                 failed = true;
                 break;
             }
             ph_slab += 1;
-            if (q + 1 < nz) load_slab(sm1, n, z + 2, y0, x0);
+            load_slab(q % 3, n, z + 2, y0, x0);
+            if (tid == 0) {
+                tc_fence_after();
+                issue_group(set ^ 1, 0, (q + 1) % 3);
+                if (q + 2 < nz) tc_commit(&bar_slab);
+                issue_group(set ^ 1, 1, (q + 2) % 3);
+            }
+            cp_wait_all();
+            gs_fence_proxy_async();
             tc_fence_before();
-            __syncthreads();  // TMEM reads of the epilogue done before the next MMAs reuse that set
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_group(set ^ 1, 2, q % 3);
+                tc_commit(&bar_done[set ^ 1]);
+            }
         }
         if (failed) break;
-        // the last item of the unit
-        if (!wait_done((it - 1) & 1)) {
+        // drain the unit's last item (centre plane z0 + nz - 1 in slot nz % 3)
+        const int lset = (it + nz - 1) & 1;
+        if (!wait_uniform(&bar_done[lset], ph_done[lset] & 1)) {
             failed = true;
             break;
         }
-        epilogue((it - 1) & 1, (nz - 1 + 1) % 3, n, z0 + nz - 1, y0, x0);
+        ph_done[lset] += 1;
+        tc_fence_after();
+        epilogue(lset, nz % 3, n, z0 + nz - 1, y0, x0);
         tc_fence_before();
         __syncthreads();
+        it += nz;
     }
     // nothing of this CTA may be in flight when its TMEM and shared memory go
     cp_wait_all();
     if (failed && tid == 0) {
+        // one more commit tracks every MMA this thread issued (fixed budget:
+        // issued MMAs always complete)
         gs_report(a.err, GS_DERR_TIMEOUT);
-        for (int s2 = 0; s2 < 2; ++s2)
-            if (pending > 0) gs_mbar_wait(&bar_done[s2], ph_done[s2] & 1, 2000000000ull);
+        tc_commit(&bar_fin);
+        gs_mbar_wait(&bar_fin, 0, 2000000000ull);
     }
     tc_fence_before();
     __syncthreads();
@@ -833,15 +867,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
     }
 }
 
-// fp32 master weights [27][cin][cout] -> tcgen05 B layout [27][CINP/8][NT][8] (zero padded)
+// fp32 master weights [27][cin][cout] (tap = 9 dz + 3 dy + dx, each + 1) ->
+// tcgen05 B layout [3 dz][3 dx][cinp/8][3 nt][8], n = (2 - (dy + 1)) * nt + cout
+// (zero padded)
 __global__ void gs_wprep_tc_kernel(const float* __restrict__ w, int cin, int cout, int cinp, int nt, bf16* __restrict__ wt)
 {
-    const int total = 27 * cinp * nt;
+    const int nn = 3 * nt;
+    const int total = 9 * cinp * nn;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int e = i % 8;
-        const int co = (i / 8) % nt;
-        const int j = (i / (8 * nt)) % (cinp / 8);
-        const int tap = i / (8 * nt * (cinp / 8));
+        const int n = (i / 8) % nn;
+        const int j = (i / (8 * nn)) % (cinp / 8);
+        const int dxi = (i / (8 * nn * (cinp / 8))) % 3;
+        const int dzi = i / (8 * nn * (cinp / 8) * 3);
+        const int dyi = 2 - n / nt;
+        const int co = n % nt;
+        const int tap = dzi * 9 + dyi * 3 + dxi;
         const int ci = j * 8 + e;
         const float val = (ci < cin && co < cout) ? w[((size_t)tap * cin + ci) * cout + co] : 0.f;
         wt[i] = __float2bfloat16_rn(val);
@@ -864,7 +905,7 @@ struct gs_surr {
     size_t woff[kSurrLayers] = {}, boff[kSurrLayers] = {};
     bf16* wf[kSurrLayers] = {};  // forward layout
     bf16* wd[kSurrLayers] = {};  // data-gradient layout (layers 1..5)
-    bf16* wt[kSurrLayers] = {};  // tcgen05 B layout [27][CINP/8][NT][8]
+    bf16* wt[kSurrLayers] = {};  // tcgen05 B layout [3 dz][3 dx][CINP/8][3 NT][8]
     bool wdirty = true;
     int backend = 0;             // 0 auto (tcgen05 when L % 128 == 0), 1 mma.sync, 2 tcgen05
     int* d_err = nullptr;

@@ -111,3 +111,39 @@ def evaluate(surr: "gs.Surrogate", pool: TrajectoryPool, pairs: int = 4):
         mx_id.append(float(ide.abs().max()))
     return {"rms_network": float(np.mean(err_net)), "rms_persistence": float(np.mean(err_id)),
             "max_network": float(np.max(mx_net)), "max_persistence": float(np.max(mx_id))}
+
+
+def time_forward(L: int = 256, reps: int = 5, backend: str = "tcgen05", seed: int = 0) -> dict:
+    """Time one network application on a random L^3 state (seeded weights with
+    a non-zero last layer); returns ms per application and TFLOP/s."""
+    import torch
+    be = {"auto": gs.GS_SURR_AUTO, "mma": gs.GS_SURR_MMA, "tcgen05": gs.GS_SURR_TCGEN05}[backend]
+    s = gs.Surrogate(inputs.surrogate_init_params(seed=seed, last_scale=1.0))
+    gs.gs_surr_set_backend(s.handle, be)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    u = torch.rand((1, L, L, L), device="cuda", generator=g)
+    v = torch.rand((1, L, L, L), device="cuda", generator=g) * 0.3
+    s.forward(u, v, [0.02], [0.05])
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        s.forward(u, v, [0.02], [0.05])
+    b.record(st)
+    gs.gs_surr_sync(s.handle)
+    ms = a.elapsed_time(b) / reps
+    flop = 2.0 * 27 * (4 * 32 + 4 * 32 * 32 + 32 * 2) * L ** 3
+    s.close()
+    return {"L": L, "backend": backend, "ms": ms, "tflops": flop / ms / 1e9}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="time the surrogate's forward pass")
+    ap.add_argument("--L", type=int, default=256)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--backend", default="tcgen05", choices=["auto", "mma", "tcgen05"])
+    args = ap.parse_args()
+    print(json.dumps(time_forward(args.L, args.reps, args.backend)))
