@@ -529,7 +529,10 @@ namespace gs {
 // (tcgen05.ld) and apply the epilogue.  Every wait is bounded; on a timeout
 // the CTA records it, lets its own MMAs and copies finish and frees its TMEM.
 
-constexpr int kTcThreads = 128;
+constexpr int kTcEpiWarps = 4;                  // warps 0-3: epilogue (TMEM lanes 32w..32w+31)
+constexpr int kTcMmaWarp = 4;                   // lane 0 issues the MMAs
+constexpr int kTcProdWarp = 5;                  // stages the input planes
+constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);
 constexpr int kTcRows = 4;
 constexpr int kTcCells = 128;
 constexpr int kTcHC = kTcCells + 2;       // cells per slab row (with halo)
@@ -632,11 +635,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
     constexpr uint32_t WBYTES = 27 * NCH * NT * 16;
     constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256);
+    constexpr int kCellsPerLane = (kTcHC + 31) / 32;
     extern __shared__ __align__(128) unsigned char smem_tc[];
-    __shared__ __align__(8) uint64_t bar_slab, bar_done[2], bar_fin;
+    // slab_full: 32 producer lanes per plane; slab_empty: the MMA commit after
+    // the plane's last tap plus one arrival per epilogue warp; acc_full: the
+    // commit after an item's last MMA; acc_empty: one arrival per epilogue warp
+    __shared__ __align__(8) uint64_t slab_full[3], slab_empty[3], acc_full[2], acc_empty[2], bar_fin;
     __shared__ uint32_t tmem_base_s;
+    __shared__ float bias_s[NT];
+    __shared__ volatile int abort_s;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = a.L;
     const long long L3 = (long long)L * L * L;
     const uint32_t sbase = gs_smem_addr(smem_tc);
@@ -649,13 +658,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        gs_mbar_init(&bar_slab, 1);
-        gs_mbar_init(&bar_done[0], 1);
-        gs_mbar_init(&bar_done[1], 1);
+        for (int i = 0; i < 3; ++i) {
+            gs_mbar_init(&slab_full[i], 32);
+            gs_mbar_init(&slab_empty[i], 1 + kTcEpiWarps);
+        }
+        for (int i = 0; i < 2; ++i) {
+            gs_mbar_init(&acc_full[i], 1);
+            gs_mbar_init(&acc_empty[i], kTcEpiWarps);
+        }
         gs_mbar_init(&bar_fin, 1);
+        abort_s = 0;
         gs_fence_mbar_init();
     }
+    if (tid < NT) bias_s[tid] = a.bias[tid];
     for (uint32_t i = tid; i < WBYTES / 16; i += kTcThreads) cp16(wbase + i * 16, a.w + (size_t)i * 8);
+    cp_wait_all();
+    gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -665,200 +683,237 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
     const int nyg = L / kTcRows;
     const int nzc = (L + kTcZChunk - 1) / kTcZChunk;
     const long long units = (long long)a.N * nyg * nseg * nzc;
-    uint32_t ph_slab = 0, ph_done[2] = {0, 0};  // completed phases seen, per barrier
-    bool failed = false;
-
-    auto load_slab = [&](int slot, int n, int zz, int y0, int x0) {
-        const uint32_t dst0 = sbase + slot * SLAB;
-        const int zw = (zz % L + L) % L;
-        for (int i = tid; i < kTcSlabRows * kTcHC * NCH; i += kTcThreads) {
-            const int j = i % NCH;
-            const int c = (i / NCH) % kTcHC;
-            const int yi = i / (NCH * kTcHC);
-            const int yy = (y0 - 1 + yi + L) % L;
-            const int xx = (x0 - 1 + c + L) % L;
-            const bf16* src = a.in + ((size_t)n * L3 + ((size_t)zw * L + yy) * L + xx) * CINP + j * 8;
-            cp16(dst0 + j * PLANE + (uint32_t)(yi * kTcHC + c) * 16, src);
-        }
+    struct Unit {
+        int n, x0, y0, z0, nz;
     };
-
-    // epilogue of one finished item: accumulator set `set`, centre plane in slot `cslot`
-    auto epilogue = [&](int set, int cslot, int n, int z, int y0, int x0) {
-        const int x = x0 + tid;
-#pragma unroll 1
-        for (int r = 0; r < kTcRows; ++r) {
-            float acc[NT];
-            tc_ld<NT>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(set * ACC_COLS + r * NT), acc);
-            const int y = y0 + r;
-            const size_t cell = (size_t)n * L3 + ((size_t)z * L + y) * L + x;
-            if constexpr (EPI == EPI_LAST) {
-                a.ou[cell] = a.su[cell] + (acc[0] + a.bias[0]);
-                a.ov[cell] = a.sv[cell] + (acc[1] + a.bias[1]);
-            } else {
-                const unsigned char* ctr = smem_tc + cslot * SLAB + (uint32_t)((r + 1) * kTcHC + 1 + tid) * 16;
-#pragma unroll
-                for (int j = 0; j < NT / 8; ++j) {
-                    float h[8], zv[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        zv[e] = acc[j * 8 + e] + a.bias[j * 8 + e];
-                        h[e] = fmaxf(zv[e], 0.f);
-                    }
-                    if constexpr (EPI == EPI_HIDDEN) {
-                        const uint4 rv = *reinterpret_cast<const uint4*>(ctr + j * PLANE);
-                        const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            h[2 * e] = __bfloat162float(rb[e].x) + h[2 * e];
-                            h[2 * e + 1] = __bfloat162float(rb[e].y) + h[2 * e + 1];
-                        }
-                    }
-                    uint4 ho, zo;
-                    __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(&ho);
-                    __nv_bfloat162* zb = reinterpret_cast<__nv_bfloat162*>(&zo);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        hb[e] = __floats2bfloat162_rn(h[2 * e], h[2 * e + 1]);
-                        zb[e] = __floats2bfloat162_rn(zv[2 * e], zv[2 * e + 1]);
-                    }
-                    *reinterpret_cast<uint4*>(a.out + cell * 32 + j * 8) = ho;
-                    if (a.zout) *reinterpret_cast<uint4*>(a.zout + cell * 32 + j * 8) = zo;
-                }
-            }
-        }
-    };
-
-    // bounded wait, decided uniformly by the whole CTA (also a barrier)
-    auto wait_uniform = [&](uint64_t* bar, uint32_t parity) -> bool {
-        return !__syncthreads_or(!gs_mbar_wait(bar, parity, a.timeout_ns));
-    };
-
-    // thread 0: the MMAs of one dz group of an item into accumulator set
-    // `set`, operand A from the slab in `slot`
-    auto issue_group = [&](int set, int dzi, int slot) {
-        // descriptors: the start-address field is the low 14 bits, so a
-        // descriptor plus (byte offset >> 4) addresses the shifted operand
-        constexpr uint32_t WCH = 3 * NT * 16;  // bytes of one weight chunk plane
-        constexpr int kOrder[kTcSlabRows] = {5, 2, 0, 1, 3, 4};
-        const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
-        const uint32_t idn[3] = {tc_idesc(NT), tc_idesc(2 * NT), tc_idesc(3 * NT)};
-        const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
-#pragma unroll
-        for (int dxi = 0; dxi < 3; ++dxi)
-#pragma unroll
-            for (int kk = 0; kk < CINP / 16; ++kk) {
-                const uint64_t bk = tc_desc(wbase + (uint32_t)((dzi * 3 + dxi) * NCH + 2 * kk) * WCH, WCH, 128);
-                const uint64_t ak = adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)dxi;
-                // slab rows 5 and 2 first: together they touch every output row once
-#pragma unroll
-                for (int q = 0; q < kTcSlabRows; ++q) {
-                    const int sr = kOrder[q];
-                    const int rlo = sr - 2 > 0 ? sr - 2 : 0;
-                    const int rhi = sr < kTcRows - 1 ? sr : kTcRows - 1;
-                    const int b0 = 2 - sr + rlo;  // first dy block (dy = +1 - block)
-                    const bool fresh = dzi == 0 && dxi == 0 && kk == 0 && q < 2;
-                    tc_mma(dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * kTcHC),
-                           bk + (uint64_t)((b0 * NT * 16) >> 4), idn[rhi - rlo], fresh ? 0u : 1u);
-                }
-            }
-    };
-
-    // Software pipeline over the items of a unit (item q = output plane
-    // z0 + q; plane z0 - 1 + i lives in slab slot i % 3).  Item q+1's taps on
-    // planes z and z+1 (resident) are issued as soon as the accumulator set
-    // of item q-1 has been drained; only its dz=+1 taps wait for plane z+2,
-    // whose load starts when item q's dz=-1 taps (the slot's last reader) are
-    // done.  The tensor pipe thus always holds more than an item of work
-    // while the CTA runs epilogues and loads.  Each barrier has at most one
-    // phase outstanding when it is waited on.
-    int it = 0;  // items started by this CTA before the current unit (set = item & 1)
-    for (long long unit = blockIdx.x; unit < units && !failed; unit += gridDim.x) {
+    auto decode = [&](long long unit) {
+        Unit u;
         const int zc = (int)(unit % nzc);
         long long r0 = unit / nzc;
         const int seg = (int)(r0 % nseg);
         r0 /= nseg;
-        const int yg = (int)(r0 % nyg);
-        const int n = (int)(r0 / nyg);
-        const int x0 = seg * kTcCells, y0 = yg * kTcRows;
-        const int z0 = zc * kTcZChunk;
-        const int nz = min(kTcZChunk, L - z0);
-        load_slab(0, n, z0 - 1, y0, x0);
-        load_slab(1, n, z0, y0, x0);
-        load_slab(2, n, z0 + 1, y0, x0);
-        cp_wait_all();
-        gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_group(it & 1, 0, 0);
-            if (nz > 1) tc_commit(&bar_slab);
-            issue_group(it & 1, 1, 1);
-            issue_group(it & 1, 2, 2);
-            tc_commit(&bar_done[it & 1]);
+        u.y0 = (int)(r0 % nyg) * kTcRows;
+        u.n = (int)(r0 / nyg);
+        u.x0 = seg * kTcCells;
+        u.z0 = zc * kTcZChunk;
+        u.nz = min(kTcZChunk, L - u.z0);
+        return u;
+    };
+    // bounded wait that also gives up once another role has aborted
+    auto bwait = [&](uint64_t* bar, uint32_t parity) -> bool {
+        if (gs_mbar_try_wait(bar, parity)) return true;
+        const uint64_t t0 = gs_globaltimer();
+        for (;;) {
+#pragma unroll 1
+            for (int i = 0; i < 32; ++i)
+                if (gs_mbar_try_wait(bar, parity)) return true;
+            if (abort_s) return false;
+            if (gs_globaltimer() - t0 > a.timeout_ns) {
+                abort_s = 1;
+                gs_report(a.err, GS_DERR_TIMEOUT);
+                return false;
+            }
         }
-        for (int q = 0; q < nz; ++q) {
-            const int z = z0 + q;
-            const int set = (it + q) & 1;
-            if (q > 0) {
-                // drain item q-1 (centre plane z-1 in slot q % 3)
-                if (!wait_uniform(&bar_done[set ^ 1], ph_done[set ^ 1] & 1)) {
-                    failed = true;
+    };
+
+    if (warp == kTcProdWarp) {
+        // ----------------------------- producer warp -----------------------------
+        // plane z0 - 1 + i of a unit (i = 0 .. nz+1) is global plane g, slot g % 3
+        uint32_t g = 0;
+        bool ok = true;
+        for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+            const Unit u = decode(unit);
+            // wrapped offsets (elements) of this lane's cells and of the 6 rows
+            long long xoff[kCellsPerLane];
+#pragma unroll
+            for (int m = 0; m < kCellsPerLane; ++m) {
+                const int c = lane + 32 * m;
+                xoff[m] = (long long)((u.x0 - 1 + c + L) % L) * CINP;
+            }
+            long long yoff[kTcSlabRows];
+#pragma unroll
+            for (int yi = 0; yi < kTcSlabRows; ++yi) yoff[yi] = (long long)((u.y0 - 1 + yi + L) % L) * L * CINP;
+            for (int i = 0; i < u.nz + 2; ++i, ++g) {
+                const int slot = (int)(g % 3u);
+                if (g >= 3 && !bwait(&slab_empty[slot], ((g / 3u) - 1u) & 1u)) {
+                    ok = false;
                     break;
                 }
-                ph_done[set ^ 1] += 1;
-                tc_fence_after();
-                epilogue(set ^ 1, q % 3, n, z - 1, y0, x0);
-            }
-            tc_fence_before();
-            __syncthreads();  // set ^ 1 drained; slot q % 3 no longer read by the epilogue
-            if (q + 1 >= nz) break;
-            // plane z+2 into slot q % 3 once item q's dz=-1 taps are done
-            if (!wait_uniform(&bar_slab, ph_slab & 1)) {
-                failed = true;
-                break;
-            }
-            ph_slab += 1;
-            load_slab(q % 3, n, z + 2, y0, x0);
-            if (tid == 0) {
-                tc_fence_after();
-                issue_group(set ^ 1, 0, (q + 1) % 3);
-                if (q + 2 < nz) tc_commit(&bar_slab);
-                issue_group(set ^ 1, 1, (q + 2) % 3);
-            }
-            cp_wait_all();
-            gs_fence_proxy_async();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                issue_group(set ^ 1, 2, q % 3);
-                tc_commit(&bar_done[set ^ 1]);
+                const int zw = (u.z0 - 1 + i + L) % L;
+                const bf16* pb = a.in + ((size_t)u.n * L3 + (size_t)zw * L * L) * CINP;
+                const uint32_t dst0 = sbase + slot * SLAB;
+#pragma unroll
+                for (int yi = 0; yi < kTcSlabRows; ++yi)
+#pragma unroll
+                    for (int m = 0; m < kCellsPerLane; ++m) {
+                        const int c = lane + 32 * m;
+                        if (c < kTcHC) {
+                            const bf16* src = pb + yoff[yi] + xoff[m];
+#pragma unroll
+                            for (int j = 0; j < NCH; ++j)
+                                cp16(dst0 + j * PLANE + (uint32_t)(yi * kTcHC + c) * 16, src + j * 8);
+                        }
+                    }
+                cp_wait_all();
+                gs_fence_proxy_async();  // this lane's writes -> visible to the tensor core
+                gs_mbar_arrive(&slab_full[slot]);
             }
         }
-        if (failed) break;
-        // drain the unit's last item (centre plane z0 + nz - 1 in slot nz % 3)
-        const int lset = (it + nz - 1) & 1;
-        if (!wait_uniform(&bar_done[lset], ph_done[lset] & 1)) {
-            failed = true;
-            break;
+    } else if (warp == kTcMmaWarp) {
+        // ------------------------------ MMA issuer -------------------------------
+        if (lane == 0) {
+            // thread 0 of the MMAs of one dz group of an item into accumulator set
+            // `set`, operand A from the slab in `slot`.  Descriptors: the start
+            // address is the low 14 bits, so a descriptor plus (byte offset >> 4)
+            // addresses the shifted operand.
+            auto issue_group = [&](int set, int dzi, int slot) {
+                constexpr uint32_t WCH = 3 * NT * 16;  // bytes of one weight chunk plane
+                constexpr int kOrder[kTcSlabRows] = {5, 2, 0, 1, 3, 4};
+                const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
+                const uint32_t idn[3] = {tc_idesc(NT), tc_idesc(2 * NT), tc_idesc(3 * NT)};
+                const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
+#pragma unroll
+                for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                    for (int kk = 0; kk < CINP / 16; ++kk) {
+                        const uint64_t bk = tc_desc(wbase + (uint32_t)((dzi * 3 + dxi) * NCH + 2 * kk) * WCH, WCH, 128);
+                        const uint64_t ak = adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)dxi;
+                        // slab rows 5 and 2 first: together they touch every output row once
+#pragma unroll
+                        for (int q = 0; q < kTcSlabRows; ++q) {
+                            const int sr = kOrder[q];
+                            const int rlo = sr - 2 > 0 ? sr - 2 : 0;
+                            const int rhi = sr < kTcRows - 1 ? sr : kTcRows - 1;
+                            const int b0 = 2 - sr + rlo;  // first dy block (dy = +1 - block)
+                            const bool fresh = dzi == 0 && dxi == 0 && kk == 0 && q < 2;
+                            tc_mma(dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * kTcHC),
+                                   bk + (uint64_t)((b0 * NT * 16) >> 4), idn[rhi - rlo], fresh ? 0u : 1u);
+                        }
+                    }
+            };
+            uint32_t g = 0, k = 0;  // planes and items seen by this CTA
+            bool ok = true;
+            for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+                const Unit u = decode(unit);
+                const uint32_t gb = g;
+                for (int q = 0; q < u.nz && ok; ++q, ++k) {
+                    const int set = (int)(k & 1u);
+                    if (k >= 2 && !bwait(&acc_empty[set], ((k / 2u) - 1u) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    for (int d = 0; d < 3; ++d) {
+                        // item q reads planes q, q+1, q+2 of the unit (dz = d - 1)
+                        const uint32_t gp = gb + (uint32_t)(q + d);
+                        const int slot = (int)(gp % 3u);
+                        if ((q == 0 || d == 2) && !bwait(&slab_full[slot], (gp / 3u) & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        issue_group(set, d, slot);
+                        // last MMA use of plane q (its dz=-1 taps); of the unit's
+                        // last two planes, the last item's dz = 0 and +1 taps
+                        if (d == 0 || q == u.nz - 1) tc_commit(&slab_empty[slot]);
+                    }
+                    if (!ok) break;
+                    tc_commit(&acc_full[set]);
+                }
+                g = gb + (uint32_t)(u.nz + 2);
+            }
+            if (!ok) {
+                // one more commit tracks every MMA issued (fixed budget: issued
+                // MMAs always complete)
+                tc_commit(&bar_fin);
+                gs_mbar_wait(&bar_fin, 0, 2000000000ull);
+            }
         }
-        ph_done[lset] += 1;
-        tc_fence_after();
-        epilogue(lset, nz % 3, n, z0 + nz - 1, y0, x0);
-        tc_fence_before();
-        __syncthreads();
-        it += nz;
+    } else {
+        // ------------------------- epilogue warps (0-3) --------------------------
+        const int x_in_seg = tid;  // this thread's cell in the 128-cell segment
+        auto epilogue = [&](int set, int cslot, int n, int z, int y0, int x0) {
+            const int x = x0 + x_in_seg;
+#pragma unroll 1
+            for (int r = 0; r < kTcRows; ++r) {
+                float acc[NT];
+                tc_ld<NT>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(set * ACC_COLS + r * NT), acc);
+                const int y = y0 + r;
+                const size_t cell = (size_t)n * L3 + ((size_t)z * L + y) * L + x;
+                if constexpr (EPI == EPI_LAST) {
+                    a.ou[cell] = a.su[cell] + (acc[0] + bias_s[0]);
+                    a.ov[cell] = a.sv[cell] + (acc[1] + bias_s[1]);
+                } else {
+                    const unsigned char* ctr = smem_tc + cslot * SLAB + (uint32_t)((r + 1) * kTcHC + 1 + x_in_seg) * 16;
+#pragma unroll
+                    for (int j = 0; j < NT / 8; ++j) {
+                        float h[8], zv[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            zv[e] = acc[j * 8 + e] + bias_s[j * 8 + e];
+                            h[e] = fmaxf(zv[e], 0.f);
+                        }
+                        if constexpr (EPI == EPI_HIDDEN) {
+                            const uint4 rv = *reinterpret_cast<const uint4*>(ctr + j * PLANE);
+                            const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                h[2 * e] = __bfloat162float(rb[e].x) + h[2 * e];
+                                h[2 * e + 1] = __bfloat162float(rb[e].y) + h[2 * e + 1];
+                            }
+                        }
+                        uint4 ho, zo;
+                        __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(&ho);
+                        __nv_bfloat162* zb = reinterpret_cast<__nv_bfloat162*>(&zo);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            hb[e] = __floats2bfloat162_rn(h[2 * e], h[2 * e + 1]);
+                            zb[e] = __floats2bfloat162_rn(zv[2 * e], zv[2 * e + 1]);
+                        }
+                        *reinterpret_cast<uint4*>(a.out + cell * 32 + j * 8) = ho;
+                        if (a.zout) *reinterpret_cast<uint4*>(a.zout + cell * 32 + j * 8) = zo;
+                    }
+                }
+            }
+        };
+        // warp-uniform bounded wait (lane 0 polls; the warp then synchronises)
+        auto wwait = [&](uint64_t* bar, uint32_t parity) -> bool {
+            int r = 0;
+            if (lane == 0) r = bwait(bar, parity) ? 1 : 0;
+            r = __shfl_sync(0xffffffffu, r, 0);
+            return r != 0;
+        };
+        uint32_t g = 0, k = 0;
+        bool ok = true;
+        for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+            const Unit u = decode(unit);
+            const uint32_t gb = g;
+            __syncwarp();
+            if (lane == 0) gs_mbar_arrive(&slab_empty[gb % 3u]);  // plane 0 of the unit: no epilogue reads it
+            for (int q = 0; q < u.nz; ++q, ++k) {
+                const int set = (int)(k & 1u);
+                const uint32_t gc = gb + (uint32_t)(q + 1);  // centre plane of item q
+                const int cslot = (int)(gc % 3u);
+                if (!wwait(&acc_full[set], (k / 2u) & 1u) || !wwait(&slab_full[cslot], (gc / 3u) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                epilogue(set, cslot, u.n, u.z0 + q, u.y0, u.x0);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    gs_mbar_arrive(&acc_empty[set]);
+                    gs_mbar_arrive(&slab_empty[cslot]);
+                }
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) gs_mbar_arrive(&slab_empty[(gb + (uint32_t)(u.nz + 1)) % 3u]);  // last plane of the unit
+            g = gb + (uint32_t)(u.nz + 2);
+        }
     }
     // nothing of this CTA may be in flight when its TMEM and shared memory go
     cp_wait_all();
-    if (failed && tid == 0) {
-        // one more commit tracks every MMA this thread issued (fixed budget:
-        // issued MMAs always complete)
-        gs_report(a.err, GS_DERR_TIMEOUT);
-        tc_commit(&bar_fin);
-        gs_mbar_wait(&bar_fin, 0, 2000000000ull);
-    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
