@@ -45,7 +45,7 @@ int num_sms()
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::once_flag g_encode_once;
 
-CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     std::call_once(g_encode_once, [] {
         void* fn = nullptr;
@@ -55,16 +55,35 @@ CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box
             q == cudaDriverEntryPointSuccess)
             g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     });
-    if (!g_encode) return CUDA_ERROR_NOT_FOUND;
+    return g_encode;
+}
+
+CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return CUDA_ERROR_NOT_FOUND;
     const size_t esz = elem_size(dtype);
     cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)L};
     cuuint64_t strides[2] = {(cuuint64_t)L * esz, (cuuint64_t)L * L * esz};
     cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    return g_encode(map, dtype == GS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                    3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return enc(map, dtype == GS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+               3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_x)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return CUDA_ERROR_NOT_FOUND;
+    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)planes};
+    cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)L * C * 2, (cuuint64_t)L * L * C * 2};
+    cuuint32_t box[4] = {8, (cuuint32_t)box_x, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
 }  // namespace gs

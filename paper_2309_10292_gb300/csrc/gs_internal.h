@@ -31,6 +31,9 @@ int num_sms();
 
 // Tensor-map encoder obtained from the driver at first use.
 CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y);
+// channels-last bf16 activations [planes][L][L][C] (planes = N * L): boxes of
+// 8 channels x box_x cells x 1 row x 1 plane
+CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_x);
 
 // ---------------------------------------------------------------------------
 // Stencil kernels (gs_stencil.cu)

@@ -535,11 +535,17 @@ constexpr int kTcProdWarp = 5;                  // stages the input planes
 constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);
 constexpr int kTcRows = 4;
 constexpr int kTcCells = 128;
-constexpr int kTcHC = kTcCells + 2;       // cells per slab row (with halo)
 constexpr int kTcSlabRows = kTcRows + 2;  // rows per slab
 constexpr int kTcZChunk = 16;
+// A slab row holds cells x0-8 .. x0+135 (144 cells, 2304 B = 18 x 128 B): three
+// TMA boxes of 8, 128 and 8 cells, each landing on a 128-byte boundary.  Input
+// cell x0 - 1 + c is row cell kTcRowX0 - 1 + c.
+constexpr int kTcRowCells = kTcCells + 16;
+constexpr int kTcRowX0 = 8;
 
 struct ConvTcArgs {
+    CUtensorMap map_main;  // a.in, boxes of 8 channels x 128 cells
+    CUtensorMap map_halo;  // a.in, boxes of 8 channels x 8 cells
     const bf16* in;     // [N][L^3][CINP]
     const bf16* w;      // [3 dz][3 dx][CINP/8][3 NT][8] (see gs_wprep_tc_kernel)
     const float* bias;  // [>= NT] fp32 (padded with zeros)
@@ -570,21 +576,40 @@ GS_HD uint32_t tc_idesc(int n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-GS_D void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum)
+// Warp-uniform issue: the whole warp runs the issuing code (so descriptors
+// and coordinates stay warp-uniform) and one elected lane executes the
+// instruction.
+GS_D uint32_t tc_elect_one()
 {
+    uint32_t is_leader;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(is_leader));
+    return is_leader;
+}
+
+GS_D void tc_mma_if(uint32_t leader, uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "setp.ne.b32 e, %5, 0;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum), "r"(leader)
         : "memory");
 }
 
-GS_D void tc_commit(uint64_t* bar)
+GS_D void tc_commit_if(uint32_t leader, uint64_t* bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     gs_smem_addr(bar))
-                 : "memory");
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "setp.ne.b32 e, %1, 0;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            gs_smem_addr(bar)),
+        "r"(leader)
+        : "memory");
 }
 
 GS_D void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -626,19 +651,43 @@ GS_D void tc_ld<16>(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 4D tiled TMA load (channels, x, y, plane) -> shared, completion on `bar`;
+// the channel coordinate is a multiple of 8 (16 bytes) by construction.
+GS_D void tc_tma_load_4d_if(uint32_t leader, uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c, int x, int y,
+                            int zp)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "setp.ne.b32 e, %7, 0;\n\t"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n\t}" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(zp), "r"(gs_smem_addr(bar)), "r"(leader)
+        : "memory");
+}
+
+GS_D void tc_arrive_expect_tx_if(uint32_t leader, uint64_t* bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "setp.ne.b32 e, %2, 0;\n\t"
+        "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}" ::"r"(gs_smem_addr(bar)),
+        "r"(bytes), "r"(leader)
+        : "memory");
+}
+
 template <int CINP, int NT, int EPI>
-__global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcArgs a)
+__global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_constant__ ConvTcArgs a)
 {
     constexpr int NCH = CINP / 8;
-    constexpr uint32_t PLANE = kTcSlabRows * kTcHC * 16;  // bytes of one chunk plane of a slab
+    constexpr uint32_t ROWB = kTcRowCells * 16;           // bytes of one slab row of one chunk
+    constexpr uint32_t PLANE = kTcSlabRows * ROWB;         // bytes of one chunk plane of a slab
     constexpr uint32_t SLAB = NCH * PLANE;
     constexpr uint32_t WBYTES = 27 * NCH * NT * 16;
     constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256);
-    constexpr int kCellsPerLane = (kTcHC + 31) / 32;
     extern __shared__ __align__(128) unsigned char smem_tc[];
-    // slab_full: 32 producer lanes per plane; slab_empty: the MMA commit after
-    // the plane's last tap plus one arrival per epilogue warp; acc_full: the
+    // slab_full: the producer's expect-tx arrival, completed by the TMA bytes;
+    // slab_empty: the MMA commit after the plane's last tap; acc_full: the
     // commit after an item's last MMA; acc_empty: one arrival per epilogue warp
     __shared__ __align__(8) uint64_t slab_full[3], slab_empty[3], acc_full[2], acc_empty[2], bar_fin;
     __shared__ uint32_t tmem_base_s;
@@ -659,8 +708,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
     }
     if (tid == 0) {
         for (int i = 0; i < 3; ++i) {
-            gs_mbar_init(&slab_full[i], 32);
-            gs_mbar_init(&slab_empty[i], 1 + kTcEpiWarps);
+            gs_mbar_init(&slab_full[i], 1);
+            gs_mbar_init(&slab_empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             gs_mbar_init(&acc_full[i], 1);
@@ -716,145 +765,183 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
         }
     };
 
+    // warp-uniform bounded wait (lane 0 polls; the result is broadcast)
+    auto wwait = [&](uint64_t* bar, uint32_t parity) -> bool {
+        int r = 0;
+        if (lane == 0) r = bwait(bar, parity) ? 1 : 0;
+        r = __shfl_sync(0xffffffffu, r, 0);
+        return r != 0;
+    };
+
     if (warp == kTcProdWarp) {
-        // ----------------------------- producer warp -----------------------------
-        // plane z0 - 1 + i of a unit (i = 0 .. nz+1) is global plane g, slot g % 3
-        uint32_t g = 0;
-        bool ok = true;
-        for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
-            const Unit u = decode(unit);
-            // wrapped offsets (elements) of this lane's cells and of the 6 rows
-            long long xoff[kCellsPerLane];
-#pragma unroll
-            for (int m = 0; m < kCellsPerLane; ++m) {
-                const int c = lane + 32 * m;
-                xoff[m] = (long long)((u.x0 - 1 + c + L) % L) * CINP;
+        // ------------------------ producer (TMA, one elected lane) ------------------------
+        // plane z0 - 1 + i of a unit (i = 0 .. nz+1) is global plane g, slot g % 3;
+        // per plane and channel chunk, each of the 6 rows is three boxes (left
+        // halo, 128 cells, right halo), wrapped periodically by their start
+        // coordinates (L is a multiple of 128, so no box straddles the wrap)
+        const uint32_t leader = tc_elect_one();
+        if ((sbase & 127u) == 0) {
+            if (leader) {
+                gs_prefetch_tmap(&a.map_main);
+                gs_prefetch_tmap(&a.map_halo);
             }
-            long long yoff[kTcSlabRows];
-#pragma unroll
-            for (int yi = 0; yi < kTcSlabRows; ++yi) yoff[yi] = (long long)((u.y0 - 1 + yi + L) % L) * L * CINP;
-            for (int i = 0; i < u.nz + 2; ++i, ++g) {
-                const int slot = (int)(g % 3u);
-                if (g >= 3 && !bwait(&slab_empty[slot], ((g / 3u) - 1u) & 1u)) {
-                    ok = false;
-                    break;
-                }
-                const int zw = (u.z0 - 1 + i + L) % L;
-                const bf16* pb = a.in + ((size_t)u.n * L3 + (size_t)zw * L * L) * CINP;
-                const uint32_t dst0 = sbase + slot * SLAB;
-#pragma unroll
-                for (int yi = 0; yi < kTcSlabRows; ++yi)
-#pragma unroll
-                    for (int m = 0; m < kCellsPerLane; ++m) {
-                        const int c = lane + 32 * m;
-                        if (c < kTcHC) {
-                            const bf16* src = pb + yoff[yi] + xoff[m];
-#pragma unroll
-                            for (int j = 0; j < NCH; ++j)
-                                cp16(dst0 + j * PLANE + (uint32_t)(yi * kTcHC + c) * 16, src + j * 8);
-                        }
-                    }
-                cp_wait_all();
-                gs_fence_proxy_async();  // this lane's writes -> visible to the tensor core
-                gs_mbar_arrive(&slab_full[slot]);
-            }
-        }
-    } else if (warp == kTcMmaWarp) {
-        // ------------------------------ MMA issuer -------------------------------
-        if (lane == 0) {
-            // thread 0 of the MMAs of one dz group of an item into accumulator set
-            // `set`, operand A from the slab in `slot`.  Descriptors: the start
-            // address is the low 14 bits, so a descriptor plus (byte offset >> 4)
-            // addresses the shifted operand.
-            auto issue_group = [&](int set, int dzi, int slot) {
-                constexpr uint32_t WCH = 3 * NT * 16;  // bytes of one weight chunk plane
-                constexpr int kOrder[kTcSlabRows] = {5, 2, 0, 1, 3, 4};
-                const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
-                const uint32_t idn[3] = {tc_idesc(NT), tc_idesc(2 * NT), tc_idesc(3 * NT)};
-                const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
-#pragma unroll
-                for (int dxi = 0; dxi < 3; ++dxi)
-#pragma unroll
-                    for (int kk = 0; kk < CINP / 16; ++kk) {
-                        const uint64_t bk = tc_desc(wbase + (uint32_t)((dzi * 3 + dxi) * NCH + 2 * kk) * WCH, WCH, 128);
-                        const uint64_t ak = adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)dxi;
-                        // slab rows 5 and 2 first: together they touch every output row once
-#pragma unroll
-                        for (int q = 0; q < kTcSlabRows; ++q) {
-                            const int sr = kOrder[q];
-                            const int rlo = sr - 2 > 0 ? sr - 2 : 0;
-                            const int rhi = sr < kTcRows - 1 ? sr : kTcRows - 1;
-                            const int b0 = 2 - sr + rlo;  // first dy block (dy = +1 - block)
-                            const bool fresh = dzi == 0 && dxi == 0 && kk == 0 && q < 2;
-                            tc_mma(dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * kTcHC),
-                                   bk + (uint64_t)((b0 * NT * 16) >> 4), idn[rhi - rlo], fresh ? 0u : 1u);
-                        }
-                    }
-            };
-            uint32_t g = 0, k = 0;  // planes and items seen by this CTA
+            __syncwarp();
+            uint32_t g = 0;
             bool ok = true;
             for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
                 const Unit u = decode(unit);
-                const uint32_t gb = g;
-                for (int q = 0; q < u.nz && ok; ++q, ++k) {
-                    const int set = (int)(k & 1u);
-                    if (k >= 2 && !bwait(&acc_empty[set], ((k / 2u) - 1u) & 1u)) {
+                const int xl = (u.x0 - kTcRowX0 + L) % L, xr = (u.x0 + kTcCells) % L;
+                int yrow[kTcSlabRows];
+#pragma unroll
+                for (int yi = 0; yi < kTcSlabRows; ++yi) yrow[yi] = (u.y0 - 1 + yi + L) % L;
+                for (int i = 0; i < u.nz + 2; ++i, ++g) {
+                    const int slot = (int)(g % 3u);
+                    if (g >= 3 && !wwait(&slab_empty[slot], ((g / 3u) - 1u) & 1u)) {
                         ok = false;
                         break;
                     }
-                    for (int d = 0; d < 3; ++d) {
-                        // item q reads planes q, q+1, q+2 of the unit (dz = d - 1)
-                        const uint32_t gp = gb + (uint32_t)(q + d);
-                        const int slot = (int)(gp % 3u);
-                        if ((q == 0 || d == 2) && !bwait(&slab_full[slot], (gp / 3u) & 1u)) {
-                            ok = false;
-                            break;
+                    const int zp = u.n * L + (u.z0 - 1 + i + L) % L;
+                    tc_arrive_expect_tx_if(leader, &slab_full[slot], SLAB);
+                    const uint32_t dst0 = sbase + slot * SLAB;
+#pragma unroll
+                    for (int j = 0; j < NCH; ++j)
+#pragma unroll
+                        for (int yi = 0; yi < kTcSlabRows; ++yi) {
+                            const uint32_t row = dst0 + j * PLANE + yi * ROWB;
+                            tc_tma_load_4d_if(leader, row, &a.map_halo, &slab_full[slot], j * 8, xl, yrow[yi], zp);
+                            tc_tma_load_4d_if(leader, row + kTcRowX0 * 16, &a.map_main, &slab_full[slot], j * 8, u.x0,
+                                              yrow[yi], zp);
+                            tc_tma_load_4d_if(leader, row + (kTcRowX0 + kTcCells) * 16, &a.map_halo, &slab_full[slot],
+                                              j * 8, xr, yrow[yi], zp);
                         }
-                        tc_fence_after();
-                        issue_group(set, d, slot);
-                        // last MMA use of plane q (its dz=-1 taps); of the unit's
-                        // last two planes, the last item's dz = 0 and +1 taps
-                        if (d == 0 || q == u.nz - 1) tc_commit(&slab_empty[slot]);
-                    }
-                    if (!ok) break;
-                    tc_commit(&acc_full[set]);
                 }
-                g = gb + (uint32_t)(u.nz + 2);
             }
-            if (!ok) {
-                // one more commit tracks every MMA issued (fixed budget: issued
-                // MMAs always complete)
-                tc_commit(&bar_fin);
-                gs_mbar_wait(&bar_fin, 0, 2000000000ull);
+            if (!ok && lane == 0) {
+                // let the copies in flight land (fixed budget)
+                for (uint32_t q = g > 3u ? g - 3u : 0u; q < g; ++q)
+                    gs_mbar_wait(&slab_full[q % 3u], (q / 3u) & 1u, 2000000000ull);
             }
+        } else if (lane == 0) {
+            abort_s = 1;  // unaligned shared memory: refuse to issue TMA
+            gs_report(a.err, GS_DERR_BADARG);
+        }
+    } else if (warp == kTcMmaWarp) {
+        // ------------------------ MMA issuer (one elected lane) ------------------------
+        const uint32_t leader = tc_elect_one();
+        // the MMAs of one dz group of an item into accumulator set `set`,
+        // operand A from the slab in `slot`.  Descriptors: the start address is
+        // the low 14 bits, so a descriptor plus (byte offset >> 4) addresses
+        // the shifted operand.
+        auto issue_group = [&](int set, int dzi, int slot) {
+            constexpr uint32_t WCH = 3 * NT * 16;  // bytes of one weight chunk plane
+            constexpr int kOrder[kTcSlabRows] = {5, 2, 0, 1, 3, 4};
+            const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
+            const uint32_t idn[3] = {tc_idesc(NT), tc_idesc(2 * NT), tc_idesc(3 * NT)};
+            const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
+#pragma unroll
+            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                for (int kk = 0; kk < CINP / 16; ++kk) {
+                    const uint64_t bk = tc_desc(wbase + (uint32_t)((dzi * 3 + dxi) * NCH + 2 * kk) * WCH, WCH, 128);
+                    // output cell i of tap dx reads input cell x0 + i + dx - 1
+                    const uint64_t ak = adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(kTcRowX0 - 1 + dxi);
+                    // slab rows 5 and 2 first: together they touch every output row once
+#pragma unroll
+                    for (int q = 0; q < kTcSlabRows; ++q) {
+                        const int sr = kOrder[q];
+                        const int rlo = sr - 2 > 0 ? sr - 2 : 0;
+                        const int rhi = sr < kTcRows - 1 ? sr : kTcRows - 1;
+                        const int b0 = 2 - sr + rlo;  // first dy block (dy = +1 - block)
+                        const bool fresh = dzi == 0 && dxi == 0 && kk == 0 && q < 2;
+                        tc_mma_if(leader, dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * (ROWB >> 4)),
+                                  bk + (uint64_t)((b0 * NT * 16) >> 4), idn[rhi - rlo], fresh ? 0u : 1u);
+                    }
+                }
+        };
+        uint32_t g = 0, k = 0;  // planes and items seen by this CTA
+        bool ok = true;
+        for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+            const Unit u = decode(unit);
+            const uint32_t gb = g;
+            for (int q = 0; q < u.nz && ok; ++q, ++k) {
+                const int set = (int)(k & 1u);
+                if (k >= 2 && !wwait(&acc_empty[set], ((k / 2u) - 1u) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                for (int d = 0; d < 3; ++d) {
+                    // item q reads planes q, q+1, q+2 of the unit (dz = d - 1)
+                    const uint32_t gp = gb + (uint32_t)(q + d);
+                    const int slot = (int)(gp % 3u);
+                    if ((q == 0 || d == 2) && !wwait(&slab_full[slot], (gp / 3u) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    issue_group(set, d, slot);
+                    // last MMA use of plane q (its dz=-1 taps); of the unit's
+                    // last two planes, the last item's dz = 0 and +1 taps
+                    if (d == 0 || q == u.nz - 1) tc_commit_if(leader, &slab_empty[slot]);
+                }
+                if (!ok) break;
+                tc_commit_if(leader, &acc_full[set]);
+            }
+            g = gb + (uint32_t)(u.nz + 2);
+        }
+        if (!ok) {
+            // one more commit tracks every MMA issued (fixed budget: issued
+            // MMAs always complete)
+            tc_commit_if(leader, &bar_fin);
+            if (lane == 0) gs_mbar_wait(&bar_fin, 0, 2000000000ull);
         }
     } else {
         // ------------------------- epilogue warps (0-3) --------------------------
         const int x_in_seg = tid;  // this thread's cell in the 128-cell segment
-        auto epilogue = [&](int set, int cslot, int n, int z, int y0, int x0) {
-            const int x = x0 + x_in_seg;
-#pragma unroll 1
+        float bias_r[NT];
+#pragma unroll
+        for (int c = 0; c < NT; ++c) bias_r[c] = bias_s[c];
+        // per-item inputs of the epilogue that do not depend on the MMAs (the
+        // residual of the hidden layers, the state of the last one), loaded one
+        // item ahead so their latency overlaps the wait for the accumulators
+        constexpr int NRES = EPI == EPI_HIDDEN ? NT / 8 : 1;
+        uint4 rv[kTcRows][NRES];
+        float sres[kTcRows][2];
+        auto cell_of = [&](const Unit& u, int q, int r) -> size_t {
+            return (size_t)u.n * L3 + ((size_t)(u.z0 + q) * L + (u.y0 + r)) * L + (u.x0 + x_in_seg);
+        };
+        auto prefetch = [&](const Unit& u, int q) {
+#pragma unroll
             for (int r = 0; r < kTcRows; ++r) {
+                const size_t cell = cell_of(u, q, r);
+                if constexpr (EPI == EPI_HIDDEN) {
+#pragma unroll
+                    for (int j = 0; j < NRES; ++j) rv[r][j] = *reinterpret_cast<const uint4*>(a.in + cell * CINP + j * 8);
+                } else if constexpr (EPI == EPI_LAST) {
+                    sres[r][0] = a.su[cell];
+                    sres[r][1] = a.sv[cell];
+                }
+            }
+        };
+        auto epilogue = [&](int set, const Unit& u, int q) {
+#pragma unroll
+            for (int r = 0; r < kTcRows; ++r) {
+                const size_t cell = cell_of(u, q, r);
                 float acc[NT];
                 tc_ld<NT>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(set * ACC_COLS + r * NT), acc);
-                const int y = y0 + r;
-                const size_t cell = (size_t)n * L3 + ((size_t)z * L + y) * L + x;
                 if constexpr (EPI == EPI_LAST) {
-                    a.ou[cell] = a.su[cell] + (acc[0] + bias_s[0]);
-                    a.ov[cell] = a.sv[cell] + (acc[1] + bias_s[1]);
+                    a.ou[cell] = sres[r][0] + (acc[0] + bias_r[0]);
+                    a.ov[cell] = sres[r][1] + (acc[1] + bias_r[1]);
                 } else {
-                    const unsigned char* ctr = smem_tc + cslot * SLAB + (uint32_t)((r + 1) * kTcHC + 1 + x_in_seg) * 16;
 #pragma unroll
                     for (int j = 0; j < NT / 8; ++j) {
                         float h[8], zv[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
-                            zv[e] = acc[j * 8 + e] + bias_s[j * 8 + e];
+                            zv[e] = acc[j * 8 + e] + bias_r[j * 8 + e];
                             h[e] = fmaxf(zv[e], 0.f);
                         }
                         if constexpr (EPI == EPI_HIDDEN) {
-                            const uint4 rv = *reinterpret_cast<const uint4*>(ctr + j * PLANE);
-                            const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv);
+                            const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv[r][j]);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 h[2 * e] = __bfloat162float(rb[e].x) + h[2 * e];
@@ -875,41 +962,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const ConvTcA
                 }
             }
         };
-        // warp-uniform bounded wait (lane 0 polls; the warp then synchronises)
-        auto wwait = [&](uint64_t* bar, uint32_t parity) -> bool {
-            int r = 0;
-            if (lane == 0) r = bwait(bar, parity) ? 1 : 0;
-            r = __shfl_sync(0xffffffffu, r, 0);
-            return r != 0;
-        };
-        uint32_t g = 0, k = 0;
+        uint32_t k = 0;
         bool ok = true;
+        if (blockIdx.x < units) prefetch(decode(blockIdx.x), 0);
         for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
             const Unit u = decode(unit);
-            const uint32_t gb = g;
-            __syncwarp();
-            if (lane == 0) gs_mbar_arrive(&slab_empty[gb % 3u]);  // plane 0 of the unit: no epilogue reads it
             for (int q = 0; q < u.nz; ++q, ++k) {
                 const int set = (int)(k & 1u);
-                const uint32_t gc = gb + (uint32_t)(q + 1);  // centre plane of item q
-                const int cslot = (int)(gc % 3u);
-                if (!wwait(&acc_full[set], (k / 2u) & 1u) || !wwait(&slab_full[cslot], (gc / 3u) & 1u)) {
+                if (!wwait(&acc_full[set], (k / 2u) & 1u)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                epilogue(set, cslot, u.n, u.z0 + q, u.y0, u.x0);
+                epilogue(set, u, q);
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) {
-                    gs_mbar_arrive(&acc_empty[set]);
-                    gs_mbar_arrive(&slab_empty[cslot]);
-                }
+                if (lane == 0) gs_mbar_arrive(&acc_empty[set]);
+                // the next item's inputs (this unit's next plane, or the next unit's first)
+                if (q + 1 < u.nz) prefetch(u, q + 1);
+                else if (unit + gridDim.x < units) prefetch(decode(unit + gridDim.x), 0);
             }
-            if (!ok) break;
-            __syncwarp();
-            if (lane == 0) gs_mbar_arrive(&slab_empty[(gb + (uint32_t)(u.nz + 1)) % 3u]);  // last plane of the unit
-            g = gb + (uint32_t)(u.nz + 2);
         }
     }
     // nothing of this CTA may be in flight when its TMEM and shared memory go
@@ -1076,8 +1148,12 @@ int wgrad_launch(gs_surr* s, WgArgs a)
 template <int CINP, int NT, int EPI>
 int tc_launch(gs_surr* s, ConvTcArgs a)
 {
-    constexpr uint32_t SLAB = (CINP / 8) * kTcSlabRows * kTcHC * 16;
+    constexpr uint32_t SLAB = (CINP / 8) * kTcSlabRows * kTcRowCells * 16;
     const size_t smem = 3 * (size_t)SLAB + (size_t)27 * (CINP / 8) * NT * 16;
+    if (a.L % kTcCells) return fail(GS_EINVAL, "the tcgen05 path needs L %% %d == 0 (L=%d)", kTcCells, a.L);
+    if (encode_act_4d(&a.map_main, a.in, CINP, a.L, (long long)a.N * a.L, kTcCells) != CUDA_SUCCESS ||
+        encode_act_4d(&a.map_halo, a.in, CINP, a.L, (long long)a.N * a.L, 8) != CUDA_SUCCESS)
+        return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for the activation maps");
     auto k = gs_conv_tc_kernel<CINP, NT, EPI>;
     GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
