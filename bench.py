@@ -247,7 +247,7 @@ def bench_batched(args, stream, hbm_peak):
 
 def bench_large(args, stream, hbm_peak):
     """L=1024 FP32 (four 4.3 GB fields), noise 0.1, plan autotuned over the plain,
-    z-march and temporally blocked (depth 2-4) kernels, 500 steps."""
+    z-march and temporally blocked (depth 2-8) kernels, 500 steps."""
     import torch
 
     from paper_2309_10292_gb300 import gs

@@ -125,8 +125,11 @@ int gs_set_step(gs_sim* sim, int64_t t);
 
 /* Choose the stencil kernel and its tile: tile_x, tile_y (cells), tile_z
  * (z-chunk per work item) and depth (fused steps per pass, GS_KERNEL_TBLOCK
- * only).  Zeros select defaults.  GS_EINVAL if the kernel cannot run this L
- * or the tile is unsupported. */
+ * only, FP32, 2..8; tile_x a multiple of 4 and tile_y dividing L, the tile
+ * plus its halo within 512 threads and the shared memory of one SM).
+ * Zeros select defaults.  GS_EINVAL if the kernel cannot run this L or the
+ * tile is unsupported.  A step count that is not a multiple of the depth
+ * runs its remainder with the z-march kernel. */
 int gs_set_plan(gs_sim* sim, int kernel, int tile_x, int tile_y, int tile_z, int depth);
 int gs_get_plan(gs_sim* sim, int* kernel, int* tile_x, int* tile_y, int* tile_z, int* depth);
 
@@ -147,9 +150,9 @@ int gs_get_plan_full(gs_sim* sim, gs_plan* out);
 
 /* Autotuner: time every candidate plan valid for this grid — the plain
  * kernel; z-march tiles x z-chunks x ring depths; for FP32, temporal
- * blocking at depths 2-4 with several tiles — over `steps_per_trial` steps
- * each (rounded up to a multiple of 12 so every depth runs whole passes;
- * CUDA events on the object's stream, after two warm-up launches), keep the
+ * blocking at depths 2-8 with several tiles — over `steps_per_trial` steps
+ * each (rounded up to a multiple of 12, then to whole passes of the plan's
+ * depth; CUDA events on the object's stream, after warm-up launches), keep the
  * fastest plan set, and restore the simulation's fields and step counter
  * exactly (the fields are copied to two temporary L^3 device buffers for the
  * duration).  `results` (may be NULL) receives up to max_results trials in

@@ -471,6 +471,10 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
     for (int d = 2; d <= 4; ++d)
         for (auto& t : bt)
             for (int tz : {64, 128}) cand.push_back(gs_plan{GS_KERNEL_TBLOCK, t[0], t[1], tz, d, 5, 0.0});
+    const int dtl[][2] = {{16, 8}, {16, 16}, {32, 8}};  // depths 5-8: small tiles (shared memory)
+    for (int d = 5; d <= 8; ++d)
+        for (auto& t : dtl)
+            for (int tz : {64, 128}) cand.push_back(gs_plan{GS_KERNEL_TBLOCK, t[0], t[1], tz, d, 5, 0.0});
     // save the state
     const size_t bytes = (size_t)s->L * s->L * s->L * elem_size(s->dtype);
     const gs_plan saved_plan = current_plan(s);
@@ -497,9 +501,11 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
         gs_plan& c = cand[i];
         if (apply_plan(s, c.kernel, c.tile_x, c.tile_y, c.tile_z, c.depth, c.stages) != GS_OK) continue;
         c = current_plan(s);
+        // a whole number of passes of this plan's depth
+        const int nc = c.kernel == GS_KERNEL_TBLOCK ? (n + c.depth - 1) / c.depth * c.depth : n;
         int r = gs_step(s, c.kernel == GS_KERNEL_TBLOCK ? 2 * c.depth : 2);
         if (!r && (e = cudaEventRecord(e0, s->stream)) != cudaSuccess) r = cuda_fail(e, "event");
-        if (!r) r = gs_step(s, n);
+        if (!r) r = gs_step(s, nc);
         if (!r && (e = cudaEventRecord(e1, s->stream)) != cudaSuccess) r = cuda_fail(e, "event");
         if (!r) r = gs_sync(s);
         float ms = 0.f;
@@ -508,7 +514,7 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
             rc = r;
             break;
         }
-        c.us_per_step = 1e3 * ms / n;
+        c.us_per_step = 1e3 * ms / nc;
         if (results && count < max_results) results[count] = c;
         ++count;
         if (win.us_per_step < 0 || c.us_per_step < win.us_per_step) win = c;

@@ -206,7 +206,10 @@ def test_bounded_wait_timeout_reports_and_recovers():
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("L,tiles,depth,n", [(32, (16, 8, 32), 2, 9), (32, (8, 4, 5), 3, 10),
                                              (48, (16, 8, 7), 4, 11), (64, (64, 16, 64), 2, 6),
-                                             (64, (32, 8, 13), 4, 8), (16, (4, 2, 3), 2, 5)])
+                                             (64, (32, 8, 13), 4, 8), (16, (4, 2, 3), 2, 5),
+                                             (32, (16, 8, 32), 5, 12), (32, (8, 4, 7), 6, 14),
+                                             (48, (16, 8, 9), 7, 15), (32, (16, 8, 32), 8, 17),
+                                             (24, (4, 2, 5), 8, 9)])
 def test_tblock_bitwise_equal_to_plain(L, tiles, depth, n):
     prm = dict(PAPER, noise=0.1, seed=3)
     ref = make(L, "f32", gs.GS_KERNEL_NAIVE, **prm)
@@ -233,13 +236,13 @@ def test_tblock_config1_parity():
     assert maxabs(u, uo) <= 1e-4 and maxabs(v, vo) <= 1e-4
 
 
-@pytest.mark.parametrize("depth", [2, 4])
-def test_tblock_full_size_sampled_cells(depth):
+@pytest.mark.parametrize("depth,tile", [(2, (64, 16)), (4, (64, 8)), (8, (16, 8))])
+def test_tblock_full_size_sampled_cells(depth, tile):
     # the L=1024 FP32 workload with temporal blocking, sampled against the oracle
     L, n = 1024, 16
     prm = dict(PAPER, noise=0.1, seed=42)
     sim = make(L, "f32", **prm)
-    sim.set_plan(gs.GS_KERNEL_TBLOCK, 64, 16 if depth == 2 else 8, 64, depth)
+    sim.set_plan(gs.GS_KERNEL_TBLOCK, *tile, 64, depth)
     sim.step(n)
     u, v = sim.read()
     m = 2
@@ -257,10 +260,13 @@ def test_tblock_rejects_unsupported_plans():
         sim.set_plan(gs.GS_KERNEL_TBLOCK, 32, 8, 32, 2)
     assert e.value.status == gs.GS_EINVAL
     s32 = make(48, "f32")
-    for bad in [(32, 8, 8, 2), (16, 7, 8, 2), (16, 8, 8, 5), (16, 8, 8, 1)]:
+    for bad in [(32, 8, 8, 2), (16, 7, 8, 2), (16, 8, 8, 9), (16, 8, 8, 1)]:
         with pytest.raises(gs.GsError):
             s32.set_plan(gs.GS_KERNEL_TBLOCK, *bad)
     assert s32.plan["kernel"] == gs.GS_KERNEL_ZMARCH
+    s64 = make(64, "f32")
+    with pytest.raises(gs.GsError, match="shared memory"):
+        s64.set_plan(gs.GS_KERNEL_TBLOCK, 32, 16, 8, 8)  # depth 8 on a 32 x 16 tile: ~405 KB
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
