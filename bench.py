@@ -245,6 +245,56 @@ def bench_batched(args, stream, hbm_peak):
             "cooperative_attribute": info["cooperative"], "graph_launches": 1}
 
 
+def bench_snapshot(args, stream):
+    """Output stage: L=256 FP32 (noise 0.1), 4000 steps with a snapshot of U
+    and V every 500 (9 records, 134 MB each, to a temporary file, written by
+    the library's writer thread while the stencil runs) against the same
+    steps without.  The interval gives each record more stencil time than
+    its write takes, as the paper's infrequent output does."""
+    import shutil
+    import tempfile
+    import time
+
+    import torch
+
+    from paper_2309_10292_gb300 import gs, snapshot
+    L, n, every = 256, 4000, 500
+    sim = gs.GrayScott(L, dtype="f32", noise=NOISE, seed=SEED, **PARAMS)
+    sim.set_plan(gs.GS_KERNEL_ZMARCH, 256, 4, 64)
+    sim.step(20)
+    torch.cuda.synchronize()
+    sim.init()
+    t0 = time.perf_counter()
+    sim.step(n)
+    sim.sync()
+    plain = time.perf_counter() - t0
+    d = tempfile.mkdtemp(prefix="gs_snap_")
+    try:
+        path = os.path.join(d, "run.gs")
+        sim.init()
+        t0 = time.perf_counter()
+        with sim.snapshots(path) as w:
+            w.write()
+            for _ in range(n // every):
+                sim.step(every)
+                w.write()
+            sim.sync()
+            t_steps = time.perf_counter() - t0  # the stencil's own time with the writer running
+            w.flush()
+            info = w.info()
+        t_all = time.perf_counter() - t0
+        hdr, recs = snapshot.read(path, load_fields=False)
+        size = os.path.getsize(path)
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    sim.close()
+    return {"workload": f"L={L} FP32, {n} steps, snapshot of U and V every {every} steps ({len(recs)} records)",
+            "records": len(recs), "file_bytes": size, "stencil_s_plain": plain, "stencil_s_with_snapshots": t_steps,
+            "overhead_frac": t_steps / plain - 1.0, "total_s_with_flush": t_all,
+            "write_gb_s": info["bytes"] / t_all / 1e9,
+            "note": "host wall-clock times; device-to-host copies and file writes overlap the stencil"}
+
+
 def bench_large(args, stream, hbm_peak):
     """L=1024 FP32 (four 4.3 GB fields), noise 0.1, plan autotuned over the plain,
     z-march and temporally blocked (depth 2-8) kernels, 500 steps."""
@@ -472,6 +522,8 @@ def run_ours(args):
         extra["l1024"] = bench_large(args, stream, hbm_peak)
     if rank == 0 and not args.no_surrogate:
         extra["surrogate"] = bench_surrogate(args, stream)
+    if rank == 0 and not args.no_snapshot:
+        extra["snapshot"] = bench_snapshot(args, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -526,6 +578,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the L=1024 measurement")
     ap.add_argument("--large-steps", type=int, default=500)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
+    ap.add_argument("--no-snapshot", action="store_true", help="skip the snapshot-writer measurement")
     ap.add_argument("--plan", default="", help="fixed plan instead of autotuning, e.g. zmarch,128,8,64,6")
     ap.add_argument("--surr-iters", type=int, default=2000)
     ap.add_argument("--surr-steps", type=int, default=1024)

@@ -51,7 +51,8 @@ enum {
     GS_ENOMEM = -2,   /* device or host allocation failed                  */
     GS_ECUDA = -3,    /* CUDA runtime / driver error or kernel fault       */
     GS_ETIMEOUT = -4, /* a device-side bounded wait expired                */
-    GS_ESTATE = -5    /* call not valid in the object's current state      */
+    GS_ESTATE = -5,   /* call not valid in the object's current state      */
+    GS_EIO = -6       /* a file could not be opened, read or written       */
 };
 
 /* Stencil kernels selectable with gs_set_plan (GS_KERNEL_AUTO picks one). */
@@ -367,6 +368,74 @@ int gs_surr_destroy(gs_surr* s);
  *   k2 = fmix32(hi32(seed) ^ fmix32(k1 ^ 0x7F4A7C15))
  *   m  = fmix32(fmix32(c ^ k1) ^ k2) >> 8,   r = (2m + 1 - 2^24) / 2^24. */
 int gs_noise_field(uint64_t seed, int64_t t, int64_t n, int dtype, void* dev_out, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Output stage: statistics, slices, snapshots, checkpoints               */
+/* ---------------------------------------------------------------------- */
+/* The paper writes U and V every few steps with a provenance record of the
+ * run's parameters and each field's min/max (Section 3.4, Listing 1; ADIOS2
+ * on Lustre, Section 5.3) and inspects 2D slices (Section 3.4).  Off the hot
+ * path.
+ *
+ * File layout of snapshots and checkpoints (little-endian):
+ *   header : 8-byte magic "GSSNAP01" (snapshots) or "GSCKPT01" (checkpoint),
+ *            uint32 n, n bytes of JSON provenance: format, version, L, dtype
+ *            ("f32"/"f64"), layout, boundary, Du, Dv, F, k, dt, noise, seed
+ *   record : 8-byte magic "GSREC001", int64 step, float64 U min, U max,
+ *            V min, V max, then U and V (L^3 elements each, [z][y][x],
+ *            x fastest, in the simulation's dtype).
+ * A checkpoint holds one record; a snapshot file one per gs_snap_write. */
+
+/* Minimum, maximum, mean and root-mean-square of a field of the current
+ * state (GPU reduction with FP64 accumulation; NaN cells are skipped and
+ * counted in *nan_count, which may be NULL).  out: 4 doubles owned by the
+ * caller.  Synchronous (stream of the object).  GS_EINVAL on a bad field or
+ * NULL pointer. */
+int gs_stats(gs_sim* sim, int field, double* out, int64_t* nan_count);
+
+/* Copy one plane of a field to host memory: axis 0 = the plane x = index,
+ * written [z][y]; axis 1 = y = index, [z][x]; axis 2 = z = index, [y][x].
+ * bytes must be L*L*sizeof(dtype).  Synchronous.  GS_EINVAL on a bad axis,
+ * index or size. */
+int gs_slice(gs_sim* sim, int field, int axis, int index, void* host_dst, size_t bytes);
+
+/* Snapshot writer bound to one simulation.  gs_snap_open creates (or
+ * truncates) `path` and writes the header; it allocates one device staging
+ * copy of the state and two pinned host slots and starts a writer thread.
+ * GS_EIO if the file cannot be created, GS_ENOMEM if the buffers cannot be
+ * allocated. */
+typedef struct gs_snap gs_snap;
+int gs_snap_open(gs_sim* sim, const char* path, gs_snap** out);
+
+/* Enqueue a record of the current state and step counter.  On the
+ * simulation's stream only a device-to-device copy of the state is
+ * inserted (after the previous snapshot has left the staging copy), so the
+ * caller may keep stepping; statistics and the device-to-host copy run on
+ * the writer's own stream and a host thread writes the file.  Blocks only
+ * while both host slots are still being written.  Reports an earlier
+ * write failure (GS_EIO / GS_ECUDA). */
+int gs_snap_write(gs_snap* snap);
+
+/* Wait until every enqueued record is written and flushed. */
+int gs_snap_flush(gs_snap* snap);
+
+/* Records written so far and their bytes (header excluded). */
+int gs_snap_info(gs_snap* snap, int64_t* records, double* bytes);
+
+/* Flush, stop the writer thread, close the file and free the buffers (the
+ * status of the flush is returned; the object is freed either way). */
+int gs_snap_close(gs_snap* snap);
+
+/* Write the current state and step counter to a checkpoint file (same
+ * layout, magic "GSCKPT01", one record).  Synchronous.  GS_EIO on a file
+ * error. */
+int gs_checkpoint_save(gs_sim* sim, const char* path);
+
+/* Restore state and step counter from a checkpoint written for the same L,
+ * dtype, parameters and seed (GS_EINVAL otherwise, GS_EIO if the file is
+ * missing or truncated); the continuation is bit for bit the uninterrupted
+ * run.  Synchronous. */
+int gs_checkpoint_load(gs_sim* sim, const char* path);
 
 #ifdef __cplusplus
 }

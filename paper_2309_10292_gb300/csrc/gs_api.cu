@@ -90,26 +90,6 @@ CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long lo
 
 using namespace gs;
 
-struct gs_sim {
-    int L = 0;
-    int dtype = GS_F32;
-    Params p{};
-    void* buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [set][field]
-    bool owns = false;
-    int cur = 0;       // set holding the current state
-    int64_t t = 0;     // step counter
-    cudaStream_t stream = nullptr;
-    int* d_err = nullptr;
-    int kernel = GS_KERNEL_NAIVE;
-    ZPlan zp{128, 8, 32, 4, 1};   // z-march plan (also runs the steps a blocked pass leaves over)
-    ZPlan tp{64, 16, 64, 5, 2};   // temporal-blocking plan (kernel GS_KERNEL_TBLOCK)
-    ZMaps maps[2];     // tensor maps reading set 0 / set 1
-    bool maps_ok = false;
-    int64_t launches = 0;
-    uint64_t timeout_ns = 2000000000ull;
-    int fault = 0;
-    double plan_us = 0.0;  // the tuner's time for the current plan (0: set by hand)
-};
 
 static bool finite_params(double a, double b, double c, double d, double e, double f)
 {

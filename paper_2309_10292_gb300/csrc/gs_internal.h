@@ -68,3 +68,29 @@ int launch_tblock(int L, const ZPlan& pl, const void* u, const void* v, void* un
                   int64_t t, cudaStream_t s);
 
 }  // namespace gs
+
+// The single-grid simulation object (gs_api.cu owns its life cycle; the
+// output stage in gs_io.cu reads its fields and stream).
+struct gs_sim {
+    using Params = gs::Params;
+    using ZPlan = gs::ZPlan;
+    using ZMaps = gs::ZMaps;
+    int L = 0;
+    int dtype = GS_F32;
+    Params p{};
+    void* buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [set][field]
+    bool owns = false;
+    int cur = 0;       // set holding the current state
+    int64_t t = 0;     // step counter
+    cudaStream_t stream = nullptr;
+    int* d_err = nullptr;
+    int kernel = GS_KERNEL_NAIVE;
+    ZPlan zp{128, 8, 32, 4, 1};   // z-march plan (also runs the steps a blocked pass leaves over)
+    ZPlan tp{64, 16, 64, 5, 2};   // temporal-blocking plan (kernel GS_KERNEL_TBLOCK)
+    ZMaps maps[2];     // tensor maps reading set 0 / set 1
+    bool maps_ok = false;
+    int64_t launches = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    int fault = 0;
+    double plan_us = 0.0;  // the tuner's time for the current plan (0: set by hand)
+};

@@ -22,10 +22,10 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "gs.h")
 
 GS_F32, GS_F64 = 0, 1
 GS_U, GS_V = 0, 1
-GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ETIMEOUT, GS_ESTATE = 0, -1, -2, -3, -4, -5
+GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ETIMEOUT, GS_ESTATE, GS_EIO = 0, -1, -2, -3, -4, -5, -6
 GS_KERNEL_AUTO, GS_KERNEL_NAIVE, GS_KERNEL_ZMARCH, GS_KERNEL_TBLOCK = 0, 1, 2, 3
 STATUS_NAMES = {0: "GS_OK", -1: "GS_EINVAL", -2: "GS_ENOMEM", -3: "GS_ECUDA", -4: "GS_ETIMEOUT",
-                -5: "GS_ESTATE"}
+                -5: "GS_ESTATE", -6: "GS_EIO"}
 
 
 class GsError(RuntimeError):
@@ -67,6 +67,15 @@ _SIGS = {
     "gs_destroy": [_vp],
     "gs_last_error": [],
     "gs_noise_field": [_u64, _i64, _i64, _i, _vp, _vp],
+    "gs_stats": [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)],
+    "gs_slice": [_vp, _i, _i, _i, _vp, ctypes.c_size_t],
+    "gs_snap_open": [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)],
+    "gs_snap_write": [_vp],
+    "gs_snap_flush": [_vp],
+    "gs_snap_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_d)],
+    "gs_snap_close": [_vp],
+    "gs_checkpoint_save": [_vp, ctypes.c_char_p],
+    "gs_checkpoint_load": [_vp, ctypes.c_char_p],
     "gs_batch_create": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _pp],
     "gs_batch_set_stream": [_vp, _vp],
     "gs_batch_init": [_vp],
@@ -289,6 +298,51 @@ def gs_destroy(sim):
 def gs_noise_field(seed, t, n, dtype, dev_out, stream=None):
     _check(lib().gs_noise_field(seed, t, n, _dtype_code(dtype), _ptr(dev_out), _stream(stream)),
            "gs_noise_field")
+
+
+def gs_stats(sim, field: int) -> dict:
+    """min, max, mean, rms and the NaN count of a field of the current state."""
+    out = (_d * 4)()
+    nan = _i64()
+    _check(lib().gs_stats(sim, field, out, ctypes.byref(nan)), "gs_stats")
+    return {"min": out[0], "max": out[1], "mean": out[2], "rms": out[3], "nan": nan.value}
+
+
+def gs_slice(sim, field: int, axis: int, index: int, dst: np.ndarray):
+    """Fill dst (an L x L array of the simulation's dtype) with one plane."""
+    _check(lib().gs_slice(sim, field, axis, index, dst.ctypes.data_as(_vp), dst.nbytes), "gs_slice")
+
+
+def gs_snap_open(sim, path: str):
+    out = ctypes.c_void_p()
+    _check(lib().gs_snap_open(sim, os.fsencode(path), ctypes.byref(out)), "gs_snap_open")
+    return out.value
+
+
+def gs_snap_write(snap):
+    _check(lib().gs_snap_write(snap), "gs_snap_write")
+
+
+def gs_snap_flush(snap):
+    _check(lib().gs_snap_flush(snap), "gs_snap_flush")
+
+
+def gs_snap_info(snap) -> dict:
+    n, b = _i64(), _d()
+    _check(lib().gs_snap_info(snap, ctypes.byref(n), ctypes.byref(b)), "gs_snap_info")
+    return {"records": n.value, "bytes": b.value}
+
+
+def gs_snap_close(snap):
+    _check(lib().gs_snap_close(snap), "gs_snap_close")
+
+
+def gs_checkpoint_save(sim, path: str):
+    _check(lib().gs_checkpoint_save(sim, os.fsencode(path)), "gs_checkpoint_save")
+
+
+def gs_checkpoint_load(sim, path: str):
+    _check(lib().gs_checkpoint_load(sim, os.fsencode(path)), "gs_checkpoint_load")
 
 
 def gs_batch_create(L, F, k, Du, Dv, dt, noise, seed, dtype):
@@ -706,6 +760,26 @@ class GrayScott:
     def sync(self):
         gs_sync(self.handle)
 
+    def stats(self, field: int = 0) -> dict:
+        """min / max / mean / rms (and NaN count) of U (field 0) or V (field 1)."""
+        return gs_stats(self.handle, field)
+
+    def slice(self, field: int = 0, axis: int = 2, index=None):
+        """One plane of a field as an L x L numpy array (default: the centre z plane)."""
+        out = np.empty((self.L, self.L), dtype=np_dtype(self.dtype))
+        gs_slice(self.handle, field, axis, self.L // 2 if index is None else index, out)
+        return out
+
+    def checkpoint(self, path: str):
+        gs_checkpoint_save(self.handle, path)
+
+    def restore(self, path: str):
+        gs_checkpoint_load(self.handle, path)
+
+    def snapshots(self, path: str) -> "SnapshotWriter":
+        """A writer appending (step, U, V) records to `path` while the run goes on."""
+        return SnapshotWriter(self, path)
+
     def close(self):
         if self.handle:
             gs_destroy(self.handle)
@@ -716,3 +790,34 @@ class GrayScott:
             self.close()
         except Exception:
             pass
+
+
+class SnapshotWriter:
+    """Context manager over gs_snap_*: `write()` enqueues the current state."""
+
+    def __init__(self, sim: GrayScott, path: str):
+        self.sim = sim
+        self.path = path
+        self.handle = gs_snap_open(sim.handle, path)
+
+    def write(self):
+        gs_snap_write(self.handle)
+
+    def flush(self):
+        gs_snap_flush(self.handle)
+
+    def info(self) -> dict:
+        return gs_snap_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            gs_snap_close(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
