@@ -61,6 +61,12 @@ def _load():
         lib.oracle_step.argtypes = [ctypes.c_int, dp, dp] + [ctypes.c_double] * 6 + [
             ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
         lib.oracle_step.restype = ctypes.c_int
+        lib.oracle_step_held.argtypes = [ctypes.c_int, dp, dp] + [ctypes.c_double] * 6 + [
+            ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_step_held.restype = ctypes.c_int
+        lib.oracle_diffuse.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int64]
+        lib.oracle_diffuse.restype = ctypes.c_int
         lib.oracle_window.argtypes = [ctypes.c_int] * 5 + [dp, dp] + [ctypes.c_double] * 6 + [
             ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, dp, dp]
         lib.oracle_window.restype = ctypes.c_int
@@ -123,6 +129,32 @@ def step(u: np.ndarray, v: np.ndarray, nsteps: int, *, Du: float, Dv: float, F: 
     if rc != 0:
         raise RuntimeError(f"oracle_step failed with status {rc}")
     return uu, vv
+
+
+def step_held(u: np.ndarray, v: np.ndarray, nsteps: int, *, Du: float, Dv: float, F: float,
+              k: float, dt: float, noise: float, seed: int, t0: int = 0):
+    """As step(), with the paper's kernel's outer layer held (cells on the first or
+    last layer of any axis keep their values; interior cells never wrap)."""
+    L = u.shape[0]
+    assert u.shape == (L, L, L) and v.shape == (L, L, L)
+    uu = np.ascontiguousarray(u, dtype=np.float64).copy()
+    vv = np.ascontiguousarray(v, dtype=np.float64).copy()
+    rc = _load().oracle_step_held(L, _dp(uu), _dp(vv), Du, Dv, F, k, dt, noise, seed, t0, nsteps)
+    if rc != 0:
+        raise RuntimeError(f"oracle_step_held failed with status {rc}")
+    return uu, vv
+
+
+def diffuse(f: np.ndarray, nsteps: int, *, D: float, dt: float, held: bool = False):
+    """One field, f' = f + dt (D lap f) ("1-variable, no random"), periodic or with
+    the outer layer held."""
+    L = f.shape[0]
+    assert f.shape == (L, L, L)
+    ff = np.ascontiguousarray(f, dtype=np.float64).copy()
+    rc = _load().oracle_diffuse(L, _dp(ff), D, dt, 1 if held else 0, nsteps)
+    if rc != 0:
+        raise RuntimeError(f"oracle_diffuse failed with status {rc}")
+    return ff
 
 
 def window(L: int, center, m: int, nsteps: int, *, Du, Dv, F, k, dt, noise, seed, t0=0,

@@ -236,6 +236,147 @@ int oracle_step(int L, double* u, double* v, double Du, double Dv, double F, dou
 }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's own kernel variants (Listing 2; bandwidth study, Section 5.1, */
+/* Tables 2-3).                                                               */
+/*                                                                            */
+/* Held outer layer: the paper's kernel returns without writing for a cell   */
+/* whose index lies on the first or last layer of any axis (on the full     */
+/* domain those faces are ghost cells filled by the MPI exchange).  On one   */
+/* grid with no neighbours the reading taken is: those cells keep their     */
+/* values, and every other cell updates by Eq. 1-3 exactly as in            */
+/* oracle_step (its six neighbours are all inside the grid, so nothing      */
+/* wraps).  The noise draw of an interior cell is the same r(seed, t, c).    */
+/*                                                                            */
+/* "1-variable, no random" (Table 2): one field, no reaction and no noise,   */
+/*   f' = f + dt (D lap f),  lap f = (s - 6 f) / 6  (Eq. 3, same order),     */
+/* with either periodic wrap or the held outer layer.                        */
+/*                                                                            */
+/* Pinned: boundary cells unchanged; Dirichlet sine modes                    */
+/* sin(pi m i / (L-1)) vanish on both held faces and decay by the closed-    */
+/* form factor; periodic sine modes; conservation; brute force on tiny       */
+/* grids.                                                                     */
+/* ------------------------------------------------------------------------ */
+static int on_face(int L, int x, int y, int z)
+{
+    return x == 0 || y == 0 || z == 0 || x == L - 1 || y == L - 1 || z == L - 1;
+}
+
+static void one_step_held(int L, const double* u, const double* v, double* un, double* vn, double Du, double Dv,
+                          double F, double k, double dt, double noise, uint64_t seed, int64_t t)
+{
+    uint32_t k1, k2;
+    step_keys(seed, t, &k1, &k2);
+    const int64_t LL = (int64_t)L * L;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < L; ++z) {
+        for (int y = 0; y < L; ++y) {
+            for (int x = 0; x < L; ++x) {
+                const int64_t c = x + (int64_t)L * y + LL * z;
+                if (on_face(L, x, y, z)) {
+                    un[c] = u[c];
+                    vn[c] = v[c];
+                    continue;
+                }
+                const double uc = u[c], vc = v[c];
+                double su = u[c - 1] + u[c + 1];
+                su = su + u[c - L];
+                su = su + u[c + L];
+                su = su + u[c - LL];
+                su = su + u[c + LL];
+                double sv = v[c - 1] + v[c + 1];
+                sv = sv + v[c - L];
+                sv = sv + v[c + L];
+                sv = sv + v[c - LL];
+                sv = sv + v[c + LL];
+                const double lapu = (su - 6.0 * uc) / 6.0;
+                const double lapv = (sv - 6.0 * vc) / 6.0;
+                const double r = code_to_r(oracle_fmix32(oracle_fmix32((uint32_t)c ^ k1) ^ k2));
+                const double uvv = uc * (vc * vc);
+                double du = Du * lapu - uvv;
+                du = du + F * (1.0 - uc);
+                du = du + noise * r;
+                double dv = Dv * lapv + uvv;
+                dv = dv - (F + k) * vc;
+                un[c] = uc + du * dt;
+                vn[c] = vc + dv * dt;
+            }
+        }
+    }
+}
+
+/* Two fields, held outer layer.  Returns 0, -1 (bad argument), -2 (memory). */
+int oracle_step_held(int L, double* u, double* v, double Du, double Dv, double F, double k, double dt,
+                     double noise, uint64_t seed, int64_t t0, int64_t nsteps)
+{
+    if (L < 1 || nsteps < 0) return -1;
+    if (nsteps == 0) return 0;
+    const int64_t n = (int64_t)L * L * L;
+    double* un = (double*)malloc((size_t)n * sizeof(double));
+    double* vn = (double*)malloc((size_t)n * sizeof(double));
+    if (!un || !vn) {
+        free(un);
+        free(vn);
+        return -2;
+    }
+    double *a = u, *b = v, *c = un, *d = vn;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        one_step_held(L, a, b, c, d, Du, Dv, F, k, dt, noise, seed, t0 + s);
+        double* tmp;
+        tmp = a; a = c; c = tmp;
+        tmp = b; b = d; d = tmp;
+    }
+    if (a != u) {
+        memcpy(u, a, (size_t)n * sizeof(double));
+        memcpy(v, b, (size_t)n * sizeof(double));
+    }
+    free(un);
+    free(vn);
+    return 0;
+}
+
+/* One field, f' = f + dt (D lap f); held = 0: periodic wrap, 1: held outer
+ * layer.  Returns 0, -1 (bad argument), -2 (memory). */
+int oracle_diffuse(int L, double* f, double D, double dt, int held, int64_t nsteps)
+{
+    if (L < 1 || nsteps < 0 || (held != 0 && held != 1)) return -1;
+    if (nsteps == 0) return 0;
+    const int64_t n = (int64_t)L * L * L, LL = (int64_t)L * L;
+    double* g = (double*)malloc((size_t)n * sizeof(double));
+    if (!g) return -2;
+    double *a = f, *b = g;
+    for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < L; ++z) {
+            const int zm = (z + L - 1) % L, zp = (z + 1) % L;
+            for (int y = 0; y < L; ++y) {
+                const int ym = (y + L - 1) % L, yp = (y + 1) % L;
+                for (int x = 0; x < L; ++x) {
+                    const int xm = (x + L - 1) % L, xp = (x + 1) % L;
+                    const int64_t c = x + (int64_t)L * y + LL * z;
+                    if (held && on_face(L, x, y, z)) {
+                        b[c] = a[c];
+                        continue;
+                    }
+                    double sum = a[xm + (int64_t)L * y + LL * z] + a[xp + (int64_t)L * y + LL * z];
+                    sum = sum + a[x + (int64_t)L * ym + LL * z];
+                    sum = sum + a[x + (int64_t)L * yp + LL * z];
+                    sum = sum + a[x + (int64_t)L * y + LL * zm];
+                    sum = sum + a[x + (int64_t)L * y + LL * zp];
+                    const double lap = (sum - 6.0 * a[c]) / 6.0;
+                    b[c] = a[c] + dt * (D * lap);
+                }
+            }
+        }
+        double* tmp = a;
+        a = b;
+        b = tmp;
+    }
+    if (a != f) memcpy(f, a, (size_t)n * sizeof(double));
+    free(g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sampled cells of a large run.  The state of a cell after n steps depends  */
 /* only on cells within n steps of it (one neighbour per step), so the       */
 /* cells of a (2m+1)^3 cube centred at (cx, cy, cz) can be computed from a   */

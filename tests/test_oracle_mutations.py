@@ -45,6 +45,11 @@ MUTANTS = {
     "bwd_weight_tap": ("int64_t q = cell_at(L, z + dz, yy + dyo, xx + dxo);",
                        "int64_t q = cell_at(L, z + dz, yy - dyo, xx + dxo);"),
     "bf16_no_tie_even": ("bits += 0x7fffu + lsb;", "bits += 0x8000u;"),
+    "held_face_off_by_one": ("x == L - 1 || y == L - 1 || z == L - 1;", "x == L - 2 || y == L - 1 || z == L - 1;"),
+    "held_neighbour": ("su = su + u[c + L];", "su = su + u[c - L];"),
+    "held_copies_u_into_v": ("vn[c] = v[c];", "vn[c] = u[c];"),
+    "diffuse_D_dropped": ("b[c] = a[c] + dt * (D * lap);", "b[c] = a[c] + dt * lap;"),
+    "diffuse_zp": ("sum = sum + a[x + (int64_t)L * y + LL * zp];", "sum = sum + a[x + (int64_t)L * y + LL * zm];"),
 }
 
 # pins exercised against every mutant (cheap ones)
@@ -62,6 +67,12 @@ PINS = [
     lambda o: pins.test_conv_fwd_matches_fft(o, 4),
     lambda o: pins.test_conv_adjoints(o),
     lambda o: pins.test_bf16_round_matches_torch(o),
+    lambda o: pins.test_held_faces_unchanged_and_interior_as_periodic(o),
+    lambda o: pins.test_held_dirichlet_mode_closed_form(o, 9, (3, 1, 2)),
+    lambda o: pins.test_held_brute_force_tiny_grids(o, 5),
+    lambda o: pins.test_diffuse_periodic_mode_closed_form(o, 9, (4, 0, 2)),
+    lambda o: pins.test_diffuse_held_dirichlet_closed_form(o, 9, (2, 3, 1)),
+    lambda o: pins.test_diffuse_brute_force_tiny_grids(o, 3, True),
 ]
 
 

@@ -310,6 +310,142 @@ def fft_conv(x, w, b):
     return y + (0 if b is None else b)
 
 
+# ---------------------------------------------------------------------------
+# The paper's kernel variants: outer layer held, one field without noise
+# ---------------------------------------------------------------------------
+def _faces(L):
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    return (x == 0) | (y == 0) | (z == 0) | (x == L - 1) | (y == L - 1) | (z == L - 1)
+
+
+def _dmode(L, m):
+    """Dirichlet mode: zero on the first and last layer of every axis (m_d >= 1)."""
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    return (np.sin(np.pi * m[0] * x / (L - 1)) * np.sin(np.pi * m[1] * y / (L - 1))
+            * np.sin(np.pi * m[2] * z / (L - 1)))
+
+
+def _dlam(L, m):
+    return -sum(1 - np.cos(np.pi * md / (L - 1)) for md in m) / 3.0
+
+
+def test_held_faces_unchanged_and_interior_as_periodic(orc):
+    L = 10
+    u0, v0 = inputs.random_fields(L, seed=5, lo=0.0, hi=1.0)
+    args = dict(Du=0.2, Dv=0.1, F=0.035, k=0.06, dt=0.5, noise=0.1, seed=77)
+    uh, vh = orc.step_held(u0, v0, 9, t0=2, **args)
+    f = _faces(L)
+    np.testing.assert_array_equal(uh[f], u0[f])
+    np.testing.assert_array_equal(vh[f], v0[f])
+    assert np.all(uh[~f] != u0[~f])
+    # one step: interior cells see no wrap, so they equal the periodic step bit for bit
+    u1, v1 = orc.step_held(u0, v0, 1, t0=2, **args)
+    up, vp = orc.step(u0, v0, 1, t0=2, **args)
+    np.testing.assert_array_equal(u1[~f], up[~f])
+    np.testing.assert_array_equal(v1[~f], vp[~f])
+
+
+def test_held_fixed_point(orc):
+    L = 7
+    u = np.ones((L, L, L))
+    v = np.zeros((L, L, L))
+    uh, vh = orc.step_held(u, v, 5, Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0, noise=0.0, seed=0)
+    np.testing.assert_array_equal(uh, 1.0)
+    np.testing.assert_array_equal(vh, 0.0)
+
+
+@pytest.mark.parametrize("L,m", [(12, (1, 2, 1)), (9, (3, 1, 2))])
+def test_held_dirichlet_mode_closed_form(orc, L, m):
+    c, A, n, Du, dt = 0.4, 0.1, 30, 0.2, 1.0
+    s = _dmode(L, m)
+    u, v = orc.step_held(c + A * s, np.zeros((L, L, L)), n, Du=Du, Dv=0.1, F=0.0, k=0.0, dt=dt,
+                         noise=0.0, seed=0)
+    g = 1 + dt * Du * _dlam(L, m)
+    np.testing.assert_allclose(u, c + A * g ** n * s, rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(v, 0.0)
+
+
+def _held_matrix(L):
+    """Neighbour-count matrix of the interior cells; rows of face cells are empty."""
+    n = L ** 3
+    A = np.zeros((n, n))
+    f = _faces(L).reshape(-1)
+    for z, y, x in itertools.product(range(L), repeat=3):
+        i = x + L * (y + L * z)
+        if f[i]:
+            continue
+        for dx, dy, dz in [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]:
+            A[i, (x + dx) + L * ((y + dy) + L * (z + dz))] += 1.0
+    return A, f
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 6])
+def test_held_brute_force_tiny_grids(orc, L):
+    u0, v0 = inputs.random_fields(L, seed=300 + L, lo=0.0, hi=1.0)
+    args = dict(Du=0.2, Dv=0.1, F=0.035, k=0.06, dt=0.5, noise=0.1, seed=7)
+    A, f = _held_matrix(L)
+    n = L ** 3
+    uf, vf = u0.reshape(-1).copy(), v0.reshape(-1).copy()
+    for s in range(6):
+        r = np_noise(7, 4 + s, np.arange(n))
+        lu = (A @ uf - 6 * uf) / 6
+        lv = (A @ vf - 6 * vf) / 6
+        du = args["Du"] * lu - uf * vf * vf + args["F"] * (1 - uf) + args["noise"] * r
+        dv = args["Dv"] * lv + uf * vf * vf - (args["F"] + args["k"]) * vf
+        uf = np.where(f, uf, uf + args["dt"] * du)
+        vf = np.where(f, vf, vf + args["dt"] * dv)
+    uo, vo = orc.step_held(u0, v0, 6, t0=4, **args)
+    np.testing.assert_allclose(uo.reshape(-1), uf, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(vo.reshape(-1), vf, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("L,m", [(16, (1, 2, 3)), (9, (4, 0, 2))])
+def test_diffuse_periodic_mode_closed_form(orc, L, m):
+    c, A, n, D, dt = 0.5, 0.2, 40, 0.3, 0.8
+    s = _mode(L, m)
+    f = orc.diffuse(c + A * s, n, D=D, dt=dt)
+    np.testing.assert_allclose(f, c + A * (1 + dt * D * _lam(L, m)) ** n * s, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("L,m", [(12, (1, 1, 1)), (9, (2, 3, 1))])
+def test_diffuse_held_dirichlet_closed_form(orc, L, m):
+    c, A, n, D, dt = -0.2, 0.3, 25, 0.2, 1.0
+    s = _dmode(L, m)
+    f = orc.diffuse(c + A * s, n, D=D, dt=dt, held=True)
+    np.testing.assert_allclose(f, c + A * (1 + dt * D * _dlam(L, m)) ** n * s, rtol=0, atol=1e-12)
+
+
+def test_diffuse_conserves_and_matches_the_two_field_step(orc):
+    L = 11
+    f0, _ = inputs.random_fields(L, seed=9, lo=0.0, hi=1.0)
+    f = orc.diffuse(f0, 20, D=0.2, dt=1.0)
+    assert abs(f.sum() - f0.sum()) <= 1e-12 * f0.sum()
+    # same arithmetic as Eq. 1-2 with v = 0, F = k = 0 and no noise
+    u, _ = orc.step(f0, np.zeros_like(f0), 20, Du=0.2, Dv=0.1, F=0.0, k=0.0, dt=1.0, noise=0.0, seed=0)
+    np.testing.assert_array_equal(f, u)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 5])
+@pytest.mark.parametrize("held", [False, True])
+def test_diffuse_brute_force_tiny_grids(orc, L, held):
+    f0, _ = inputs.random_fields(L, seed=400 + L, lo=0.0, hi=1.0)
+    n = L ** 3
+    if held:
+        A, fm = _held_matrix(L)
+    else:
+        A = np.zeros((n, n))
+        fm = np.zeros(n, dtype=bool)
+        for z, y, x in itertools.product(range(L), repeat=3):
+            i = x + L * (y + L * z)
+            for dx, dy, dz in [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]:
+                A[i, (x + dx) % L + L * ((y + dy) % L + L * ((z + dz) % L))] += 1.0
+    g = f0.reshape(-1).copy()
+    for _ in range(7):
+        g = np.where(fm, g, g + 0.5 * (0.25 * ((A @ g - 6 * g) / 6)))
+    fo = orc.diffuse(f0, 7, D=0.25, dt=0.5, held=held)
+    np.testing.assert_allclose(fo.reshape(-1), g, rtol=0, atol=1e-14)
+
+
 @pytest.mark.parametrize("L", [3, 4, 6])
 def test_conv_fwd_matches_fft(orc, L):
     x = inputs.random_tensor((2, L, L, L, 3), seed=1)
