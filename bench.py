@@ -295,6 +295,62 @@ def bench_snapshot(args, stream):
             "note": "host wall-clock times; device-to-host copies and file writes overlap the stencil"}
 
 
+def bench_paper_variants(args, stream, hbm_peak):
+    """The paper's own kernel forms on this GPU, with its effective-bandwidth
+    accounting (Eq. 4a, 4b: fetch = L^3 - 8 - 12 (L - 2), write = (L - 2)^3
+    elements per variable): the 2-variable application kernel (outer layer
+    held, noise 0.1) and the 1-variable no-random update, FP64 like the
+    paper's runs and FP32, at L = 1024.  The paper's MI250x figures (Table 2,
+    one GCD): Julia 2-variable 312 GB/s (111.07 ms), Julia 1-variable no
+    random 312 GB/s (54.03 ms), HIP 1-variable 599 GB/s (28.74 ms), peak
+    1600 GB/s."""
+    import torch
+
+    from paper_2309_10292_gb300 import gs
+    L, n = 1024, 6
+    out = {"L": L, "steps": n, "accounting": "paper Eq. 4a-4b effective bytes / kernel time",
+           "paper_mi250x_gb_s": {"julia_2var": 312, "julia_1var_no_random": 312, "hip_1var": 599, "peak": 1600},
+           "paper_mi250x_ms": {"julia_2var": 111.07, "julia_1var_no_random": 54.03, "hip_1var": 28.74}}
+
+    def eff_bytes(esz, nvar):
+        return nvar * ((L ** 3 - 8 - 12 * (L - 2)) + (L - 2) ** 3) * esz
+
+    def timed(step, sync):
+        step(2)
+        sync()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    for dtype, esz in (("f64", 8), ("f32", 4)):
+        sim = gs.GrayScott(L, dtype=dtype, noise=NOISE, seed=SEED, **PARAMS)
+        sim.boundary = gs.GS_BOUNDARY_HELD
+        if dtype == "f32":
+            sim.autotune(steps_per_trial=12)  # (temporal blocking is skipped: periodic only)
+        ms = timed(sim.step, sim.sync)
+        plan = sim.plan
+        sim.close()
+        torch.cuda.empty_cache()
+        out[f"two_var_{dtype}"] = {"ms_per_step": ms, "effective_gb_s": eff_bytes(esz, 2) / ms / 1e6,
+                                   "plan": {k: plan[k] for k in ("kernel", "tile_x", "tile_y", "tile_z", "stages")},
+                                   "gcups": L ** 3 / ms / 1e6,
+                                   "hbm_frac": eff_bytes(esz, 2) / ms / 1e6 / hbm_peak}
+        one = gs.SingleField(L, D=PARAMS["Du"], dt=PARAMS["dt"], dtype=dtype, boundary=gs.GS_BOUNDARY_HELD)
+        ms = timed(one.step, one.sync)
+        info = one.info
+        one.close()
+        torch.cuda.empty_cache()
+        out[f"one_var_{dtype}"] = {"ms_per_step": ms, "effective_gb_s": eff_bytes(esz, 1) / ms / 1e6,
+                                   "gcups": L ** 3 / ms / 1e6,
+                                   "hbm_frac": eff_bytes(esz, 1) / ms / 1e6 / hbm_peak,
+                                   "kernel": "z-march single field" if info["zmarch"] else "one thread per cell"}
+    return out
+
+
 def bench_large(args, stream, hbm_peak):
     """L=1024 FP32 (four 4.3 GB fields), noise 0.1, plan autotuned over the plain,
     z-march and temporally blocked (depth 2-8) kernels, 500 steps."""
@@ -524,6 +580,8 @@ def run_ours(args):
         extra["surrogate"] = bench_surrogate(args, stream)
     if rank == 0 and not args.no_snapshot:
         extra["snapshot"] = bench_snapshot(args, stream)
+    if rank == 0 and not args.no_variants:
+        extra["paper_variants"] = bench_paper_variants(args, stream, hbm_peak)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -579,6 +637,7 @@ def main():
     ap.add_argument("--large-steps", type=int, default=500)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     ap.add_argument("--no-snapshot", action="store_true", help="skip the snapshot-writer measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the paper-variant kernels (L=1024 FP64/FP32)")
     ap.add_argument("--plan", default="", help="fixed plan instead of autotuning, e.g. zmarch,128,8,64,6")
     ap.add_argument("--surr-iters", type=int, default=2000)
     ap.add_argument("--surr-steps", type=int, default=1024)

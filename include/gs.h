@@ -63,6 +63,14 @@ enum {
     GS_KERNEL_TBLOCK = 3  /* z-marching with `depth` fused steps per HBM pass  */
 };
 
+/* Boundary of the single-grid simulations (gs_set_boundary, gs_single_create). */
+enum {
+    GS_BOUNDARY_PERIODIC = 0, /* wrap in every axis (default)                      */
+    GS_BOUNDARY_HELD = 1      /* cells on the first or last layer of any axis keep
+                                 their values, as the paper's kernel (Listing 2)
+                                 skips them; interior cells never wrap            */
+};
+
 /* Largest supported edge: the cell counter of the noise hash is 32-bit. */
 #define GS_MAX_L 1625
 
@@ -179,8 +187,41 @@ int gs_launch_count(gs_sim* sim, int64_t* count);
 
 int gs_destroy(gs_sim* sim);
 
+/* Boundary treatment (GS_BOUNDARY_PERIODIC or GS_BOUNDARY_HELD).  With the
+ * held outer layer every step is the chosen stencil kernel followed by a
+ * copy of the six faces of the input state over the output (interior
+ * results are unaffected: they read only the input state).  Temporal
+ * blocking supports the periodic boundary only: GS_EINVAL if the current
+ * plan is GS_KERNEL_TBLOCK (and gs_set_plan refuses it while held). */
+int gs_set_boundary(gs_sim* sim, int boundary);
+int gs_get_boundary(gs_sim* sim, int* boundary);
+
 /* Thread-local message describing the last failure ("" if none). */
 const char* gs_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* One field without reaction or noise (the paper's "1-variable no        */
+/* random" kernel, Table 2): f' = f + dt (D lap f), lap of Eq. 3          */
+/* ---------------------------------------------------------------------- */
+typedef struct gs_single gs_single;
+
+/* Allocate two L^3 device buffers (the field starts at 0; set it with
+ * gs_single_write).  boundary: GS_BOUNDARY_PERIODIC or GS_BOUNDARY_HELD.
+ * The z-marching kernel (TMA, register z-queue) runs when L is a multiple of
+ * the vector width (4 FP32, 2 FP64), else a one-thread-per-cell kernel.
+ * GS_EINVAL on bad arguments, GS_ENOMEM if the buffers cannot be allocated. */
+int gs_single_create(int L, double D, double dt, int dtype, int boundary, gs_single** out);
+int gs_single_set_stream(gs_single* s, void* cuda_stream);
+/* Host <-> device copies of the current field (bytes = L^3 * sizeof(dtype),
+ * [z][y][x], x fastest).  Synchronous. */
+int gs_single_write(gs_single* s, const void* host_src, size_t bytes);
+int gs_single_read(gs_single* s, void* host_dst, size_t bytes);
+/* n steps, asynchronous on the object's stream. */
+int gs_single_step(gs_single* s, int64_t n);
+/* Whether the z-marching kernel is used, steps taken, kernel launches. */
+int gs_single_info(gs_single* s, int* zmarch, int64_t* steps, int64_t* launches);
+int gs_single_sync(gs_single* s);
+int gs_single_destroy(gs_single* s);
 
 /* ---------------------------------------------------------------------- */
 /* Batch: many independent grids of different sizes advanced together     */

@@ -278,6 +278,12 @@ int gs_step(gs_sim* s, int64_t n)
         }
         if (rc) return rc;
         s->launches += 1;
+        if (s->boundary == GS_BOUNDARY_HELD) {
+            rc = launch_hold_faces(s->dtype, s->L, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1],
+                                   s->stream);
+            if (rc) return rc;
+            s->launches += 1;
+        }
         s->cur = outs;
         s->t += 1;
     }
@@ -380,6 +386,8 @@ static int apply_plan(gs_sim* s, int kernel, int tile_x, int tile_y, int tile_z,
         return rc;
     }
     if (kernel == GS_KERNEL_TBLOCK) {
+        if (s->boundary != GS_BOUNDARY_PERIODIC)
+            return fail(GS_EINVAL, "temporal blocking supports the periodic boundary only");
         ZPlan pl = s->tp;
         pl.tx = tile_x > 0 ? tile_x : 64;
         pl.ty = tile_y > 0 ? tile_y : 16;
@@ -531,6 +539,24 @@ int gs_get_plan(gs_sim* s, int* kernel, int* tx, int* ty, int* tz, int* depth)
     if (ty) *ty = z ? pl.ty : 0;
     if (tz) *tz = z ? pl.tz : 0;
     if (depth) *depth = z ? pl.depth : 1;
+    return GS_OK;
+}
+
+int gs_set_boundary(gs_sim* s, int boundary)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (boundary != GS_BOUNDARY_PERIODIC && boundary != GS_BOUNDARY_HELD)
+        return fail(GS_EINVAL, "boundary=%d must be GS_BOUNDARY_PERIODIC or GS_BOUNDARY_HELD", boundary);
+    if (boundary == GS_BOUNDARY_HELD && s->kernel == GS_KERNEL_TBLOCK)
+        return fail(GS_EINVAL, "temporal blocking supports the periodic boundary only; choose another plan first");
+    s->boundary = boundary;
+    return GS_OK;
+}
+
+int gs_get_boundary(gs_sim* s, int* boundary)
+{
+    if (!s || !boundary) return fail(GS_EINVAL, "sim or boundary is NULL");
+    *boundary = s->boundary;
     return GS_OK;
 }
 

@@ -62,6 +62,10 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
                   const Params& p, int64_t t, int* d_err, uint64_t timeout_ns, int stall,
                   cudaStream_t s);
 
+// Held outer layer (gs_variants.cu): copy the six faces of the input state
+// over the output state (iv/ov may be NULL for one field).
+int launch_hold_faces(int dtype, int L, const void* iu, const void* iv, void* ou, void* ov, cudaStream_t s);
+
 // Temporally blocked kernel (gs_tblock.cu): `depth` steps per pass, FP32.
 int tblock_validate(int dtype, int L, const ZPlan& pl);
 int launch_tblock(int L, const ZPlan& pl, const void* u, const void* v, void* un, void* vn, const Params& p,
@@ -93,4 +97,5 @@ struct gs_sim {
     uint64_t timeout_ns = 2000000000ull;
     int fault = 0;
     double plan_us = 0.0;  // the tuner's time for the current plan (0: set by hand)
+    int boundary = GS_BOUNDARY_PERIODIC;  // or GS_BOUNDARY_HELD (gs_set_boundary)
 };

@@ -67,6 +67,16 @@ _SIGS = {
     "gs_destroy": [_vp],
     "gs_last_error": [],
     "gs_noise_field": [_u64, _i64, _i64, _i, _vp, _vp],
+    "gs_set_boundary": [_vp, _i],
+    "gs_get_boundary": [_vp, ctypes.POINTER(_i)],
+    "gs_single_create": [_i, _d, _d, _i, _i, ctypes.POINTER(_vp)],
+    "gs_single_set_stream": [_vp, _vp],
+    "gs_single_write": [_vp, _vp, ctypes.c_size_t],
+    "gs_single_read": [_vp, _vp, ctypes.c_size_t],
+    "gs_single_step": [_vp, _i64],
+    "gs_single_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
+    "gs_single_sync": [_vp],
+    "gs_single_destroy": [_vp],
     "gs_stats": [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)],
     "gs_slice": [_vp, _i, _i, _i, _vp, ctypes.c_size_t],
     "gs_snap_open": [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)],
@@ -298,6 +308,55 @@ def gs_destroy(sim):
 def gs_noise_field(seed, t, n, dtype, dev_out, stream=None):
     _check(lib().gs_noise_field(seed, t, n, _dtype_code(dtype), _ptr(dev_out), _stream(stream)),
            "gs_noise_field")
+
+
+GS_BOUNDARY_PERIODIC, GS_BOUNDARY_HELD = 0, 1
+
+
+def gs_set_boundary(sim, boundary: int):
+    _check(lib().gs_set_boundary(sim, boundary), "gs_set_boundary")
+
+
+def gs_get_boundary(sim) -> int:
+    b = _i()
+    _check(lib().gs_get_boundary(sim, ctypes.byref(b)), "gs_get_boundary")
+    return b.value
+
+
+def gs_single_create(L: int, D: float, dt: float, dtype, boundary: int = 0):
+    out = ctypes.c_void_p()
+    _check(lib().gs_single_create(L, D, dt, _dtype_code(dtype), boundary, ctypes.byref(out)), "gs_single_create")
+    return out.value
+
+
+def gs_single_set_stream(h, stream=None):
+    _check(lib().gs_single_set_stream(h, _stream(stream)), "gs_single_set_stream")
+
+
+def gs_single_write(h, src: np.ndarray):
+    _check(lib().gs_single_write(h, src.ctypes.data_as(_vp), src.nbytes), "gs_single_write")
+
+
+def gs_single_read(h, dst: np.ndarray):
+    _check(lib().gs_single_read(h, dst.ctypes.data_as(_vp), dst.nbytes), "gs_single_read")
+
+
+def gs_single_step(h, n: int):
+    _check(lib().gs_single_step(h, n), "gs_single_step")
+
+
+def gs_single_info(h) -> dict:
+    z, st, la = _i(), _i64(), _i64()
+    _check(lib().gs_single_info(h, ctypes.byref(z), ctypes.byref(st), ctypes.byref(la)), "gs_single_info")
+    return {"zmarch": bool(z.value), "steps": st.value, "launches": la.value}
+
+
+def gs_single_sync(h):
+    _check(lib().gs_single_sync(h), "gs_single_sync")
+
+
+def gs_single_destroy(h):
+    _check(lib().gs_single_destroy(h), "gs_single_destroy")
 
 
 def gs_stats(sim, field: int) -> dict:
@@ -722,6 +781,14 @@ class GrayScott:
         gs_set_plan(self.handle, kernel, tile_x, tile_y, tile_z, depth)
 
     @property
+    def boundary(self) -> int:
+        return gs_get_boundary(self.handle)
+
+    @boundary.setter
+    def boundary(self, value: int):
+        gs_set_boundary(self.handle, value)
+
+    @property
     def plan(self) -> dict:
         """Every field of the current plan (gs_get_plan_full)."""
         return gs_get_plan_full(self.handle)
@@ -820,4 +887,45 @@ class SnapshotWriter:
     def __exit__(self, *exc):
         self.close()
         return False
+
+
+class SingleField:
+    """One field f' = f + dt (D lap f) (the paper's "1-variable no random"
+    kernel) on the current CUDA device, stepped on torch's current stream."""
+
+    def __init__(self, L: int, D: float = 0.2, dt: float = 1.0, dtype: str = "f32",
+                 boundary: int = GS_BOUNDARY_PERIODIC):
+        import torch
+        self.L, self.dtype = L, _dtype_code(dtype)
+        self.handle = gs_single_create(L, D, dt, dtype, boundary)
+        gs_single_set_stream(self.handle, torch.cuda.current_stream().cuda_stream)
+
+    def write(self, f):
+        gs_single_write(self.handle, np.ascontiguousarray(f, dtype=np_dtype(self.dtype)))
+
+    def read(self):
+        out = np.empty((self.L,) * 3, dtype=np_dtype(self.dtype))
+        gs_single_read(self.handle, out)
+        return out
+
+    def step(self, n: int = 1):
+        gs_single_step(self.handle, n)
+
+    @property
+    def info(self) -> dict:
+        return gs_single_info(self.handle)
+
+    def sync(self):
+        gs_single_sync(self.handle)
+
+    def close(self):
+        if self.handle:
+            gs_single_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
