@@ -199,6 +199,49 @@ struct ZArgs {
     int stall;               // failure injection: the producer issues nothing
 };
 
+// Work of the persistent CTAs: tiles in the order x fastest, then y, then
+// z-chunk, round-robin over the CTAs (all CTAs work on neighbouring tiles of
+// the same z-chunk at a time, so the tiles' halo rows are L2 hits).  The
+// partial last round is split along z so that every CTA gets a share: each
+// of its `rem` tiles becomes s = G / rem pieces (G = CTAs) of about nz / s
+// planes, and no CTA idles while others finish whole tiles.
+struct ZSeg {
+    int x0, y0, z0, nz;
+};
+
+template <typename T>
+GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
+{
+    const int G = gridDim.x, c = blockIdx.x;
+    const int R = a.ntiles / G, rem = a.ntiles - R * G;
+    for (;;) {
+        int tile, part = 0, parts = 1;
+        if (k < R) {
+            tile = c + k * G;
+        } else if (k == R && rem) {
+            parts = G / rem;
+            if (c >= rem * parts) return false;
+            tile = R * G + c / parts;
+            part = c % parts;
+        } else {
+            return false;
+        }
+        ++k;
+        const int txi = tile % a.ntx;
+        const int tyi = (tile / a.ntx) % a.nty;
+        const int tzi = tile / (a.ntx * a.nty);
+        const int z0 = tzi * a.tz;
+        const int nz = min(a.tz, a.L - z0);
+        const int lo = nz * part / parts, hi = nz * (part + 1) / parts;
+        if (hi <= lo) continue;  // more pieces than planes: this one is empty
+        g.x0 = txi * a.tx;
+        g.y0 = tyi * a.ty;
+        g.z0 = z0 + lo;
+        g.nz = hi - lo;
+        return true;
+    }
+}
+
 template <typename T, bool NOISE>
 __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
 {
@@ -238,12 +281,11 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         int ps = 0;                 // stage of the next plane
         uint32_t pph = 0;           // its round's parity
         bool wrapped = false;       // every stage used once: wait for the consumers' release
-        for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-            const int txi = tile % a.ntx;
-            const int tyi = (tile / a.ntx) % a.nty;
-            const int tzi = tile / (a.ntx * a.nty);
-            const int x0 = txi * a.tx, y0 = tyi * a.ty, z0 = tzi * a.tz;
-            const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0), nz = min(a.tz, L - z0);
+        int wk = 0;
+        ZSeg sg;
+        while (zmarch_next_seg(wk, a, sg)) {
+            const int x0 = sg.x0, y0 = sg.y0, z0 = sg.z0, nz = sg.nz;
+            const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0);
             const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
             const int xl = (x0 - V + L) % L, xr = (x0 + nvx) % L;
             int zp = (z0 - 1 + L) % L;
@@ -306,12 +348,11 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
     // planes z-1, z, z+1 of this thread's group in three register sets that
     // rotate by renaming (the loop below is unrolled by 3)
     T qu[3][V], qv[3][V];
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const int txi = tile % a.ntx;
-        const int tyi = (tile / a.ntx) % a.nty;
-        const int tzi = tile / (a.ntx * a.nty);
-        const int x0 = txi * a.tx, y0 = tyi * a.ty, z0 = tzi * a.tz;
-        const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0), nz = min(a.tz, L - z0);
+    int wk = 0;
+    ZSeg sg;
+    while (zmarch_next_seg(wk, a, sg)) {
+        const int x0 = sg.x0, y0 = sg.y0, z0 = sg.z0, nz = sg.nz;
+        const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0);
         const bool active = row < nvy && xv * V < nvx;
         const int rr = row < a.ty ? row : 0;  // padding threads read a valid address
         const int moff = a.lay.main_off + rr * a.tx + xv * V;
