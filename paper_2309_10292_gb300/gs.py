@@ -24,6 +24,7 @@ GS_F32, GS_F64 = 0, 1
 GS_U, GS_V = 0, 1
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ETIMEOUT, GS_ESTATE, GS_EIO = 0, -1, -2, -3, -4, -5, -6
 GS_KERNEL_AUTO, GS_KERNEL_NAIVE, GS_KERNEL_ZMARCH, GS_KERNEL_TBLOCK = 0, 1, 2, 3
+GS_MAX_L = 1625  # largest edge (the noise hash counts cells in 32 bits)
 STATUS_NAMES = {0: "GS_OK", -1: "GS_EINVAL", -2: "GS_ENOMEM", -3: "GS_ECUDA", -4: "GS_ETIMEOUT",
                 -5: "GS_ESTATE", -6: "GS_EIO"}
 

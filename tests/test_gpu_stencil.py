@@ -164,6 +164,29 @@ def test_full_size_sampled_cells(L, dtype):
     sim.close()
 
 
+def test_largest_grid_sampled_cells():
+    # the largest edge (1625^3 cells: the noise counter is 32-bit), FP32:
+    # 69 GB of fields; L is not a multiple of 4, so the one-thread-per-cell
+    # kernel runs.  Planes around sampled cells are read with gs_slice.
+    L, n, m = gs.GS_MAX_L, 3, 2
+    assert L ** 3 < 2 ** 32 <= (L + 1) ** 3
+    prm = dict(PAPER, noise=0.1, seed=42)
+    sim = make(L, "f32", **prm)
+    assert sim.plan["kernel"] == gs.GS_KERNEL_NAIVE
+    sim.step(n)
+    for c in [(L // 2, L // 2, L // 2), (0, 0, 0), (L - 1, 3, L - 2), (812, 809, 815)]:
+        uo, vo = oracle.window(L, c, m, n, **prm)
+        zs = [(c[2] + d) % L for d in range(-m, m + 1)]
+        idx = [(np.arange(-m, m + 1) + cc) % L for cc in c[:2]]
+        for fld, ref in ((gs.GS_U, uo), (gs.GS_V, vo)):
+            planes = np.stack([sim.slice(fld, 2, z) for z in zs])  # [z][y][x]
+            got = planes[np.ix_(range(len(zs)), idx[1], idx[0])]
+            assert maxabs(got, ref) <= TOL["f32"], (c, fld)
+    sim.close()
+    with pytest.raises(gs.GsError):
+        gs.GrayScott(L + 1, dtype="f32", **prm)
+
+
 def test_step_zero_and_argument_errors():
     sim = make(8, "f32")
     sim.step(0)
