@@ -63,6 +63,17 @@ enum {
     GS_KERNEL_TBLOCK = 3  /* z-marching with `depth` fused steps per HBM pass  */
 };
 
+/* Arithmetic of FP64 fields (gs_set_arith).  GB300's FP64 pipe is narrow
+ * (about 2 FP64 FMAs per clock per SM): GS_ARITH_DS keeps the fields in FP64
+ * but computes each step in double-single arithmetic (pairs of floats,
+ * about 48 significant bits, error-free transformations on the FP32 pipe;
+ * values below 2^-126 flush to zero), which matches the FP64 oracle within
+ * its 1e-10 tolerance. */
+enum {
+    GS_ARITH_IEEE = 0, /* the dtype's own IEEE arithmetic (default)         */
+    GS_ARITH_DS = 1    /* FP64 fields only: double-single arithmetic        */
+};
+
 /* Boundary of the single-grid simulations (gs_set_boundary, gs_single_create). */
 enum {
     GS_BOUNDARY_PERIODIC = 0, /* wrap in every axis (default)                      */
@@ -195,6 +206,11 @@ int gs_destroy(gs_sim* sim);
  * plan is GS_KERNEL_TBLOCK (and gs_set_plan refuses it while held). */
 int gs_set_boundary(gs_sim* sim, int boundary);
 int gs_get_boundary(gs_sim* sim, int* boundary);
+
+/* Arithmetic mode (GS_ARITH_IEEE or GS_ARITH_DS; GS_EINVAL for GS_ARITH_DS on
+ * an FP32 simulation).  Applies to the plain and z-marching kernels. */
+int gs_set_arith(gs_sim* sim, int arith);
+int gs_get_arith(gs_sim* sim, int* arith);
 
 /* Thread-local message describing the last failure ("" if none). */
 const char* gs_last_error(void);

@@ -553,6 +553,24 @@ int gs_set_boundary(gs_sim* s, int boundary)
     return GS_OK;
 }
 
+int gs_set_arith(gs_sim* s, int arith)
+{
+    if (!s) return fail(GS_EINVAL, "sim is NULL");
+    if (arith != GS_ARITH_IEEE && arith != GS_ARITH_DS)
+        return fail(GS_EINVAL, "arith=%d must be GS_ARITH_IEEE or GS_ARITH_DS", arith);
+    if (arith == GS_ARITH_DS && s->dtype != GS_F64)
+        return fail(GS_EINVAL, "double-single arithmetic applies to FP64 fields only");
+    s->p.arith = arith;
+    return GS_OK;
+}
+
+int gs_get_arith(gs_sim* s, int* arith)
+{
+    if (!s || !arith) return fail(GS_EINVAL, "sim or arith is NULL");
+    *arith = s->p.arith;
+    return GS_OK;
+}
+
 int gs_get_boundary(gs_sim* s, int* boundary)
 {
     if (!s || !boundary) return fail(GS_EINVAL, "sim or boundary is NULL");

@@ -15,6 +15,7 @@ namespace gs {
 struct Params {
     double Du, Dv, F, k, dt, noise;
     uint64_t seed;
+    int arith = GS_ARITH_IEEE;  // GS_ARITH_DS: FP64 fields in double-single arithmetic
 };
 
 // Thread-local error message + status helper.

@@ -19,7 +19,10 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <type_traits>
+
 #include "gs_common.cuh"
+#include "gs_ds.cuh"
 #include "gs_internal.h"
 
 namespace gs {
@@ -61,10 +64,10 @@ static GsCoef<T> make_coef(const Params& p)
     return gs_make_coef<T>(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
 }
 
-template <typename T, bool NOISE>
+template <typename T, bool NOISE, bool DS>
 __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, const T* __restrict__ v,
                                                        T* __restrict__ un, T* __restrict__ vn, int L,
-                                                       GsCoef<T> c, GsKeys k)
+                                                       GsCoef<T> c, GsCoefDS cds, GsKeys k)
 {
     const int64_t n = (int64_t)L * L * L;
     const int64_t LL = (int64_t)L * L;
@@ -83,15 +86,29 @@ __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, 
         const int64_t base = i - (int64_t)z * LL;
         const int64_t izm = base + (int64_t)(z == 0 ? L - 1 : z - 1) * LL;
         const int64_t izp = base + (int64_t)(z == L - 1 ? 0 : z + 1) * LL;
-        const T uc = u[i], vc = v[i];
-        const T su = gs_nsum(u[ixm], u[ixp], u[iym], u[iyp], u[izm], u[izp]);
-        const T sv = gs_nsum(v[ixm], v[ixp], v[iym], v[iyp], v[izm], v[izp]);
-        T rn = (T)0;
-        if (NOISE) rn = (T)gs_noise_num((uint32_t)i, k);
-        T a, b;
-        gs_update<T, NOISE>(c, uc, vc, su, sv, rn, a, b);
-        un[i] = a;
-        vn[i] = b;
+        if constexpr (DS) {
+            // FP64 fields in double-single arithmetic (gs_ds.cuh)
+            const GsDS uc = ds_from_double(u[i]), vc = ds_from_double(v[i]);
+            const GsDS su = ds_nsum(ds_from_double(u[ixm]), ds_from_double(u[ixp]), ds_from_double(u[iym]),
+                                    ds_from_double(u[iyp]), ds_from_double(u[izm]), ds_from_double(u[izp]));
+            const GsDS sv = ds_nsum(ds_from_double(v[ixm]), ds_from_double(v[ixp]), ds_from_double(v[iym]),
+                                    ds_from_double(v[iyp]), ds_from_double(v[izm]), ds_from_double(v[izp]));
+            const float rn = NOISE ? (float)gs_noise_num((uint32_t)i, k) : 0.0f;
+            GsDS a, b;
+            gs_update_ds<NOISE>(cds, uc, vc, su, sv, rn, a, b);
+            un[i] = ds_to_double(a);
+            vn[i] = ds_to_double(b);
+        } else {
+            const T uc = u[i], vc = v[i];
+            const T su = gs_nsum(u[ixm], u[ixp], u[iym], u[iyp], u[izm], u[izp]);
+            const T sv = gs_nsum(v[ixm], v[ixp], v[iym], v[iyp], v[izm], v[izp]);
+            T rn = (T)0;
+            if (NOISE) rn = (T)gs_noise_num((uint32_t)i, k);
+            T a, b;
+            gs_update<T, NOISE>(c, uc, vc, su, sv, rn, a, b);
+            un[i] = a;
+            vn[i] = b;
+        }
     }
 }
 
@@ -134,11 +151,24 @@ static int naive_t(int L, const void* u, const void* v, void* un, void* vn, cons
     const int64_t n = (int64_t)L * L * L;
     const int g = grid_for(n, 256);
     GsCoef<T> c = make_coef<T>(p);
+    const GsCoefDS cds = gs_make_coef_ds(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     GsKeys k = gs_step_keys(p.seed, t);
-    if (p.noise != 0.0)
-        gs_naive_kernel<T, true><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, k);
-    else
-        gs_naive_kernel<T, false><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, k);
+    bool launched = false;
+    if constexpr (std::is_same<T, double>::value) {
+        if (p.arith == GS_ARITH_DS) {
+            if (p.noise != 0.0)
+                gs_naive_kernel<T, true, true><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
+            else
+                gs_naive_kernel<T, false, true><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
+            launched = true;
+        }
+    }
+    if (!launched) {
+        if (p.noise != 0.0)
+            gs_naive_kernel<T, true, false><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
+        else
+            gs_naive_kernel<T, false, false><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
+    }
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
@@ -193,6 +223,7 @@ struct ZArgs {
     int stages;
     ZLayout lay;
     GsCoef<T> c;
+    GsCoefDS cds;            // the same coefficients as double-single pairs (DS kernels)
     GsKeys keys;
     int* err;
     uint64_t timeout_ns;
@@ -242,7 +273,7 @@ GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
     }
 }
 
-template <typename T, bool NOISE>
+template <typename T, bool NOISE, bool DS>
 __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
 {
     constexpr int V = GsVec<T>::N;
@@ -398,8 +429,12 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                 if (l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
                 if (r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
                 const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
-                gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
-                                          xlv, xrv, outu, outv);
+                if constexpr (DS)
+                    gs_update_group_ds<NOISE>(a.cds, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
+                                              xlv, xrv, outu, outv);
+                else
+                    gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
+                                              xlv, xrv, outu, outv);
                 *reinterpret_cast<VT*>(a.un + gidx) = gs_pack<T>(outu);
                 *reinterpret_cast<VT*>(a.vn + gidx) = gs_pack<T>(outv);
             }
@@ -478,7 +513,7 @@ int zmarch_encode(int dtype, int L, const ZPlan& pl, void* u, void* v, ZMaps* ma
     return GS_OK;
 }
 
-template <typename T, bool NOISE>
+template <typename T, bool NOISE, bool DS>
 static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
                            const Params& p, int64_t t, int* d_err, uint64_t timeout_ns,
                            int stall, cudaStream_t s)
@@ -498,6 +533,7 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     a.stages = pl.stages;
     a.lay = make_layout(sizeof(T), V, pl.tx, pl.ty);
     a.c = make_coef<T>(p);
+    a.cds = gs_make_coef_ds(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     a.keys = gs_step_keys(p.seed, t);
     a.err = d_err;
     a.timeout_ns = timeout_ns;
@@ -505,7 +541,7 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     const int ncons = (pl.tx / V) * pl.ty;
     const int threads = ((ncons + 31) & ~31) + 32;
     const size_t smem = (size_t)a.lay.stage_bytes * pl.stages;
-    auto kern = gs_zmarch_kernel<T, NOISE>;
+    auto kern = gs_zmarch_kernel<T, NOISE, DS>;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -522,10 +558,13 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
 {
     const bool noise = p.noise != 0.0;
     if (dtype == GS_F32)
-        return noise ? zmarch_launch_t<float, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                     : zmarch_launch_t<float, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
-    return noise ? zmarch_launch_t<double, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                 : zmarch_launch_t<double, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+        return noise ? zmarch_launch_t<float, true, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                     : zmarch_launch_t<float, false, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+    if (p.arith == GS_ARITH_DS)
+        return noise ? zmarch_launch_t<double, true, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                     : zmarch_launch_t<double, false, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+    return noise ? zmarch_launch_t<double, true, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                 : zmarch_launch_t<double, false, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
 }
 
 }  // namespace gs

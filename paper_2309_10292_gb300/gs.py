@@ -69,6 +69,8 @@ _SIGS = {
     "gs_last_error": [],
     "gs_noise_field": [_u64, _i64, _i64, _i, _vp, _vp],
     "gs_set_boundary": [_vp, _i],
+    "gs_set_arith": [_vp, _i],
+    "gs_get_arith": [_vp, ctypes.POINTER(_i)],
     "gs_get_boundary": [_vp, ctypes.POINTER(_i)],
     "gs_single_create": [_i, _d, _d, _i, _i, ctypes.POINTER(_vp)],
     "gs_single_set_stream": [_vp, _vp],
@@ -312,6 +314,17 @@ def gs_noise_field(seed, t, n, dtype, dev_out, stream=None):
 
 
 GS_BOUNDARY_PERIODIC, GS_BOUNDARY_HELD = 0, 1
+GS_ARITH_IEEE, GS_ARITH_DS = 0, 1
+
+
+def gs_set_arith(sim, arith: int):
+    _check(lib().gs_set_arith(sim, arith), "gs_set_arith")
+
+
+def gs_get_arith(sim) -> int:
+    a = _i()
+    _check(lib().gs_get_arith(sim, ctypes.byref(a)), "gs_get_arith")
+    return a.value
 
 
 def gs_set_boundary(sim, boundary: int):
@@ -780,6 +793,15 @@ class GrayScott:
 
     def set_plan(self, kernel, tile_x=0, tile_y=0, tile_z=0, depth=0):
         gs_set_plan(self.handle, kernel, tile_x, tile_y, tile_z, depth)
+
+    @property
+    def arith(self) -> int:
+        """GS_ARITH_IEEE, or GS_ARITH_DS (FP64 fields in double-single arithmetic)."""
+        return gs_get_arith(self.handle)
+
+    @arith.setter
+    def arith(self, value: int):
+        gs_set_arith(self.handle, value)
 
     @property
     def boundary(self) -> int:

@@ -321,3 +321,83 @@ def test_autotune_restores_state_and_keeps_fastest_plan(dtype):
     np.testing.assert_array_equal(va, vr)
     a.set_plan(best["kernel"], best["tile_x"], best["tile_y"], best["tile_z"], best["depth"])
     assert a.plan["us_per_step"] == 0.0  # a plan set by hand carries no tuner time
+
+
+# ---------------------------------------------------------------------------
+# FP64 fields in double-single arithmetic (GS_ARITH_DS)
+# ---------------------------------------------------------------------------
+def make_ds(L, kernel=None, **kw):
+    sim = make(L, "f64", kernel, **kw)
+    sim.arith = gs.GS_ARITH_DS
+    return sim
+
+
+@pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
+def test_ds_config1_parity(kernel):
+    L, n = 64, 100
+    u0, v0 = oracle.init(L)
+    uo, vo = oracle.step(u0, v0, n, **PAPER, noise=0.0, seed=0)
+    sim = make_ds(L, kernel, noise=0.0, seed=0)
+    assert sim.arith == gs.GS_ARITH_DS
+    sim.step(n)
+    u, v = sim.read()
+    err = max(maxabs(u, uo), maxabs(v, vo))
+    print(f"double-single config 1: max-abs error vs oracle {err:.3e}")
+    assert err <= TOL["f64"]
+
+
+@pytest.mark.parametrize("L", [48, 17, 5, 2])
+def test_ds_random_state_parity_with_noise(L):
+    prm = dict(Du=0.2, Dv=0.1, F=0.035, k=0.06, dt=0.5, noise=0.1, seed=77)
+    u0, v0 = inputs.random_fields(L, seed=600 + L, lo=0.0, hi=1.0)
+    sim = gs.GrayScott(L, dtype="f64", **prm)
+    sim.arith = gs.GS_ARITH_DS
+    sim.write(u0, v0)
+    sim.t = 7
+    sim.step(40)
+    u, v = sim.read()
+    uo, vo = oracle.step(u0, v0, 40, t0=7, **prm)
+    assert max(maxabs(u, uo), maxabs(v, vo)) <= TOL["f64"]
+
+
+def test_ds_kernels_bitwise_equal_and_close_to_ieee():
+    L, n = 64, 60
+    prm = dict(PAPER, noise=0.1, seed=3)
+    a = make_ds(L, gs.GS_KERNEL_NAIVE, **prm)
+    b = make_ds(L, gs.GS_KERNEL_ZMARCH, **prm)
+    c = make(L, "f64", gs.GS_KERNEL_ZMARCH, **prm)
+    for s in (a, b, c):
+        s.step(n)
+    ua, va = a.read()
+    ub, vb = b.read()
+    uc, vc = c.read()
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(va, vb)
+    d = max(maxabs(ua, uc), maxabs(va, vc))
+    print(f"double-single vs IEEE FP64 after {n} steps: {d:.3e}")
+    assert 0 < d <= 1e-11
+
+
+def test_ds_full_size_sampled_cells():
+    L, n, m = 512, 16, 2
+    prm = dict(PAPER, noise=0.1, seed=42)
+    sim = make_ds(L, **prm)
+    sim.step(n)
+    for c in [(L // 2, L // 2, L // 2), (0, 0, 0), (L - 1, 5, L // 2)]:
+        uo, vo = oracle.window(L, c, m, n, **prm)
+        zs = [(c[2] + d) % L for d in range(-m, m + 1)]
+        idx = [(np.arange(-m, m + 1) + cc) % L for cc in c[:2]]
+        for fld, ref in ((gs.GS_U, uo), (gs.GS_V, vo)):
+            planes = np.stack([sim.slice(fld, 2, z) for z in zs])
+            assert maxabs(planes[np.ix_(range(len(zs)), idx[1], idx[0])], ref) <= TOL["f64"], (c, fld)
+    sim.close()
+
+
+def test_ds_only_for_fp64_fields():
+    s32 = make(16, "f32")
+    with pytest.raises(gs.GsError) as e:
+        s32.arith = gs.GS_ARITH_DS
+    assert e.value.status == gs.GS_EINVAL and s32.arith == gs.GS_ARITH_IEEE
+    s64 = make(16, "f64")
+    with pytest.raises(gs.GsError):
+        s64.arith = 5
