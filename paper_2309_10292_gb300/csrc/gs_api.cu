@@ -492,6 +492,9 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
         // a whole number of passes of this plan's depth
         const int nc = c.kernel == GS_KERNEL_TBLOCK ? (n + c.depth - 1) / c.depth * c.depth : n;
         int r = gs_step(s, c.kernel == GS_KERNEL_TBLOCK ? 2 * c.depth : 2);
+        // a plan that validates but cannot be launched on this GPU (its block
+        // does not fit an SM) is skipped; the state is restored at the end
+        if (r == GS_EINVAL) continue;
         if (!r && (e = cudaEventRecord(e0, s->stream)) != cudaSuccess) r = cuda_fail(e, "event");
         if (!r) r = gs_step(s, nc);
         if (!r && (e = cudaEventRecord(e1, s->stream)) != cudaSuccess) r = cuda_fail(e, "event");
