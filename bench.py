@@ -25,6 +25,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -91,9 +92,9 @@ def profiled_traffic():
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, log_dir: str | None = None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(log_dir or tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -501,7 +502,7 @@ def run_ours(args):
     launches0 = gs.gs_launch_count(sim.handle)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(local) if rank == 0 else None
+    clocks = Clocks(local, args.clocks_log) if rank == 0 else None
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
@@ -648,6 +649,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     ap.add_argument("--no-snapshot", action="store_true", help="skip the snapshot-writer measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the paper-variant kernels (L=1024 FP64/FP32)")
+    ap.add_argument("--clocks-log", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--plan", default="", help="fixed plan instead of autotuning, e.g. zmarch,128,8,64,6")
     ap.add_argument("--surr-iters", type=int, default=2000)
     ap.add_argument("--surr-steps", type=int, default=1024)

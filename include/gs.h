@@ -392,7 +392,7 @@ int gs_surr_train_step(gs_surr* s, int N, int L, const float* u, const float* v,
 /* max |a - b| and root-mean-square difference of n device floats. */
 int gs_surr_diff(gs_surr* s, const float* a, const float* b, int64_t n, double* maxabs, double* rms);
 /* Advance an FP32 simulation (noise 0 expected; the network cannot predict
- * noise) nsteps with the network, judged by the stencil: each segment of
+ * noise) nsteps with the network, checked against the stencil: each segment of
  * check_every steps (a multiple of 16) applies the network check_every/16 - 1
  * times, then compares one more application against 16 stencil steps from
  * the same state and keeps the stencil's state.  A check error (max-abs over

@@ -3,7 +3,7 @@
  *
  * Plain, slow, FP64 restatement of what the GPU path computes, used by the
  * test suite, by the smoke check and by the benchmark's CPU-baseline leg to
- * judge the CUDA kernels.  Nothing in the product library may link, load or
+ * check the CUDA kernels.  Nothing in the product library may link, load or
  * call this file; it shares no code, header or constant table with the CUDA
  * sources (it re-derives everything from the paper and from the published
  * definitions cited below).
