@@ -73,17 +73,18 @@ CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_x)
+CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_c, int box_x,
+                       bool swizzle64)
 {
     auto enc = tensor_map_encoder();
     if (!enc) return CUDA_ERROR_NOT_FOUND;
     cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)planes};
     cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)L * C * 2, (cuuint64_t)L * L * C * 2};
-    cuuint32_t box[4] = {8, (cuuint32_t)box_x, 1, 1};
+    cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)box_x, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
 }  // namespace gs

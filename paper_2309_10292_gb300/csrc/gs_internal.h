@@ -33,8 +33,10 @@ int num_sms();
 // Tensor-map encoder obtained from the driver at first use.
 CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y);
 // channels-last bf16 activations [planes][L][L][C] (planes = N * L): boxes of
-// 8 channels x box_x cells x 1 row x 1 plane
-CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_x);
+// box_c channels x box_x cells x 1 row x 1 plane, optionally with the 64-byte
+// swizzle (box_c = 32)
+CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_c, int box_x,
+                       bool swizzle64);
 
 // ---------------------------------------------------------------------------
 // Stencil kernels (gs_stencil.cu)

@@ -544,8 +544,8 @@ constexpr int kTcRowCells = kTcCells + 16;
 constexpr int kTcRowX0 = 8;
 
 struct ConvTcArgs {
-    CUtensorMap map_main;  // a.in, boxes of 8 channels x 128 cells
-    CUtensorMap map_halo;  // a.in, boxes of 8 channels x 8 cells
+    CUtensorMap map_main;  // a.in, boxes of 8 (32: swizzled) channels x 128 cells
+    CUtensorMap map_halo;  // a.in, boxes of 8 (32: swizzled) channels x 8 cells
     const bf16* in;     // [N][L^3][CINP]
     const bf16* w;      // [3 dz][3 dx][CINP/8][3 NT][8] (see gs_wprep_tc_kernel)
     const float* bias;  // [>= NT] fp32 (padded with zeros)
@@ -567,6 +567,14 @@ GS_D uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
     // bits 46-48 = 0b001, base offset 0, layout type 0
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+GS_D uint64_t tc_desc_sw64(uint32_t saddr, uint32_t sbo)
+{
+    // the same with the 64-byte swizzle (layout type 4 at bits 61-63): K-major
+    // rows of 64 bytes in 8-row, 512-byte atoms; LBO unused (16 B)
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) |
+           (4ull << 61);
 }
 
 GS_HD uint32_t tc_idesc(int n)
@@ -682,10 +690,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
     constexpr uint32_t ROWB = kTcRowCells * 16;           // bytes of one slab row of one chunk
     constexpr uint32_t PLANE = kTcSlabRows * ROWB;         // bytes of one chunk plane of a slab
     constexpr uint32_t SLAB = NCH * PLANE;
+    // 32 input channels: a slab row is [cell][32 channels] (64 bytes a cell)
+    // with the 64-byte swizzle, one TMA line per cell instead of four
+    constexpr bool SW = CINP == 32;
+    constexpr uint32_t SROWB = kTcRowCells * 64;          // bytes of one swizzled slab row
+    static_assert(!SW || kTcSlabRows * SROWB == SLAB, "swizzled slab size");
     constexpr uint32_t WBYTES = 27 * NCH * NT * 16;
     constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256);
-    extern __shared__ __align__(128) unsigned char smem_tc[];
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
     // slab_full: the producer's expect-tx arrival, completed by the TMA bytes;
     // slab_empty: the MMA commit after the plane's last tap; acc_full: the
     // commit after an item's last MMA; acc_empty: one arrival per epilogue warp
@@ -780,7 +793,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         // halo, 128 cells, right halo), wrapped periodically by their start
         // coordinates (L is a multiple of 128, so no box straddles the wrap)
         const uint32_t leader = tc_elect_one();
-        if ((sbase & 127u) == 0) {
+        if ((sbase & (SW ? 511u : 127u)) == 0) {
             if (leader) {
                 gs_prefetch_tmap(&a.map_main);
                 gs_prefetch_tmap(&a.map_halo);
@@ -803,6 +816,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                     const int zp = u.n * L + (u.z0 - 1 + i + L) % L;
                     tc_arrive_expect_tx_if(leader, &slab_full[slot], SLAB);
                     const uint32_t dst0 = sbase + slot * SLAB;
+                    if constexpr (SW) {
+                        // three boxes of 32 channels per row, each landing on a
+                        // 512-byte boundary (cell slots 0, 8 and 136 of 64 bytes)
+#pragma unroll
+                        for (int yi = 0; yi < kTcSlabRows; ++yi) {
+                            const uint32_t row = dst0 + yi * SROWB;
+                            tc_tma_load_4d_if(leader, row, &a.map_halo, &slab_full[slot], 0, xl, yrow[yi], zp);
+                            tc_tma_load_4d_if(leader, row + kTcRowX0 * 64, &a.map_main, &slab_full[slot], 0, u.x0,
+                                              yrow[yi], zp);
+                            tc_tma_load_4d_if(leader, row + (kTcRowX0 + kTcCells) * 64, &a.map_halo, &slab_full[slot],
+                                              0, xr, yrow[yi], zp);
+                        }
+                    } else
 #pragma unroll
                     for (int j = 0; j < NCH; ++j)
 #pragma unroll
@@ -837,14 +863,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
             constexpr int kOrder[kTcSlabRows] = {5, 2, 0, 1, 3, 4};
             const uint32_t dset = tmem + (uint32_t)(set * ACC_COLS);
             const uint32_t idn[3] = {tc_idesc(NT), tc_idesc(2 * NT), tc_idesc(3 * NT)};
-            const uint64_t adz = tc_desc(sbase + slot * SLAB, PLANE, 128);
+            // A: no swizzle (LBO = one chunk plane, SBO = 8 cells), or the
+            // 64-byte swizzle (SBO = one 8-cell atom; K steps of 32 bytes)
+            const uint64_t adz = SW ? tc_desc_sw64(sbase + slot * SLAB, 512) : tc_desc(sbase + slot * SLAB, PLANE, 128);
+            constexpr uint32_t AROW = SW ? SROWB : ROWB;  // bytes between slab rows
 #pragma unroll
             for (int dxi = 0; dxi < 3; ++dxi)
 #pragma unroll
                 for (int kk = 0; kk < CINP / 16; ++kk) {
                     const uint64_t bk = tc_desc(wbase + (uint32_t)((dzi * 3 + dxi) * NCH + 2 * kk) * WCH, WCH, 128);
                     // output cell i of tap dx reads input cell x0 + i + dx - 1
-                    const uint64_t ak = adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(kTcRowX0 - 1 + dxi);
+                    const uint64_t ak = SW ? adz + (uint64_t)((kk * 32) >> 4) + (uint64_t)(((kTcRowX0 - 1 + dxi) * 64) >> 4)
+                                           : adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(kTcRowX0 - 1 + dxi);
                     // slab rows 5 and 2 first: together they touch every output row once
 #pragma unroll
                     for (int q = 0; q < kTcSlabRows; ++q) {
@@ -853,7 +883,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                         const int rhi = sr < kTcRows - 1 ? sr : kTcRows - 1;
                         const int b0 = 2 - sr + rlo;  // first dy block (dy = +1 - block)
                         const bool fresh = dzi == 0 && dxi == 0 && kk == 0 && q < 2;
-                        tc_mma_if(leader, dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * (ROWB >> 4)),
+                        tc_mma_if(leader, dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * (AROW >> 4)),
                                   bk + (uint64_t)((b0 * NT * 16) >> 4), idn[rhi - rlo], fresh ? 0u : 1u);
                     }
                 }
@@ -1151,8 +1181,10 @@ int tc_launch(gs_surr* s, ConvTcArgs a)
     constexpr uint32_t SLAB = (CINP / 8) * kTcSlabRows * kTcRowCells * 16;
     const size_t smem = 3 * (size_t)SLAB + (size_t)27 * (CINP / 8) * NT * 16;
     if (a.L % kTcCells) return fail(GS_EINVAL, "the tcgen05 path needs L %% %d == 0 (L=%d)", kTcCells, a.L);
-    if (encode_act_4d(&a.map_main, a.in, CINP, a.L, (long long)a.N * a.L, kTcCells) != CUDA_SUCCESS ||
-        encode_act_4d(&a.map_halo, a.in, CINP, a.L, (long long)a.N * a.L, 8) != CUDA_SUCCESS)
+    constexpr bool SW = CINP == 32;  // see gs_conv_tc_kernel
+    const int box_c = SW ? 32 : 8;
+    if (encode_act_4d(&a.map_main, a.in, CINP, a.L, (long long)a.N * a.L, box_c, kTcCells, SW) != CUDA_SUCCESS ||
+        encode_act_4d(&a.map_halo, a.in, CINP, a.L, (long long)a.N * a.L, box_c, 8, SW) != CUDA_SUCCESS)
         return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for the activation maps");
     auto k = gs_conv_tc_kernel<CINP, NT, EPI>;
     GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

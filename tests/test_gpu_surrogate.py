@@ -173,10 +173,11 @@ def test_surrogate_argument_errors():
 # ---------------------------------------------------------------------------
 # 5th-generation tensor-core (tcgen05) forward path, L % 128 == 0
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("N", [1, 2])
-def test_tcgen05_forward_matches_mma_path_and_oracle(N):
+# L = 128: three boxes per slab row; 256: a 136-cell box plus the wrapped
+# halo (both end segments); 384: also one 144-cell box (the middle segment)
+@pytest.mark.parametrize("L,N", [(128, 1), (128, 2), (256, 1), (384, 1)])
+def test_tcgen05_forward_matches_mma_path_and_oracle(L, N):
     torch = need_cuda()
-    L = 128
     params = inputs.surrogate_init_params(seed=21, last_scale=1.0)
     rng = np.random.default_rng(N)
     u = rng.uniform(0, 1, (N, L, L, L)).astype(np.float32)
@@ -196,7 +197,8 @@ def test_tcgen05_forward_matches_mma_path_and_oracle(N):
     print(f"tcgen05 vs mma.sync: max |d| {scale:.3e} max err {err.max():.3e} mean {err.mean():.3e}")
     assert err.max() <= 2e-2 * scale and err.mean() <= 1e-3 * scale
     for n in range(N):
-        for c in [(0, 0, 0), (127, 5, 64), (64, 127, 127)]:
+        # (x, y, z): segment edges in x (127 | 128, L - 1), wrap rows in y and z
+        for c in [(0, 0, 0), (127, 5, 64), (64, 127, 127), (L - 1, L - 4, L // 2), (L // 2, 0, L - 1)]:
             idx = [(np.arange(-6, 7) + cc) % L for cc in c]
             sel = np.ix_(idx[2], idx[1], idx[0])
             wu, wv = u[n][sel][None].astype(np.float64), v[n][sel][None].astype(np.float64)
