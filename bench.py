@@ -156,6 +156,13 @@ def cpu_oracle_sample(target_s: float = 12.0, L: int = L_MAIN):
                       f"({n} time steps, {dt:.1f} s, {threads} OpenMP threads)"}
 
 
+def main_workload(L: int, time_steps: int) -> str:
+    """The headline workload, named the same in both arms' config."""
+    return (f"plain stencil FP32, L={L} ({L ** 3} cells), periodic, noise {NOISE} "
+            f"(counter hash, seed {SEED}), Du=0.2 Dv=0.1 F=0.02 k=0.048 dt=1, "
+            f"centred-cube start, {time_steps} time steps per bench step")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -182,11 +189,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"FP64 CPU oracle, L={L}, noise {NOISE}, seed {SEED}; each bench step "
-                               f"= {per_step_time_steps} time steps (bounded sample of the 1000-step run)",
-                   "L": L},
+        "config": {"workload": main_workload(L, args.time_steps), "L": L, "time_steps": args.time_steps,
+                   "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": threads, "kind": "oracle",
-                         "sample": f"{per_step_time_steps} time steps per bench step at L={L}"},
+                         "sample": f"the FP64 oracle on a bounded sample of that workload: {per_step_time_steps} "
+                                   f"of its time steps per bench step at L={L}, timed on {threads} threads"},
         "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -603,9 +610,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"plain stencil FP32, L={L} ({cells} cells), periodic, noise {NOISE} "
-                                   f"(counter hash, seed {SEED}), Du=0.2 Dv=0.1 F=0.02 k=0.048 dt=1, "
-                                   f"centred-cube start, {args.time_steps} time steps per bench step",
+            "config": {"workload": main_workload(L, args.time_steps),
                        "L": L, "time_steps": args.time_steps,
                        "plan": plan,
                        "autotune": {"candidates": len(tune_trials), "best_us_per_step": tune_best["us_per_step"]},
