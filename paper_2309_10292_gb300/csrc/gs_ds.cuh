@@ -69,14 +69,17 @@ GS_D GsDS ds_from_double(double x)
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
     const uint32_t sign = h & 0x80000000u;
-    const int e = (int)((h >> 20) & 0x7FFu);  // biased FP64 exponent
-    // hi: sign, exponent e - 1023 (float bias 127), the top 23 stored bits
-    const uint32_t mhi = ((h & 0xFFFFFu) << 3) | (l >> 29);
-    const float hi = e >= 897 ? __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | mhi) : __uint_as_float(sign);
-    // lo: the remaining 29 bits, weight 2^(e - 1075)
+    const uint32_t ah = h & 0x7FFFFFFFu;  // |x|: biased exponent e at bits 20-30
+    // hi: (h:l) << 3 puts e's low 8 bits at 23-30 and the top 23 stored bits
+    // at 0-22; the float exponent e - 896 is e's low 8 bits with bit 7
+    // flipped (896 = 3 * 256 + 128), exact for 897 <= e <= 1150
+    const uint32_t hb = ((__funnelshift_l(l, h, 3) & 0x7FFFFFFFu) ^ 0x40000000u) | sign;
+    const float hi = __uint_as_float(ah >= (897u << 20) ? hb : sign);
+    // lo: the remaining 29 bits, weight 2^(e - 1075) = the float exponent
+    // field of hi minus 52
     const float r = __uint2float_rn(l & 0x1FFFFFFFu);
-    const float scale = __uint_as_float((uint32_t)(e >= 949 ? e - 948 : 1) << 23);
-    const float lo = e >= 949 ? __uint_as_float(sign | __float_as_uint(__fmul_rn(r, scale))) : 0.0f;
+    const float scale = __uint_as_float((hb & 0x7F800000u) - (52u << 23));
+    const float lo = ah >= (949u << 20) ? __uint_as_float(sign | __float_as_uint(__fmul_rn(r, scale))) : 0.0f;
     return GsDS{hi, lo};
 }
 
@@ -119,13 +122,21 @@ inline GsCoefDS gs_make_coef_ds(double Du, double Dv, double F, double k, double
     return c;
 }
 
+// sum of the six neighbours: the hi parts through error-free two-sums, their
+// errors and the lo parts accumulated in one float, one renormalisation
 GS_D GsDS ds_nsum(GsDS xm, GsDS xp, GsDS ym, GsDS yp, GsDS zm, GsDS zp)
 {
-    GsDS s = ds_add(xm, xp);
-    s = ds_add(s, ym);
-    s = ds_add(s, yp);
-    s = ds_add(s, zm);
-    return ds_add(s, zp);
+    GsDS s = ds_two_sum(xm.hi, xp.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(xm.lo, xp.lo));
+    s = ds_two_sum(s.hi, ym.hi);
+    e = __fadd_rn(e, __fadd_rn(s.lo, ym.lo));
+    s = ds_two_sum(s.hi, yp.hi);
+    e = __fadd_rn(e, __fadd_rn(s.lo, yp.lo));
+    s = ds_two_sum(s.hi, zm.hi);
+    e = __fadd_rn(e, __fadd_rn(s.lo, zm.lo));
+    s = ds_two_sum(s.hi, zp.hi);
+    e = __fadd_rn(e, __fadd_rn(s.lo, zp.lo));
+    return ds_fast_two_sum(s.hi, e);
 }
 
 // gs_update's steps in double-single (same order; rnum is the exact noise numerator)
