@@ -155,27 +155,51 @@ GS_D void gs_update_ds(const GsCoefDS& c, GsDS u, GsDS v, GsDS su, GsDS sv, floa
     vn = ds_add(ds_mul(dv, c.dt), v);
 }
 
-// A 2-cell group of FP64 cells (the z-marching kernels' double2 groups).
-template <bool NOISE>
+// A double-single pair kept in the 8 bytes of a double (hi in the low word):
+// the z-marching kernel converts each staged plane in place once, so its
+// neighbours are read already converted.
+GS_D double ds_pack(GsDS a)
+{
+    return __longlong_as_double(
+        (long long)(((unsigned long long)__float_as_uint(a.lo) << 32) | (unsigned long long)__float_as_uint(a.hi)));
+}
+
+GS_D GsDS ds_unpack(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return GsDS{__uint_as_float((uint32_t)b), __uint_as_float((uint32_t)(b >> 32))};
+}
+
+struct GsFromDouble {
+    GS_D GsDS operator()(double x) const { return ds_from_double(x); }
+};
+struct GsFromPacked {
+    GS_D GsDS operator()(double x) const { return ds_unpack(x); }
+};
+
+// A 2-cell group of FP64 cells (the z-marching kernels' double2 groups);
+// `get` turns an input into a pair (conversion of an FP64 value, or a pair
+// packed by ds_pack): the arithmetic is the same either way.
+template <bool NOISE, typename Get = GsFromDouble>
 GS_D void gs_update_group_ds(const GsCoefDS& c, uint32_t pre, uint32_t kk2, const double* cu, const double* cv,
                              const double* pu, const double* pv, const double* nu, const double* nv,
                              const double* ymu, const double* ypu, const double* ymv, const double* ypv,
-                             double xlu, double xru, double xlv, double xrv, double* ou, double* ov)
+                             double xlu, double xru, double xlv, double xrv, double* ou, double* ov, Get get = Get())
 {
     GsDS u[2], v[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        u[e] = ds_from_double(cu[e]);
-        v[e] = ds_from_double(cv[e]);
+        u[e] = get(cu[e]);
+        v[e] = get(cv[e]);
     }
-    const GsDS xlU = ds_from_double(xlu), xrU = ds_from_double(xru);
-    const GsDS xlV = ds_from_double(xlv), xrV = ds_from_double(xrv);
+    const GsDS xlU = get(xlu), xrU = get(xru);
+    const GsDS xlV = get(xlv), xrV = get(xrv);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const GsDS su = ds_nsum(e > 0 ? u[0] : xlU, e < 1 ? u[1] : xrU, ds_from_double(ymu[e]),
-                                ds_from_double(ypu[e]), ds_from_double(pu[e]), ds_from_double(nu[e]));
-        const GsDS sv = ds_nsum(e > 0 ? v[0] : xlV, e < 1 ? v[1] : xrV, ds_from_double(ymv[e]),
-                                ds_from_double(ypv[e]), ds_from_double(pv[e]), ds_from_double(nv[e]));
+        const GsDS su = ds_nsum(e > 0 ? u[0] : xlU, e < 1 ? u[1] : xrU, get(ymu[e]), get(ypu[e]), get(pu[e]),
+                                get(nu[e]));
+        const GsDS sv = ds_nsum(e > 0 ? v[0] : xlV, e < 1 ? v[1] : xrV, get(ymv[e]), get(ypv[e]), get(pv[e]),
+                                get(nv[e]));
         const float rn = NOISE ? (float)gs_group_num(pre, (uint32_t)e, kk2) : 0.0f;
         GsDS un, vn;
         gs_update_ds<NOISE>(c, u[e], v[e], su, sv, rn, un, vn);

@@ -279,12 +279,15 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
     constexpr int V = GsVec<T>::N;
     using VT = typename GsVec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2 * 8];
+    // full / empty per stage; with DS also `conv`: one arrival per consumer
+    // warp once its part of the stage has been converted in place
+    __shared__ __align__(8) uint64_t bars[(DS ? 3 : 2) * 8];
     __shared__ volatile int abort_flag;
 
     const int S = a.stages;
     uint64_t* full = bars;
     uint64_t* empty = bars + S;
+    uint64_t* conv = bars + 2 * S;  // DS only
     const int nxv = a.tx / V;
     const int ncons = nxv * a.ty;
     const int cons_threads = (ncons + 31) & ~31;
@@ -297,6 +300,7 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         for (int s = 0; s < S; ++s) {
             gs_mbar_init(&full[s], 1);
             gs_mbar_init(&empty[s], cons_warps);
+            if constexpr (DS) gs_mbar_init(&conv[s], cons_warps);
         }
         abort_flag = 0;
         gs_fence_mbar_init();
@@ -366,6 +370,9 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         if (++cs == S) { cs = 0; cph ^= 1u; }
     };
     auto release = [&](int s) {
+        // DS: the in-place conversion wrote the stage; order those writes
+        // before the copy engine's next fill of it
+        if constexpr (DS) gs_fence_proxy_async();
         __syncwarp();
         if (lane == 0) gs_mbar_arrive(&empty[s]);
     };
@@ -400,6 +407,30 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         const int oxr = has_r ? moff + V : a.lay.right_off + rr * V;
         int64_t gidx = (int64_t)z0 * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
 
+        // DS: convert this thread's cells of stage s, and the halo entries only
+        // it reads, to packed double-single pairs in place, then announce it;
+        // every FP64 value is converted once per pass instead of at each use
+        auto convert_stage = [&](int s) {
+            if constexpr (DS) {
+                if (active) {
+#pragma unroll
+                    for (int f = 0; f < 2; ++f) {
+                        T* bf = ring + s * stage_elems + f * a.lay.field_elems;
+                        auto cvt = [&](int off) { bf[off] = ds_pack(ds_from_double(bf[off])); };
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            cvt(moff + e);
+                            if (row == 0) cvt(a.lay.top_off + xv * V + e);
+                            if (row + 1 == nvy) cvt(a.lay.bot_off + xv * V + e);
+                        }
+                        if (xv == 0) cvt(oxl);
+                        if (!has_r) cvt(oxr);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) gs_mbar_arrive(&conv[s]);
+            }
+        };
         auto load_centre = [&](T (&u)[V], T (&v)[V]) {
             const T* b = ring + cs * stage_elems;
             gs_unpack<T>(*reinterpret_cast<const VT*>(b + moff), u);
@@ -408,14 +439,25 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         // one plane: P, C, N are planes z-1, z, z+1 (N is loaded here); the
         // centre plane's stage is released afterwards
         int sc = 0;
+        uint32_t scp = 0;  // the centre stage's round parity
         auto plane = [&](T (&pu)[V], T (&pv)[V], T (&cu)[V], T (&cv)[V], T (&nu)[V], T (&nv)[V]) -> bool {
             const int sn = cs;
+            const uint32_t snp = cph;
             if (!wait_full()) return false;
+            convert_stage(cs);
             load_centre(nu, nv);
             const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
             const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
             const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
             const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
+            if constexpr (DS) {
+                // every warp's part of the centre stage is converted
+                if (!gs_mbar_wait(&conv[sc], scp, a.timeout_ns)) {
+                    gs_report(a.err, GS_DERR_TIMEOUT);
+                    abort_flag = 1;
+                    return false;
+                }
+            }
             if (active) {
                 T outu[V], outv[V];
                 const T* bu = ring + sc * stage_elems;
@@ -431,7 +473,7 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                 const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
                 if constexpr (DS)
                     gs_update_group_ds<NOISE>(a.cds, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
-                                              xlv, xrv, outu, outv);
+                                              xlv, xrv, outu, outv, GsFromPacked());
                 else
                     gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
                                               xlv, xrv, outu, outv);
@@ -440,6 +482,7 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
             }
             release(sc);
             sc = sn;
+            scp = snp;
             advance();
             gidx += LL;
             return true;
@@ -447,12 +490,15 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
 
         // plane z0 - 1: centre values only
         if (!wait_full()) return;
+        convert_stage(cs);
         load_centre(qu[0], qv[0]);
         release(cs);
         advance();
         // plane z0
         sc = cs;
+        scp = cph;
         if (!wait_full()) return;
+        convert_stage(cs);
         load_centre(qu[1], qv[1]);
         advance();
 
