@@ -326,10 +326,30 @@ def test_autotune_restores_state_and_keeps_fastest_plan(dtype):
 # ---------------------------------------------------------------------------
 # FP64 fields in double-single arithmetic (GS_ARITH_DS)
 # ---------------------------------------------------------------------------
-def make_ds(L, kernel=None, **kw):
-    sim = make(L, "f64", kernel, **kw)
+def make_ds(L, kernel=None, tiles=(0, 0, 0), **kw):
+    sim = make(L, "f64", kernel, tiles, **kw)
     sim.arith = gs.GS_ARITH_DS
     return sim
+
+
+# partial tiles in x and y (the z-march kernel converts each staged plane in
+# place, its own cells and the halo entries each thread alone reads)
+@pytest.mark.parametrize("tiles", [(32, 16, 16), (16, 6, 7), (8, 4, 40), (40, 1, 3)])
+def test_ds_zmarch_partial_tiles_bitwise_equal_plain(tiles):
+    L, n = 40, 12
+    prm = dict(PAPER, noise=0.1, seed=11)
+    u0, v0 = inputs.random_fields(L, seed=5, lo=0.0, hi=1.0)
+    a = make_ds(L, gs.GS_KERNEL_NAIVE, **prm)
+    b = make_ds(L, gs.GS_KERNEL_ZMARCH, tiles, **prm)
+    for s in (a, b):
+        s.write(u0, v0)
+        s.step(n)
+    ua, va = a.read()
+    ub, vb = b.read()
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(va, vb)
+    uo, vo = oracle.step(u0, v0, n, **prm)
+    assert max(maxabs(ub, uo), maxabs(vb, vo)) <= TOL["f64"]
 
 
 @pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
