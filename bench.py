@@ -443,6 +443,7 @@ def bench_surrogate(args, stream):
         return sim
     plain = fresh("f32")
     plain.autotune(steps_per_trial=12)
+    tuned = plain.plan
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plain.step(n)
@@ -451,6 +452,8 @@ def bench_surrogate(args, stream):
     up, vp = plain.read()
     plain.close()
     s32 = fresh("f32")
+    # the surrogate's stencil checks and fallbacks use the same tuned plan
+    s32.set_plan(tuned["kernel"], tuned["tile_x"], tuned["tile_y"], tuned["tile_z"], tuned["depth"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rep = net.run(s32, F, k, n, check_every=64, tol=args.surr_tol)
@@ -472,6 +475,7 @@ def bench_surrogate(args, stream):
             "forward_ms_L256": fwd_s * 1e3,
             "forward_tflops": flop / fwd_s / 1e12,
             "time_to_state_s": {"surrogate_run": t_surr, "plain_fp32": t_plain},
+            "plain_plan": tuned,
             "speedup_vs_plain": t_plain / t_surr,
             "report": rep,
             "max_abs_error_vs_fp32_stencil": err((us, vs), (up, vp)),
