@@ -69,6 +69,18 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def source_digest() -> str:
+    """sha256 (16 hex digits) of every library source and header: names the
+    exact code a bench line measured."""
+    import glob
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", "*")) +
+                    glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_digest() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SRC:
@@ -631,7 +643,8 @@ def run_ours(args):
                        "plan": plan,
                        "autotune": {"candidates": len(tune_trials), "best_us_per_step": tune_best["us_per_step"]},
                        "l2": "inputs larger than L2 (4 field buffers of %.2f GB)" % (cells * 4 / 1e9),
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "source_sha256_16": source_digest()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic,
                          "kernel": kname, "launches": stencil_launches,

@@ -1,0 +1,89 @@
+"""Out-of-bounds writes, caught without a sanitizer: the four field buffers
+of a grid live inside one device allocation, separated by guard bands
+filled with a NaN bit pattern.  Every kernel runs a few steps (odd and even
+counts, so both buffers of each pair are written); the guard bands must keep
+their bits and the fields must equal an ordinary run's bit for bit.
+"""
+import numpy as np
+import pytest
+
+from paper_2309_10292_gb300 import gs
+from tests.gpu_util import PAPER, need_cuda
+
+pytestmark = pytest.mark.gpu
+
+GUARD = 64 * 1024  # bytes before, between and after the four fields
+POISON = {"f32": 0x7FC0BEEF, "f64": 0x7FF8DEADBEEFCAFE}
+
+
+def _guarded(torch, L, dtype):
+    esz = 4 if dtype == "f32" else 8
+    itype = torch.int32 if dtype == "f32" else torch.int64
+    ftype = torch.float32 if dtype == "f32" else torch.float64
+    field = -(-L ** 3 * esz // 256) * 256  # bytes, rounded up to 256
+    total = GUARD + 4 * (field + GUARD)
+    raw = torch.empty(total // esz, dtype=itype, device="cuda")
+    assert raw.data_ptr() % 256 == 0
+    raw.fill_(POISON[dtype])
+    fields, guards, pos = [], [(0, GUARD // esz)], GUARD // esz
+    for _ in range(4):
+        n = field // esz
+        fields.append(raw[pos:pos + L ** 3].view(ftype).view(L, L, L))
+        guards.append((pos + L ** 3, pos + n + GUARD // esz))
+        pos += n + GUARD // esz
+    return raw, fields, guards
+
+
+def _check_guards(raw, guards, dtype):
+    want = POISON[dtype]
+    host = raw.cpu().numpy()
+    for a, b in guards:
+        bad = np.nonzero(host[a:b] != want)[0]
+        assert bad.size == 0, f"guard band [{a}, {b}) overwritten at {a + bad[:5]}"
+
+
+CASES = [
+    # (L, dtype, kernel, tiles, depth, arith, boundary)
+    (17, "f32", gs.GS_KERNEL_NAIVE, (0, 0, 0), 0, None, None),
+    (17, "f64", gs.GS_KERNEL_NAIVE, (0, 0, 0), 0, None, None),
+    (40, "f32", gs.GS_KERNEL_ZMARCH, (32, 16, 16), 0, None, None),
+    (40, "f64", gs.GS_KERNEL_ZMARCH, (16, 6, 7), 0, None, None),
+    (40, "f64", gs.GS_KERNEL_ZMARCH, (32, 16, 16), 0, gs.GS_ARITH_DS, None),
+    (48, "f32", gs.GS_KERNEL_TBLOCK, (16, 16, 16), 2, None, None),
+    (48, "f32", gs.GS_KERNEL_TBLOCK, (16, 16, 24), 3, None, None),
+    (48, "f32", gs.GS_KERNEL_TBLOCK, (16, 8, 48), 5, None, None),
+    (40, "f32", gs.GS_KERNEL_ZMARCH, (32, 8, 40), 0, None, gs.GS_BOUNDARY_HELD),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"L{c[0]}-{c[1]}-k{c[2]}-d{c[4]}-a{c[5]}-b{c[6]}")
+def test_kernels_stay_inside_their_fields(case):
+    torch = need_cuda()
+    L, dtype, kernel, tiles, depth, arith, boundary = case
+    prm = dict(PAPER, noise=0.1, seed=9)
+    raw, fields, guards = _guarded(torch, L, dtype)
+    stream = torch.cuda.current_stream()
+    h = gs.gs_create_on(L, prm["Du"], prm["Dv"], prm["F"], prm["k"], prm["dt"], prm["noise"], prm["seed"],
+                        dtype, *fields, stream=stream)
+    ref = gs.GrayScott(L, dtype=dtype, **prm)
+    try:
+        for sim in (h, ref.handle):
+            if boundary is not None:
+                gs.gs_set_boundary(sim, boundary)
+            if arith is not None:
+                gs.gs_set_arith(sim, arith)
+        gs.gs_set_plan(h, kernel, *tiles, depth)
+        for n in (3, 4):  # an odd and an even count: both buffers of each field written
+            gs.gs_step(h, n)
+            ref.step(n)
+            gs.gs_sync(h)
+            _check_guards(raw, guards, dtype)
+        out = np.empty((L, L, L), dtype=np.float32 if dtype == "f32" else np.float64)
+        for f in (gs.GS_U, gs.GS_V):
+            gs.gs_read(h, f, out)
+            want = ref.read()[f]
+            np.testing.assert_array_equal(out, want)
+        assert np.isfinite(out).all()
+    finally:
+        gs.gs_destroy(h)
+        ref.close()
