@@ -180,6 +180,20 @@ int gs_get_plan_full(gs_sim* sim, gs_plan* out);
 int gs_autotune(gs_sim* sim, int steps_per_trial, gs_plan* results, int max_results, int* n_results,
                 gs_plan* best);
 
+/* Autotuner with a plan cache file `path` (not in the paper).  The key is
+ * the device name and compute capability, L, dtype, FP64 arithmetic,
+ * boundary and whether noise is on.  If the file holds a plan for this key
+ * (the last such line) that this build still accepts, it is set without
+ * timing and *hit = 1; otherwise gs_autotune runs, its plan is appended to
+ * the file and *hit = 0.  *best (may be NULL) receives the plan with the
+ * tuner's time per step.  File format, one line per plan:
+ *   gs-plan-v1 <key> <kernel> <tile_x> <tile_y> <tile_z> <depth> <stages> <us_per_step>
+ * with key = <device>/sm<major><minor>/L<L>/<f32|f64>/<ieee|ds>/<periodic|held>/<noise|still>
+ * (spaces in the device name as '_'); lines that do not parse are skipped.
+ * GS_EINVAL for NULL sim / path or steps_per_trial < 1, GS_EIO if the file
+ * cannot be appended to, else as gs_autotune.  Synchronous. */
+int gs_autotune_cached(gs_sim* sim, int steps_per_trial, const char* path, gs_plan* best, int* hit);
+
 /* Wait for the object's stream and report any device-side failure. */
 int gs_sync(gs_sim* sim);
 

@@ -533,6 +533,76 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
     return GS_OK;
 }
 
+// Plan cache: one text line per tuned configuration,
+//   gs-plan-v1 <key> <kernel> <tile_x> <tile_y> <tile_z> <depth> <stages> <us_per_step>
+// with key = <device name>/sm<major><minor>/L<L>/<f32|f64>/<ieee|ds>/<periodic|held>/<noise|still>
+// (spaces and '/' in the device name written as '_').
+static int plan_key(gs_sim* s, char* key, size_t n)
+{
+    int dev = 0;
+    GS_CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp pr;
+    GS_CUDA_TRY(cudaGetDeviceProperties(&pr, dev));
+    char name[sizeof(pr.name) + 1];
+    size_t i = 0;
+    for (; i < sizeof(pr.name) && pr.name[i]; ++i) name[i] = (pr.name[i] == ' ' || pr.name[i] == '/') ? '_' : pr.name[i];
+    name[i] = 0;
+    snprintf(key, n, "%s/sm%d%d/L%d/%s/%s/%s/%s", name, pr.major, pr.minor, s->L, s->dtype == GS_F32 ? "f32" : "f64",
+             s->p.arith == GS_ARITH_DS ? "ds" : "ieee", s->boundary == GS_BOUNDARY_HELD ? "held" : "periodic",
+             s->p.noise != 0.0 ? "noise" : "still");
+    return GS_OK;
+}
+
+int gs_autotune_cached(gs_sim* s, int steps_per_trial, const char* path, gs_plan* best, int* hit)
+{
+    if (!s || !path) return fail(GS_EINVAL, "sim and path must not be NULL");
+    if (steps_per_trial < 1) return fail(GS_EINVAL, "steps_per_trial must be >= 1");
+    char key[512];
+    int rc = plan_key(s, key, sizeof key);
+    if (rc) return rc;
+    // the last line with this key wins; lines that do not parse are skipped
+    gs_plan found{};
+    bool have = false;
+    if (FILE* f = fopen(path, "r")) {
+        char line[1024];
+        while (fgets(line, sizeof line, f)) {
+            char k[512];
+            gs_plan q{};
+            if (sscanf(line, "gs-plan-v1 %511s %d %d %d %d %d %d %lf", k, &q.kernel, &q.tile_x, &q.tile_y, &q.tile_z,
+                       &q.depth, &q.stages, &q.us_per_step) == 8 &&
+                strcmp(k, key) == 0) {
+                found = q;
+                have = true;
+            }
+        }
+        fclose(f);
+    }
+    if (have) {
+        const gs_plan before = current_plan(s);
+        if (apply_plan(s, found.kernel, found.tile_x, found.tile_y, found.tile_z, found.depth, found.stages) == GS_OK) {
+            s->plan_us = found.us_per_step;
+            if (best) {
+                *best = current_plan(s);
+                best->us_per_step = found.us_per_step;
+            }
+            if (hit) *hit = 1;
+            return GS_OK;
+        }
+        // a plan this build or GPU no longer accepts: tune afresh
+        apply_plan(s, before.kernel, before.tile_x, before.tile_y, before.tile_z, before.depth, before.stages);
+    }
+    gs_plan b{};
+    if ((rc = gs_autotune(s, steps_per_trial, nullptr, 0, nullptr, &b))) return rc;
+    FILE* w = fopen(path, "a");
+    if (!w) return fail(GS_EIO, "cannot append to the plan cache %s", path);
+    const int n = fprintf(w, "gs-plan-v1 %s %d %d %d %d %d %d %.17g\n", key, b.kernel, b.tile_x, b.tile_y, b.tile_z,
+                          b.depth, b.stages, b.us_per_step);
+    if (fclose(w) != 0 || n < 0) return fail(GS_EIO, "writing the plan cache %s failed", path);
+    if (best) *best = b;
+    if (hit) *hit = 0;
+    return GS_OK;
+}
+
 int gs_get_plan(gs_sim* s, int* kernel, int* tx, int* ty, int* tz, int* depth)
 {
     if (!s) return fail(GS_EINVAL, "sim is NULL");

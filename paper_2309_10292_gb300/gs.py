@@ -63,6 +63,7 @@ _SIGS = {
     "gs_sync": [_vp],
     "gs_set_plan_full": [_vp, _vp],
     "gs_autotune": [_vp, _i, _vp, _i, ctypes.POINTER(_i), _vp],
+    "gs_autotune_cached": [_vp, _i, ctypes.c_char_p, _vp, ctypes.POINTER(_i)],
     "gs_set_fault": [_vp, _i, _u64],
     "gs_launch_count": [_vp, ctypes.POINTER(_i64)],
     "gs_destroy": [_vp],
@@ -288,6 +289,15 @@ def gs_autotune(sim, steps_per_trial: int = 12, max_results: int = 256):
     _check(lib().gs_autotune(sim, steps_per_trial, res, max_results, ctypes.byref(n), ctypes.byref(best)),
            "gs_autotune")
     return best.as_dict(), [res[i].as_dict() for i in range(min(n.value, max_results))]
+
+
+def gs_autotune_cached(sim, path: str, steps_per_trial: int = 12):
+    """Autotune through the plan cache file `path`; returns (best plan dict, hit)."""
+    best = GsPlan()
+    hit = _i()
+    _check(lib().gs_autotune_cached(sim, steps_per_trial, os.fsencode(path), ctypes.byref(best), ctypes.byref(hit)),
+           "gs_autotune_cached")
+    return best.as_dict(), bool(hit.value)
 
 
 def gs_sync(sim):
@@ -819,6 +829,11 @@ class GrayScott:
     def autotune(self, steps_per_trial: int = 12):
         """Pick the fastest plan for this grid (state is left unchanged)."""
         return gs_autotune(self.handle, steps_per_trial)
+
+    def autotune_cached(self, path: str, steps_per_trial: int = 12):
+        """Autotune once per device / grid configuration, remembered in the
+        plan cache file `path`; returns (plan, hit)."""
+        return gs_autotune_cached(self.handle, path, steps_per_trial)
 
     @property
     def t(self) -> int:

@@ -87,3 +87,45 @@ def test_kernels_stay_inside_their_fields(case):
     finally:
         gs.gs_destroy(h)
         ref.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_noalloc_stays_inside_its_instances(dtype):
+    # a caller-owned arena between guard bands; the alignment padding between
+    # the instances' fields is poisoned too and must keep its bits
+    torch = need_cuda()
+    v4 = dtype == "f32"
+    Ls = [8, 12 if v4 else 6, 32, 48, 4 if v4 else 2, 64]
+    F = list(np.linspace(0.01, 0.06, len(Ls)))
+    k = list(np.linspace(0.07, 0.04, len(Ls)))
+    base = dict(Du=0.2, Dv=0.1, dt=1.0)
+    ref = gs.GrayScottBatch(Ls, F, k, noise=0.1, seed=3, dtype=dtype, **base)
+    offs, total = gs.noalloc_arena_offsets(Ls, dtype)
+    esz = 4 if v4 else 8
+    g = GUARD // esz
+    itype = torch.int32 if v4 else torch.int64
+    ftype = torch.float32 if v4 else torch.float64
+    raw = torch.empty(g + total + g, dtype=itype, device="cuda")
+    raw.fill_(POISON[dtype])
+    arena = raw[g:g + total].view(ftype)
+    assert arena.data_ptr() % 256 == 0
+    live = np.zeros(total, dtype=bool)
+    for i, L in enumerate(Ls):
+        u, v = ref.read(i)
+        for j, f in enumerate((u, v)):
+            arena[offs[i][j]:offs[i][j] + L ** 3] = torch.from_numpy(f.ravel()).to("cuda")
+        for j in range(4):
+            live[offs[i][j]:offs[i][j] + L ** 3] = True
+    torch.cuda.synchronize()
+    gs.gs_batch_step_noalloc(Ls, F, k, base["Du"], base["Dv"], base["dt"], 0.1, 3, dtype, arena, 0, 0, 5,
+                             torch.cuda.current_stream())
+    ref.step(5)
+    host = raw.cpu().numpy()
+    want = POISON[dtype]
+    assert (host[:g] == want).all() and (host[g + total:] == want).all()
+    pad = host[g:g + total][~live]
+    assert (pad == want).all(), f"{int((pad != want).sum())} padding elements overwritten"
+    for i, L in enumerate(Ls):  # the state after an odd step count is in set 1
+        got = arena[offs[i][2]:offs[i][2] + L ** 3].cpu().numpy().reshape(L, L, L)
+        np.testing.assert_array_equal(got, ref.read(i)[0])
+    ref.close()

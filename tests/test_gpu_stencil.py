@@ -421,3 +421,39 @@ def test_ds_only_for_fp64_fields():
     s64 = make(16, "f64")
     with pytest.raises(gs.GsError):
         s64.arith = 5
+
+
+# ---------------------------------------------------------------------------
+# Plan cache (gs_autotune_cached)
+# ---------------------------------------------------------------------------
+def test_plan_cache_tunes_once_per_configuration(tmp_path):
+    need_cuda()
+    path = str(tmp_path / "plans.txt")
+    with open(path, "w") as f:
+        f.write("not a plan line\ngs-plan-v1 too few fields\n")
+    a = make(24, "f32", noise=0.1, seed=1)
+    best, hit = a.autotune_cached(path, steps_per_trial=1)
+    assert not hit and best["us_per_step"] > 0
+    lines = [l for l in open(path) if l.startswith("gs-plan-v1 ") and len(l.split()) == 9]
+    assert len(lines) == 1 and "/L24/f32/ieee/periodic/noise" in lines[0]
+    # same configuration: the cached plan, no timing, same fields afterwards
+    b = make(24, "f32", noise=0.1, seed=1)
+    best2, hit2 = b.autotune_cached(path, steps_per_trial=1)
+    assert hit2 and best2 == best
+    assert b.plan["kernel"] == best["kernel"] and b.plan["tile_x"] == best["tile_x"]
+    for s in (a, b):
+        s.step(5)
+    ua, va = a.read()
+    ub, vb = b.read()
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(va, vb)
+    # another configuration (no noise) is a miss and appends a second line
+    c = make(24, "f32", noise=0.0, seed=1)
+    _, hit3 = c.autotune_cached(path, steps_per_trial=1)
+    assert not hit3
+    assert sum(1 for l in open(path) if l.startswith("gs-plan-v1 ") and len(l.split()) == 9) == 2
+    # a directory is not a writable cache file
+    d = make(16, "f32")
+    with pytest.raises(gs.GsError) as e:
+        d.autotune_cached(str(tmp_path), steps_per_trial=1)
+    assert e.value.status == gs.GS_EIO
