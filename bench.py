@@ -612,6 +612,18 @@ def run_ours(args):
         n64 = 100
         g64 = fp64_rate(gs.GS_ARITH_IEEE)
         g64ds = fp64_rate(gs.GS_ARITH_DS)
+        # precision: the FP32 result of the whole workload (the e2e run's
+        # output) against the same run in IEEE FP64 on the GPU
+        s64 = gs.GrayScott(L, dtype="f64", noise=NOISE, seed=SEED, **PARAMS)
+        s64.step(args.time_steps)
+        u64, v64 = s64.read()
+        s64.close()
+        du = float(np.abs(uo.numpy().astype(np.float64) - u64).max())
+        dv = float(np.abs(vo.numpy().astype(np.float64) - v64).max())
+        del u64, v64
+        extra["accuracy"] = {"fp32_vs_fp64_max_abs": {"u": du, "v": dv}, "time_steps": args.time_steps,
+                             "note": "the FP32 workload's final fields against the same run in IEEE FP64 "
+                                     "on the GPU (the FP64 kernels match the FP64 oracle within 1e-10, tested)"}
         extra["fp64"] = {"value": g64, "unit": "GCUPS", "time_steps": n64,
                          "hbm_frac": g64 * 32.0 / hbm_peak, "note": "same workload in FP64 (IEEE arithmetic)",
                          "double_single": {"value": g64ds, "unit": "GCUPS", "hbm_frac": g64ds * 32.0 / hbm_peak,
