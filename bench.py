@@ -473,9 +473,21 @@ def bench_surrogate(args, stream):
     us, vs = s32.read()
     s32.close()
     s64 = fresh("f64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     s64.step(n)
+    s64.sync()
+    t_fp64 = time.perf_counter() - t0
     u64, v64 = s64.read()
     s64.close()
+    sds = fresh("f64")
+    sds.arith = gs.GS_ARITH_DS
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sds.step(n)
+    sds.sync()
+    t_ds = time.perf_counter() - t0
+    sds.close()
     net.close()
     err = lambda a, b: float(max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()))
     return {"workload": f"surrogate trained on {args.surr_iters} pairs of L=128 stencil trajectories "
@@ -486,7 +498,8 @@ def bench_surrogate(args, stream):
             "heldout_rms_network": ev["rms_network"], "heldout_rms_no_change": ev["rms_persistence"],
             "forward_ms_L256": fwd_s * 1e3,
             "forward_tflops": flop / fwd_s / 1e12,
-            "time_to_state_s": {"surrogate_run": t_surr, "plain_fp32": t_plain},
+            "time_to_state_s": {"surrogate_run": t_surr, "plain_fp32": t_plain, "plain_fp64_ieee": t_fp64,
+                                "plain_fp64_double_single": t_ds},
             "plain_plan": tuned,
             "speedup_vs_plain": t_plain / t_surr,
             "report": rep,
