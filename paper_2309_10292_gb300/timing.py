@@ -1,0 +1,58 @@
+"""Time one stencil configuration from the command line (cell updates per
+second, CUDA events on the grid's stream), e.g.
+
+    python -m paper_2309_10292_gb300.timing --L 256 --dtype f64 --arith ds \
+        --plan zmarch,128,8,32 --steps 6
+
+prints one JSON line with the plan and the rate.  All compute runs in libgs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+KERNELS = {"naive": 1, "zmarch": 2, "tblock": 3}
+
+
+def main(argv=None):
+    import torch
+
+    from paper_2309_10292_gb300 import gs
+    ap = argparse.ArgumentParser(description="time the Gray-Scott stencil on one grid")
+    ap.add_argument("--L", type=int, default=512)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--arith", default="ieee", choices=["ieee", "ds"])
+    ap.add_argument("--noise", type=float, default=0.1)
+    ap.add_argument("--plan", default="", help="kernel,tile_x,tile_y,tile_z[,depth[,stages]]; empty: autotune")
+    ap.add_argument("--steps", type=int, default=100, help="timed steps")
+    ap.add_argument("--warmup", type=int, default=5)
+    a = ap.parse_args(argv)
+    sim = gs.GrayScott(a.L, Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0, noise=a.noise, seed=42, dtype=a.dtype)
+    if a.arith == "ds":
+        sim.arith = gs.GS_ARITH_DS
+    if a.plan:
+        f = a.plan.split(",")
+        nums = [int(x) for x in f[1:]] + [0] * (5 - len(f[1:]))
+        plan = {"kernel": KERNELS[f[0]], "tile_x": nums[0], "tile_y": nums[1], "tile_z": nums[2],
+                "depth": nums[3] or 1, "stages": nums[4], "us_per_step": 0.0}
+        gs.gs_set_plan_full(sim.handle, plan)
+    else:
+        sim.autotune()
+    sim.step(a.warmup)
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    sim.step(a.steps)
+    t1.record(stream)
+    sim.sync()
+    ms = t0.elapsed_time(t1)
+    out = {"L": a.L, "dtype": a.dtype, "arith": a.arith, "noise": a.noise, "plan": sim.plan,
+           "steps": a.steps, "ms": ms, "gcups": a.L ** 3 * a.steps / (ms / 1e3) / 1e9}
+    sim.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
