@@ -101,6 +101,7 @@ GS_D double ds_to_double(GsDS a) { return __dadd_rn(ds_widen(a.hi), ds_widen(a.l
 // nearest float to the rest.
 struct GsCoefDS {
     GsDS Du6, Dv6, F, Fk, dt, noise24, one;
+    int dt_one;  // dt == 1 exactly: the products du * dt are skipped (same bits)
 };
 
 inline GsDS gs_ds_host(double d)
@@ -119,6 +120,7 @@ inline GsCoefDS gs_make_coef_ds(double Du, double Dv, double F, double k, double
     c.dt = gs_ds_host(dt);
     c.noise24 = gs_ds_host(noise / 16777216.0);
     c.one = GsDS{1.0f, 0.0f};
+    c.dt_one = dt == 1.0;
     return c;
 }
 
@@ -151,8 +153,11 @@ GS_D void gs_update_ds(const GsCoefDS& c, GsDS u, GsDS v, GsDS su, GsDS sv, floa
     if (NOISE) du = ds_add(ds_mul_f(c.noise24, rnum), du);      // + n r
     GsDS dv = ds_add(ds_mul(c.Dv6, lv), uvv);                   // Dv lap v + u v^2
     dv = ds_add(ds_mul(ds_neg(c.Fk), v), dv);                   // - (F + k) v
-    un = ds_add(ds_mul(du, c.dt), u);                           // u + dt du
-    vn = ds_add(ds_mul(dv, c.dt), v);
+    // u + dt du.  With dt = 1 the product is skipped: du leaves ds_add
+    // through a fast two-sum, whose output it reproduces bit for bit, so the
+    // result is identical either way.
+    un = ds_add(c.dt_one ? du : ds_mul(du, c.dt), u);
+    vn = ds_add(c.dt_one ? dv : ds_mul(dv, c.dt), v);
 }
 
 // A double-single pair kept in the 8 bytes of a double (hi in the low word):
