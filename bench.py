@@ -639,6 +639,12 @@ def run_ours(args):
                                      "on the GPU (the FP64 kernels match the FP64 oracle within 1e-10, tested)"}
         extra["fp64"] = {"value": g64, "unit": "GCUPS", "time_steps": n64,
                          "hbm_frac": g64 * 32.0 / hbm_peak, "note": "same workload in FP64 (IEEE arithmetic)",
+                         # the FP64 pipe bounds it: 22 FP64 operations per cell (11 adds,
+                         # 9 FMAs, 2 multiplies) against the nominal 1.25 TFLOP/s = 0.625 T
+                         # FP64 pipe operations/s (an FMA counts 2 FLOP)
+                         "alu_roofline": {"bound": "alu", "achieved": g64 * 22.0, "peak": 625.0,
+                                          "unit": "G FP64 operations/s", "frac": g64 * 22.0 / 625.0,
+                                          "peak_kind": "nominal (1.25 TFLOP/s FP64)"},
                          "double_single": {"value": g64ds, "unit": "GCUPS", "hbm_frac": g64ds * 32.0 / hbm_peak,
                                            "note": "FP64 fields, double-single arithmetic on the FP32 pipe "
                                                    "(within 1e-13 of the FP64 oracle)"}}
