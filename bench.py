@@ -224,6 +224,7 @@ def bench_batched(args, stream, hbm_peak):
     cells = sum(L ** 3 for L in Ls)
     nsteps, nseq = args.batch_steps, max(1, args.batch_steps // 10)
     b = gs.GrayScottBatch(Ls, F, k, noise=NOISE, seed=SEED, dtype="f32", **base)
+    plan = b.autotune(steps_per_trial=20)  # z-chunk and ring depth of the persistent launch
     b.step(nsteps)  # capture + warm-up
     b.sync()
     b.init()
@@ -261,7 +262,7 @@ def bench_batched(args, stream, hbm_peak):
             "sequential_launches_per_step": len(Ls),
             "speedup_vs_sequential": g_pers / g_seq,
             "bitwise_equal_to_sequential": bool(equal),
-            "persistent_grid": info["grid"], "work_items_per_step": info["items"],
+            "persistent_grid": info["grid"], "work_items_per_step": info["items"], "plan": plan,
             "cooperative_attribute": info["cooperative"], "graph_launches": 1}
 
 

@@ -310,6 +310,16 @@ int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns);
  * drops the captured graphs. */
 int gs_batch_set_plan(gs_batch* b, int tile_z, int stages);
 
+/* Autotuner of the batched launch (not in the paper): time every z-chunk in
+ * {16, 32, 64} x ring depth in {4, 6, 8} that fits (steps_per_trial steps
+ * each, after one untimed run of the same length that captures the graph;
+ * CUDA events on the batch's stream), restore every instance's fields and
+ * the step counter exactly (the arena is copied to a temporary device buffer
+ * for the duration), and keep the fastest plan.  *best_tile_z,
+ * *best_stages, *best_us (may be NULL) receive it and its time per step.
+ * GS_EINVAL for a NULL batch or steps_per_trial < 1.  Synchronous. */
+int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* best_stages, double* best_us);
+
 /* Launch shape of the persistent kernel (CTAs, work items per step, whether
  * the cooperative launch attribute was accepted) and the number of kernel
  * launches issued so far. */

@@ -336,6 +336,7 @@ struct gs_batch {
     std::vector<ZPlan> zplan;               // per-instance plan of the sequential path
     std::vector<ZMaps> zmaps[2];            // per-instance tensor maps of the sequential path
     int nitems = 0, tz = 32, stages = 8, main_elems = 0, row_elems = 0, field_elems = 0;
+    size_t arena_bytes = 0;
     int grid = 0;
     int64_t t = 0;
     int cur = 0;
@@ -526,6 +527,7 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
     b->nitems = (int)item_inst.size();
     int rc = GS_OK;
     cudaError_t e;
+    b->arena_bytes = (size_t)off * esz;
     if ((e = cudaMalloc(&b->arena, (size_t)off * esz)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_inst, sizeof(BInst) * n)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_item_inst, sizeof(int) * b->nitems)) != cudaSuccess ||
@@ -651,6 +653,68 @@ int gs_batch_step_sequential(gs_batch* b, int64_t n)
         b->t += 1;
     }
     b->ctrl_dirty = true;
+    return GS_OK;
+}
+
+int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* best_stages, double* best_us)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (steps_per_trial < 1) return fail(GS_EINVAL, "steps_per_trial must be >= 1");
+    const int tz0 = b->tz, st0 = b->stages;
+    const int64_t t0 = b->t;
+    const int cur0 = b->cur;
+    void* saved = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    int rc = GS_OK;
+    if ((e = cudaMalloc(&saved, b->arena_bytes)) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
+        (e = cudaEventCreate(&e1)) != cudaSuccess)
+        rc = cuda_fail(e, "batch autotune set-up");
+    if (!rc && (e = cudaMemcpyAsync(saved, b->arena, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess)
+        rc = cuda_fail(e, "batch autotune save");
+    int win_tz = tz0, win_st = st0;
+    double win_us = -1.0;
+    for (int tz : {16, 32, 64}) {
+        for (int st : {4, 6, 8}) {
+            if (rc) break;
+            if (gs_batch_set_plan(b, tz, st) != GS_OK) continue;  // a ring that does not fit
+            int r = gs_batch_step(b, steps_per_trial);            // captures the graph, warms up
+            if (!r) r = gs_batch_sync(b);
+            if (!r && (e = cudaEventRecord(e0, b->stream)) != cudaSuccess) r = cuda_fail(e, "event");
+            if (!r) r = gs_batch_step(b, steps_per_trial);
+            if (!r && (e = cudaEventRecord(e1, b->stream)) != cudaSuccess) r = cuda_fail(e, "event");
+            if (!r) r = gs_batch_sync(b);
+            float ms = 0.f;
+            if (!r && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) r = cuda_fail(e, "event");
+            if (r) {
+                rc = r;
+                break;
+            }
+            const double us = 1e3 * ms / steps_per_trial;
+            if (win_us < 0 || us < win_us) {
+                win_us = us;
+                win_tz = tz;
+                win_st = st;
+            }
+        }
+    }
+    // restore the state, keep the winner (the previous plan on failure)
+    if (saved) {
+        cudaMemcpyAsync(b->arena, saved, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaStreamSynchronize(b->stream);
+        cudaFree(saved);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->t = t0;
+    b->cur = cur0;
+    b->ctrl_dirty = true;
+    const int rc2 = rc ? gs_batch_set_plan(b, tz0, st0) : gs_batch_set_plan(b, win_tz, win_st);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (best_tile_z) *best_tile_z = win_tz;
+    if (best_stages) *best_stages = win_st;
+    if (best_us) *best_us = win_us;
     return GS_OK;
 }
 

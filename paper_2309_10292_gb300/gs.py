@@ -63,6 +63,7 @@ _SIGS = {
     "gs_sync": [_vp],
     "gs_set_plan_full": [_vp, _vp],
     "gs_autotune": [_vp, _i, _vp, _i, ctypes.POINTER(_i), _vp],
+    "gs_batch_autotune": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)],
     "gs_autotune_cached": [_vp, _i, ctypes.c_char_p, _vp, ctypes.POINTER(_i)],
     "gs_set_fault": [_vp, _i, _u64],
     "gs_launch_count": [_vp, ctypes.POINTER(_i64)],
@@ -298,6 +299,14 @@ def gs_autotune_cached(sim, path: str, steps_per_trial: int = 12):
     _check(lib().gs_autotune_cached(sim, steps_per_trial, os.fsencode(path), ctypes.byref(best), ctypes.byref(hit)),
            "gs_autotune_cached")
     return best.as_dict(), bool(hit.value)
+
+
+def gs_batch_autotune(b, steps_per_trial: int = 20) -> dict:
+    """Tune the batched launch's z-chunk and ring depth; returns the kept plan."""
+    tz, st, us = _i(), _i(), ctypes.c_double()
+    _check(lib().gs_batch_autotune(b, steps_per_trial, ctypes.byref(tz), ctypes.byref(st), ctypes.byref(us)),
+           "gs_batch_autotune")
+    return {"tile_z": tz.value, "stages": st.value, "us_per_step": us.value}
 
 
 def gs_sync(sim):
@@ -756,6 +765,10 @@ class GrayScottBatch:
 
     def sync(self):
         gs_batch_sync(self.handle)
+
+    def autotune(self, steps_per_trial: int = 20) -> dict:
+        """Pick the batched launch's z-chunk and ring depth (state left unchanged)."""
+        return gs_batch_autotune(self.handle, steps_per_trial)
 
     @property
     def info(self) -> dict:

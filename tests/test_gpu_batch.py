@@ -174,3 +174,28 @@ def test_batch_plan_changes_no_bits(tz, stages):
     b.step(2)  # still usable after the rejected plans
     ref.close()
     b.close()
+
+
+def test_batch_autotune_keeps_state_and_results():
+    need_cuda()
+    Ls = [8, 16, 32, 48, 64]
+    F = list(np.linspace(0.02, 0.05, len(Ls)))
+    k = list(np.linspace(0.06, 0.045, len(Ls)))
+    a = gs.GrayScottBatch(Ls, F, k, noise=0.1, seed=11, **BASE)
+    b = gs.GrayScottBatch(Ls, F, k, noise=0.1, seed=11, **BASE)
+    a.step(3)
+    b.step(3)
+    before = [a.read(i) for i in range(len(Ls))]
+    plan = a.autotune(steps_per_trial=4)
+    assert plan["tile_z"] in (16, 32, 64) and plan["stages"] in (4, 6, 8) and plan["us_per_step"] > 0
+    assert a.t == 3
+    for i in range(len(Ls)):
+        np.testing.assert_array_equal(a.read(i)[0], before[i][0])
+        np.testing.assert_array_equal(a.read(i)[1], before[i][1])
+    a.step(7)
+    b.step(7)
+    for i in range(len(Ls)):
+        np.testing.assert_array_equal(a.read(i)[0], b.read(i)[0])
+        np.testing.assert_array_equal(a.read(i)[1], b.read(i)[1])
+    a.close()
+    b.close()
