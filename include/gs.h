@@ -133,6 +133,17 @@ int gs_read(gs_sim* sim, int field, void* host_dst, size_t bytes);
  * Synchronises the stream.  The step counter is unchanged. */
 int gs_write(gs_sim* sim, int field, const void* host_src, size_t bytes);
 
+/* Asynchronous forms of gs_read / gs_write (not in the paper): the copy is
+ * enqueued on the object's stream, in order with its steps, and the call
+ * returns.  The host buffer must stay valid, and for gs_read_async must not
+ * be read, until the stream has passed the copy (gs_sync, or an event the
+ * caller records on the stream).  With page-locked host memory the copy
+ * overlaps work on other streams, e.g. another simulation's steps.
+ * GS_EINVAL as gs_read / gs_write; a failed copy surfaces at the next
+ * synchronising call. */
+int gs_read_async(gs_sim* sim, int field, void* host_dst, size_t bytes);
+int gs_write_async(gs_sim* sim, int field, const void* host_src, size_t bytes);
+
 /* Device pointer of the current state's field (valid until the next
  * gs_step, which swaps the double buffers). */
 int gs_device_ptr(gs_sim* sim, int field, void** dev_ptr);

@@ -329,6 +329,24 @@ int gs_write(gs_sim* s, int field, const void* src, size_t bytes)
     return gs_sync(s);
 }
 
+int gs_read_async(gs_sim* s, int field, void* dst, size_t bytes)
+{
+    int rc = check_field(s, field, bytes);
+    if (rc) return rc;
+    if (!dst) return fail(GS_EINVAL, "dst is NULL");
+    GS_CUDA_TRY(cudaMemcpyAsync(dst, s->buf[s->cur][field], bytes, cudaMemcpyDeviceToHost, s->stream));
+    return GS_OK;
+}
+
+int gs_write_async(gs_sim* s, int field, const void* src, size_t bytes)
+{
+    int rc = check_field(s, field, bytes);
+    if (rc) return rc;
+    if (!src) return fail(GS_EINVAL, "src is NULL");
+    GS_CUDA_TRY(cudaMemcpyAsync(s->buf[s->cur][field], src, bytes, cudaMemcpyHostToDevice, s->stream));
+    return GS_OK;
+}
+
 int gs_device_ptr(gs_sim* s, int field, void** p)
 {
     if (!s || !p) return fail(GS_EINVAL, "NULL argument");

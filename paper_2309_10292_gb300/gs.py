@@ -64,6 +64,8 @@ _SIGS = {
     "gs_set_plan_full": [_vp, _vp],
     "gs_autotune": [_vp, _i, _vp, _i, ctypes.POINTER(_i), _vp],
     "gs_batch_autotune": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)],
+    "gs_read_async": [_vp, _i, _vp, _sz],
+    "gs_write_async": [_vp, _i, _vp, _sz],
     "gs_autotune_cached": [_vp, _i, ctypes.c_char_p, _vp, ctypes.POINTER(_i)],
     "gs_set_fault": [_vp, _i, _u64],
     "gs_launch_count": [_vp, ctypes.POINTER(_i64)],
@@ -307,6 +309,21 @@ def gs_batch_autotune(b, steps_per_trial: int = 20) -> dict:
     _check(lib().gs_batch_autotune(b, steps_per_trial, ctypes.byref(tz), ctypes.byref(st), ctypes.byref(us)),
            "gs_batch_autotune")
     return {"tile_z": tz.value, "stages": st.value, "us_per_step": us.value}
+
+
+def gs_read_async(sim, field: int, dst):
+    """Enqueue a copy of a field into the host buffer dst (page-locked for
+    overlap); dst is valid once the object's stream has passed it."""
+    nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+    _check(lib().gs_read_async(sim, field, _ptr(dst), nbytes), "gs_read_async")
+    return dst
+
+
+def gs_write_async(sim, field: int, src):
+    """Enqueue a copy of the host buffer src into a field (src must stay
+    unchanged until the object's stream has passed the copy)."""
+    nbytes = src.nbytes if isinstance(src, np.ndarray) else src.numel() * src.element_size()
+    _check(lib().gs_write_async(sim, field, _ptr(src), nbytes), "gs_write_async")
 
 
 def gs_sync(sim):

@@ -457,3 +457,42 @@ def test_plan_cache_tunes_once_per_configuration(tmp_path):
     with pytest.raises(gs.GsError) as e:
         d.autotune_cached(str(tmp_path), steps_per_trial=1)
     assert e.value.status == gs.GS_EIO
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_async_copies_match_blocking_ones_on_two_streams(dtype):
+    # two grids on two streams: async write -> steps -> async read per grid,
+    # both enqueued before either stream is waited on; the fields must equal
+    # those of the blocking calls and the oracle
+    import torch
+    need_cuda()
+    L, n = 40, 7
+    u0, v0 = oracle.init(L)
+    dt = np.float32 if dtype == "f32" else np.float64
+    uo, vo = oracle.step(u0, v0, n, **PAPER, noise=0.1, seed=9)
+    ref = make(L, dtype, noise=0.1, seed=9)
+    ref.write(u0, v0)
+    ref.step(n)
+    ur, vr = ref.read()
+    sims, bufs = [], []
+    for i in range(2):
+        sim = make(L, dtype, noise=0.1, seed=9, stream=torch.cuda.Stream())
+        hin = [torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory() for a in (u0, v0)]
+        hout = [torch.full((L, L, L), float("nan"), dtype=hin[0].dtype).pin_memory() for _ in range(2)]
+        sims.append(sim)
+        bufs.append((hin, hout))
+    torch.cuda.synchronize()
+    for sim, (hin, hout) in zip(sims, bufs):
+        gs.gs_write_async(sim.handle, gs.GS_U, hin[0])
+        gs.gs_write_async(sim.handle, gs.GS_V, hin[1])
+        sim.step(n)
+        gs.gs_read_async(sim.handle, gs.GS_U, hout[0])
+        gs.gs_read_async(sim.handle, gs.GS_V, hout[1])
+    for sim, (_, hout) in zip(sims, bufs):
+        sim.sync()
+        np.testing.assert_array_equal(hout[0].numpy(), ur)
+        np.testing.assert_array_equal(hout[1].numpy(), vr)
+        assert maxabs(hout[0].numpy(), uo) <= TOL[dtype] and maxabs(hout[1].numpy(), vo) <= TOL[dtype]
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_read_async(sims[0].handle, gs.GS_U, torch.empty(7, dtype=hout[0].dtype))
+    assert e.value.status == gs.GS_EINVAL
