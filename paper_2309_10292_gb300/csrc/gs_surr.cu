@@ -375,19 +375,35 @@ __global__ void __launch_bounds__(kWgThreads, 1) gs_wgrad_kernel(const WgArgs a)
     }
 }
 
-// x0 = bf16(u - 1, v, 20 F, 20 k, 0, ...) : [N][L^3][16]
+// x0 = bf16(u - 1, v, 20 F, 20 k, 0, ...) : [N][L^3][16].  With xtaps set
+// (the tensor-core inference path), channels 4 d + c hold channel c of the x
+// neighbour x + d - 1 (d = 0, 1, 2; periodic in x) and 12..15 are zero, so one
+// 16-deep K step of the first layer covers its three dx taps.
 __global__ void gs_pack_kernel(const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ Fk,
-                               bf16* __restrict__ x0, long long L3, int N)
+                               bf16* __restrict__ x0, long long L3, int N, int L, int xtaps)
 {
     const long long total = L3 * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int n = (int)(i / L3);
+        const bf16 f = __float2bfloat16_rn(Fk[2 * n] * kFkScale);
+        const bf16 k = __float2bfloat16_rn(Fk[2 * n + 1] * kFkScale);
         __align__(16) bf16 c[16];
-        c[0] = __float2bfloat16_rn(u[i] - 1.f);  // zero on the u = 1 background
-        c[1] = __float2bfloat16_rn(v[i]);
-        c[2] = __float2bfloat16_rn(Fk[2 * n] * kFkScale);
-        c[3] = __float2bfloat16_rn(Fk[2 * n + 1] * kFkScale);
-        for (int j = 4; j < 16; ++j) c[j] = __float2bfloat16_rn(0.f);
+        for (int j = 0; j < 16; ++j) c[j] = __float2bfloat16_rn(0.f);
+        if (xtaps) {
+            const int x = (int)(i % L);
+            for (int d = 0; d < 3; ++d) {
+                const long long src = i - x + (x + d - 1 + L) % L;
+                c[4 * d] = __float2bfloat16_rn(u[src] - 1.f);
+                c[4 * d + 1] = __float2bfloat16_rn(v[src]);
+                c[4 * d + 2] = f;
+                c[4 * d + 3] = k;
+            }
+        } else {
+            c[0] = __float2bfloat16_rn(u[i] - 1.f);  // zero on the u = 1 background
+            c[1] = __float2bfloat16_rn(v[i]);
+            c[2] = f;
+            c[3] = k;
+        }
         uint4* dst = reinterpret_cast<uint4*>(x0 + i * 16);
         dst[0] = reinterpret_cast<const uint4*>(c)[0];
         dst[1] = reinterpret_cast<const uint4*>(c)[1];
@@ -683,9 +699,12 @@ GS_D void tc_arrive_expect_tx_if(uint32_t leader, uint64_t* bar, uint32_t bytes)
         : "memory");
 }
 
-template <int CINP, int NT, int EPI>
+template <int CINP, int NT, int EPI, bool XT>
 __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_constant__ ConvTcArgs a)
 {
+    // XT: the input is x-tap packed (gs_pack_kernel with xtaps), so the three
+    // dx taps are one K step: one MMA per (dz, slab row), no x halo boxes
+    static_assert(!XT || CINP == 16, "x-tap packing is for the 16-channel first layer");
     constexpr int NCH = CINP / 8;
     constexpr uint32_t ROWB = kTcRowCells * 16;           // bytes of one slab row of one chunk
     constexpr uint32_t PLANE = kTcSlabRows * ROWB;         // bytes of one chunk plane of a slab
@@ -695,7 +714,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
     constexpr bool SW = CINP == 32;
     constexpr uint32_t SROWB = kTcRowCells * 64;          // bytes of one swizzled slab row
     static_assert(!SW || kTcSlabRows * SROWB == SLAB, "swizzled slab size");
-    constexpr uint32_t WBYTES = 27 * NCH * NT * 16;
+    constexpr uint32_t WBYTES = (XT ? 9 : 27) * NCH * NT * 16;
+    // bytes the TMA delivers per slab (x-tap input: the 128 cells of each row only)
+    constexpr uint32_t SLAB_TX = XT ? NCH * kTcSlabRows * kTcCells * 16 : SLAB;
     constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256);
     extern __shared__ __align__(1024) unsigned char smem_tc[];
@@ -814,7 +835,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                         break;
                     }
                     const int zp = u.n * L + (u.z0 - 1 + i + L) % L;
-                    tc_arrive_expect_tx_if(leader, &slab_full[slot], SLAB);
+                    tc_arrive_expect_tx_if(leader, &slab_full[slot], SLAB_TX);
                     const uint32_t dst0 = sbase + slot * SLAB;
                     if constexpr (SW) {
                         // three boxes of 32 channels per row, each landing on a
@@ -834,11 +855,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
 #pragma unroll
                         for (int yi = 0; yi < kTcSlabRows; ++yi) {
                             const uint32_t row = dst0 + j * PLANE + yi * ROWB;
-                            tc_tma_load_4d_if(leader, row, &a.map_halo, &slab_full[slot], j * 8, xl, yrow[yi], zp);
+                            if constexpr (!XT)
+                                tc_tma_load_4d_if(leader, row, &a.map_halo, &slab_full[slot], j * 8, xl, yrow[yi], zp);
                             tc_tma_load_4d_if(leader, row + kTcRowX0 * 16, &a.map_main, &slab_full[slot], j * 8, u.x0,
                                               yrow[yi], zp);
-                            tc_tma_load_4d_if(leader, row + (kTcRowX0 + kTcCells) * 16, &a.map_halo, &slab_full[slot],
-                                              j * 8, xr, yrow[yi], zp);
+                            if constexpr (!XT)
+                                tc_tma_load_4d_if(leader, row + (kTcRowX0 + kTcCells) * 16, &a.map_halo,
+                                                  &slab_full[slot], j * 8, xr, yrow[yi], zp);
                         }
                 }
             }
@@ -867,11 +890,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
             // 64-byte swizzle (SBO = one 8-cell atom; K steps of 32 bytes)
             const uint64_t adz = SW ? tc_desc_sw64(sbase + slot * SLAB, 512) : tc_desc(sbase + slot * SLAB, PLANE, 128);
             constexpr uint32_t AROW = SW ? SROWB : ROWB;  // bytes between slab rows
+            constexpr int DX0 = XT ? 1 : 0, DX1 = XT ? 2 : 3;  // x-tap input: the unshifted operand only
 #pragma unroll
-            for (int dxi = 0; dxi < 3; ++dxi)
+            for (int dxi = DX0; dxi < DX1; ++dxi)
 #pragma unroll
                 for (int kk = 0; kk < CINP / 16; ++kk) {
-                    const uint64_t bk = tc_desc(wbase + (uint32_t)((dzi * 3 + dxi) * NCH + 2 * kk) * WCH, WCH, 128);
+                    const int wplane = XT ? dzi * NCH + 2 * kk : (dzi * 3 + dxi) * NCH + 2 * kk;
+                    const uint64_t bk = tc_desc(wbase + (uint32_t)wplane * WCH, WCH, 128);
                     // output cell i of tap dx reads input cell x0 + i + dx - 1
                     const uint64_t ak = SW ? adz + (uint64_t)((kk * 32) >> 4) + (uint64_t)(((kTcRowX0 - 1 + dxi) * 64) >> 4)
                                            : adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(kTcRowX0 - 1 + dxi);
@@ -882,7 +907,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                         const int rlo = sr - 2 > 0 ? sr - 2 : 0;
                         const int rhi = sr < kTcRows - 1 ? sr : kTcRows - 1;
                         const int b0 = 2 - sr + rlo;  // first dy block (dy = +1 - block)
-                        const bool fresh = dzi == 0 && dxi == 0 && kk == 0 && q < 2;
+                        const bool fresh = dzi == 0 && dxi == DX0 && kk == 0 && q < 2;
                         tc_mma_if(leader, dset + (uint32_t)(rlo * NT), ak + (uint64_t)(sr * (AROW >> 4)),
                                   bk + (uint64_t)((b0 * NT * 16) >> 4), idn[rhi - rlo], fresh ? 0u : 1u);
                     }
@@ -1046,6 +1071,27 @@ __global__ void gs_wprep_tc_kernel(const float* __restrict__ w, int cin, int cou
     }
 }
 
+// the first layer's weights for x-tap packed input (gs_pack_kernel with
+// xtaps): [3 dz][2 chunks][3 NT][8], K index k = 4 dx + ci (k < 12), the three
+// dy taps side by side along N as in gs_wprep_tc_kernel
+__global__ void gs_wprep_tc_xtaps_kernel(const float* __restrict__ w, int cin, int cout, int nt, bf16* __restrict__ wt)
+{
+    const int nn = 3 * nt;
+    const int total = 3 * 2 * nn * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i % 8;
+        const int n = (i / 8) % nn;
+        const int j = (i / (8 * nn)) % 2;
+        const int dzi = i / (8 * nn * 2);
+        const int kx = j * 8 + e, dxi = kx / 4, ci = kx % 4;
+        const int dyi = 2 - n / nt;
+        const int co = n % nt;
+        const int tap = dzi * 9 + dyi * 3 + dxi;
+        const float val = (kx < 12 && ci < cin && co < cout) ? w[((size_t)tap * cin + ci) * cout + co] : 0.f;
+        wt[i] = __float2bfloat16_rn(val);
+    }
+}
+
 }  // namespace gs
 
 // ===========================================================================
@@ -1063,6 +1109,7 @@ struct gs_surr {
     bf16* wf[kSurrLayers] = {};  // forward layout
     bf16* wd[kSurrLayers] = {};  // data-gradient layout (layers 1..5)
     bf16* wt[kSurrLayers] = {};  // tcgen05 B layout [3 dz][3 dx][CINP/8][3 NT][8]
+    bf16* wt0x = nullptr;        // the first layer's for x-tap packed input [3 dz][2][3 NT][8]
     bool wdirty = true;
     int backend = 0;             // 0 auto (tcgen05 when L % 128 == 0), 1 mma.sync, 2 tcgen05
     int* d_err = nullptr;
@@ -1175,18 +1222,18 @@ int wgrad_launch(gs_surr* s, WgArgs a)
     return GS_OK;
 }
 
-template <int CINP, int NT, int EPI>
+template <int CINP, int NT, int EPI, bool XT = false>
 int tc_launch(gs_surr* s, ConvTcArgs a)
 {
     constexpr uint32_t SLAB = (CINP / 8) * kTcSlabRows * kTcRowCells * 16;
-    const size_t smem = 3 * (size_t)SLAB + (size_t)27 * (CINP / 8) * NT * 16;
+    const size_t smem = 3 * (size_t)SLAB + (size_t)(XT ? 9 : 27) * (CINP / 8) * NT * 16;
     if (a.L % kTcCells) return fail(GS_EINVAL, "the tcgen05 path needs L %% %d == 0 (L=%d)", kTcCells, a.L);
     constexpr bool SW = CINP == 32;  // see gs_conv_tc_kernel
     const int box_c = SW ? 32 : 8;
     if (encode_act_4d(&a.map_main, a.in, CINP, a.L, (long long)a.N * a.L, box_c, kTcCells, SW) != CUDA_SUCCESS ||
         encode_act_4d(&a.map_halo, a.in, CINP, a.L, (long long)a.N * a.L, box_c, 8, SW) != CUDA_SUCCESS)
         return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for the activation maps");
-    auto k = gs_conv_tc_kernel<CINP, NT, EPI>;
+    auto k = gs_conv_tc_kernel<CINP, NT, EPI, XT>;
     GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, smem));
@@ -1218,6 +1265,9 @@ int prep_weights(gs_surr* s)
         GS_CUDA_TRY(cudaGetLastError());
         s->launches += 2;
     }
+    gs_wprep_tc_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[0], kChan[0], kChan[1], 32, s->wt0x);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
     s->wdirty = false;
     return GS_OK;
 }
@@ -1239,21 +1289,25 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
     int rc = prep_weights(s);
     if (rc) return rc;
     const long long cells = (long long)N * L * L * L;
-    gs_pack_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(u, v, s->fk, s->x0, (long long)L * L * L, N);
-    GS_CUDA_TRY(cudaGetLastError());
-    s->launches += 1;
     const bool tc = s->backend != 1 && L % kTcCells == 0;
     if (s->backend == 2 && !tc) return fail(GS_EINVAL, "the tcgen05 path needs L %% 128 == 0 (L=%d)", L);
+    // inference on the tensor cores packs the x taps into the first layer's
+    // input; training keeps the plain layout, which its weight gradient reads
+    const bool xtaps = tc && !train;
+    gs_pack_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(u, v, s->fk, s->x0, (long long)L * L * L, N, L,
+                                                              xtaps ? 1 : 0);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
     if (tc) {
         ConvTcArgs t{};
         t.N = N;
         t.L = L;
         t.in = s->x0;
-        t.w = s->wt[0];
+        t.w = xtaps ? s->wt0x : s->wt[0];
         t.bias = s->params + s->boff[0];
         t.out = s->h[1];
         t.zout = train ? s->z[0] : nullptr;
-        if ((rc = tc_launch<16, 32, EPI_FIRST>(s, t))) return rc;
+        if ((rc = xtaps ? tc_launch<16, 32, EPI_FIRST, true>(s, t) : tc_launch<16, 32, EPI_FIRST>(s, t))) return rc;
         for (int l = 1; l <= 4; ++l) {
             t.in = train ? s->h[l] : s->h[1 + ((l - 1) & 1)];
             t.out = train ? s->h[l + 1] : s->h[1 + (l & 1)];
@@ -1434,6 +1488,7 @@ int gs_surr_destroy(gs_surr* s)
         cudaFree(s->wd[l]);
         cudaFree(s->wt[l]);
     }
+    cudaFree(s->wt0x);
     cudaFree(s->d_err);
     cudaFree(s->d_loss);
     cudaFree(s->d_max);
@@ -1472,6 +1527,7 @@ int gs_surr_create(gs_surr** out)
         if (e == cudaSuccess) e = cudaMalloc(&s->wt[l], (size_t)27 * kCinP[l] * (l == 5 ? 16 : 32) * sizeof(bf16));
         if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wd[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
     }
+    if (e == cudaSuccess) e = cudaMalloc(&s->wt0x, (size_t)9 * kCinP[0] * 32 * sizeof(bf16));
     if (e != cudaSuccess || (e = cudaMemset(s->params, 0, off * 4)) != cudaSuccess ||
         (e = cudaMemset(s->m, 0, off * 4)) != cudaSuccess || (e = cudaMemset(s->v, 0, off * 4)) != cudaSuccess) {
         int rc = cuda_fail(e, "surrogate allocation");
