@@ -675,6 +675,30 @@ GS_D void tc_ld<16>(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <>
+GS_D void tc_ld<8>(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// zero 32 consecutive columns of this warp's 32 TMEM lanes (and wait for it)
+GS_D void tc_st_zero32(uint32_t taddr)
+{
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // 4D tiled TMA load (channels, x, y, plane) -> shared, completion on `bar`;
 // the channel coordinate is a multiple of 8 (16 bytes) by construction.
 GS_D void tc_tma_load_4d_if(uint32_t leader, uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c, int x, int y,
@@ -714,11 +738,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
     constexpr bool SW = CINP == 32;
     constexpr uint32_t SROWB = kTcRowCells * 64;          // bytes of one swizzled slab row
     static_assert(!SW || kTcSlabRows * SROWB == SLAB, "swizzled slab size");
-    constexpr uint32_t WBYTES = (XT ? 9 : 27) * NCH * NT * 16;
+    // EPI_LAST (2 output channels): the dz taps side by side along N, each
+    // block holding the 4 output rows x 2 channels (8 columns, padded to 16),
+    // so each input plane is read by one group of MMAs (N = 48, fewer at the
+    // ends of a z-chunk) that adds into the accumulators of the three output
+    // planes it feeds; an accumulator set holds a whole z-chunk (16 columns a
+    // plane), zeroed by the epilogue before use
+    constexpr bool ZS = EPI == EPI_LAST;
+    static_assert(!ZS || (CINP == 32 && kTcRows == 4 && kTcSlabRows == 6), "dz-stacked last layer");
+    constexpr uint32_t ZS_SETC = kTcZChunk * 16;
+    constexpr uint32_t ZS_WB = 2 * 48 * 16;  // bytes of B per (slab row, dx, K step)
+    constexpr uint32_t WBYTES = ZS ? kTcSlabRows * 3 * 2 * ZS_WB : (XT ? 9 : 27) * NCH * NT * 16;
     // bytes the TMA delivers per slab (x-tap input: the 128 cells of each row only)
     constexpr uint32_t SLAB_TX = XT ? NCH * kTcSlabRows * kTcCells * 16 : SLAB;
     constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
-    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256);
+    constexpr uint32_t TMEM_COLS = ZS ? 512 : (2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256));
+    static_assert(!ZS || 2 * ZS_SETC <= TMEM_COLS, "accumulator sets fit in TMEM");
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     // slab_full: the producer's expect-tx arrival, completed by the TMA bytes;
     // slab_empty: the MMA commit after the plane's last tap; acc_full: the
@@ -753,7 +788,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         abort_s = 0;
         gs_fence_mbar_init();
     }
-    if (tid < NT) bias_s[tid] = a.bias[tid];
+    if (tid < NT) bias_s[tid] = (EPI == EPI_LAST && tid >= 2) ? 0.f : a.bias[tid];  // the last layer has 2
     for (uint32_t i = tid; i < WBYTES / 16; i += kTcThreads) cp16(wbase + i * 16, a.w + (size_t)i * 8);
     cp_wait_all();
     gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
@@ -913,35 +948,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                     }
                 }
         };
-        uint32_t g = 0, k = 0;  // planes and items seen by this CTA
+        // EPI_LAST: all MMAs of input plane i (i = 0 .. nz+1, plane z0 - 1 + i)
+        // of a unit.  It feeds output planes i - 2, i - 1, i (dz blocks 0-2);
+        // those inside the unit, plo .. phi, are one N window at column
+        // 16 plo of the set, B rows from block plo - (i - 2) on
+        auto issue_zs = [&](int set, int i, int slot, int nz) {
+            const int plo = i - 2 > 0 ? i - 2 : 0, phi = i < nz - 1 ? i : nz - 1;
+            const uint32_t dcol = tmem + (uint32_t)(set * ZS_SETC + plo * 16);
+            const uint32_t boff = (uint32_t)(plo - (i - 2)) * 16 * 16;
+            const uint64_t adz = tc_desc_sw64(sbase + slot * SLAB, 512);
+            const uint32_t idz = tc_idesc((phi - plo + 1) * 16);
+#pragma unroll
+            for (int sr = 0; sr < kTcSlabRows; ++sr)
+#pragma unroll
+                for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t ak = adz + (uint64_t)((kk * 32) >> 4) +
+                                            (uint64_t)(((kTcRowX0 - 1 + dxi) * 64) >> 4) +
+                                            (uint64_t)(sr * (SROWB >> 4));
+                        const uint64_t bk =
+                            tc_desc(wbase + (uint32_t)((sr * 3 + dxi) * 2 + kk) * ZS_WB + boff, 48 * 16, 128);
+                        tc_mma_if(leader, dcol, ak, bk, idz, 1u);
+                    }
+        };
         bool ok = true;
-        for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
-            const Unit u = decode(unit);
-            const uint32_t gb = g;
-            for (int q = 0; q < u.nz && ok; ++q, ++k) {
+        if constexpr (ZS) {
+            uint32_t g = 0, k = 0;  // planes and units seen by this CTA
+            for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x, ++k) {
+                const Unit u = decode(unit);
                 const int set = (int)(k & 1u);
-                if (k >= 2 && !wwait(&acc_empty[set], ((k / 2u) - 1u) & 1u)) {
+                // completion 0 of acc_empty is the epilogue's initial zeroing
+                if (!wwait(&acc_empty[set], (k / 2u) & 1u)) {
                     ok = false;
                     break;
                 }
-                for (int d = 0; d < 3; ++d) {
-                    // item q reads planes q, q+1, q+2 of the unit (dz = d - 1)
-                    const uint32_t gp = gb + (uint32_t)(q + d);
-                    const int slot = (int)(gp % 3u);
-                    if ((q == 0 || d == 2) && !wwait(&slab_full[slot], (gp / 3u) & 1u)) {
+                tc_fence_after();
+                for (int i = 0; i < u.nz + 2; ++i, ++g) {
+                    const int slot = (int)(g % 3u);
+                    if (!wwait(&slab_full[slot], (g / 3u) & 1u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    issue_group(set, d, slot);
-                    // last MMA use of plane q (its dz=-1 taps); of the unit's
-                    // last two planes, the last item's dz = 0 and +1 taps
-                    if (d == 0 || q == u.nz - 1) tc_commit_if(leader, &slab_empty[slot]);
+                    issue_zs(set, i, slot, u.nz);
+                    tc_commit_if(leader, &slab_empty[slot]);  // each plane has one group of MMAs
                 }
                 if (!ok) break;
                 tc_commit_if(leader, &acc_full[set]);
             }
-            g = gb + (uint32_t)(u.nz + 2);
+        } else {
+            uint32_t g = 0, k = 0;  // planes and items seen by this CTA
+            for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+                const Unit u = decode(unit);
+                const uint32_t gb = g;
+                for (int q = 0; q < u.nz && ok; ++q, ++k) {
+                    const int set = (int)(k & 1u);
+                    if (k >= 2 && !wwait(&acc_empty[set], ((k / 2u) - 1u) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    for (int d = 0; d < 3; ++d) {
+                        // item q reads planes q, q+1, q+2 of the unit (dz = d - 1)
+                        const uint32_t gp = gb + (uint32_t)(q + d);
+                        const int slot = (int)(gp % 3u);
+                        if ((q == 0 || d == 2) && !wwait(&slab_full[slot], (gp / 3u) & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        issue_group(set, d, slot);
+                        // last MMA use of plane q (its dz=-1 taps); of the unit's
+                        // last two planes, the last item's dz = 0 and +1 taps
+                        if (d == 0 || q == u.nz - 1) tc_commit_if(leader, &slab_empty[slot]);
+                    }
+                    if (!ok) break;
+                    tc_commit_if(leader, &acc_full[set]);
+                }
+                g = gb + (uint32_t)(u.nz + 2);
+            }
         }
         if (!ok) {
             // one more commit tracks every MMA issued (fixed budget: issued
@@ -1017,25 +1102,76 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                 }
             }
         };
-        uint32_t k = 0;
-        bool ok = true;
-        if (blockIdx.x < units) prefetch(decode(blockIdx.x), 0);
-        for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
-            const Unit u = decode(unit);
-            for (int q = 0; q < u.nz; ++q, ++k) {
+        if constexpr (ZS) {
+            // this warp's 32 lanes of a set's columns
+            const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);
+            auto zero_set = [&](int set) {
+#pragma unroll
+                for (int c = 0; c < (int)ZS_SETC; c += 32) tc_st_zero32(lanes + (uint32_t)(set * ZS_SETC + c));
+            };
+            zero_set(0);
+            zero_set(1);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                gs_mbar_arrive(&acc_empty[0]);
+                gs_mbar_arrive(&acc_empty[1]);
+            }
+            uint32_t k = 0;
+            bool ok = true;
+            if (blockIdx.x < units) prefetch(decode(blockIdx.x), 0);
+            for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x, ++k) {
+                const Unit u = decode(unit);
                 const int set = (int)(k & 1u);
                 if (!wwait(&acc_full[set], (k / 2u) & 1u)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                epilogue(set, u, q);
+                for (int q = 0; q < u.nz; ++q) {
+                    float st[kTcRows][2];
+#pragma unroll
+                    for (int r = 0; r < kTcRows; ++r) {
+                        st[r][0] = sres[r][0];
+                        st[r][1] = sres[r][1];
+                    }
+                    if (q + 1 < u.nz) prefetch(u, q + 1);
+                    else if (unit + gridDim.x < units) prefetch(decode(unit + gridDim.x), 0);
+                    float acc[8];  // (row, channel) pairs of output plane q
+                    tc_ld<8>(lanes + (uint32_t)(set * ZS_SETC + q * 16), acc);
+#pragma unroll
+                    for (int r = 0; r < kTcRows; ++r) {
+                        const size_t cell = cell_of(u, q, r);
+                        a.ou[cell] = st[r][0] + (acc[2 * r] + bias_r[0]);
+                        a.ov[cell] = st[r][1] + (acc[2 * r + 1] + bias_r[1]);
+                    }
+                }
+                zero_set(set);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) gs_mbar_arrive(&acc_empty[set]);
-                // the next item's inputs (this unit's next plane, or the next unit's first)
-                if (q + 1 < u.nz) prefetch(u, q + 1);
-                else if (unit + gridDim.x < units) prefetch(decode(unit + gridDim.x), 0);
+            }
+        } else {
+            uint32_t k = 0;
+            bool ok = true;
+            if (blockIdx.x < units) prefetch(decode(blockIdx.x), 0);
+            for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+                const Unit u = decode(unit);
+                for (int q = 0; q < u.nz; ++q, ++k) {
+                    const int set = (int)(k & 1u);
+                    if (!wwait(&acc_full[set], (k / 2u) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    epilogue(set, u, q);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) gs_mbar_arrive(&acc_empty[set]);
+                    // the next item's inputs (this unit's next plane, or the next unit's first)
+                    if (q + 1 < u.nz) prefetch(u, q + 1);
+                    else if (unit + gridDim.x < units) prefetch(decode(unit + gridDim.x), 0);
+                }
             }
         }
     }
@@ -1067,6 +1203,30 @@ __global__ void gs_wprep_tc_kernel(const float* __restrict__ w, int cin, int cou
         const int tap = dzi * 9 + dyi * 3 + dxi;
         const int ci = j * 8 + e;
         const float val = (ci < cin && co < cout) ? w[((size_t)tap * cin + ci) * cout + co] : 0.f;
+        wt[i] = __float2bfloat16_rn(val);
+    }
+}
+
+// the last layer's weights for its dz-stacked schedule (EPI_LAST in
+// gs_conv_tc_kernel): [6 slab rows][3 dx][2 K steps][2 chunks][48][8], row
+// n = 16 b + 2 r + co (2 r + co < 8, the rest zero): block b feeds output
+// plane z' - 1 + b from input plane z' (dz = 1 - b), and slab row sr feeds
+// output row r through dy = sr - 1 - r (zero where |dy| > 1)
+__global__ void gs_wprep_tc_last_kernel(const float* __restrict__ w, int cin, int cout, bf16* __restrict__ wt)
+{
+    const int total = 6 * 3 * 2 * 2 * 48 * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i % 8;
+        const int n = (i / 8) % 48;
+        const int j = (i / (8 * 48)) % 2;
+        const int kk = (i / (8 * 48 * 2)) % 2;
+        const int dxi = (i / (8 * 48 * 4)) % 3;
+        const int sr = i / (8 * 48 * 12);
+        const int b = n / 16, rc = n % 16, r = rc / 2, co = rc % 2;
+        const int dzi = 2 - b, dyi = sr - r;
+        const int ci = kk * 16 + j * 8 + e;
+        const bool on = rc < 8 && dyi >= 0 && dyi <= 2 && ci < cin && co < cout;
+        const float val = on ? w[((size_t)(dzi * 9 + dyi * 3 + dxi) * cin + ci) * cout + co] : 0.f;
         wt[i] = __float2bfloat16_rn(val);
     }
 }
@@ -1226,7 +1386,8 @@ template <int CINP, int NT, int EPI, bool XT = false>
 int tc_launch(gs_surr* s, ConvTcArgs a)
 {
     constexpr uint32_t SLAB = (CINP / 8) * kTcSlabRows * kTcRowCells * 16;
-    const size_t smem = 3 * (size_t)SLAB + (size_t)(XT ? 9 : 27) * (CINP / 8) * NT * 16;
+    const size_t wbytes = EPI == EPI_LAST ? (size_t)6 * 3 * 2 * 2 * 48 * 16 : (size_t)(XT ? 9 : 27) * (CINP / 8) * NT * 16;
+    const size_t smem = 3 * (size_t)SLAB + wbytes;
     if (a.L % kTcCells) return fail(GS_EINVAL, "the tcgen05 path needs L %% %d == 0 (L=%d)", kTcCells, a.L);
     constexpr bool SW = CINP == 32;  // see gs_conv_tc_kernel
     const int box_c = SW ? 32 : 8;
@@ -1238,7 +1399,7 @@ int tc_launch(gs_surr* s, ConvTcArgs a)
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, smem));
     if (per_sm < 1) return fail(GS_EINVAL, "tensor-core convolution does not fit on an SM");
-    per_sm = std::min(per_sm, 2);  // TMEM: at most 2 x 128 columns per SM
+    per_sm = std::min(per_sm, EPI == EPI_LAST ? 1 : 2);  // TMEM: 512 columns a CTA (last layer), else <= 256
     a.err = s->d_err;
     a.timeout_ns = 2000000000ull;
     const long long units = (long long)a.N * (a.L / kTcRows) * (a.L / kTcCells) * ((a.L + kTcZChunk - 1) / kTcZChunk);
@@ -1260,8 +1421,10 @@ int prep_weights(gs_surr* s)
         gs_wprep_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, s->wf[l], kCoutP[l], kCinP[l],
                                                   l >= 1 ? s->wd[l] : nullptr, dk);
         GS_CUDA_TRY(cudaGetLastError());
-        gs_wprep_tc_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, kCinP[l], l == 5 ? 16 : 32,
-                                                     s->wt[l]);
+        if (l == 5)
+            gs_wprep_tc_last_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, s->wt[l]);
+        else
+            gs_wprep_tc_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, kCinP[l], 32, s->wt[l]);
         GS_CUDA_TRY(cudaGetLastError());
         s->launches += 2;
     }
@@ -1524,7 +1687,8 @@ int gs_surr_create(gs_surr** out)
     }
     for (int l = 0; l < kSurrLayers && e == cudaSuccess; ++l) {
         e = cudaMalloc(&s->wf[l], (size_t)27 * kCoutP[l] * kCinP[l] * sizeof(bf16));
-        if (e == cudaSuccess) e = cudaMalloc(&s->wt[l], (size_t)27 * kCinP[l] * (l == 5 ? 16 : 32) * sizeof(bf16));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s->wt[l], (l == 5 ? (size_t)6 * 3 * 2 * 2 * 48 * 8 : (size_t)27 * kCinP[l] * 32) * sizeof(bf16));
         if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wd[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->wt0x, (size_t)9 * kCinP[0] * 32 * sizeof(bf16));
