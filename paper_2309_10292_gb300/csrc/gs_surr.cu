@@ -751,6 +751,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
     constexpr uint32_t WBYTES = ZS ? kTcSlabRows * 3 * 2 * ZS_WB : (XT ? 9 : 27) * NCH * NT * 16;
     // bytes the TMA delivers per slab (x-tap input: the 128 cells of each row only)
     constexpr uint32_t SLAB_TX = XT ? NCH * kTcSlabRows * kTcCells * 16 : SLAB;
+    // slab ring depth: the x-tap first layer does little MMA work per plane,
+    // so its small slabs are prefetched further ahead to cover the copy latency
+    constexpr uint32_t NSLAB = XT ? 6 : 3;
     constexpr uint32_t ACC_COLS = kTcRows * NT;            // one accumulator set (4 output rows)
     constexpr uint32_t TMEM_COLS = ZS ? 512 : (2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128 : 256));
     static_assert(!ZS || 2 * ZS_SETC <= TMEM_COLS, "accumulator sets fit in TMEM");
@@ -758,7 +761,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
     // slab_full: the producer's expect-tx arrival, completed by the TMA bytes;
     // slab_empty: the MMA commit after the plane's last tap; acc_full: the
     // commit after an item's last MMA; acc_empty: one arrival per epilogue warp
-    __shared__ __align__(8) uint64_t slab_full[3], slab_empty[3], acc_full[2], acc_empty[2], bar_fin;
+    __shared__ __align__(8) uint64_t slab_full[NSLAB], slab_empty[NSLAB], acc_full[2], acc_empty[2], bar_fin;
     __shared__ uint32_t tmem_base_s;
     __shared__ float bias_s[NT];
     __shared__ volatile int abort_s;
@@ -767,7 +770,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
     const int L = a.L;
     const long long L3 = (long long)L * L * L;
     const uint32_t sbase = gs_smem_addr(smem_tc);
-    const uint32_t wbase = sbase + 3 * SLAB;
+    const uint32_t wbase = sbase + NSLAB * SLAB;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gs_smem_addr(&tmem_base_s)),
@@ -776,7 +779,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) {
+        for (uint32_t i = 0; i < NSLAB; ++i) {
             gs_mbar_init(&slab_full[i], 1);
             gs_mbar_init(&slab_empty[i], 1);
         }
@@ -844,7 +847,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
 
     if (warp == kTcProdWarp) {
         // ------------------------ producer (TMA, one elected lane) ------------------------
-        // plane z0 - 1 + i of a unit (i = 0 .. nz+1) is global plane g, slot g % 3;
+        // plane z0 - 1 + i of a unit (i = 0 .. nz+1) is global plane g, slot g % NSLAB;
         // per plane and channel chunk, each of the 6 rows is three boxes (left
         // halo, 128 cells, right halo), wrapped periodically by their start
         // coordinates (L is a multiple of 128, so no box straddles the wrap)
@@ -864,8 +867,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
 #pragma unroll
                 for (int yi = 0; yi < kTcSlabRows; ++yi) yrow[yi] = (u.y0 - 1 + yi + L) % L;
                 for (int i = 0; i < u.nz + 2; ++i, ++g) {
-                    const int slot = (int)(g % 3u);
-                    if (g >= 3 && !wwait(&slab_empty[slot], ((g / 3u) - 1u) & 1u)) {
+                    const int slot = (int)(g % NSLAB);
+                    if (g >= NSLAB && !wwait(&slab_empty[slot], ((g / NSLAB) - 1u) & 1u)) {
                         ok = false;
                         break;
                     }
@@ -902,8 +905,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
             }
             if (!ok && lane == 0) {
                 // let the copies in flight land (fixed budget)
-                for (uint32_t q = g > 3u ? g - 3u : 0u; q < g; ++q)
-                    gs_mbar_wait(&slab_full[q % 3u], (q / 3u) & 1u, 2000000000ull);
+                for (uint32_t q = g > NSLAB ? g - NSLAB : 0u; q < g; ++q)
+                    gs_mbar_wait(&slab_full[q % NSLAB], (q / NSLAB) & 1u, 2000000000ull);
             }
         } else if (lane == 0) {
             abort_s = 1;  // unaligned shared memory: refuse to issue TMA
@@ -985,8 +988,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                 }
                 tc_fence_after();
                 for (int i = 0; i < u.nz + 2; ++i, ++g) {
-                    const int slot = (int)(g % 3u);
-                    if (!wwait(&slab_full[slot], (g / 3u) & 1u)) {
+                    const int slot = (int)(g % NSLAB);
+                    if (!wwait(&slab_full[slot], (g / NSLAB) & 1u)) {
                         ok = false;
                         break;
                     }
@@ -1011,8 +1014,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                     for (int d = 0; d < 3; ++d) {
                         // item q reads planes q, q+1, q+2 of the unit (dz = d - 1)
                         const uint32_t gp = gb + (uint32_t)(q + d);
-                        const int slot = (int)(gp % 3u);
-                        if ((q == 0 || d == 2) && !wwait(&slab_full[slot], (gp / 3u) & 1u)) {
+                        const int slot = (int)(gp % NSLAB);
+                        if ((q == 0 || d == 2) && !wwait(&slab_full[slot], (gp / NSLAB) & 1u)) {
                             ok = false;
                             break;
                         }
@@ -1387,7 +1390,7 @@ int tc_launch(gs_surr* s, ConvTcArgs a)
 {
     constexpr uint32_t SLAB = (CINP / 8) * kTcSlabRows * kTcRowCells * 16;
     const size_t wbytes = EPI == EPI_LAST ? (size_t)6 * 3 * 2 * 2 * 48 * 16 : (size_t)(XT ? 9 : 27) * (CINP / 8) * NT * 16;
-    const size_t smem = 3 * (size_t)SLAB + wbytes;
+    const size_t smem = (XT ? 6 : 3) * (size_t)SLAB + wbytes;  // the kernel's slab ring depth
     if (a.L % kTcCells) return fail(GS_EINVAL, "the tcgen05 path needs L %% %d == 0 (L=%d)", kTcCells, a.L);
     constexpr bool SW = CINP == 32;  // see gs_conv_tc_kernel
     const int box_c = SW ? 32 : 8;
