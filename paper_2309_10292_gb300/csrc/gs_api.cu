@@ -74,8 +74,9 @@ CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box
 }
 
 CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_c, int box_x,
-                       bool swizzle64)
+                       int swizzle)
 {
+    if (swizzle != 0 && swizzle != 32 && swizzle != 64) return CUDA_ERROR_INVALID_VALUE;
     auto enc = tensor_map_encoder();
     if (!enc) return CUDA_ERROR_NOT_FOUND;
     cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)planes};
@@ -83,7 +84,8 @@ CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long lo
     cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)box_x, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_INTERLEAVE_NONE,
+               swizzle == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : (swizzle == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE),
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 

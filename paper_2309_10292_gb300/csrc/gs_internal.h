@@ -33,10 +33,10 @@ int num_sms();
 // Tensor-map encoder obtained from the driver at first use.
 CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y);
 // channels-last bf16 activations [planes][L][L][C] (planes = N * L): boxes of
-// box_c channels x box_x cells x 1 row x 1 plane, optionally with the 64-byte
-// swizzle (box_c = 32)
+// box_c channels x box_x cells x 1 row x 1 plane, with the 32- or 64-byte
+// swizzle (swizzle = 32: box_c = 16; 64: box_c = 32) or none (0)
 CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long long planes, int box_c, int box_x,
-                       bool swizzle64);
+                       int swizzle);
 
 // ---------------------------------------------------------------------------
 // Stencil kernels (gs_stencil.cu)

@@ -593,6 +593,14 @@ GS_D uint64_t tc_desc_sw64(uint32_t saddr, uint32_t sbo)
            (4ull << 61);
 }
 
+GS_D uint64_t tc_desc_sw32(uint32_t saddr, uint32_t sbo)
+{
+    // the 32-byte swizzle (layout type 6): K-major rows of 32 bytes in
+    // 8-row, 256-byte atoms; LBO unused (16 B)
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) |
+           (6ull << 61);
+}
+
 GS_HD uint32_t tc_idesc(int n)
 {
     // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
@@ -738,6 +746,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
     constexpr bool SW = CINP == 32;
     constexpr uint32_t SROWB = kTcRowCells * 64;          // bytes of one swizzled slab row
     static_assert(!SW || kTcSlabRows * SROWB == SLAB, "swizzled slab size");
+    // x-tap input: a slab row is [cell][16 channels] (32 bytes a cell) with the
+    // 32-byte swizzle, one TMA line per cell instead of two 16-byte ones
+    constexpr uint32_t XROWB = kTcRowCells * 32;          // bytes of one 32-byte-swizzled slab row
+    static_assert(!XT || kTcSlabRows * XROWB == SLAB, "x-tap slab size");
     // EPI_LAST (2 output channels): the dz taps side by side along N, each
     // block holding the 4 output rows x 2 channels (8 columns, padded to 16),
     // so each input plane is read by one group of MMAs (N = 48, fewer at the
@@ -852,7 +864,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         // halo, 128 cells, right halo), wrapped periodically by their start
         // coordinates (L is a multiple of 128, so no box straddles the wrap)
         const uint32_t leader = tc_elect_one();
-        if ((sbase & (SW ? 511u : 127u)) == 0) {
+        if ((sbase & (SW ? 511u : (XT ? 255u : 127u))) == 0) {
             if (leader) {
                 gs_prefetch_tmap(&a.map_main);
                 gs_prefetch_tmap(&a.map_halo);
@@ -875,7 +887,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                     const int zp = u.n * L + (u.z0 - 1 + i + L) % L;
                     tc_arrive_expect_tx_if(leader, &slab_full[slot], SLAB_TX);
                     const uint32_t dst0 = sbase + slot * SLAB;
-                    if constexpr (SW) {
+                    if constexpr (XT) {
+                        // one 16-channel box of the 128 cells per row, at cell
+                        // slot 8 (a 256-byte boundary); no halo boxes
+#pragma unroll
+                        for (int yi = 0; yi < kTcSlabRows; ++yi)
+                            tc_tma_load_4d_if(leader, dst0 + yi * XROWB + kTcRowX0 * 32, &a.map_main, &slab_full[slot],
+                                              0, u.x0, yrow[yi], zp);
+                    } else if constexpr (SW) {
                         // three boxes of 32 channels per row, each landing on a
                         // 512-byte boundary (cell slots 0, 8 and 136 of 64 bytes)
 #pragma unroll
@@ -893,13 +912,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
 #pragma unroll
                         for (int yi = 0; yi < kTcSlabRows; ++yi) {
                             const uint32_t row = dst0 + j * PLANE + yi * ROWB;
-                            if constexpr (!XT)
-                                tc_tma_load_4d_if(leader, row, &a.map_halo, &slab_full[slot], j * 8, xl, yrow[yi], zp);
+                            tc_tma_load_4d_if(leader, row, &a.map_halo, &slab_full[slot], j * 8, xl, yrow[yi], zp);
                             tc_tma_load_4d_if(leader, row + kTcRowX0 * 16, &a.map_main, &slab_full[slot], j * 8, u.x0,
                                               yrow[yi], zp);
-                            if constexpr (!XT)
-                                tc_tma_load_4d_if(leader, row + (kTcRowX0 + kTcCells) * 16, &a.map_halo,
-                                                  &slab_full[slot], j * 8, xr, yrow[yi], zp);
+                            tc_tma_load_4d_if(leader, row + (kTcRowX0 + kTcCells) * 16, &a.map_halo, &slab_full[slot],
+                                              j * 8, xr, yrow[yi], zp);
                         }
                 }
             }
@@ -926,8 +943,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
             const uint32_t idn[3] = {tc_idesc(NT), tc_idesc(2 * NT), tc_idesc(3 * NT)};
             // A: no swizzle (LBO = one chunk plane, SBO = 8 cells), or the
             // 64-byte swizzle (SBO = one 8-cell atom; K steps of 32 bytes)
-            const uint64_t adz = SW ? tc_desc_sw64(sbase + slot * SLAB, 512) : tc_desc(sbase + slot * SLAB, PLANE, 128);
-            constexpr uint32_t AROW = SW ? SROWB : ROWB;  // bytes between slab rows
+            const uint64_t adz = SW   ? tc_desc_sw64(sbase + slot * SLAB, 512)
+                                 : XT ? tc_desc_sw32(sbase + slot * SLAB, 256)
+                                      : tc_desc(sbase + slot * SLAB, PLANE, 128);
+            constexpr uint32_t AROW = SW ? SROWB : (XT ? XROWB : ROWB);  // bytes between slab rows
             constexpr int DX0 = XT ? 1 : 0, DX1 = XT ? 2 : 3;  // x-tap input: the unshifted operand only
 #pragma unroll
             for (int dxi = DX0; dxi < DX1; ++dxi)
@@ -936,8 +955,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                     const int wplane = XT ? dzi * NCH + 2 * kk : (dzi * 3 + dxi) * NCH + 2 * kk;
                     const uint64_t bk = tc_desc(wbase + (uint32_t)wplane * WCH, WCH, 128);
                     // output cell i of tap dx reads input cell x0 + i + dx - 1
-                    const uint64_t ak = SW ? adz + (uint64_t)((kk * 32) >> 4) + (uint64_t)(((kTcRowX0 - 1 + dxi) * 64) >> 4)
-                                           : adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(kTcRowX0 - 1 + dxi);
+                    // (x-tap input: dxi = 1 and kk = 0 only, an atom-aligned start)
+                    const uint64_t ak = SW   ? adz + (uint64_t)((kk * 32) >> 4) + (uint64_t)(((kTcRowX0 - 1 + dxi) * 64) >> 4)
+                                        : XT ? adz + (uint64_t)(((kTcRowX0 - 1 + dxi) * 32) >> 4)
+                                             : adz + (uint64_t)((2 * kk * PLANE) >> 4) + (uint64_t)(kTcRowX0 - 1 + dxi);
                     // slab rows 5 and 2 first: together they touch every output row once
 #pragma unroll
                     for (int q = 0; q < kTcSlabRows; ++q) {
@@ -1392,10 +1413,12 @@ int tc_launch(gs_surr* s, ConvTcArgs a)
     const size_t wbytes = EPI == EPI_LAST ? (size_t)6 * 3 * 2 * 2 * 48 * 16 : (size_t)(XT ? 9 : 27) * (CINP / 8) * NT * 16;
     const size_t smem = (XT ? 6 : 3) * (size_t)SLAB + wbytes;  // the kernel's slab ring depth
     if (a.L % kTcCells) return fail(GS_EINVAL, "the tcgen05 path needs L %% %d == 0 (L=%d)", kTcCells, a.L);
-    constexpr bool SW = CINP == 32;  // see gs_conv_tc_kernel
-    const int box_c = SW ? 32 : 8;
-    if (encode_act_4d(&a.map_main, a.in, CINP, a.L, (long long)a.N * a.L, box_c, kTcCells, SW) != CUDA_SUCCESS ||
-        encode_act_4d(&a.map_halo, a.in, CINP, a.L, (long long)a.N * a.L, box_c, 8, SW) != CUDA_SUCCESS)
+    // see gs_conv_tc_kernel: 32 channels with the 64-byte swizzle, x-tap
+    // input (16 channels) with the 32-byte swizzle, else 16-byte chunks
+    constexpr int SWZ = CINP == 32 ? 64 : (XT ? 32 : 0);
+    const int box_c = SWZ ? CINP : 8;
+    if (encode_act_4d(&a.map_main, a.in, CINP, a.L, (long long)a.N * a.L, box_c, kTcCells, SWZ) != CUDA_SUCCESS ||
+        encode_act_4d(&a.map_halo, a.in, CINP, a.L, (long long)a.N * a.L, box_c, 8, SWZ) != CUDA_SUCCESS)
         return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for the activation maps");
     auto k = gs_conv_tc_kernel<CINP, NT, EPI, XT>;
     GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
