@@ -522,28 +522,32 @@ namespace gs {
 // 5th-generation tensor-core forward convolution (tcgen05, TMEM accumulators)
 // ===========================================================================
 //
-// One 4-warp CTA per SM.  A work unit is a column of 4 output rows (y0..y0+3)
-// by 128 cells (x0..x0+127) of one grid, marched over a z-chunk.  The input
-// planes z-1, z, z+1 (each: 6 rows y0-1..y0+4 by 130 cells x0-1..x0+128,
-// periodic) sit in a 3-slab shared ring in the canonical K-major layout
-// without swizzle: slab[chunk j][row][cell][8 channels], one 16-byte core
-// matrix row per cell and chunk.  The A operand of tap (dz, dy, dx) for
-// output row r is then 128 consecutive cells starting at (row r+1+dy, cell
-// 1+dx) of the dz slab: a descriptor offset, no data movement (LBO = one
-// chunk plane, SBO = 8 cells).  Weights (B) stay in shared memory, K-major
-// [dz][dx][chunk][n][8] with n = (2 - (dy + 1)) * NT + cout: for a fixed
-// (dz, dx) the three dy taps sit side by side along N.  One input slab row
-// feeds output rows row-2 (dy = +1), row-1 (dy = 0) and row (dy = -1), whose
-// accumulators are adjacent in TMEM (one per output row), so a single MMA
-// with N = 3 NT (fewer at the slab's edge rows) covers all three: half the
-// MMAs and half the A-operand reads of one MMA per (row, tap).  Thread 0
-// issues tcgen05.mma (M=128, N=NT..3NT, K=16); the first MMAs into a fresh
-// accumulator set (slab rows 5 and 2, which together touch every row once)
-// overwrite, the rest accumulate.  It commits once after the dz=-1 taps (that
-// slab is then refilled with plane z+2 by cp.async while the rest of the MMAs
-// run) and once at the end; the 4 warps read their 32 TMEM lanes each
-// (tcgen05.ld) and apply the epilogue.  Every wait is bounded; on a timeout
-// the CTA records it, lets its own MMAs and copies finish and frees its TMEM.
+// One persistent CTA per SM, three warp roles: a TMA warp stages input
+// planes, one elected lane of the MMA warp issues tcgen05.mma (M = 128, K =
+// 16, bf16 x bf16 -> fp32 in TMEM), four epilogue warps drain the
+// accumulators (tcgen05.ld, 32 TMEM lanes each).  A work unit is a column of
+// 4 output rows (y0..y0+3) by 128 cells (x0..x0+127) of one grid, marched
+// over a z-chunk.  Input planes (each: 6 rows y0-1..y0+4 by the 128 cells
+// plus an x halo, periodic) sit in a shared ring of slabs, K-major with one
+// cell per row of the A operand:
+//   - 32 channels: 64-byte rows with the 64-byte swizzle (one TMA line a cell);
+//   - the first layer's 16-channel x-tap input (inference): 32-byte rows with
+//     the 32-byte swizzle, no x halo (its channels already hold x +- 1);
+//   - otherwise (16 channels, training): 16-byte chunk planes, no swizzle.
+// The A operand of tap (dz, dy, dx) for output row r is 128 consecutive cells
+// from (row r+1+dy, cell 1+dx) of the dz slab: a descriptor offset, no data
+// movement.  Weights (B) stay in shared memory, K-major.  In the hidden and
+// first layers the three dy taps of a (dz, dx) sit side by side along N and
+// the 4 output rows' accumulators are adjacent in TMEM, so one input slab
+// row feeds up to three output rows in one MMA (N = NT .. 3 NT); the first
+// MMAs into a fresh accumulator set (slab rows 5 and 2, which together touch
+// every row once) overwrite, the rest accumulate, and two sets alternate
+// between output planes.  The last layer (2 channels) instead stacks the
+// three dz taps along N: each input plane is one group of MMAs into z-chunk
+// accumulators that the epilogue zeroes (see EPI_LAST below).  Slabs are
+// released by tcgen05.commit as soon as their last MMA is issued.  Every wait
+// is bounded; on a timeout the CTA records it, lets its own MMAs and copies
+// finish and frees its TMEM.
 
 constexpr int kTcEpiWarps = 4;                  // warps 0-3: epilogue (TMEM lanes 32w..32w+31)
 constexpr int kTcMmaWarp = 4;                   // lane 0 issues the MMAs
@@ -560,11 +564,13 @@ constexpr int kTcRowCells = kTcCells + 16;
 constexpr int kTcRowX0 = 8;
 
 struct ConvTcArgs {
-    CUtensorMap map_main;  // a.in, boxes of 8 (32: swizzled) channels x 128 cells
-    CUtensorMap map_halo;  // a.in, boxes of 8 (32: swizzled) channels x 8 cells
+    CUtensorMap map_main;  // a.in, boxes of 8 channels (or all 16 / 32, swizzled) x 128 cells
+    CUtensorMap map_halo;  // a.in, the same x 8 cells
     const bf16* in;     // [N][L^3][CINP]
-    const bf16* w;      // [3 dz][3 dx][CINP/8][3 NT][8] (see gs_wprep_tc_kernel)
-    const float* bias;  // [>= NT] fp32 (padded with zeros)
+    const bf16* w;      // B operands: gs_wprep_tc_kernel's layout, or the x-tap first
+                        // layer's (gs_wprep_tc_xtaps_kernel) or the last layer's
+                        // (gs_wprep_tc_last_kernel)
+    const float* bias;  // fp32, the layer's output channels (NT, or 2 for the last layer)
     int N, L;
     const bf16* res;    // unused (the residual comes from the centre slab)
     bf16* out;
