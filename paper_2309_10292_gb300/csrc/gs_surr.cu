@@ -557,9 +557,9 @@ constexpr int kTcRows = 4;
 constexpr int kTcCells = 128;
 constexpr int kTcSlabRows = kTcRows + 2;  // rows per slab
 constexpr int kTcZChunk = 16;
-// A slab row holds cells x0-8 .. x0+135 (144 cells, 2304 B = 18 x 128 B): three
-// TMA boxes of 8, 128 and 8 cells, each landing on a 128-byte boundary.  Input
-// cell x0 - 1 + c is row cell kTcRowX0 - 1 + c.
+// A slab row holds cells x0-8 .. x0+135 (144 cells of 16, 32 or 64 bytes):
+// TMA boxes of 8, 128 and 8 cells, each landing on a 128-byte (swizzled:
+// atom) boundary.  Input cell x0 - 1 + c is row cell kTcRowX0 - 1 + c.
 constexpr int kTcRowCells = kTcCells + 16;
 constexpr int kTcRowX0 = 8;
 
