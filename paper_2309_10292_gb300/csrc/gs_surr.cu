@@ -549,10 +549,12 @@ namespace gs {
 // is bounded; on a timeout the CTA records it, lets its own MMAs and copies
 // finish and frees its TMEM.
 
-constexpr int kTcEpiWarps = 4;                  // warps 0-3: epilogue (TMEM lanes 32w..32w+31)
-constexpr int kTcMmaWarp = 4;                   // lane 0 issues the MMAs
-constexpr int kTcProdWarp = 5;                  // stages the input planes
-constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);
+// Warp roles: epilogue warps 0 .. E-1 (warp w reads TMEM lanes 32 (w % 4) ..
+// 32 (w % 4) + 31), then the MMA warp and the TMA warp.  E = 4, except for the
+// x-tap first layer: it has little MMA work per plane, so its epilogue runs
+// on 8 warps, two per SM sub-partition, each draining 2 of the 4 output rows.
+GS_HD constexpr int tc_epi_warps(bool xt) { return xt ? 8 : 4; }
+GS_HD constexpr int tc_threads(bool xt) { return 32 * (tc_epi_warps(xt) + 2); }
 constexpr int kTcRows = 4;
 constexpr int kTcCells = 128;
 constexpr int kTcSlabRows = kTcRows + 2;  // rows per slab
@@ -738,8 +740,10 @@ GS_D void tc_arrive_expect_tx_if(uint32_t leader, uint64_t* bar, uint32_t bytes)
 }
 
 template <int CINP, int NT, int EPI, bool XT>
-__global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_constant__ ConvTcArgs a)
+__global__ void __launch_bounds__(tc_threads(XT), 1) gs_conv_tc_kernel(const __grid_constant__ ConvTcArgs a)
 {
+    constexpr int EPIW = tc_epi_warps(XT), MMAW = EPIW, PRODW = EPIW + 1, NTHR = tc_threads(XT);
+    constexpr int EROWS = kTcRows * 4 / EPIW;  // output rows drained by one epilogue warp
     // XT: the input is x-tap packed (gs_pack_kernel with xtaps), so the three
     // dx taps are one K step: one MMA per (dz, slab row), no x halo boxes
     static_assert(!XT || CINP == 16, "x-tap packing is for the 16-channel first layer");
@@ -803,14 +807,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         }
         for (int i = 0; i < 2; ++i) {
             gs_mbar_init(&acc_full[i], 1);
-            gs_mbar_init(&acc_empty[i], kTcEpiWarps);
+            gs_mbar_init(&acc_empty[i], EPIW);
         }
         gs_mbar_init(&bar_fin, 1);
         abort_s = 0;
         gs_fence_mbar_init();
     }
     if (tid < NT) bias_s[tid] = (EPI == EPI_LAST && tid >= 2) ? 0.f : a.bias[tid];  // the last layer has 2
-    for (uint32_t i = tid; i < WBYTES / 16; i += kTcThreads) cp16(wbase + i * 16, a.w + (size_t)i * 8);
+    for (uint32_t i = tid; i < WBYTES / 16; i += NTHR) cp16(wbase + i * 16, a.w + (size_t)i * 8);
     cp_wait_all();
     gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
     tc_fence_before();
@@ -863,7 +867,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         return r != 0;
     };
 
-    if (warp == kTcProdWarp) {
+    if (warp == PRODW) {
         // ------------------------ producer (TMA, one elected lane) ------------------------
         // plane z0 - 1 + i of a unit (i = 0 .. nz+1) is global plane g, slot g % NSLAB;
         // per plane and channel chunk, each of the 6 rows is three boxes (left
@@ -935,7 +939,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
             abort_s = 1;  // unaligned shared memory: refuse to issue TMA
             gs_report(a.err, GS_DERR_BADARG);
         }
-    } else if (warp == kTcMmaWarp) {
+    } else if (warp == MMAW) {
         // ------------------------ MMA issuer (one elected lane) ------------------------
         const uint32_t leader = tc_elect_one();
         // the MMAs of one dz group of an item into accumulator set `set`,
@@ -1065,8 +1069,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
             if (lane == 0) gs_mbar_wait(&bar_fin, 0, 2000000000ull);
         }
     } else {
-        // ------------------------- epilogue warps (0-3) --------------------------
-        const int x_in_seg = tid;  // this thread's cell in the 128-cell segment
+        // --------------------- epilogue warps (0 .. EPIW-1) ----------------------
+        static_assert(!ZS || EPIW == 4, "the last layer drains all 4 rows per warp");
+        const int x_in_seg = tid & 127;      // this thread's cell in the 128-cell segment
+        const int r0 = (warp >> 2) * EROWS;  // its first output row
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         float bias_r[NT];
 #pragma unroll
         for (int c = 0; c < NT; ++c) bias_r[c] = bias_s[c];
@@ -1074,33 +1081,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         // residual of the hidden layers, the state of the last one), loaded one
         // item ahead so their latency overlaps the wait for the accumulators
         constexpr int NRES = EPI == EPI_HIDDEN ? NT / 8 : 1;
-        uint4 rv[kTcRows][NRES];
-        float sres[kTcRows][2];
+        uint4 rv[EROWS][NRES];
+        float sres[EROWS][2];
         auto cell_of = [&](const Unit& u, int q, int r) -> size_t {
             return (size_t)u.n * L3 + ((size_t)(u.z0 + q) * L + (u.y0 + r)) * L + (u.x0 + x_in_seg);
         };
         auto prefetch = [&](const Unit& u, int q) {
 #pragma unroll
-            for (int r = 0; r < kTcRows; ++r) {
-                const size_t cell = cell_of(u, q, r);
+            for (int rr = 0; rr < EROWS; ++rr) {
+                const size_t cell = cell_of(u, q, r0 + rr);
                 if constexpr (EPI == EPI_HIDDEN) {
 #pragma unroll
-                    for (int j = 0; j < NRES; ++j) rv[r][j] = *reinterpret_cast<const uint4*>(a.in + cell * CINP + j * 8);
+                    for (int j = 0; j < NRES; ++j) rv[rr][j] = *reinterpret_cast<const uint4*>(a.in + cell * CINP + j * 8);
                 } else if constexpr (EPI == EPI_LAST) {
-                    sres[r][0] = a.su[cell];
-                    sres[r][1] = a.sv[cell];
+                    sres[rr][0] = a.su[cell];
+                    sres[rr][1] = a.sv[cell];
                 }
             }
         };
         auto epilogue = [&](int set, const Unit& u, int q) {
 #pragma unroll
-            for (int r = 0; r < kTcRows; ++r) {
+            for (int rr = 0; rr < EROWS; ++rr) {
+                const int r = r0 + rr;
                 const size_t cell = cell_of(u, q, r);
                 float acc[NT];
-                tc_ld<NT>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(set * ACC_COLS + r * NT), acc);
+                tc_ld<NT>(lane_base + (uint32_t)(set * ACC_COLS + r * NT), acc);
                 if constexpr (EPI == EPI_LAST) {
-                    a.ou[cell] = sres[r][0] + (acc[0] + bias_r[0]);
-                    a.ov[cell] = sres[r][1] + (acc[1] + bias_r[1]);
+                    a.ou[cell] = sres[rr][0] + (acc[0] + bias_r[0]);
+                    a.ov[cell] = sres[rr][1] + (acc[1] + bias_r[1]);
                 } else {
 #pragma unroll
                     for (int j = 0; j < NT / 8; ++j) {
@@ -1111,7 +1119,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
                             h[e] = fmaxf(zv[e], 0.f);
                         }
                         if constexpr (EPI == EPI_HIDDEN) {
-                            const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv[r][j]);
+                            const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv[rr][j]);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 h[2 * e] = __bfloat162float(rb[e].x) + h[2 * e];
@@ -1134,7 +1142,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gs_conv_tc_kernel(const __grid_
         };
         if constexpr (ZS) {
             // this warp's 32 lanes of a set's columns
-            const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);
+            const uint32_t lanes = lane_base;
             auto zero_set = [&](int set) {
 #pragma unroll
                 for (int c = 0; c < (int)ZS_SETC; c += 32) tc_st_zero32(lanes + (uint32_t)(set * ZS_SETC + c));
@@ -1429,14 +1437,14 @@ int tc_launch(gs_surr* s, ConvTcArgs a)
     auto k = gs_conv_tc_kernel<CINP, NT, EPI, XT>;
     GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTcThreads, smem));
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tc_threads(XT), smem));
     if (per_sm < 1) return fail(GS_EINVAL, "tensor-core convolution does not fit on an SM");
     per_sm = std::min(per_sm, EPI == EPI_LAST ? 1 : 2);  // TMEM: 512 columns a CTA (last layer), else <= 256
     a.err = s->d_err;
     a.timeout_ns = 2000000000ull;
     const long long units = (long long)a.N * (a.L / kTcRows) * (a.L / kTcCells) * ((a.L + kTcZChunk - 1) / kTcZChunk);
     const int grid = (int)std::min<long long>(units, (long long)per_sm * num_sms());
-    k<<<grid, kTcThreads, smem, s->stream>>>(a);
+    k<<<grid, tc_threads(XT), smem, s->stream>>>(a);
     GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
     return GS_OK;
