@@ -703,6 +703,21 @@ GS_D void tc_ld<8>(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32-byte global store / load (p 32-byte aligned): one whole sector per thread
+GS_D void gs_st_v8(void* p, const uint4& a, const uint4& b)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
+                 "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+
+GS_D void gs_ld_v8(const void* p, uint4& a, uint4& b)
+{
+    asm volatile("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
+
 // zero 32 consecutive columns of this warp's 32 TMEM lanes (and wait for it)
 GS_D void tc_st_zero32(uint32_t taddr)
 {
@@ -1091,8 +1106,9 @@ __global__ void __launch_bounds__(tc_threads(XT), 1) gs_conv_tc_kernel(const __g
             for (int rr = 0; rr < EROWS; ++rr) {
                 const size_t cell = cell_of(u, q, r0 + rr);
                 if constexpr (EPI == EPI_HIDDEN) {
+                    // 32-byte loads: each a whole sector of the cell's 64 bytes
 #pragma unroll
-                    for (int j = 0; j < NRES; ++j) rv[rr][j] = *reinterpret_cast<const uint4*>(a.in + cell * CINP + j * 8);
+                    for (int j = 0; j < NRES; j += 2) gs_ld_v8(a.in + cell * CINP + j * 8, rv[rr][j], rv[rr][j + 1]);
                 } else if constexpr (EPI == EPI_LAST) {
                     sres[rr][0] = a.su[cell];
                     sres[rr][1] = a.sv[cell];
@@ -1110,6 +1126,8 @@ __global__ void __launch_bounds__(tc_threads(XT), 1) gs_conv_tc_kernel(const __g
                     a.ou[cell] = sres[rr][0] + (acc[0] + bias_r[0]);
                     a.ov[cell] = sres[rr][1] + (acc[1] + bias_r[1]);
                 } else {
+                    static_assert(NT % 16 == 0, "the epilogue stores 16 channels (32 bytes) at a time");
+                    uint4 ho[NT / 8], zo[NT / 8];
 #pragma unroll
                     for (int j = 0; j < NT / 8; ++j) {
                         float h[8], zv[8];
@@ -1126,16 +1144,19 @@ __global__ void __launch_bounds__(tc_threads(XT), 1) gs_conv_tc_kernel(const __g
                                 h[2 * e + 1] = __bfloat162float(rb[e].y) + h[2 * e + 1];
                             }
                         }
-                        uint4 ho, zo;
-                        __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(&ho);
-                        __nv_bfloat162* zb = reinterpret_cast<__nv_bfloat162*>(&zo);
+                        __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(&ho[j]);
+                        __nv_bfloat162* zb = reinterpret_cast<__nv_bfloat162*>(&zo[j]);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             hb[e] = __floats2bfloat162_rn(h[2 * e], h[2 * e + 1]);
                             zb[e] = __floats2bfloat162_rn(zv[2 * e], zv[2 * e + 1]);
                         }
-                        *reinterpret_cast<uint4*>(a.out + cell * 32 + j * 8) = ho;
-                        if (a.zout) *reinterpret_cast<uint4*>(a.zout + cell * 32 + j * 8) = zo;
+                    }
+                    // 32-byte stores: each writes a whole sector of the cell's 64 bytes
+#pragma unroll
+                    for (int j = 0; j < NT / 8; j += 2) {
+                        gs_st_v8(a.out + cell * 32 + j * 8, ho[j], ho[j + 1]);
+                        if (a.zout) gs_st_v8(a.zout + cell * 32 + j * 8, zo[j], zo[j + 1]);
                     }
                 }
             }
