@@ -375,6 +375,21 @@ __global__ void __launch_bounds__(kWgThreads, 1) gs_wgrad_kernel(const WgArgs a)
     }
 }
 
+// 32-byte global store / load (p 32-byte aligned): one whole sector per thread
+GS_D void gs_st_v8(void* p, const uint4& a, const uint4& b)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
+                 "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+
+GS_D void gs_ld_v8(const void* p, uint4& a, uint4& b)
+{
+    asm volatile("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
+
 // x0 = bf16(u - 1, v, 20 F, 20 k, 0, ...) : [N][L^3][16].  With xtaps set
 // (the tensor-core inference path), channels 4 d + c hold channel c of the x
 // neighbour x + d - 1 (d = 0, 1, 2; periodic in x) and 12..15 are zero, so one
@@ -404,9 +419,8 @@ __global__ void gs_pack_kernel(const float* __restrict__ u, const float* __restr
             c[2] = f;
             c[3] = k;
         }
-        uint4* dst = reinterpret_cast<uint4*>(x0 + i * 16);
-        dst[0] = reinterpret_cast<const uint4*>(c)[0];
-        dst[1] = reinterpret_cast<const uint4*>(c)[1];
+        // one 32-byte store: the cell's whole sector
+        gs_st_v8(x0 + i * 16, reinterpret_cast<const uint4*>(c)[0], reinterpret_cast<const uint4*>(c)[1]);
     }
 }
 
@@ -551,10 +565,11 @@ namespace gs {
 
 // Warp roles: epilogue warps 0 .. E-1 (warp w reads TMEM lanes 32 (w % 4) ..
 // 32 (w % 4) + 31), then the MMA warp and the TMA warp.  E = 4, except for the
-// x-tap first layer: it has little MMA work per plane, so its epilogue runs
-// on 8 warps, two per SM sub-partition, each draining 2 of the 4 output rows.
-GS_HD constexpr int tc_epi_warps(bool xt) { return xt ? 8 : 4; }
-GS_HD constexpr int tc_threads(bool xt) { return 32 * (tc_epi_warps(xt) + 2); }
+// x-tap first layer, whose few MMAs per plane leave the epilogue as the
+// longer role: it runs on E = 8 warps, two per SM sub-partition, each taking
+// 2 of the 4 rows (measured slower for the MMA-bound hidden layers).
+GS_HD constexpr int tc_epi_warps(int epi, bool xt) { return (void)epi, xt ? 8 : 4; }
+GS_HD constexpr int tc_threads(int epi, bool xt) { return 32 * (tc_epi_warps(epi, xt) + 2); }
 constexpr int kTcRows = 4;
 constexpr int kTcCells = 128;
 constexpr int kTcSlabRows = kTcRows + 2;  // rows per slab
@@ -703,21 +718,6 @@ GS_D void tc_ld<8>(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 32-byte global store / load (p 32-byte aligned): one whole sector per thread
-GS_D void gs_st_v8(void* p, const uint4& a, const uint4& b)
-{
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
-                 "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
-                 : "memory");
-}
-
-GS_D void gs_ld_v8(const void* p, uint4& a, uint4& b)
-{
-    asm volatile("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
-                 : "l"(p));
-}
-
 // zero 32 consecutive columns of this warp's 32 TMEM lanes (and wait for it)
 GS_D void tc_st_zero32(uint32_t taddr)
 {
@@ -755,9 +755,9 @@ GS_D void tc_arrive_expect_tx_if(uint32_t leader, uint64_t* bar, uint32_t bytes)
 }
 
 template <int CINP, int NT, int EPI, bool XT>
-__global__ void __launch_bounds__(tc_threads(XT), 1) gs_conv_tc_kernel(const __grid_constant__ ConvTcArgs a)
+__global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(const __grid_constant__ ConvTcArgs a)
 {
-    constexpr int EPIW = tc_epi_warps(XT), MMAW = EPIW, PRODW = EPIW + 1, NTHR = tc_threads(XT);
+    constexpr int EPIW = tc_epi_warps(EPI, XT), MMAW = EPIW, PRODW = EPIW + 1, NTHR = tc_threads(EPI, XT);
     constexpr int EROWS = kTcRows * 4 / EPIW;  // output rows drained by one epilogue warp
     // XT: the input is x-tap packed (gs_pack_kernel with xtaps), so the three
     // dx taps are one K step: one MMA per (dz, slab row), no x halo boxes
@@ -1089,9 +1089,7 @@ __global__ void __launch_bounds__(tc_threads(XT), 1) gs_conv_tc_kernel(const __g
         const int x_in_seg = tid & 127;      // this thread's cell in the 128-cell segment
         const int r0 = (warp >> 2) * EROWS;  // its first output row
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        float bias_r[NT];
-#pragma unroll
-        for (int c = 0; c < NT; ++c) bias_r[c] = bias_s[c];
+        const float* bias_r = bias_s;  // shared memory: same-address reads broadcast
         // per-item inputs of the epilogue that do not depend on the MMAs (the
         // residual of the hidden layers, the state of the last one), loaded one
         // item ahead so their latency overlaps the wait for the accumulators
@@ -1458,14 +1456,14 @@ int tc_launch(gs_surr* s, ConvTcArgs a)
     auto k = gs_conv_tc_kernel<CINP, NT, EPI, XT>;
     GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tc_threads(XT), smem));
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tc_threads(EPI, XT), smem));
     if (per_sm < 1) return fail(GS_EINVAL, "tensor-core convolution does not fit on an SM");
     per_sm = std::min(per_sm, EPI == EPI_LAST ? 1 : 2);  // TMEM: 512 columns a CTA (last layer), else <= 256
     a.err = s->d_err;
     a.timeout_ns = 2000000000ull;
     const long long units = (long long)a.N * (a.L / kTcRows) * (a.L / kTcCells) * ((a.L + kTcZChunk - 1) / kTcZChunk);
     const int grid = (int)std::min<long long>(units, (long long)per_sm * num_sms());
-    k<<<grid, tc_threads(XT), smem, s->stream>>>(a);
+    k<<<grid, tc_threads(EPI, XT), smem, s->stream>>>(a);
     GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
     return GS_OK;
