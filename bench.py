@@ -155,13 +155,16 @@ def cpu_oracle_sample(target_s: float = 12.0, L: int = L_MAIN):
     import oracle
     threads = oracle.set_threads(os.cpu_count() or 1)
     u, v = oracle.init(L)
-    t0 = time.perf_counter()
+    # step 0 warms the threads and pages; then chunks of 1, 2, 4, ... steps
+    # continue the trajectory until the timed sample reaches target_s
     u, v = oracle.step(u, v, 1, **PARAMS, noise=NOISE, seed=SEED, t0=0)
-    one = time.perf_counter() - t0
-    n = max(1, min(50, int(target_s / max(one, 1e-3))))
-    t0 = time.perf_counter()
-    u, v = oracle.step(u, v, n, **PARAMS, noise=NOISE, seed=SEED, t0=1)
-    dt = time.perf_counter() - t0
+    n, dt, chunk = 0, 0.0, 1
+    while dt < target_s and n < 2000:
+        t0 = time.perf_counter()
+        u, v = oracle.step(u, v, chunk, **PARAMS, noise=NOISE, seed=SEED, t0=1 + n)
+        dt += time.perf_counter() - t0
+        n += chunk
+        chunk = min(2 * chunk, 2000 - n) if dt < target_s / 2 else max(1, min(chunk, 2000 - n))
     assert np.isfinite(u).all()
     return {"value": L ** 3 * n / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
             "sample": f"FP64 oracle, L={L}, steps 1..{n} of the noise-0.1 centred-cube run "
