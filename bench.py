@@ -187,7 +187,9 @@ def run_reference(args):
     threads = oracle.set_threads(os.cpu_count() or 1)
     L = L_MAIN
     u, v = oracle.init(L)
-    per_step_time_steps = 2
+    # 16 time steps per bench step (about 1 s on 16 cores): long enough that the
+    # per-call copies of the FP64 fields in and out of the oracle do not dominate
+    per_step_time_steps = 16
     times = []
     t = 0
     for i in range(args.warmup + args.steps):
