@@ -1120,10 +1120,7 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                 const size_t cell = cell_of(u, q, r);
                 float acc[NT];
                 tc_ld<NT>(lane_base + (uint32_t)(set * ACC_COLS + r * NT), acc);
-                if constexpr (EPI == EPI_LAST) {
-                    a.ou[cell] = sres[rr][0] + (acc[0] + bias_r[0]);
-                    a.ov[cell] = sres[rr][1] + (acc[1] + bias_r[1]);
-                } else {
+                if constexpr (EPI != EPI_LAST) {  // (the last layer drains in its own loop below)
                     static_assert(NT % 16 == 0, "the epilogue stores 16 channels (32 bytes) at a time");
                     uint4 ho[NT / 8], zo[NT / 8];
 #pragma unroll
