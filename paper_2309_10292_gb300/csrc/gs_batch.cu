@@ -6,7 +6,9 @@
 // rows, times a z-chunk of tz planes.  Every work item therefore holds about
 // the same number of cells, and because a tile spans whole rows the x wrap is
 // an index wrap inside shared memory (no x-halo copies).  Work items are
-// numbered instance by instance; CTA b takes items b, b + grid, ...
+// numbered instance by instance; CTA b takes items b, b + grid, ...  The
+// items of a partial last round are cut along z into up to four pieces, so
+// that round ends after a fraction of an item instead of a whole one.
 //
 // Per item a producer warp streams the planes z0-1 .. z0+nz with TMA (tile
 // box + two wrapped halo rows per field, per-instance tensor maps in global
@@ -58,7 +60,7 @@ template <typename T>
 struct BArgs {
     T* arena;
     const BInst* inst;
-    const int* item_inst;     // work item -> instance
+    const int4* items;        // work item -> (instance, y0, z0, nz)
     const CUtensorMap* maps;  // [inst][set][field][kind]: kind 0 tile box, 1 halo row
     BCtrl* ctrl;
     int nitems, tz, stages;
@@ -167,12 +169,12 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
             // planes z-1, z, z+1 in three register sets rotated by renaming
             T qu[3][V], qv[3][V];
             for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x) {
-                const int ii = a.item_inst[item];
+                const int4 it = a.items[item];
+                const int ii = it.x;
                 const BInst& I = a.inst[ii];
                 const int L = I.L, ty = I.ty, nxv = L / V;
-                const int local = item - I.item0;
-                const int y0 = (local % I.nty) * ty, z0 = (local / I.nty) * a.tz;
-                const int nvy = min(ty, L - y0), nz = min(a.tz, L - z0);
+                const int y0 = it.y, z0 = it.z, nz = it.w;
+                const int nvy = min(ty, L - y0);
                 const int xv = tid % nxv, row = tid / nxv;
                 const bool active = row < nvy;
                 const int rr = row < ty ? row : 0;
@@ -265,12 +267,12 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
             // ------------------------------ producer -------------------------------
             gs_fence_proxy_async_global();  // the previous step's stores (acquired at the barrier)
             for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x) {
-                const int ii = a.item_inst[item];
+                const int4 it = a.items[item];
+                const int ii = it.x;
                 const BInst& I = a.inst[ii];
                 const int L = I.L, ty = I.ty;
-                const int local = item - I.item0;
-                const int y0 = (local % I.nty) * ty, z0 = (local / I.nty) * a.tz;
-                const int nvy = min(ty, L - y0), nz = min(a.tz, L - z0);
+                const int y0 = it.y, z0 = it.z, nz = it.w;
+                const int nvy = min(ty, L - y0);
                 const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
                 const uint32_t bytes = 2u * (uint32_t)(L * ty + 2 * L) * (uint32_t)sizeof(T);
                 const CUtensorMap* mu = a.maps + (((size_t)ii * 2 + in) * 2 + 0) * 2;
@@ -330,7 +332,10 @@ struct gs_batch {
     std::vector<BInst> h_inst;
     void* arena = nullptr;
     BInst* d_inst = nullptr;
-    int* d_item_inst = nullptr;
+    std::vector<int4> base_items;           // (instance, y0, z0, nz) before the tail split
+    int4* d_items = nullptr;                // the table the kernel walks
+    int items_cap = 0;                      // capacity of d_items
+    int items_grid = -1;                    // grid the device table was cut for (-1: none yet)
     CUtensorMap* d_maps = nullptr;
     BCtrl* d_ctrl = nullptr;
     std::vector<ZPlan> zplan;               // per-instance plan of the sequential path
@@ -349,6 +354,60 @@ struct gs_batch {
     int fault = 0;
     bool cooperative = true;
 };
+
+// the work items of instances [0, n): (instance, y0, z0, nz), instance by
+// instance, y tiles fastest
+static void plain_items(const BInst* inst, int n, int tz, std::vector<int4>& out)
+{
+    out.clear();
+    for (int i = 0; i < n; ++i) {
+        const BInst& I = inst[i];
+        for (int j = 0; j < I.nty * I.ntz; ++j) {
+            const int y0 = (j % I.nty) * I.ty, z0 = (j / I.nty) * tz;
+            out.push_back(make_int4(i, y0, z0, std::min(tz, I.L - z0)));
+        }
+    }
+}
+
+// With `grid` CTAs taking items round robin, the last round holds
+// rem = n mod grid items and lasts a whole item for the CTAs that have one.
+// Cut each of those items along z into f = min(4, grid / rem) pieces (fewer
+// when it has fewer planes) appended after the full rounds, so the last
+// round lasts about 1/f of an item.  Every cell is still updated once.
+static void split_tail(const std::vector<int4>& base, int grid, std::vector<int4>& out)
+{
+    out = base;
+    const int n = (int)base.size();
+    if (grid < 1 || n <= grid) return;
+    const int rem = n % grid;
+    if (rem == 0) return;
+    const int f = std::min(4, grid / rem);
+    if (f < 2) return;
+    out.resize(n - rem);
+    for (int q = n - rem; q < n; ++q) {
+        const int4 it = base[q];
+        const int parts = std::min(f, it.w);
+        for (int p = 0; p < parts; ++p) {
+            const int za = it.w * p / parts, zb = it.w * (p + 1) / parts;
+            out.push_back(make_int4(it.x, it.y, it.z + za, zb - za));
+        }
+    }
+}
+
+// upload `items` as the kernel's table (growing the device buffer if needed)
+static int upload_items(gs_batch* b, const std::vector<int4>& items)
+{
+    if ((int)items.size() > b->items_cap) {
+        int4* d = nullptr;
+        GS_CUDA_TRY(cudaMalloc(&d, sizeof(int4) * items.size()));
+        cudaFree(b->d_items);
+        b->d_items = d;
+        b->items_cap = (int)items.size();
+    }
+    GS_CUDA_TRY(cudaMemcpy(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    b->nitems = (int)items.size();
+    return GS_OK;
+}
 
 static int batch_upload_ctrl(gs_batch* b)
 {
@@ -376,10 +435,8 @@ static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
     BArgs<T> a;
     a.arena = (T*)b->arena;
     a.inst = b->d_inst;
-    a.item_inst = b->d_item_inst;
     a.maps = b->d_maps;
     a.ctrl = b->d_ctrl;
-    a.nitems = b->nitems;
     a.tz = b->tz;
     a.stages = b->stages;
     a.main_elems = b->main_elems;
@@ -399,7 +456,20 @@ static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem));
     if (per_sm < 1) return fail(GS_EINVAL, "batch kernel does not fit on an SM");
-    b->grid = std::min(per_sm * num_sms(), b->nitems);
+    const int grid = std::min(per_sm * num_sms(), (int)b->base_items.size());
+    if (b->items_grid != grid) {
+        // cut the partial last round for this grid (once per plan)
+        std::vector<int4> items;
+        split_tail(b->base_items, grid, items);
+        GS_CUDA_TRY(cudaStreamSynchronize(b->stream));  // no launch still reads the old table
+        const int rc = upload_items(b, items);
+        if (rc) return rc;
+        b->items_grid = grid;
+        drop_graphs(b);  // graphs captured with the old table
+    }
+    b->grid = grid;
+    a.items = b->d_items;
+    a.nitems = b->nitems;
     for (int attempt = 0; attempt < 2; ++attempt) {
         cudaGraph_t g = nullptr;
         GS_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -454,7 +524,7 @@ int gs_batch_destroy(gs_batch* b)
     drop_graphs(b);
     if (b->arena) cudaFree(b->arena);
     if (b->d_inst) cudaFree(b->d_inst);
-    if (b->d_item_inst) cudaFree(b->d_item_inst);
+    if (b->d_items) cudaFree(b->d_items);
     if (b->d_maps) cudaFree(b->d_maps);
     if (b->d_ctrl) cudaFree(b->d_ctrl);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -499,7 +569,7 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
     b->row_elems = (maxL + a128 - 1) / a128 * a128;
     b->field_elems = b->main_elems + 2 * b->row_elems;
     // instance table, arena offsets, work items
-    std::vector<int> item_inst;
+    int nit = 0;
     long long off = 0;
     const long long align = 256 / esz;
     for (int i = 0; i < n; ++i) {
@@ -508,8 +578,9 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
         I.ty = std::min(L[i], kBatchConsumers * V / L[i]);
         I.nty = (L[i] + I.ty - 1) / I.ty;
         I.ntz = (L[i] + b->tz - 1) / b->tz;
-        I.item0 = (int)item_inst.size();
+        I.item0 = nit;
         I.nitems = I.nty * I.ntz;
+        nit += I.nitems;
         const uint64_t si = seed + (uint64_t)i;
         I.seed_lo = (uint32_t)si;
         I.seed_hi = (uint32_t)(si >> 32);
@@ -521,16 +592,15 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
                 I.off[s][f] = off;
                 off += (cells + align - 1) / align * align;
             }
-        for (int j = 0; j < I.nitems; ++j) item_inst.push_back(i);
         b->h_inst.push_back(I);
     }
-    b->nitems = (int)item_inst.size();
+    plain_items(b->h_inst.data(), n, b->tz, b->base_items);
+    b->nitems = (int)b->base_items.size();
     int rc = GS_OK;
     cudaError_t e;
     b->arena_bytes = (size_t)off * esz;
     if ((e = cudaMalloc(&b->arena, (size_t)off * esz)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_inst, sizeof(BInst) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_item_inst, sizeof(int) * b->nitems)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * (size_t)n * 8)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_ctrl, sizeof(BCtrl))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -567,13 +637,12 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
     }
     if (rc == GS_OK) {
         if ((e = cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(b->d_item_inst, item_inst.data(), sizeof(int) * b->nitems, cudaMemcpyHostToDevice)) !=
-                cudaSuccess ||
             (e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice)) !=
                 cudaSuccess ||
             (e = cudaMemset(b->d_ctrl, 0, sizeof(BCtrl))) != cudaSuccess)
             rc = cuda_fail(e, "uploading the batch tables");
     }
+    if (rc == GS_OK) rc = upload_items(b, b->base_items);
     if (rc == GS_OK) rc = gs_batch_init(b);
     if (rc != GS_OK) {
         gs_batch_destroy(b);
@@ -793,23 +862,23 @@ int gs_batch_set_plan(gs_batch* b, int tile_z, int stages)
     if (stages < 3 || stages > 8) return fail(GS_EINVAL, "stages=%d must be in [3, 8]", stages);
     const size_t esz = elem_size(b->dtype);
     if ((size_t)2 * b->field_elems * esz * stages > 200 * 1024) return fail(GS_EINVAL, "ring too large");
-    // rebuild the work-item tables for the new z-chunk
-    std::vector<int> item_inst;
+    // rebuild the work-item tables for the new z-chunk (the tail is cut again
+    // at the next capture, when the grid is known)
+    int nit = 0;
     for (int i = 0; i < b->n; ++i) {
         BInst& I = b->h_inst[i];
         I.ntz = (I.L + tile_z - 1) / tile_z;
-        I.item0 = (int)item_inst.size();
+        I.item0 = nit;
         I.nitems = I.nty * I.ntz;
-        for (int j = 0; j < I.nitems; ++j) item_inst.push_back(i);
+        nit += I.nitems;
     }
-    if ((int)item_inst.size() != b->nitems) {
-        int* d = nullptr;
-        GS_CUDA_TRY(cudaMalloc(&d, sizeof(int) * item_inst.size()));
-        cudaFree(b->d_item_inst);
-        b->d_item_inst = d;
-        b->nitems = (int)item_inst.size();
+    plain_items(b->h_inst.data(), b->n, tile_z, b->base_items);
+    GS_CUDA_TRY(cudaStreamSynchronize(b->stream));  // no launch still reads the old table
+    {
+        const int rc = upload_items(b, b->base_items);
+        if (rc) return rc;
     }
-    GS_CUDA_TRY(cudaMemcpy(b->d_item_inst, item_inst.data(), sizeof(int) * item_inst.size(), cudaMemcpyHostToDevice));
+    b->items_grid = -1;
     GS_CUDA_TRY(cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(BInst) * b->n, cudaMemcpyHostToDevice));
     b->tz = tile_z;
     b->stages = stages;
@@ -846,7 +915,7 @@ constexpr int kNoAllocMaxItems = 8192;
 constexpr size_t kNaCtrlOff = 0;
 constexpr size_t kNaInstOff = 256;
 constexpr size_t kNaItemOff = kNaInstOff + (kNoAllocMaxInst * sizeof(BInst) + 255) / 256 * 256;
-constexpr size_t kNaMapOff = kNaItemOff + (kNoAllocMaxItems * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kNaMapOff = kNaItemOff + (kNoAllocMaxItems * sizeof(int4) + 255) / 256 * 256;
 constexpr size_t kNaBytes = kNaMapOff + (size_t)kNoAllocMaxInst * 8 * sizeof(CUtensorMap);
 constexpr int kNaMaxDevices = 64;
 
@@ -857,7 +926,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 static std::mutex g_na_mutex;
 static void* g_na_addr[kNaMaxDevices] = {};
 static BInst g_na_inst[kNoAllocMaxInst];
-static int g_na_items[kNoAllocMaxItems];
+static int4 g_na_items[kNoAllocMaxItems];
 static CUtensorMap g_na_maps[(size_t)kNoAllocMaxInst * 8];
 
 template <typename T, bool NOISE>
@@ -867,7 +936,7 @@ static int noalloc_launch_t(char* scratch, void* arena, int n, int nitems, int m
     BArgs<T> a;
     a.arena = (T*)arena;
     a.inst = (const BInst*)(scratch + kNaInstOff);
-    a.item_inst = (const int*)(scratch + kNaItemOff);
+    a.items = (const int4*)(scratch + kNaItemOff);
     a.maps = (const CUtensorMap*)(scratch + kNaMapOff);
     a.ctrl = (BCtrl*)(scratch + kNaCtrlOff);
     a.nitems = nitems;
@@ -977,7 +1046,10 @@ extern "C" int gs_batch_step_noalloc(int n, const int* L, const double* F, const
                 I.off[s][f] = off;
                 off += (cells + align - 1) / align * align;
             }
-        for (int j = 0; j < I.nitems; ++j) g_na_items[nit++] = i;
+        for (int j = 0; j < I.nitems; ++j) {
+            const int y0 = (j % I.nty) * I.ty, z0 = (j / I.nty) * 32;
+            g_na_items[nit++] = make_int4(i, y0, z0, std::min(32, I.L - z0));
+        }
         g_na_inst[i] = I;
         for (int s = 0; s < 2; ++s)
             for (int f = 0; f < 2; ++f) {
@@ -994,7 +1066,7 @@ extern "C" int gs_batch_step_noalloc(int n, const int* L, const double* F, const
     cudaStream_t s = (cudaStream_t)stream;
     GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaCtrlOff, &h, sizeof(BCtrl), cudaMemcpyHostToDevice, s));
     GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaInstOff, g_na_inst, sizeof(BInst) * n, cudaMemcpyHostToDevice, s));
-    GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaItemOff, g_na_items, sizeof(int) * nit, cudaMemcpyHostToDevice, s));
+    GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaItemOff, g_na_items, sizeof(int4) * nit, cudaMemcpyHostToDevice, s));
     GS_CUDA_TRY(cudaMemcpyAsync(scratch + kNaMapOff, g_na_maps, sizeof(CUtensorMap) * (size_t)n * 8,
                                 cudaMemcpyHostToDevice, s));
     const bool nz = noise != 0.0;
