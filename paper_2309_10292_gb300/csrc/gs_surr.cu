@@ -840,11 +840,11 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
     const int nseg = L / kTcCells;
     const int nyg = L / kTcRows;
     const int nzc = (L + kTcZChunk - 1) / kTcZChunk;
-    const long long units = (long long)a.N * nyg * nseg * nzc;
+    const long long nunits = (long long)a.N * nyg * nseg * nzc;
     struct Unit {
         int n, x0, y0, z0, nz;
     };
-    auto decode = [&](long long unit) {
+    auto decode_unit = [&](long long unit) {
         Unit u;
         const int zc = (int)(unit % nzc);
         long long r0 = unit / nzc;
@@ -855,6 +855,25 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
         u.x0 = seg * kTcCells;
         u.z0 = zc * kTcZChunk;
         u.nz = min(kTcZChunk, L - u.z0);
+        return u;
+    };
+    // CTAs take units round robin; the units of a partial last round are cut
+    // along z into up to 4 pieces, so that round ends after a fraction of a
+    // unit.  Every role walks the same sequence: index v < full is unit v,
+    // beyond it piece (v - full) % nsplit of unit full + (v - full) / nsplit.
+    const long long full = nunits / gridDim.x * gridDim.x;
+    const long long rem = nunits - full;
+    const int fsplit = (full > 0 && rem > 0) ? (int)min(4LL, (long long)gridDim.x / rem) : 1;
+    const int nsplit = fsplit >= 2 ? fsplit : 1;
+    const long long units = full + rem * nsplit;
+    auto decode = [&](long long v) -> Unit {
+        if (v < full) return decode_unit(v);
+        const long long p = v - full;
+        Unit u = decode_unit(full + p / nsplit);
+        const int part = (int)(p % nsplit);
+        const int za = u.nz * part / nsplit, zb = u.nz * (part + 1) / nsplit;
+        u.z0 += za;
+        u.nz = zb - za;
         return u;
     };
     // bounded wait that also gives up once another role has aborted
