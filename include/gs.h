@@ -348,9 +348,9 @@ int gs_batch_destroy(gs_batch* b);
  * out-of-memory halfway through a run.  This call advances a batch like
  * gs_batch_step but creates no object and allocates no device memory: the
  * control block, instance and work-item tables and TMA descriptors live in
- * one fixed file-scope device array of about 309 KB (enough for 256
- * instances and 8192 work items), which every GPU that loads the library
- * holds until the process exits.  Larger batches are rejected with
+ * one fixed file-scope device array of 413,952 bytes (404 KiB; enough for
+ * 256 instances and 8192 work items), which every GPU that loads the
+ * library holds until the process exits.  Larger batches are rejected with
  * GS_EINVAL and a message naming the limit.
  *
  * Arguments as in gs_batch_create, plus:
@@ -366,9 +366,13 @@ int gs_batch_destroy(gs_batch* b);
  * array's device address there (cudaGetSymbolAddress, with that device
  * current); make that first call before any stream capture.  Every call
  * shares the one array and leaves the last call's tables in it (the call
- * resets the barrier counter and error word it needs); calls that overlap on
- * the GPU (other streams, other host threads on the same device) race on it
- * and must be serialised by the caller. */
+ * resets the barrier counter and error word it needs).  Calls that
+ * overlapped on the GPU would race on the array; within one process this
+ * call holds a lock from building its tables until its stream has finished,
+ * so calls from several host threads run one after the other (another
+ * process has its own copy of the array).  Its work items are the plain
+ * (instance, y tile, 32-plane z-chunk) table: unlike gs_batch_step it does
+ * not cut the partial last round of items along z. */
 int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k, double Du,
                           double Dv, double dt, double noise, uint64_t seed, int dtype, void* arena,
                           int64_t t, int cur, int64_t nsteps, void* stream);

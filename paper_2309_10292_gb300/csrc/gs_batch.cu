@@ -98,7 +98,10 @@ GS_D bool batch_grid_sync(BCtrl* ctrl, unsigned target, uint64_t timeout_ns, boo
         if (ok) {
             uint64_t t0 = 0;
             bool timing = false;
-            while (gs_ld_acquire_gpu(&ctrl->bar) < target) {
+            // the arrival counter and the target both wrap modulo 2^32 on long
+            // runs (steps x CTAs); their signed difference stays exact because
+            // the counter is never more than one step's arrivals away from it
+            while ((int)(gs_ld_acquire_gpu(&ctrl->bar) - target) < 0) {
                 if (gs_ld_relaxed_gpu(&ctrl->err)) {
                     ok = false;
                     break;
@@ -305,7 +308,9 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
             }
         }
         const bool skip = a.fault == 2 && blockIdx.x == 0;
-        if (!batch_grid_sync(a.ctrl, (unsigned)(s + 1) * gridDim.x, a.timeout_ns, skip, &s_abort)) break;
+        if (!batch_grid_sync(a.ctrl, (unsigned)((unsigned long long)(s + 1) * gridDim.x), a.timeout_ns, skip,
+                             &s_abort))
+            break;
     }
     if (tid == kBatchConsumers && s_abort) {
         // a failure stopped the consumers: let every copy this thread issued
@@ -918,6 +923,10 @@ constexpr size_t kNaItemOff = kNaInstOff + (kNoAllocMaxInst * sizeof(BInst) + 25
 constexpr size_t kNaMapOff = kNaItemOff + (kNoAllocMaxItems * sizeof(int4) + 255) / 256 * 256;
 constexpr size_t kNaBytes = kNaMapOff + (size_t)kNoAllocMaxInst * 8 * sizeof(CUtensorMap);
 constexpr int kNaMaxDevices = 64;
+// 256 B control block + 20,480 B instance table + 131,072 B work items +
+// 262,144 B TMA descriptors (quoted in the public header)
+static_assert(sizeof(BInst) == 80 && sizeof(CUtensorMap) == 128, "scratch layout");
+static_assert(kNaBytes == 413952, "allocation-free scratch size");
 
 // The scratch itself.  In host code this name is only a stand-in for the
 // symbol: the device address comes from cudaGetSymbolAddress, per device.

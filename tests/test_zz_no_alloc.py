@@ -27,6 +27,14 @@ def _fill_arena(torch, ref, Ls, offs, arena):
         arena[offs[i][1]:offs[i][1] + n] = torch.from_numpy(v.ravel()).to(arena.device)
 
 
+def _fill_set(torch, ref, Ls, offs, arena, cur):
+    for i, L in enumerate(Ls):
+        u, v = ref.read(i)
+        n = L ** 3
+        arena[offs[i][2 * cur]:offs[i][2 * cur] + n] = torch.from_numpy(u.ravel()).to(arena.device)
+        arena[offs[i][2 * cur + 1]:offs[i][2 * cur + 1] + n] = torch.from_numpy(v.ravel()).to(arena.device)
+
+
 def _arena_state(arena, offs, i, L, cur):
     n = L ** 3
     u = arena[offs[i][2 * cur]:offs[i][2 * cur] + n].cpu().numpy().reshape(L, L, L)
@@ -72,6 +80,37 @@ def test_noalloc_equals_batch_step_two_calls(dtype):
         ur, vr = ref.read(i)
         np.testing.assert_array_equal(ua, ur)
         np.testing.assert_array_equal(va, vr)
+    ref.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_noalloc_from_second_buffer_set_odd_steps_largest_L(dtype):
+    # entry with the state in buffer set 1 at a nonzero step, an odd step
+    # count (the state ends in set 0), and the largest instance the call
+    # takes (L = 256; for FP64 its y tile is two rows)
+    torch = need_cuda()
+    v4 = dtype == "f32"
+    Ls = [256, 16, 40 if v4 else 10, 64]
+    F = [0.02, 0.035, 0.05, 0.03]
+    k = [0.048, 0.06, 0.065, 0.05]
+    ref = gs.GrayScottBatch(Ls, F, k, noise=0.1, seed=11, dtype=dtype, **BASE)
+    ref.step(3)  # state at step 3
+    offs, total = gs.noalloc_arena_offsets(Ls, dtype)
+    tdt = torch.float32 if v4 else torch.float64
+    arena = torch.full((total,), float("nan"), dtype=tdt, device="cuda")
+    _fill_set(torch, ref, Ls, offs, arena, 1)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    for call, n in enumerate((5, 2)):
+        cur = 1 if call == 0 else 0
+        gs.gs_batch_step_noalloc(Ls, F, k, BASE["Du"], BASE["Dv"], BASE["dt"], 0.1, 11, dtype, arena,
+                                 ref.t, cur, n, stream)
+        ref.step(n)
+        for i, L in enumerate(Ls):
+            ua, va = _arena_state(arena, offs, i, L, 0)
+            ur, vr = ref.read(i)
+            np.testing.assert_array_equal(ua, ur)
+            np.testing.assert_array_equal(va, vr)
     ref.close()
 
 
