@@ -414,6 +414,19 @@ int gs_surr_set_params(gs_surr* s, const float* host, size_t count);
 int gs_surr_get_params(gs_surr* s, float* host, size_t count);
 /* Gradients of the last gs_surr_grad / gs_surr_train_step, same layout. */
 int gs_surr_get_grads(gs_surr* s, float* host, size_t count);
+/* Checking aids for the gradients (tests and debugging; not needed to train).
+ * gs_surr_trace_grads: while dh is not NULL, every gs_surr_grad /
+ * gs_surr_train_step also copies the gradient of the loss with respect to
+ * each residual activation h_l (l = 1..5: FP32, layout [l-1][N][L^3][32],
+ * channels fastest) into the caller's device array dh of `count` floats;
+ * the grad call returns GS_EINVAL unless count == 5 * N * L^3 * 32.  NULL
+ * turns the copies off.  The array stays owned by the caller.
+ * gs_surr_get_train_output: copy the prediction made by the forward pass of
+ * the last gradient computation (the training form of the network, which
+ * keeps every activation) into device arrays of `cells` = N * L^3 floats;
+ * GS_ESTATE before any gradient computation.  Synchronous. */
+int gs_surr_trace_grads(gs_surr* s, float* dh, size_t count);
+int gs_surr_get_train_output(gs_surr* s, float* u_out, float* v_out, size_t cells);
 /* Apply the network: (u_out, v_out) = prediction of the state 16 steps after
  * (u, v) for N grids (device arrays; outputs may not alias inputs). */
 int gs_surr_forward(gs_surr* s, int N, int L, const float* u, const float* v, const double* F,

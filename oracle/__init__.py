@@ -280,21 +280,37 @@ def mse_loss(out: np.ndarray, target: np.ndarray) -> tuple[float, np.ndarray]:
     return float(np.sum(diff * diff) / n), 2.0 * diff / n
 
 
-def surrogate_backward(cache, dout: np.ndarray):
-    """Gradients of the loss w.r.t. each layer's (w, b), given dL/dout."""
+def surrogate_backward(cache, dout: np.ndarray, *, emulate_bf16: bool = False, return_dh: bool = False):
+    """Gradients of the loss w.r.t. each layer's (w, b), given dL/dout.
+
+    Chain rule through the network of surrogate_forward: for the residual
+    layers h_{l+1} = h_l + relu(z_l), dL/dh_l = dL/dh_{l+1} + conv_l^T(dz_l)
+    with dz_l = dL/dh_{l+1} * [z_l > 0].  With emulate_bf16 the two kinds of
+    back-propagated values the GPU stores in bfloat16 are rounded where it
+    rounds them: dL/dout (its storage has the first layer's 16-channel
+    format) and every dz_l; the residual-path sums dL/dh_l stay unrounded
+    (FP32 on the GPU).  With return_dh the list [dL/dh_1, ..., dL/dh_5] is
+    returned as well.
+    """
     hs, zs, ws = cache["hs"], cache["zs"], cache["ws"]
     grads = [None] * 6
+    dhs = [None] * 6
+    dout = _q(dout, emulate_bf16)
     dw, db = conv3d_bwd_weight(hs[5], dout)
     grads[5] = (dw, db)
     dh = conv3d_bwd_data(dout, ws[5])
+    dhs[5] = dh
     for l in range(4, 0, -1):
-        dz = dh * (zs[l] > 0.0)
+        dz = _q(dh * (zs[l] > 0.0), emulate_bf16)
         dw, db = conv3d_bwd_weight(hs[l], dz)
         grads[l] = (dw, db)
         dh = dh + conv3d_bwd_data(dz, ws[l])
-    dz = dh * (zs[0] > 0.0)
+        dhs[l] = dh
+    dz = _q(dh * (zs[0] > 0.0), emulate_bf16)
     dw, db = conv3d_bwd_weight(hs[0], dz)
     grads[0] = (dw, db)
+    if return_dh:
+        return grads, dhs[1:]
     return grads
 
 

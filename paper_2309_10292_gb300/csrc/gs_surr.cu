@@ -1364,6 +1364,8 @@ struct gs_surr {
     cudaStream_t stream = nullptr;
     int64_t adam_t = 0;
     int64_t launches = 0;
+    float* trace_dh = nullptr;  // checking aid: caller's array for dL/dh_l, l = 1..5
+    size_t trace_count = 0;
 };
 
 namespace {
@@ -1602,6 +1604,17 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
     return conv_launch<32, 8, EPI_LAST>(s, b);
 }
 
+// checking aid: copy the residual-path gradient gh = dL/dh_l (fp32) into
+// slot l - 1 of the caller's trace array
+int trace_dh(gs_surr* s, int l, long long cells)
+{
+    if (!s->trace_dh) return GS_OK;
+    const size_t n = (size_t)cells * 32;
+    GS_CUDA_TRY(cudaMemcpyAsync(s->trace_dh + (size_t)(l - 1) * n, s->gh, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                s->stream));
+    return GS_OK;
+}
+
 // gradients of the MSE loss into s->grads (zeroed first); loss into *loss
 int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double* loss)
 {
@@ -1641,6 +1654,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     d.zprev = s->z[4];
     d.gz = s->gz[0];
     if ((rc = conv_launch<16, 32, EPI_DGRAD>(s, d))) return rc;
+    if ((rc = trace_dh(s, 5, cells))) return rc;
     int cur = 0;
     for (int l = 4; l >= 1; --l) {
         w.in = s->h[l];
@@ -1657,6 +1671,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
         d.zprev = s->z[l - 1];
         d.gz = s->gz[cur ^ 1];
         if ((rc = conv_launch<32, 32, EPI_DGRAD>(s, d))) return rc;
+        if ((rc = trace_dh(s, l, cells))) return rc;
         cur ^= 1;
     }
     // layer 0
@@ -1832,10 +1847,32 @@ int gs_surr_grad(gs_surr* s, int N, int L, const float* u, const float* v, const
     if (!s || !F || !k || !u_tgt || !v_tgt) return fail(GS_EINVAL, "NULL argument");
     int rc = check_fields(N, L, u, v);
     if (rc) return rc;
+    if (s->trace_dh && s->trace_count != (size_t)5 * N * L * L * L * 32)
+        return fail(GS_EINVAL, "gradient trace holds %zu floats, this call needs 5 x N x L^3 x 32", s->trace_count);
     if ((rc = ensure_ws(s, N, L, true))) return rc;
     if ((rc = upload_fk(s, N, F, k))) return rc;
     if ((rc = forward(s, N, L, u, v, s->ou, s->ov, true))) return rc;
     return backward(s, N, L, u_tgt, v_tgt, loss);
+}
+
+int gs_surr_trace_grads(gs_surr* s, float* dh, size_t count)
+{
+    if (!s) return fail(GS_EINVAL, "surrogate is NULL");
+    if (dh && count == 0) return fail(GS_EINVAL, "count must be > 0 with a trace array");
+    s->trace_dh = dh;
+    s->trace_count = dh ? count : 0;
+    return GS_OK;
+}
+
+int gs_surr_get_train_output(gs_surr* s, float* u_out, float* v_out, size_t cells)
+{
+    if (!s || !u_out || !v_out) return fail(GS_EINVAL, "NULL argument");
+    if (!s->train_ws || !s->ou) return fail(GS_ESTATE, "no gradient computation has run yet");
+    const size_t have = (size_t)s->N * s->L * s->L * s->L;
+    if (cells != have) return fail(GS_EINVAL, "cells=%zu, the last gradient computation had %zu", cells, have);
+    GS_CUDA_TRY(cudaMemcpyAsync(u_out, s->ou, cells * 4, cudaMemcpyDeviceToDevice, s->stream));
+    GS_CUDA_TRY(cudaMemcpyAsync(v_out, s->ov, cells * 4, cudaMemcpyDeviceToDevice, s->stream));
+    return gs_surr_sync(s);
 }
 
 int gs_surr_adam(gs_surr* s, double lr, double beta1, double beta2, double eps)

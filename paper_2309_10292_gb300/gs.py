@@ -116,6 +116,8 @@ _SIGS = {
     "gs_surr_set_params": [_vp, _vp, _sz],
     "gs_surr_get_params": [_vp, _vp, _sz],
     "gs_surr_get_grads": [_vp, _vp, _sz],
+    "gs_surr_trace_grads": [_vp, _vp, _sz],
+    "gs_surr_get_train_output": [_vp, _vp, _vp, _sz],
     "gs_surr_forward": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "gs_surr_grad": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)],
     "gs_surr_adam": [_vp, _d, _d, _d, _d],
@@ -612,6 +614,16 @@ def gs_surr_get_grads(s) -> np.ndarray:
     out = np.empty(gs_surr_param_count(), dtype=np.float32)
     _check(lib().gs_surr_get_grads(s, out.ctypes.data, out.size), "gs_surr_get_grads")
     return out
+
+
+def gs_surr_trace_grads(s, dh, count: int = 0):
+    """dh: a float32 CUDA tensor of 5 * N * L^3 * 32 elements, or None (off)."""
+    _check(lib().gs_surr_trace_grads(s, _ptr(dh) if dh is not None else None,
+                                     int(count) if dh is not None else 0), "gs_surr_trace_grads")
+
+
+def gs_surr_get_train_output(s, u_out, v_out, cells: int):
+    _check(lib().gs_surr_get_train_output(s, _ptr(u_out), _ptr(v_out), int(cells)), "gs_surr_get_train_output")
 
 
 def gs_surr_forward(s, N, L, u, v, F, k, u_out, v_out):

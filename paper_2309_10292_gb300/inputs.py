@@ -10,7 +10,10 @@ record gives Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1, noise=0.1):
   * random grids   u, v ~ U[lo, hi) for tiny or odd L in parity tests
   * batch          256 instances, L_i uniform on {32, 48, 64, 96, 128},
                    F_i ~ U[0.01, 0.06], k_i ~ U[0.04, 0.07]
-  * surrogate      He-uniform initial weights for the 6-layer conv network
+  * surrogate      He-uniform initial weights for the 6-layer conv network;
+                   for gradient parity, sparse dyadic weights and fields on a
+                   coarse grid (few significant bits), so that every sum the
+                   network forms is exact in FP32 as in FP64
 """
 from __future__ import annotations
 
@@ -62,3 +65,29 @@ def random_tensor(shape, seed: int, lo: float = -1.0, hi: float = 1.0):
     """Uniform float64 tensor of the given shape (conv parity inputs)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(lo, hi, size=shape)
+
+
+def dyadic_fields(shape, seed: int, step: float = 1.0 / 16, lo: float = 0.0, hi: float = 1.0):
+    """Float64 array of the given shape with values k * step in [lo, hi] (step a power of two)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(round((hi - lo) / step))
+    return lo + step * rng.integers(0, n + 1, size=shape).astype(np.float64)
+
+
+def surrogate_dyadic_params(seed: int = 0, channels=(4, 32, 32, 32, 32, 32, 2),
+                            wstep: float = 0.25, density=(0.3, 0.02, 0.02, 0.02, 0.02, 0.005),
+                            bstep: float = 1.0 / 64, bmax: int = 8):
+    """Sparse weights on a dyadic grid: each entry is 0, or +-wstep, +-2 wstep
+    with probability density[l]; biases are integers in [-bmax, bmax] times
+    bstep.  Values with so few significant bits keep the network's sums
+    exactly representable (in FP32 as in FP64) over several layers."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    params = []
+    for l in range(len(channels) - 1):
+        cin, cout = channels[l], channels[l + 1]
+        on = rng.uniform(size=(27, cin, cout)) < density[l]
+        mag = rng.integers(1, 3, size=(27, cin, cout)) * rng.choice([-1.0, 1.0], size=(27, cin, cout))
+        w = np.where(on, mag * wstep, 0.0)
+        b = bstep * rng.integers(-bmax, bmax + 1, size=cout).astype(np.float64)
+        params.append((w, b))
+    return params

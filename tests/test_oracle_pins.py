@@ -516,6 +516,65 @@ def test_surrogate_gradients_finite_differences(orc):
         assert abs(fd - grads[l][1][j]) <= 1e-6 * max(1e-3, abs(fd))
 
 
+def _rest_of_network(orc, params, h, l, u, v):
+    # the network's layers l .. 5 applied to a given h_l (composed here from the
+    # convolution primitive, independently of surrogate_forward/backward)
+    for j in range(l, 5):
+        h = h + np.maximum(orc.conv3d_fwd(h, params[j][0], params[j][1]), 0.0)
+    return np.stack([u, v], axis=-1) + orc.conv3d_fwd(h, params[5][0], params[5][1])
+
+
+def test_surrogate_activation_gradients_finite_differences(orc):
+    # dL/dh_l returned by surrogate_backward against central differences of
+    # the loss in single entries of h_l
+    L, N = 4, 1
+    params = inputs.surrogate_init_params(seed=6, last_scale=1.0)
+    u, v = inputs.random_fields(L, seed=10, lo=0.0, hi=1.0)
+    u, v = u[None], v[None]
+    F, k = np.array([0.03]), np.array([0.055])
+    tgt = inputs.random_tensor((N, L, L, L, 2), seed=11, lo=0.0, hi=1.0)
+    out, cache = orc.surrogate_forward(params, u, v, F, k)
+    _, dout = orc.mse_loss(out, tgt)
+    _, dhs = orc.surrogate_backward(cache, dout, return_dh=True)
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for l in range(1, 6):
+        for _ in range(3):
+            idx = (0,) + tuple(int(i) for i in rng.integers(0, L, 3)) + (int(rng.integers(0, 32)),)
+            hp = cache["hs"][l].copy()
+            hp[idx] += h
+            lp = orc.mse_loss(_rest_of_network(orc, params, hp, l, u, v), tgt)[0]
+            hp[idx] -= 2 * h
+            lm = orc.mse_loss(_rest_of_network(orc, params, hp, l, u, v), tgt)[0]
+            fd = (lp - lm) / (2 * h)
+            an = dhs[l - 1][idx]
+            assert abs(fd - an) <= 1e-6 * max(1e-3, abs(an)), (l, idx, fd, an)
+
+
+def test_surrogate_backward_bf16_emulation(orc):
+    # rounding dL/dout and every dz_l to bfloat16 keeps the gradients within a
+    # few bfloat16 rounding errors of the exact ones, and the last layer's
+    # bias gradient is then exactly the sum of the rounded dL/dout
+    L, N = 4, 2
+    params = inputs.surrogate_init_params(seed=4, last_scale=1.0)
+    u, v = inputs.random_fields(L, seed=12, lo=0.0, hi=1.0)
+    u = np.stack([u, 1 - u]); v = np.stack([v, 0.5 * v])
+    F, k = np.array([0.02, 0.05]), np.array([0.048, 0.06])
+    tgt = inputs.random_tensor((N, L, L, L, 2), seed=13, lo=0.0, hi=1.0)
+    out, cache = orc.surrogate_forward(params, u, v, F, k)
+    _, dout = orc.mse_loss(out, tgt)
+    g0, d0 = orc.surrogate_backward(cache, dout, return_dh=True)
+    g1, d1 = orc.surrogate_backward(cache, dout, emulate_bf16=True, return_dh=True)
+    for l in range(6):
+        for j in range(2):
+            rel = np.linalg.norm(g1[l][j] - g0[l][j]) / np.linalg.norm(g0[l][j])
+            assert 0 < rel < 2 ** -6, (l, j, rel)
+    for a, b in zip(d0, d1):
+        assert 0 < np.linalg.norm(a - b) / np.linalg.norm(a) < 2 ** -6
+    np.testing.assert_allclose(g1[5][1], orc.bf16_round(dout).sum(axis=(0, 1, 2, 3)), rtol=1e-13, atol=0)
+    assert np.abs(g1[5][1] - dout.sum(axis=(0, 1, 2, 3))).max() > 0
+
+
 def test_surrogate_zero_last_layer_is_identity(orc):
     L = 4
     params = inputs.surrogate_init_params(seed=1)
