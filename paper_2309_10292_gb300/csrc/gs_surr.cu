@@ -568,7 +568,7 @@ namespace gs {
 // x-tap first layer, whose few MMAs per plane leave the epilogue as the
 // longer role: it runs on E = 8 warps, two per SM sub-partition, each taking
 // 2 of the 4 rows (measured slower for the MMA-bound hidden layers).
-GS_HD constexpr int tc_epi_warps(int epi, bool xt) { return (void)epi, xt ? 8 : 4; }
+GS_HD constexpr int tc_epi_warps(int epi, bool xt) { return (xt || epi == EPI_DGRAD) ? 8 : 4; }
 GS_HD constexpr int tc_threads(int epi, bool xt) { return 32 * (tc_epi_warps(epi, xt) + 2); }
 constexpr int kTcRows = 4;
 constexpr int kTcCells = 128;
@@ -596,6 +596,15 @@ struct ConvTcArgs {
     const float* sv;
     float* ou;
     float* ov;
+    // EPI_DGRAD (data gradient: the convolution of gz_l with the tap-flipped,
+    // transposed weights of layer l): gh = acc (+ gh when gh_acc), fp32
+    // [..][32]; gz = bf16(gh * (zprev > 0)) for the layer below, [..][32];
+    // db[c] += sum over cells of gz[c] (that layer's bias gradient)
+    float* gh;
+    int gh_acc;
+    const bf16* zprev;
+    bf16* gz;
+    float* db;
     int* err;
     uint64_t timeout_ns;
 };
@@ -828,7 +837,7 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
         abort_s = 0;
         gs_fence_mbar_init();
     }
-    if (tid < NT) bias_s[tid] = (EPI == EPI_LAST && tid >= 2) ? 0.f : a.bias[tid];  // the last layer has 2
+    if (tid < NT) bias_s[tid] = (EPI == EPI_DGRAD || (EPI == EPI_LAST && tid >= 2)) ? 0.f : a.bias[tid];
     for (uint32_t i = tid; i < WBYTES / 16; i += NTHR) cp16(wbase + i * 16, a.w + (size_t)i * 8);
     cp_wait_all();
     gs_fence_proxy_async();  // cp.async (generic) writes -> visible to the tensor core
@@ -1115,6 +1124,17 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
         constexpr int NRES = EPI == EPI_HIDDEN ? NT / 8 : 1;
         uint4 rv[EROWS][NRES];
         float sres[EROWS][2];
+        // EPI_DGRAD: the layer below's pre-activation (bf16, 4 x 16 bytes a
+        // cell) one item ahead; the incoming residual-path gradient (fp32)
+        // is loaded in the epilogue itself (registers)
+        constexpr bool DG = EPI == EPI_DGRAD;
+        static_assert(!DG || NT == 32, "the data gradient has 32 output channels");
+        uint4 pz[DG ? EROWS : 1][DG ? 4 : 1];
+        float dbacc[DG ? NT : 1];
+        if constexpr (DG) {
+#pragma unroll
+            for (int j = 0; j < NT; ++j) dbacc[j] = 0.f;
+        }
         auto cell_of = [&](const Unit& u, int q, int r) -> size_t {
             return (size_t)u.n * L3 + ((size_t)(u.z0 + q) * L + (u.y0 + r)) * L + (u.x0 + x_in_seg);
         };
@@ -1129,6 +1149,9 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                 } else if constexpr (EPI == EPI_LAST) {
                     sres[rr][0] = a.su[cell];
                     sres[rr][1] = a.sv[cell];
+                } else if constexpr (DG) {
+#pragma unroll
+                    for (int j = 0; j < 4; j += 2) gs_ld_v8(a.zprev + cell * 32 + j * 8, pz[rr][j], pz[rr][j + 1]);
                 }
             }
         };
@@ -1137,9 +1160,45 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
             for (int rr = 0; rr < EROWS; ++rr) {
                 const int r = r0 + rr;
                 const size_t cell = cell_of(u, q, r);
+                uint4 gin[DG ? 8 : 1];
+                if constexpr (DG) {
+                    if (a.gh_acc) {  // issued before the TMEM load, which overlaps its latency
+#pragma unroll
+                        for (int j = 0; j < 8; j += 2) gs_ld_v8(a.gh + cell * 32 + j * 4, gin[j], gin[j + 1]);
+                    }
+                }
                 float acc[NT];
                 tc_ld<NT>(lane_base + (uint32_t)(set * ACC_COLS + r * NT), acc);
-                if constexpr (EPI != EPI_LAST) {  // (the last layer drains in its own loop below)
+                if constexpr (DG) {
+                    if (a.gh_acc) {
+                        const float* go = reinterpret_cast<const float*>(&gin[0]);
+#pragma unroll
+                        for (int j = 0; j < NT; ++j) acc[j] += go[j];
+                    }
+                    uint4 gout[8];
+                    float* gf = reinterpret_cast<float*>(&gout[0]);
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) gf[j] = acc[j];
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2) gs_st_v8(a.gh + cell * 32 + j * 4, gout[j], gout[j + 1]);
+                    uint4 zo[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const __nv_bfloat162* zb = reinterpret_cast<const __nv_bfloat162*>(&pz[rr][j]);
+                        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&zo[j]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int c = j * 8 + 2 * e;
+                            const float m0 = __bfloat162float(zb[e].x) > 0.f ? acc[c] : 0.f;
+                            const float m1 = __bfloat162float(zb[e].y) > 0.f ? acc[c + 1] : 0.f;
+                            ob[e] = __floats2bfloat162_rn(m0, m1);
+                            dbacc[c] += __bfloat162float(ob[e].x);
+                            dbacc[c + 1] += __bfloat162float(ob[e].y);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; j += 2) gs_st_v8(a.gz + cell * 32 + j * 8, zo[j], zo[j + 1]);
+                } else if constexpr (EPI != EPI_LAST) {  // (the last layer drains in its own loop below)
                     static_assert(NT % 16 == 0, "the epilogue stores 16 channels (32 bytes) at a time");
                     uint4 ho[NT / 8], zo[NT / 8];
 #pragma unroll
@@ -1246,6 +1305,20 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                     else if (unit + gridDim.x < units) prefetch(decode(unit + gridDim.x), 0);
                 }
             }
+            if constexpr (DG) {
+                // this warp's bias-gradient partial sums: reduce over the lanes, one atomic per channel
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    float t = dbacc[j];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                    dbacc[j] = t;
+                }
+                if (lane == 0 && a.db) {
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) atomicAdd(a.db + j, dbacc[j]);
+                }
+            }
         }
     }
     // nothing of this CTA may be in flight when its TMEM and shared memory go
@@ -1276,6 +1349,30 @@ __global__ void gs_wprep_tc_kernel(const float* __restrict__ w, int cin, int cou
         const int tap = dzi * 9 + dyi * 3 + dxi;
         const int ci = j * 8 + e;
         const float val = (ci < cin && co < cout) ? w[((size_t)tap * cin + ci) * cout + co] : 0.f;
+        wt[i] = __float2bfloat16_rn(val);
+    }
+}
+
+// the data gradient's weights in the same B layout: the convolution of gz
+// (K = the forward layer's output channels, padded to kp) with tap-flipped,
+// transposed weights, W'[tap][k][n] = W[26 - tap][n][k] (n = the forward
+// layer's input channels, padded to nt)
+__global__ void gs_wprep_tc_dgrad_kernel(const float* __restrict__ w, int cin, int cout, int kp, int nt,
+                                         bf16* __restrict__ wt)
+{
+    const int nn = 3 * nt;
+    const int total = 9 * kp * nn;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i % 8;
+        const int n = (i / 8) % nn;
+        const int j = (i / (8 * nn)) % (kp / 8);
+        const int dxi = (i / (8 * nn * (kp / 8))) % 3;
+        const int dzi = i / (8 * nn * (kp / 8) * 3);
+        const int dyi = 2 - n / nt;
+        const int ci = n % nt;     // forward input channel (this convolution's output)
+        const int co = j * 8 + e;  // forward output channel (this convolution's input)
+        const int tap = dzi * 9 + dyi * 3 + dxi;
+        const float val = (ci < cin && co < cout) ? w[((size_t)(26 - tap) * cin + ci) * cout + co] : 0.f;
         wt[i] = __float2bfloat16_rn(val);
     }
 }
@@ -1343,6 +1440,7 @@ struct gs_surr {
     bf16* wd[kSurrLayers] = {};  // data-gradient layout (layers 1..5)
     bf16* wt[kSurrLayers] = {};  // tcgen05 B layout [3 dz][3 dx][CINP/8][3 NT][8]
     bf16* wt0x = nullptr;        // the first layer's for x-tap packed input [3 dz][2][3 NT][8]
+    bf16* wdt[kSurrLayers] = {}; // tcgen05 B layout of the data gradient (layers 1..5)
     bool wdirty = true;
     int backend = 0;             // 0 auto (tcgen05 when L % 128 == 0), 1 mma.sync, 2 tcgen05
     int* d_err = nullptr;
@@ -1504,6 +1602,12 @@ int prep_weights(gs_surr* s)
             gs_wprep_tc_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, kCinP[l], 32, s->wt[l]);
         GS_CUDA_TRY(cudaGetLastError());
         s->launches += 2;
+        if (l >= 1) {
+            gs_wprep_tc_dgrad_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, l == 5 ? 16 : 32, 32,
+                                                               s->wdt[l]);
+            GS_CUDA_TRY(cudaGetLastError());
+            s->launches += 1;
+        }
     }
     gs_wprep_tc_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[0], kChan[0], kChan[1], 32, s->wt0x);
     GS_CUDA_TRY(cudaGetLastError());
@@ -1619,6 +1723,9 @@ int trace_dh(gs_surr* s, int l, long long cells)
 int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double* loss)
 {
     const long long cells = (long long)N * L * L * L;
+    // the tensor-core path (as in forward()) also takes the data gradients,
+    // whose epilogue adds up the bias gradient of the layer below
+    const bool tc = s->backend != 1 && L % kTcCells == 0;
     GS_CUDA_TRY(cudaMemsetAsync(s->grads, 0, s->np * sizeof(float), s->stream));
     GS_CUDA_TRY(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
     gs_mse_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(s->ou, s->ov, tu, tv, cells, 1.0 / (2.0 * cells), s->gd,
@@ -1632,6 +1739,35 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
         s->launches += 1;
         return GS_OK;
     };
+    // data gradient of layer l (input g, 16 or 32 channels): gh (+)= conv^T, gz
+    // for the layer below; on the tensor-core path also db of the layer below
+    auto dgrad = [&](int l, const bf16* g, int gh_acc, bf16* gz) -> int {
+        if (tc) {
+            ConvTcArgs t{};
+            t.N = N;
+            t.L = L;
+            t.in = g;
+            t.w = s->wdt[l];
+            t.gh = s->gh;
+            t.gh_acc = gh_acc;
+            t.zprev = s->z[l - 1];
+            t.gz = gz;
+            t.db = s->grads + s->boff[l - 1];
+            return l == 5 ? tc_launch<16, 32, EPI_DGRAD>(s, t) : tc_launch<32, 32, EPI_DGRAD>(s, t);
+        }
+        ConvArgs d{};
+        d.N = N;
+        d.L = L;
+        d.in = g;
+        d.w = s->wd[l];
+        d.gh = s->gh;
+        d.gh_acc = gh_acc;
+        d.zprev = s->z[l - 1];
+        d.gz = gz;
+        int r = l == 5 ? conv_launch<16, 32, EPI_DGRAD>(s, d) : conv_launch<32, 32, EPI_DGRAD>(s, d);
+        if (r) return r;
+        return bias_grad(gz, 32, 32, s->grads + s->boff[l - 1]);
+    };
     // layer 5
     WgArgs w{};
     w.N = N;
@@ -1644,16 +1780,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     w.dw = s->grads + s->woff[5];
     if ((rc = wgrad_launch<32, 8>(s, w))) return rc;
     if ((rc = bias_grad(s->gd, 16, 2, s->grads + s->boff[5]))) return rc;
-    ConvArgs d{};
-    d.N = N;
-    d.L = L;
-    d.in = s->gd;
-    d.w = s->wd[5];
-    d.gh = s->gh;
-    d.gh_acc = 0;
-    d.zprev = s->z[4];
-    d.gz = s->gz[0];
-    if ((rc = conv_launch<16, 32, EPI_DGRAD>(s, d))) return rc;
+    if ((rc = dgrad(5, s->gd, 0, s->gz[0]))) return rc;
     if ((rc = trace_dh(s, 5, cells))) return rc;
     int cur = 0;
     for (int l = 4; l >= 1; --l) {
@@ -1664,13 +1791,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
         w.cout = 32;
         w.dw = s->grads + s->woff[l];
         if ((rc = wgrad_launch<32, 32>(s, w))) return rc;
-        if ((rc = bias_grad(s->gz[cur], 32, 32, s->grads + s->boff[l]))) return rc;
-        d.in = s->gz[cur];
-        d.w = s->wd[l];
-        d.gh_acc = 1;
-        d.zprev = s->z[l - 1];
-        d.gz = s->gz[cur ^ 1];
-        if ((rc = conv_launch<32, 32, EPI_DGRAD>(s, d))) return rc;
+        if ((rc = dgrad(l, s->gz[cur], 1, s->gz[cur ^ 1]))) return rc;
         if ((rc = trace_dh(s, l, cells))) return rc;
         cur ^= 1;
     }
@@ -1682,7 +1803,6 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     w.cout = 32;
     w.dw = s->grads + s->woff[0];
     if ((rc = wgrad_launch<16, 32>(s, w))) return rc;
-    if ((rc = bias_grad(s->gz[cur], 32, 32, s->grads + s->boff[0]))) return rc;
     if (loss) GS_CUDA_TRY(cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     return gs_surr_sync(s);
 }
@@ -1740,6 +1860,7 @@ int gs_surr_destroy(gs_surr* s)
         cudaFree(s->wf[l]);
         cudaFree(s->wd[l]);
         cudaFree(s->wt[l]);
+        cudaFree(s->wdt[l]);
     }
     cudaFree(s->wt0x);
     cudaFree(s->d_err);
@@ -1780,6 +1901,7 @@ int gs_surr_create(gs_surr** out)
         if (e == cudaSuccess)
             e = cudaMalloc(&s->wt[l], (l == 5 ? (size_t)6 * 3 * 2 * 2 * 48 * 8 : (size_t)27 * kCinP[l] * 32) * sizeof(bf16));
         if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wd[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
+        if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wdt[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->wt0x, (size_t)9 * kCinP[0] * 32 * sizeof(bf16));
     if (e != cudaSuccess || (e = cudaMemset(s->params, 0, off * 4)) != cudaSuccess ||
