@@ -446,31 +446,58 @@ __global__ void gs_wprep_kernel(const float* __restrict__ w, int cin, int cout, 
     }
 }
 
-// loss = sum (out - tgt)^2 / count;  gd[cell][0..1] = 2 (out - tgt) / count, rest 0
+// loss = sum (out - tgt)^2 / count;  gd[cell][0..1] = 2 (out - tgt) / count, rest 0;
+// db[0..1] += sum over cells of the stored (bf16) gd[cell][0..1] (the last
+// layer's bias gradient; db may be null)
 __global__ void gs_mse_kernel(const float* __restrict__ ou, const float* __restrict__ ov, const float* __restrict__ tu,
                               const float* __restrict__ tv, long long total, double inv_count, bf16* __restrict__ gd,
-                              double* __restrict__ loss)
+                              double* __restrict__ loss, float* __restrict__ db)
 {
-    double local = 0.0;
+    // FP32 arithmetic per cell (GB300's FP64 pipe is narrow); 2 / count is a
+    // power of two whenever the cell count is, and the per-thread partial
+    // losses are added in FP64
+    float lf = 0.f, su = 0.f, sv = 0.f;
+    const float scale = (float)(2.0 * inv_count);
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const float du = ou[i] - tu[i], dv = ov[i] - tv[i];
-        local += (double)du * du + (double)dv * dv;
-        __align__(16) bf16 c[16];
-        c[0] = __float2bfloat16_rn((float)(2.0 * du * inv_count));
-        c[1] = __float2bfloat16_rn((float)(2.0 * dv * inv_count));
-        for (int j = 2; j < 16; ++j) c[j] = __float2bfloat16_rn(0.f);
-        uint4* dst = reinterpret_cast<uint4*>(gd + i * 16);
-        dst[0] = reinterpret_cast<const uint4*>(c)[0];
-        dst[1] = reinterpret_cast<const uint4*>(c)[1];
+        lf = fmaf(du, du, fmaf(dv, dv, lf));
+        __nv_bfloat162 c01;
+        c01.x = __float2bfloat16_rn(du * scale);
+        c01.y = __float2bfloat16_rn(dv * scale);
+        su += __bfloat162float(c01.x);
+        sv += __bfloat162float(c01.y);
+        uint4 first = zero;
+        first.x = *reinterpret_cast<const uint32_t*>(&c01);
+        gs_st_v8(gd + i * 16, first, zero);  // 32 bytes: the whole cell
     }
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    double local = lf;
+    for (int o = 16; o > 0; o >>= 1) {
+        local += __shfl_xor_sync(0xffffffffu, local, o);
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
     __shared__ double red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __shared__ float reds[32][2];
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = local;
+        reds[threadIdx.x >> 5][0] = su;
+        reds[threadIdx.x >> 5][1] = sv;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        atomicAdd(loss, s * inv_count);
+        double t = 0.0;
+        float a0 = 0.f, a1 = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += red[w];
+            a0 += reds[w][0];
+            a1 += reds[w][1];
+        }
+        atomicAdd(loss, t * inv_count);
+        if (db) {
+            atomicAdd(db, a0);
+            atomicAdd(db + 1, a1);
+        }
     }
 }
 
@@ -598,13 +625,11 @@ struct ConvTcArgs {
     float* ov;
     // EPI_DGRAD (data gradient: the convolution of gz_l with the tap-flipped,
     // transposed weights of layer l): gh = acc (+ gh when gh_acc), fp32
-    // [..][32]; gz = bf16(gh * (zprev > 0)) for the layer below, [..][32];
-    // db[c] += sum over cells of gz[c] (that layer's bias gradient)
+    // [..][32]; gz = bf16(gh * (zprev > 0)) for the layer below, [..][32]
     float* gh;
     int gh_acc;
     const bf16* zprev;
     bf16* gz;
-    float* db;
     int* err;
     uint64_t timeout_ns;
 };
@@ -1130,11 +1155,6 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
         constexpr bool DG = EPI == EPI_DGRAD;
         static_assert(!DG || NT == 32, "the data gradient has 32 output channels");
         uint4 pz[DG ? EROWS : 1][DG ? 4 : 1];
-        float dbacc[DG ? NT : 1];
-        if constexpr (DG) {
-#pragma unroll
-            for (int j = 0; j < NT; ++j) dbacc[j] = 0.f;
-        }
         auto cell_of = [&](const Unit& u, int q, int r) -> size_t {
             return (size_t)u.n * L3 + ((size_t)(u.z0 + q) * L + (u.y0 + r)) * L + (u.x0 + x_in_seg);
         };
@@ -1156,22 +1176,28 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
             }
         };
         auto epilogue = [&](int set, const Unit& u, int q) {
+            // EPI_DGRAD: the incoming gh of all this warp's rows, issued before the
+            // first TMEM load so their latencies overlap
+            uint4 gin[DG ? EROWS : 1][DG ? 8 : 1];
+            if constexpr (DG) {
+                if (a.gh_acc) {
+#pragma unroll
+                    for (int rr = 0; rr < EROWS; ++rr) {
+                        const size_t cell = cell_of(u, q, r0 + rr);
+#pragma unroll
+                        for (int j = 0; j < 8; j += 2) gs_ld_v8(a.gh + cell * 32 + j * 4, gin[rr][j], gin[rr][j + 1]);
+                    }
+                }
+            }
 #pragma unroll
             for (int rr = 0; rr < EROWS; ++rr) {
                 const int r = r0 + rr;
                 const size_t cell = cell_of(u, q, r);
-                uint4 gin[DG ? 8 : 1];
-                if constexpr (DG) {
-                    if (a.gh_acc) {  // issued before the TMEM load, which overlaps its latency
-#pragma unroll
-                        for (int j = 0; j < 8; j += 2) gs_ld_v8(a.gh + cell * 32 + j * 4, gin[j], gin[j + 1]);
-                    }
-                }
                 float acc[NT];
                 tc_ld<NT>(lane_base + (uint32_t)(set * ACC_COLS + r * NT), acc);
                 if constexpr (DG) {
                     if (a.gh_acc) {
-                        const float* go = reinterpret_cast<const float*>(&gin[0]);
+                        const float* go = reinterpret_cast<const float*>(&gin[rr][0]);
 #pragma unroll
                         for (int j = 0; j < NT; ++j) acc[j] += go[j];
                     }
@@ -1192,8 +1218,6 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                             const float m0 = __bfloat162float(zb[e].x) > 0.f ? acc[c] : 0.f;
                             const float m1 = __bfloat162float(zb[e].y) > 0.f ? acc[c + 1] : 0.f;
                             ob[e] = __floats2bfloat162_rn(m0, m1);
-                            dbacc[c] += __bfloat162float(ob[e].x);
-                            dbacc[c + 1] += __bfloat162float(ob[e].y);
                         }
                     }
 #pragma unroll
@@ -1305,20 +1329,6 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                     else if (unit + gridDim.x < units) prefetch(decode(unit + gridDim.x), 0);
                 }
             }
-            if constexpr (DG) {
-                // this warp's bias-gradient partial sums: reduce over the lanes, one atomic per channel
-#pragma unroll
-                for (int j = 0; j < NT; ++j) {
-                    float t = dbacc[j];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                    dbacc[j] = t;
-                }
-                if (lane == 0 && a.db) {
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) atomicAdd(a.db + j, dbacc[j]);
-                }
-            }
         }
     }
     // nothing of this CTA may be in flight when its TMEM and shared memory go
@@ -1328,6 +1338,419 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ===========================================================================
+// 5th-generation tensor-core weight gradient (tcgen05, TMEM accumulators)
+// ===========================================================================
+//
+//   dW[tap][ci][co] = sum over cells c of h[c + d(tap)][ci] * g[c][co]
+//
+// is a contraction over cells (K), so both operands are read MN-major from
+// channels-last slabs: a row of 128 cells of HC (or GC) channels staged with
+// the 64-byte (32 channels) or 32-byte (16 channels) swizzle is, read with
+// K = cells, one swizzle atom column of an MN-major operand.  A work unit is
+// 2 output rows (y0, y0+1) x 128 cells x a z-chunk of 8 planes.
+//   A (M = 128): MB = 128 / HC consecutive rows of an input slab (rows y0-1
+//     .. y0+2 of input plane p, with an x halo), starting at row i for output
+//     row i, so M block j holds dy = j - 1 (blocks j >= 3 are never used:
+//     their products land in TMEM lanes that are not read); the dx tap is a
+//     start offset of dx cells.
+//   B (N = 3 GC at most): the gradient planes p-1, p, p+1 of the unit (dz =
+//     +1, 0, -1), row i, clipped to the unit's planes.  They sit in a ring of
+//     4 slots whose first two are mirrored after the fourth, so any three
+//     consecutive planes are at a uniform stride.
+// Every MMA accumulates into one of 3 (dx) x 3 (dz) column blocks of GC
+// columns; the CTA keeps all 27 taps in TMEM for its whole life (zeroed
+// first), and its epilogue warps drain them once into per-CTA partial sums
+// that gs_wgrad_reduce_kernel adds up in a fixed order.  While the MMAs run,
+// the epilogue warps add up every gradient plane the ring receives (once per
+// unit, so once per cell) per channel: the layer's bias gradient, reduced
+// the same way.  Three warp roles as in gs_conv_tc_kernel (TMA producer, MMA
+// issuer, 4 epilogue warps); every wait is bounded.
+constexpr int kWgRows = 2;     // output rows per unit
+constexpr int kWgZChunk = 8;   // planes per unit
+constexpr int kWgHSlabs = 3;   // input-slab ring depth
+constexpr int kWgGSlots = 4;   // gradient-plane ring depth (+ 2 mirrored slots)
+constexpr int kWgTcThreads = 192;
+
+struct WgTcArgs {
+    CUtensorMap map_hmain;  // h: HC channels x 128 cells
+    CUtensorMap map_hhalo;  // h: HC channels x 8 cells
+    CUtensorMap map_g;      // g: GC channels x 128 cells
+    float* part;            // [gridDim.x][27 HC GC + GC] partial sums (weights, then biases)
+    int N, L;
+    int* err;
+    uint64_t timeout_ns;
+};
+
+GS_D uint64_t tc_desc_lay(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout)
+{
+    // shared-memory matrix descriptor with an explicit LBO and layout type
+    // (4: 64-byte swizzle, 6: 32-byte swizzle)
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
+}
+
+GS_HD uint32_t tc_idesc_mn(int n)
+{
+    // kind::f16, D fp32, A and B bf16, both MN-major (bits 15, 16), M = 128
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int HC, int GC>
+__global__ void __launch_bounds__(kWgTcThreads, 1) gs_wgrad_tc_kernel(const __grid_constant__ WgTcArgs a)
+{
+    static_assert((HC == 32 || HC == 16) && (GC == 32 || GC == 16), "16 or 32 channels");
+    constexpr int MB = 128 / HC;                          // M blocks (slab rows) per MMA
+    constexpr uint32_t HROWB = kTcRowCells * HC * 2;     // bytes of one input-slab row
+    constexpr uint32_t HSLAB = (kWgRows + 2) * HROWB;
+    constexpr uint32_t GROWB = kTcCells * GC * 2;         // bytes of one gradient row
+    constexpr uint32_t GSLOT = kWgRows * GROWB;
+    constexpr uint32_t HLAY = HC == 32 ? 4u : 6u, GLAY = GC == 32 ? 4u : 6u;
+    constexpr uint32_t HATOM = HC == 32 ? 512u : 256u, GATOM = GC == 32 ? 512u : 256u;
+    constexpr uint32_t ACOLS = 9 * GC;                    // accumulator columns (3 dx x 3 dz x GC)
+    constexpr uint32_t TMEM_COLS = ACOLS <= 256 ? 256 : 512;
+    constexpr int MMAW = 4, PRODW = 5;
+    // blocks j >= 3 of the last slab read up to MB - 3 rows past it: the
+    // gradient ring that follows is larger
+    static_assert((MB - 3) * HROWB <= (kWgGSlots + 2) * GSLOT, "A reads stay in shared memory");
+    static_assert(HSLAB % 1024 == 0 && GSLOT % 1024 == 0, "slabs keep the swizzle atoms aligned");
+    extern __shared__ __align__(1024) unsigned char smem_wg[];
+    __shared__ __align__(8) uint64_t h_full[kWgHSlabs], h_empty[kWgHSlabs], g_full[kWgGSlots], g_empty[kWgGSlots];
+    __shared__ __align__(8) uint64_t zero_bar, done_bar, fin_bar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = a.L;
+    const uint32_t hbase = gs_smem_addr(smem_wg);
+    const uint32_t gbase = hbase + kWgHSlabs * HSLAB;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gs_smem_addr(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kWgHSlabs; ++i) {
+            gs_mbar_init(&h_full[i], 1);
+            gs_mbar_init(&h_empty[i], 1);
+        }
+        for (int i = 0; i < kWgGSlots; ++i) {
+            gs_mbar_init(&g_full[i], 1);
+            gs_mbar_init(&g_empty[i], 1 + 4);  // the MMA commit and the 4 epilogue warps
+        }
+        gs_mbar_init(&zero_bar, 4);
+        gs_mbar_init(&done_bar, 1);
+        gs_mbar_init(&fin_bar, 1);
+        abort_s = 0;
+        gs_fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    const int nseg = L / kTcCells, nyg = L / kWgRows, nzc = (L + kWgZChunk - 1) / kWgZChunk;
+    const long long units = (long long)a.N * nyg * nseg * nzc;
+    struct Unit {
+        int n, x0, y0, z0, nz;
+    };
+    auto decode = [&](long long unit) {
+        Unit u;
+        const int zc = (int)(unit % nzc);
+        long long r0 = unit / nzc;
+        const int seg = (int)(r0 % nseg);
+        r0 /= nseg;
+        u.y0 = (int)(r0 % nyg) * kWgRows;
+        u.n = (int)(r0 / nyg);
+        u.x0 = seg * kTcCells;
+        u.z0 = zc * kWgZChunk;
+        u.nz = min(kWgZChunk, L - u.z0);
+        return u;
+    };
+    auto bwait = [&](uint64_t* bar, uint32_t parity) -> bool {
+        if (gs_mbar_try_wait(bar, parity)) return true;
+        const uint64_t t0 = gs_globaltimer();
+        for (;;) {
+#pragma unroll 1
+            for (int i = 0; i < 32; ++i)
+                if (gs_mbar_try_wait(bar, parity)) return true;
+            if (abort_s) return false;
+            if (gs_globaltimer() - t0 > a.timeout_ns) {
+                abort_s = 1;
+                gs_report(a.err, GS_DERR_TIMEOUT);
+                return false;
+            }
+        }
+    };
+    auto wwait = [&](uint64_t* bar, uint32_t parity) -> bool {
+        int r = 0;
+        if (lane == 0) r = bwait(bar, parity) ? 1 : 0;
+        r = __shfl_sync(0xffffffffu, r, 0);
+        return r != 0;
+    };
+
+    if (warp == PRODW) {
+        // ------------------------ producer (TMA, one elected lane) ------------------------
+        // per unit, for pi = 0 .. nz+1: gradient plane z0 + pi (if pi < nz; into
+        // slot G % 4, and also slot G % 4 + 4 when G % 4 < 2), then input plane
+        // z0 - 1 + pi (rows y0-1 .. y0+2, each as halo / 128-cell / halo boxes)
+        const uint32_t leader = tc_elect_one();
+        if ((hbase & 1023u) == 0) {
+            if (leader) {
+                gs_prefetch_tmap(&a.map_hmain);
+                gs_prefetch_tmap(&a.map_hhalo);
+                gs_prefetch_tmap(&a.map_g);
+            }
+            __syncwarp();
+            uint32_t H = 0, G = 0;
+            bool ok = true;
+            for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+                const Unit u = decode(unit);
+                const int xl = (u.x0 - kTcRowX0 + L) % L, xr = (u.x0 + kTcCells) % L;
+                for (int pi = 0; pi < u.nz + 2 && ok; ++pi) {
+                    if (pi < u.nz) {
+                        const uint32_t gs = G % kWgGSlots;
+                        if (G >= (uint32_t)kWgGSlots && !wwait(&g_empty[gs], ((G / kWgGSlots) - 1u) & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        const bool mirror = gs < 2;
+                        tc_arrive_expect_tx_if(leader, &g_full[gs], GSLOT * (mirror ? 2u : 1u));
+                        const int zq = u.n * L + u.z0 + pi;
+#pragma unroll
+                        for (int r = 0; r < kWgRows; ++r) {
+                            const uint32_t dst = gbase + gs * GSLOT + r * GROWB;
+                            tc_tma_load_4d_if(leader, dst, &a.map_g, &g_full[gs], 0, u.x0, u.y0 + r, zq);
+                            if (mirror)
+                                tc_tma_load_4d_if(leader, dst + kWgGSlots * GSLOT, &a.map_g, &g_full[gs], 0, u.x0,
+                                                  u.y0 + r, zq);
+                        }
+                        ++G;
+                    }
+                    const uint32_t hs = H % kWgHSlabs;
+                    if (H >= (uint32_t)kWgHSlabs && !wwait(&h_empty[hs], ((H / kWgHSlabs) - 1u) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_arrive_expect_tx_if(leader, &h_full[hs], HSLAB);
+                    const int zp = u.n * L + (u.z0 - 1 + pi + L) % L;
+#pragma unroll
+                    for (int r = 0; r < kWgRows + 2; ++r) {
+                        const int yy = (u.y0 - 1 + r + L) % L;
+                        const uint32_t row = hbase + hs * HSLAB + r * HROWB;
+                        tc_tma_load_4d_if(leader, row, &a.map_hhalo, &h_full[hs], 0, xl, yy, zp);
+                        tc_tma_load_4d_if(leader, row + kTcRowX0 * HC * 2, &a.map_hmain, &h_full[hs], 0, u.x0, yy, zp);
+                        tc_tma_load_4d_if(leader, row + (kTcRowX0 + kTcCells) * HC * 2, &a.map_hhalo, &h_full[hs], 0,
+                                          xr, yy, zp);
+                    }
+                    ++H;
+                }
+            }
+            if (!ok && lane == 0) {
+                // let the copies in flight land (fixed budget)
+                for (uint32_t q = H > (uint32_t)kWgHSlabs ? H - kWgHSlabs : 0u; q < H; ++q)
+                    gs_mbar_wait(&h_full[q % kWgHSlabs], (q / kWgHSlabs) & 1u, 2000000000ull);
+                for (uint32_t q = G > (uint32_t)kWgGSlots ? G - kWgGSlots : 0u; q < G; ++q)
+                    gs_mbar_wait(&g_full[q % kWgGSlots], (q / kWgGSlots) & 1u, 2000000000ull);
+            }
+        } else if (lane == 0) {
+            abort_s = 1;  // unaligned shared memory: refuse to issue TMA
+            gs_report(a.err, GS_DERR_BADARG);
+        }
+    } else if (warp == MMAW) {
+        // ------------------------ MMA issuer (one elected lane) ------------------------
+        const uint32_t leader = tc_elect_one();
+        bool ok = wwait(&zero_bar, 0);
+        tc_fence_after();
+        uint32_t H = 0, G = 0;
+        for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+            const Unit u = decode(unit);
+            const uint32_t Gb = G;
+            for (int pi = 0; pi < u.nz + 2; ++pi) {
+                // gradient plane z0 + pi is first needed now
+                if (pi < u.nz && !wwait(&g_full[(Gb + pi) % kWgGSlots], ((Gb + pi) / kWgGSlots) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t hs = H % kWgHSlabs;
+                if (!wwait(&h_full[hs], (H / kWgHSlabs) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                // gradient planes q = p - 1 + b (b = 0, 1, 2 <-> dz = +1, 0, -1) inside the unit
+                const int b_lo = max(0, 2 - pi), b_hi = min(2, u.nz + 1 - pi);
+                const uint32_t gslot = (Gb + (uint32_t)(pi - 2 + b_lo)) % kWgGSlots;
+                const uint32_t idesc = tc_idesc_mn((b_hi - b_lo + 1) * GC);
+#pragma unroll 1
+                for (int i = 0; i < kWgRows; ++i) {
+                    const uint32_t arow = hbase + hs * HSLAB + i * HROWB;
+                    const uint32_t brow = gbase + gslot * GSLOT + i * GROWB;
+#pragma unroll
+                    for (int dxi = 0; dxi < 3; ++dxi) {
+                        const uint32_t dcol = tmem + (uint32_t)(dxi * 3 * GC + b_lo * GC);
+#pragma unroll
+                        for (int ks = 0; ks < kTcCells / 16; ++ks) {
+                            // output cell x0 + 16 ks + k reads input cell x0 + 16 ks + k + dx
+                            const uint64_t ad = tc_desc_lay(arow + (uint32_t)(kTcRowX0 + 16 * ks + dxi - 1) * HC * 2,
+                                                            HROWB, 8 * HC * 2, HLAY);
+                            const uint64_t bd = tc_desc_lay(brow + (uint32_t)(16 * ks) * GC * 2, GSLOT, 8 * GC * 2, GLAY);
+                            tc_mma_if(leader, dcol, ad, bd, idesc, 1u);
+                        }
+                    }
+                }
+                tc_commit_if(leader, &h_empty[hs]);
+                // gradient plane z0 + pi - 2 (= p - 1) had its last use
+                if (pi >= 2) tc_commit_if(leader, &g_empty[(Gb + pi - 2) % kWgGSlots]);
+                ++H;
+            }
+            G = Gb + (uint32_t)u.nz;
+        }
+        if (ok) {
+            tc_commit_if(leader, &done_bar);
+        } else {
+            tc_commit_if(leader, &fin_bar);
+            if (lane == 0) gs_mbar_wait(&fin_bar, 0, 2000000000ull);
+        }
+        (void)HATOM;
+        (void)GATOM;
+    } else {
+        // --------------------- epilogue warps 0..3 ----------------------
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (uint32_t c = 0; c < ACOLS; c += 32) tc_st_zero32(lane_base + c);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) gs_mbar_arrive(&zero_bar);
+        // bias gradient: thread t sums channel pair t % (GC/2) over the cells
+        // t / (GC/2), + 128/(GC/2), ... of every gradient plane (2 rows x 128
+        // cells, channels-last with the TMA's 64- or 32-byte swizzle: the
+        // 16-byte chunk index is XORed with address bits 7-8, resp. bit 7)
+        constexpr int NPAIR = GC / 2, NGRP = 128 / NPAIR;
+        const int cp = tid % NPAIR, cg = tid / NPAIR;
+        float db0 = 0.f, db1 = 0.f;
+        bool ok = true;
+        {
+            uint32_t G = 0;
+            for (long long unit = blockIdx.x; unit < units && ok; unit += gridDim.x) {
+                const Unit u = decode(unit);
+                for (int pi = 0; pi < u.nz; ++pi, ++G) {
+                    const uint32_t gs = G % kWgGSlots;
+                    if (!wwait(&g_full[gs], (G / kWgGSlots) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned char* slot = smem_wg + kWgHSlabs * HSLAB + gs * GSLOT;
+#pragma unroll 4
+                    for (int c = cg; c < kWgRows * kTcCells; c += NGRP) {
+                        const uint32_t off = (uint32_t)c * GC * 2 + (uint32_t)cp * 4;
+                        const uint32_t sw = GC == 32 ? ((off >> 7) & 3u) : ((off >> 7) & 1u);
+                        const __nv_bfloat162 v2 =
+                            *reinterpret_cast<const __nv_bfloat162*>(slot + (off ^ (sw << 4)));
+                        db0 += __bfloat162float(v2.x);
+                        db1 += __bfloat162float(v2.y);
+                    }
+                    __syncwarp();
+                    if (lane == 0) gs_mbar_arrive(&g_empty[gs]);
+                }
+            }
+        }
+        if (ok && wwait(&done_bar, 0)) {
+            tc_fence_after();
+            // TMEM lane m = 32 warp + lane is M row m: block j = m / HC (dy = j - 1), channel ci = m % HC
+            const int m = warp * 32 + lane;
+            const int j = m / HC, ci = m % HC;
+#pragma unroll 1
+            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll 1
+                for (int b = 0; b < 3; ++b) {
+                    float v[GC];
+                    tc_ld<GC>(lane_base + (uint32_t)(dxi * 3 * GC + b * GC), v);
+                    if (j <= 2) {
+                        const int tap = 9 * (2 - b) + 3 * j + dxi;  // dz = 1 - b, dy = j - 1, dx = dxi - 1
+                        float* dst = a.part + (size_t)blockIdx.x * (27 * HC * GC + GC) + ((size_t)tap * HC + ci) * GC;
+#pragma unroll
+                        for (int e = 0; e < GC; e += 8) {
+                            uint4 lo, hi;
+                            lo.x = __float_as_uint(v[e]);
+                            lo.y = __float_as_uint(v[e + 1]);
+                            lo.z = __float_as_uint(v[e + 2]);
+                            lo.w = __float_as_uint(v[e + 3]);
+                            hi.x = __float_as_uint(v[e + 4]);
+                            hi.y = __float_as_uint(v[e + 5]);
+                            hi.z = __float_as_uint(v[e + 6]);
+                            hi.w = __float_as_uint(v[e + 7]);
+                            gs_st_v8(dst + e, lo, hi);
+                        }
+                    }
+                }
+        }
+        // bias partial sums: the cell groups of a channel pair, in a fixed order
+        __shared__ float dbs[128][2];
+        dbs[tid][0] = db0;
+        dbs[tid][1] = db1;
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // the 4 epilogue warps only
+        if (tid < NPAIR) {
+            float s0 = 0.f, s1 = 0.f;
+            for (int g = 0; g < NGRP; ++g) {
+                s0 += dbs[g * NPAIR + tid][0];
+                s1 += dbs[g * NPAIR + tid][1];
+            }
+            float* dst = a.part + (size_t)blockIdx.x * (27 * HC * GC + GC) + 27 * HC * GC;
+            dst[2 * tid] = s0;
+            dst[2 * tid + 1] = s1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// dW[tap][ci][co] and db[co] = sums over the CTAs' partial sums (ci < cin,
+// co < cout); part is [nblk][27 HC GC + GC].  A block takes 32 consecutive
+// outputs; its 8 thread groups sum every 8th CTA's partials (several loads in
+// flight per thread), then the 8 sums are added in a fixed order (the result
+// does not depend on timing).
+constexpr int kWgRedOut = 32, kWgRedGrp = 8;
+__global__ void __launch_bounds__(kWgRedOut * kWgRedGrp) gs_wgrad_reduce_kernel(const float* __restrict__ part, int nblk,
+                                                                                int HC, int GC, int cin, int cout,
+                                                                                float* __restrict__ dw,
+                                                                                float* __restrict__ db)
+{
+    __shared__ float red[kWgRedGrp][kWgRedOut];
+    const int nw = 27 * cin * cout;
+    const int o = threadIdx.x % kWgRedOut, grp = threadIdx.x / kWgRedOut;
+    const int i = blockIdx.x * kWgRedOut + o;
+    float acc = 0.f;
+    if (i < nw + cout) {
+        size_t off;
+        if (i < nw) {
+            const int co = i % cout, ci = (i / cout) % cin, tap = i / (cout * cin);
+            off = ((size_t)tap * HC + ci) * GC + co;
+        } else {
+            off = (size_t)27 * HC * GC + (i - nw);
+        }
+        const float* p = part + off;
+        const size_t stride = (size_t)27 * HC * GC + GC;
+#pragma unroll 4
+        for (int b = grp; b < nblk; b += kWgRedGrp) acc += p[(size_t)b * stride];
+    }
+    red[grp][o] = acc;
+    __syncthreads();
+    if (grp == 0 && i < nw + cout) {
+        float v = 0.f;
+#pragma unroll
+        for (int g = 0; g < kWgRedGrp; ++g) v += red[g][o];
+        if (i < nw) dw[i] = v;
+        else db[i - nw] = v;
     }
 }
 
@@ -1456,6 +1879,7 @@ struct gs_surr {
     float* ou = nullptr;
     float* ov = nullptr;
     float* fk = nullptr;
+    float* wpart = nullptr;  // per-CTA weight-gradient partial sums (tensor-core path)
     double* d_loss = nullptr;
     unsigned* d_max = nullptr;
     double* d_ss = nullptr;
@@ -1487,6 +1911,8 @@ void free_ws(gs_surr* s)
     cudaFree(s->ou);
     cudaFree(s->ov);
     cudaFree(s->fk);
+    cudaFree(s->wpart);
+    s->wpart = nullptr;
     s->x0 = nullptr; s->gh = nullptr; s->gz[0] = s->gz[1] = nullptr; s->gd = nullptr;
     s->ou = s->ov = nullptr; s->fk = nullptr;
     s->N = s->L = 0;
@@ -1511,6 +1937,7 @@ int ensure_ws(gs_surr* s, int N, int L, bool train)
         ALLOC(s->gd, cells * 16 * sizeof(bf16));
         ALLOC(s->ou, cells * sizeof(float));
         ALLOC(s->ov, cells * sizeof(float));
+        ALLOC(s->wpart, (size_t)num_sms() * (27 * 32 * 32 + 32) * sizeof(float));
     }
 #undef ALLOC
     s->N = N;
@@ -1552,6 +1979,41 @@ int wgrad_launch(gs_surr* s, WgArgs a)
     k<<<grid, kWgThreads, smem, s->stream>>>(a);
     GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
+    return GS_OK;
+}
+
+// weight and bias gradients on the tensor cores: h (HC channels), g (GC
+// channels) -> dw [27][cin][cout], db [cout] (overwritten)
+template <int HC, int GC>
+int wgrad_tc_launch(gs_surr* s, int N, int L, const bf16* h, const bf16* g, int cin, int cout, float* dw, float* db)
+{
+    constexpr uint32_t HSLAB = (kWgRows + 2) * kTcRowCells * HC * 2;
+    constexpr uint32_t GSLOT = kWgRows * kTcCells * GC * 2;
+    const size_t smem = (size_t)kWgHSlabs * HSLAB + (size_t)(kWgGSlots + 2) * GSLOT;
+    if (L % kTcCells) return fail(GS_EINVAL, "the tcgen05 path needs L %% %d == 0 (L=%d)", kTcCells, L);
+    WgTcArgs a{};
+    a.N = N;
+    a.L = L;
+    if (encode_act_4d(&a.map_hmain, h, HC, L, (long long)N * L, HC, kTcCells, HC == 32 ? 64 : 32) != CUDA_SUCCESS ||
+        encode_act_4d(&a.map_hhalo, h, HC, L, (long long)N * L, HC, 8, HC == 32 ? 64 : 32) != CUDA_SUCCESS ||
+        encode_act_4d(&a.map_g, g, GC, L, (long long)N * L, GC, kTcCells, GC == 32 ? 64 : 32) != CUDA_SUCCESS)
+        return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for the weight-gradient maps");
+    auto k = gs_wgrad_tc_kernel<HC, GC>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWgTcThreads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "tensor-core weight gradient does not fit on an SM");
+    const long long units = (long long)N * (L / kWgRows) * (L / kTcCells) * ((L + kWgZChunk - 1) / kWgZChunk);
+    const int grid = (int)std::min<long long>(units, (long long)num_sms());
+    a.part = s->wpart;
+    a.err = s->d_err;
+    a.timeout_ns = 2000000000ull;
+    k<<<grid, kWgTcThreads, smem, s->stream>>>(a);
+    GS_CUDA_TRY(cudaGetLastError());
+    gs_wgrad_reduce_kernel<<<(27 * cin * cout + cout + kWgRedOut - 1) / kWgRedOut, kWgRedOut * kWgRedGrp, 0, s->stream>>>(
+        s->wpart, grid, HC, GC, cin, cout, dw, db);
+    GS_CUDA_TRY(cudaGetLastError());
+    s->launches += 2;
     return GS_OK;
 }
 
@@ -1723,13 +2185,13 @@ int trace_dh(gs_surr* s, int l, long long cells)
 int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double* loss)
 {
     const long long cells = (long long)N * L * L * L;
-    // the tensor-core path (as in forward()) also takes the data gradients,
-    // whose epilogue adds up the bias gradient of the layer below
+    // the tensor-core path (as in forward()) also takes the data and weight
+    // gradients; the weight-gradient kernel also sums the bias gradients
     const bool tc = s->backend != 1 && L % kTcCells == 0;
     GS_CUDA_TRY(cudaMemsetAsync(s->grads, 0, s->np * sizeof(float), s->stream));
     GS_CUDA_TRY(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
     gs_mse_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(s->ou, s->ov, tu, tv, cells, 1.0 / (2.0 * cells), s->gd,
-                                                            s->d_loss);
+                                                            s->d_loss, tc ? nullptr : s->grads + s->boff[5]);
     GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
     int rc;
@@ -1740,7 +2202,8 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
         return GS_OK;
     };
     // data gradient of layer l (input g, 16 or 32 channels): gh (+)= conv^T, gz
-    // for the layer below; on the tensor-core path also db of the layer below
+    // for the layer below (on the mma.sync path also db of the layer below; the
+    // tensor-core weight gradient sums the bias gradients itself)
     auto dgrad = [&](int l, const bf16* g, int gh_acc, bf16* gz) -> int {
         if (tc) {
             ConvTcArgs t{};
@@ -1752,7 +2215,6 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
             t.gh_acc = gh_acc;
             t.zprev = s->z[l - 1];
             t.gz = gz;
-            t.db = s->grads + s->boff[l - 1];
             return l == 5 ? tc_launch<16, 32, EPI_DGRAD>(s, t) : tc_launch<32, 32, EPI_DGRAD>(s, t);
         }
         ConvArgs d{};
@@ -1778,8 +2240,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     w.cin = 32;
     w.cout = 2;
     w.dw = s->grads + s->woff[5];
-    if ((rc = wgrad_launch<32, 8>(s, w))) return rc;
-    if ((rc = bias_grad(s->gd, 16, 2, s->grads + s->boff[5]))) return rc;
+    if ((rc = tc ? wgrad_tc_launch<32, 16>(s, N, L, s->h[5], s->gd, 32, 2, w.dw, s->grads + s->boff[5]) : wgrad_launch<32, 8>(s, w))) return rc;
     if ((rc = dgrad(5, s->gd, 0, s->gz[0]))) return rc;
     if ((rc = trace_dh(s, 5, cells))) return rc;
     int cur = 0;
@@ -1790,7 +2251,8 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
         w.cin = 32;
         w.cout = 32;
         w.dw = s->grads + s->woff[l];
-        if ((rc = wgrad_launch<32, 32>(s, w))) return rc;
+        if ((rc = tc ? wgrad_tc_launch<32, 32>(s, N, L, s->h[l], s->gz[cur], 32, 32, w.dw, s->grads + s->boff[l]) : wgrad_launch<32, 32>(s, w)))
+            return rc;
         if ((rc = dgrad(l, s->gz[cur], 1, s->gz[cur ^ 1]))) return rc;
         if ((rc = trace_dh(s, l, cells))) return rc;
         cur ^= 1;
@@ -1802,7 +2264,8 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     w.cin = 4;
     w.cout = 32;
     w.dw = s->grads + s->woff[0];
-    if ((rc = wgrad_launch<16, 32>(s, w))) return rc;
+    if ((rc = tc ? wgrad_tc_launch<16, 32>(s, N, L, s->x0, s->gz[cur], 4, 32, w.dw, s->grads + s->boff[0]) : wgrad_launch<16, 32>(s, w)))
+        return rc;
     if (loss) GS_CUDA_TRY(cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     return gs_surr_sync(s);
 }

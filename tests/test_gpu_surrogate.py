@@ -143,7 +143,8 @@ def test_gradients_match_oracle(L, N, seed):
     np.testing.assert_array_equal(np.stack([ou.cpu().numpy(), ov.cpu().numpy()], axis=-1), out)
     loss_o, dout = oracle.mse_loss(out, np.stack([tu, tv], axis=-1).astype(np.float64))
     go, dho = oracle.surrogate_backward(cache, dout, emulate_bf16=True, return_dh=True)
-    assert abs(loss_gpu - loss_o) <= 1e-12 * loss_o
+    # the loss adds FP32 per-thread partial sums (in FP64 across threads)
+    assert abs(loss_gpu - loss_o) <= 1e-6 * loss_o
     for l in range(6):
         _assert_close(grads[l][0], go[l][0], f"layer {l} dW")
         _assert_close(grads[l][1], go[l][1], f"layer {l} db")
