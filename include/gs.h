@@ -378,6 +378,54 @@ int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k,
                           int64_t t, int cur, int64_t nsteps, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* z-slab decomposition of one grid (Section 3.3, Listing 3)               */
+/* ---------------------------------------------------------------------- */
+/* The paper splits the domain over MPI ranks and exchanges faces with the
+ * neighbours every step (Section 3.3; Listing 3's Sendrecv).  Here one
+ * periodic L^3 grid is cut along z into slabs; slab i holds the nz global
+ * planes z0 .. z0+nz-1 and `depth` = D ghost planes on each side, so D steps
+ * run between two exchanges (local plane zl is global plane
+ * (z0 - D + zl) mod L).  Slabs of one grid reproduce the single-grid run bit
+ * for bit (same update, neighbour order, step index and global cell index
+ * for the noise draw).
+ *
+ * gs_slab_create_on: four caller-owned device buffers (u0, v0, u1, v1) of
+ *   L * L * (nz + 2 depth) elements of dtype each, [zl][y][x], x fastest;
+ *   1 <= depth <= nz <= L, 0 <= z0 < L.  GS_EINVAL otherwise.
+ * gs_slab_init: the centred-cube state at step 0 on every local plane
+ *   (ghosts included), in buffer set 0.
+ * gs_slab_pass: D steps (step counter t -> t + D): sub-step s updates local
+ *   planes s+1 .. nz+2D-s-2, so the nz interior planes come out exact and
+ *   the ghosts must hold the neighbours' planes at step t before the call.
+ *   Asynchronous on the slab's stream.
+ * gs_slab_state / gs_slab_set_state: step counter and the buffer set (0 or
+ *   1) holding the current state.  After the call the interior planes
+ *   (local planes D .. D+nz-1) of set `cur` are the state; a transport that
+ *   moves the ghosts itself reads them there.
+ * gs_slab_exchange: the exchange among the n slabs of one grid in one
+ *   process (slab i+1 must start where slab i ends, periodically; same L,
+ *   depth, dtype and step): each slab's D low ghost planes receive the
+ *   lower slab's last D interior planes and its high ghost planes the upper
+ *   slab's first D, by device-to-device copies into the receiving slab's
+ *   own memory on its stream, ordered after every sender's pass and before
+ *   any slab's next pass by events.  Asynchronous.
+ * gs_slab_sync waits for the slab's stream; gs_slab_destroy frees the slab
+ *   (not the caller's buffers). */
+typedef struct gs_slab gs_slab;
+int gs_slab_create_on(int L, int z0, int nz, int depth, double Du, double Dv, double F, double k, double dt,
+                      double noise, uint64_t seed, int dtype, void* u0, void* v0, void* u1, void* v1,
+                      gs_slab** out);
+int gs_slab_set_stream(gs_slab* s, void* stream);
+int gs_slab_init(gs_slab* s);
+int gs_slab_pass(gs_slab* s);
+int gs_slab_state(gs_slab* s, int64_t* t, int* cur);
+int gs_slab_set_state(gs_slab* s, int64_t t, int cur);
+int gs_slab_exchange(gs_slab** slabs, int n);
+int gs_slab_sync(gs_slab* s);
+int gs_slab_launch_count(gs_slab* s, int64_t* count);
+int gs_slab_destroy(gs_slab* s);
+
+/* ---------------------------------------------------------------------- */
 /* Learned surrogate (not in the paper): a network that advances a grid by  */
 /* K = 16 steps, trained on trajectories of the stencil itself             */
 /* ---------------------------------------------------------------------- */

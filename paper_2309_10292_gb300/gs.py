@@ -129,6 +129,16 @@ _SIGS = {
     "gs_surr_launch_count": [_vp, ctypes.POINTER(_i64)],
     "gs_surr_destroy": [_vp],
     "gs_batch_step_noalloc": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _vp, _i64, _i, _i64, _vp],
+    "gs_slab_create_on": [_i, _i, _i, _i, _d, _d, _d, _d, _d, _d, _u64, _i, _vp, _vp, _vp, _vp, _pp],
+    "gs_slab_set_stream": [_vp, _vp],
+    "gs_slab_init": [_vp],
+    "gs_slab_pass": [_vp],
+    "gs_slab_state": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i)],
+    "gs_slab_set_state": [_vp, _i64, _i],
+    "gs_slab_exchange": [_vp, _i],
+    "gs_slab_sync": [_vp],
+    "gs_slab_launch_count": [_vp, ctypes.POINTER(_i64)],
+    "gs_slab_destroy": [_vp],
 }
 _RESTYPES = {"gs_last_error": ctypes.c_char_p}
 
@@ -750,6 +760,130 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# z-slab decomposition (gs_slab_*)
+# ---------------------------------------------------------------------------
+def slab_bounds(L: int, nslabs: int) -> list:
+    """(z0, nz) of nslabs z-slabs of an L^3 grid, as even as possible."""
+    return [(L * i // nslabs, L * (i + 1) // nslabs - L * i // nslabs) for i in range(nslabs)]
+
+
+class GrayScottSlab:
+    """One z-slab (global planes z0 .. z0+nz-1) of a periodic L^3 grid with
+    `depth` ghost planes on each side; its four buffers are torch tensors
+    [nz + 2 depth, L, L] on the current CUDA device."""
+
+    def __init__(self, L, z0, nz, depth, Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0, noise=0.0, seed=0,
+                 dtype="f32", stream=None, device=None):
+        import torch
+        self.L, self.z0, self.nz, self.depth = int(L), int(z0), int(nz), int(depth)
+        self.dtype = _dtype_code(dtype)
+        tdt = torch.float32 if self.dtype == GS_F32 else torch.float64
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        planes = self.nz + 2 * self.depth
+        self._bufs = [torch.empty((planes, L, L), dtype=tdt, device=dev) for _ in range(4)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        out = ctypes.c_void_p()
+        _check(lib().gs_slab_create_on(self.L, self.z0, self.nz, self.depth, Du, Dv, F, k, dt, noise, seed,
+                                       self.dtype, *(_ptr(b) for b in self._bufs), ctypes.byref(out)),
+               "gs_slab_create_on")
+        self.handle = out.value
+        _check(lib().gs_slab_set_stream(self.handle, _stream(self.stream)), "gs_slab_set_stream")
+
+    def init(self):
+        _check(lib().gs_slab_init(self.handle), "gs_slab_init")
+
+    def run_pass(self):
+        """`depth` steps; the ghosts must hold the neighbours' planes at the current step."""
+        _check(lib().gs_slab_pass(self.handle), "gs_slab_pass")
+
+    def state(self):
+        t, cur = _i64(), _i()
+        _check(lib().gs_slab_state(self.handle, ctypes.byref(t), ctypes.byref(cur)), "gs_slab_state")
+        return t.value, cur.value
+
+    @property
+    def t(self) -> int:
+        return self.state()[0]
+
+    def fields(self, cur=None):
+        """(u, v) tensors of buffer set cur (default: the current one), all planes."""
+        c = self.state()[1] if cur is None else cur
+        return self._bufs[2 * c], self._bufs[2 * c + 1]
+
+    def halo_views(self):
+        """Per field, the four plane ranges a transport moves in one exchange
+        (views of the current set): send_lo / send_hi = the D interior planes
+        next to the low / high face, recv_lo / recv_hi = the ghost planes."""
+        D, nz = self.depth, self.nz
+        out = []
+        for f in self.fields():
+            out.append({"send_lo": f[D:2 * D], "send_hi": f[nz:nz + D],
+                        "recv_lo": f[0:D], "recv_hi": f[nz + D:nz + 2 * D]})
+        return out
+
+    def read(self):
+        """Interior planes of u and v as numpy arrays [nz, L, L]."""
+        self.sync()
+        u, v = self.fields()
+        D = self.depth
+        return u[D:D + self.nz].cpu().numpy(), v[D:D + self.nz].cpu().numpy()
+
+    def sync(self):
+        _check(lib().gs_slab_sync(self.handle), "gs_slab_sync")
+
+    def launches(self) -> int:
+        c = _i64()
+        _check(lib().gs_slab_launch_count(self.handle, ctypes.byref(c)), "gs_slab_launch_count")
+        return c.value
+
+    def close(self):
+        if self.handle:
+            lib().gs_slab_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def slab_exchange(slabs):
+    """The halo exchange among the slabs of one grid in this process (z order,
+    periodic), by device-to-device copies on each slab's stream."""
+    arr = (ctypes.c_void_p * len(slabs))(*[s.handle for s in slabs])
+    _check(lib().gs_slab_exchange(arr, len(slabs)), "gs_slab_exchange")
+
+
+def slab_exchange_dist(views, group=None):
+    """The same exchange between ranks, one slab per rank in z order
+    (periodic), over torch.distributed point-to-point messages (NCCL for
+    device tensors, gloo for host tensors).  `views` is halo_views() of this
+    rank's slab (or the same dictionaries over host arrays).  Each rank sends
+    its low interior planes to the rank below (its high ghosts) and its high
+    interior planes to the rank above (its low ghosts); with one rank the
+    copies stay local.  The tags tell the two faces apart when both
+    neighbours are the same rank."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    if world == 1:
+        for v in views:
+            v["recv_hi"].copy_(v["send_lo"])
+            v["recv_lo"].copy_(v["send_hi"])
+        return
+    rank = dist.get_rank(group)
+    lo, hi = (rank - 1) % world, (rank + 1) % world
+    ops = []
+    for f, v in enumerate(views):
+        ops += [dist.P2POp(dist.isend, v["send_lo"].contiguous(), lo, group, tag=2 * f),
+                dist.P2POp(dist.irecv, v["recv_hi"], hi, group, tag=2 * f),
+                dist.P2POp(dist.isend, v["send_hi"].contiguous(), hi, group, tag=2 * f + 1),
+                dist.P2POp(dist.irecv, v["recv_lo"], lo, group, tag=2 * f + 1)]
+    for r in dist.batch_isend_irecv(ops):
+        r.wait()
 
 
 class GrayScottBatch:
