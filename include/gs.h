@@ -462,6 +462,15 @@ int gs_surr_set_params(gs_surr* s, const float* host, size_t count);
 int gs_surr_get_params(gs_surr* s, float* host, size_t count);
 /* Gradients of the last gs_surr_grad / gs_surr_train_step, same layout. */
 int gs_surr_get_grads(gs_surr* s, float* host, size_t count);
+/* Weights file (the training's result): 8-byte magic "GSSURR01", uint32
+ * parameter count, then the FP32 parameters in gs_surr_set_params' layout,
+ * little-endian.  gs_surr_save writes the current parameters (GS_EIO if the
+ * file cannot be written); gs_surr_load reads them and resets the Adam
+ * moments like gs_surr_set_params (GS_EIO if the file cannot be opened or
+ * is truncated, GS_EINVAL for another magic, another parameter count or
+ * trailing bytes).  Synchronous. */
+int gs_surr_save(gs_surr* s, const char* path);
+int gs_surr_load(gs_surr* s, const char* path);
 /* Checking aids for the gradients (tests and debugging; not needed to train).
  * gs_surr_trace_grads: while dh is not NULL, every gs_surr_grad /
  * gs_surr_train_step also copies the gradient of the loss with respect to

@@ -1892,6 +1892,8 @@ struct gs_surr {
 
 namespace {
 
+constexpr char kSurrMagic[8] = {'G', 'S', 'S', 'U', 'R', 'R', '0', '1'};
+
 int surr_valid_L(int L)
 {
     if (L < 16 || L % 16 || (L > 128 && L % 128))
@@ -2438,6 +2440,43 @@ int gs_surr_grad(gs_surr* s, int N, int L, const float* u, const float* v, const
     if ((rc = upload_fk(s, N, F, k))) return rc;
     if ((rc = forward(s, N, L, u, v, s->ou, s->ov, true))) return rc;
     return backward(s, N, L, u_tgt, v_tgt, loss);
+}
+
+int gs_surr_save(gs_surr* s, const char* path)
+{
+    if (!s || !path) return fail(GS_EINVAL, "NULL argument");
+    std::vector<float> h(s->np);
+    int rc = gs_surr_get_params(s, h.data(), h.size());
+    if (rc) return rc;
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(GS_EIO, "cannot create %s", path);
+    const uint32_t n = (uint32_t)s->np;
+    bool ok = fwrite(kSurrMagic, 1, 8, f) == 8 && fwrite(&n, sizeof(n), 1, f) == 1 &&
+              fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? GS_OK : fail(GS_EIO, "writing %s failed", path);
+}
+
+int gs_surr_load(gs_surr* s, const char* path)
+{
+    if (!s || !path) return fail(GS_EINVAL, "NULL argument");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(GS_EIO, "cannot open %s", path);
+    char magic[8] = {};
+    uint32_t n = 0;
+    std::vector<float> h(s->np);
+    const bool head = fread(magic, 1, 8, f) == 8 && fread(&n, sizeof(n), 1, f) == 1;
+    const bool body = head && memcmp(magic, kSurrMagic, 8) == 0 && n == (uint32_t)s->np &&
+                      fread(h.data(), sizeof(float), h.size(), f) == h.size();
+    char extra;
+    const bool at_end = body && fread(&extra, 1, 1, f) == 0;
+    fclose(f);
+    if (!head) return fail(GS_EIO, "%s: truncated header", path);
+    if (memcmp(magic, kSurrMagic, 8) != 0) return fail(GS_EINVAL, "%s is not a surrogate weights file", path);
+    if (n != (uint32_t)s->np) return fail(GS_EINVAL, "%s holds %u parameters, the network has %zu", path, n, s->np);
+    if (!body) return fail(GS_EIO, "%s: truncated parameters", path);
+    if (!at_end) return fail(GS_EINVAL, "%s: trailing bytes after the parameters", path);
+    return gs_surr_set_params(s, h.data(), h.size());
 }
 
 int gs_surr_trace_grads(gs_surr* s, float* dh, size_t count)

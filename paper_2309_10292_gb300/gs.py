@@ -117,6 +117,8 @@ _SIGS = {
     "gs_surr_get_params": [_vp, _vp, _sz],
     "gs_surr_get_grads": [_vp, _vp, _sz],
     "gs_surr_trace_grads": [_vp, _vp, _sz],
+    "gs_surr_save": [_vp, ctypes.c_char_p],
+    "gs_surr_load": [_vp, ctypes.c_char_p],
     "gs_surr_get_train_output": [_vp, _vp, _vp, _sz],
     "gs_surr_forward": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "gs_surr_grad": [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)],
@@ -626,6 +628,14 @@ def gs_surr_get_grads(s) -> np.ndarray:
     return out
 
 
+def gs_surr_save(s, path: str):
+    _check(lib().gs_surr_save(s, os.fsencode(path)), "gs_surr_save")
+
+
+def gs_surr_load(s, path: str):
+    _check(lib().gs_surr_load(s, os.fsencode(path)), "gs_surr_load")
+
+
 def gs_surr_trace_grads(s, dh, count: int = 0):
     """dh: a float32 CUDA tensor of 5 * N * L^3 * 32 elements, or None (off)."""
     _check(lib().gs_surr_trace_grads(s, _ptr(dh) if dh is not None else None,
@@ -732,6 +742,12 @@ class Surrogate:
 
     def grads(self):
         return surr_unflatten(gs_surr_get_grads(self.handle))
+
+    def save(self, path: str):
+        gs_surr_save(self.handle, path)
+
+    def load(self, path: str):
+        gs_surr_load(self.handle, path)
 
     def forward(self, u, v, F, k):
         """u, v: torch float32 CUDA tensors [N, L, L, L]; returns predicted (u, v) after 16 steps."""

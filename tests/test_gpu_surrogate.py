@@ -414,6 +414,32 @@ def test_checked_run_at_L128_sampled_cells_match_oracle():
     sim.close()
 
 
+def test_weights_file_round_trip_and_refusals(tmp_path):
+    need_cuda()
+    params = inputs.surrogate_init_params(seed=12, last_scale=1.0)
+    a = gs.Surrogate(params)
+    path = str(tmp_path / "w.gssurr")
+    a.save(path)
+    b = gs.Surrogate()
+    b.load(path)
+    np.testing.assert_array_equal(gs.gs_surr_get_params(b.handle), gs.gs_surr_get_params(a.handle))
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"GSSURR01" and len(raw) == 12 + 4 * gs.gs_surr_param_count()
+    for name, data, status in [("magic", b"XXXXXXXX" + raw[8:], gs.GS_EINVAL),
+                               ("short", raw[:100], gs.GS_EIO),
+                               ("long", raw + b"\0", gs.GS_EINVAL)]:
+        bad = str(tmp_path / name)
+        open(bad, "wb").write(data)
+        with pytest.raises(gs.GsError) as e:
+            b.load(bad)
+        assert e.value.status == status, name
+    with pytest.raises(gs.GsError) as e:
+        b.load(str(tmp_path / "missing"))
+    assert e.value.status == gs.GS_EIO
+    a.close()
+    b.close()
+
+
 def test_surrogate_argument_errors():
     torch = need_cuda()
     s = gs.Surrogate()
