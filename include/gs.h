@@ -378,6 +378,16 @@ int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k,
                           int64_t t, int cur, int64_t nsteps, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Measurement aid (not in the paper)                                      */
+/* ---------------------------------------------------------------------- */
+/* FP64 fused multiply-adds per second this GPU sustains (independent chains
+ * on every SM, best of three timed launches after a warm-up, CUDA events on
+ * `stream`): the FP64 pipe's rate, against which the FP64 stencil's
+ * operations per cell are compared.  Allocates 8 bytes of device memory for
+ * the duration.  Synchronous. */
+int gs_measure_fp64_fma(void* stream, double* fma_per_s);
+
+/* ---------------------------------------------------------------------- */
 /* z-slab decomposition of one grid (Section 3.3, Listing 3)               */
 /* ---------------------------------------------------------------------- */
 /* The paper splits the domain over MPI ranks and exchanges faces with the

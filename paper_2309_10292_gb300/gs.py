@@ -131,6 +131,7 @@ _SIGS = {
     "gs_surr_launch_count": [_vp, ctypes.POINTER(_i64)],
     "gs_surr_destroy": [_vp],
     "gs_batch_step_noalloc": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _vp, _i64, _i, _i64, _vp],
+    "gs_measure_fp64_fma": [_vp, ctypes.POINTER(_d)],
     "gs_slab_create_on": [_i, _i, _i, _i, _d, _d, _d, _d, _d, _d, _u64, _i, _vp, _vp, _vp, _vp, _pp],
     "gs_slab_set_stream": [_vp, _vp],
     "gs_slab_init": [_vp],
@@ -776,6 +777,13 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def gs_measure_fp64_fma(stream=None) -> float:
+    """FP64 fused multiply-adds per second of this GPU (measured)."""
+    r = _d()
+    _check(lib().gs_measure_fp64_fma(_stream(stream), ctypes.byref(r)), "gs_measure_fp64_fma")
+    return r.value
 
 
 # ---------------------------------------------------------------------------

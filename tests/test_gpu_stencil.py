@@ -496,3 +496,12 @@ def test_async_copies_match_blocking_ones_on_two_streams(dtype):
     with pytest.raises(gs.GsError) as e:
         gs.gs_read_async(sims[0].handle, gs.GS_U, torch.empty(7, dtype=hout[0].dtype))
     assert e.value.status == gs.GS_EINVAL
+
+
+def test_fp64_fma_rate_is_measured():
+    # the FP64 pipe's rate the bench divides by: positive, and within a wide
+    # band around GB300's nominal 1.25 TFLOP/s (0.625 T FMA/s)
+    need_cuda()
+    r = gs.gs_measure_fp64_fma()
+    print(f"FP64 FMA/s: {r:.4e}")
+    assert 0.1 * 0.625e12 < r < 4 * 0.625e12
