@@ -452,10 +452,7 @@ def bench_surrogate(args, stream):
     step_s = a.elapsed_time(b) / 1e4
     timer.close()
     del xu, xv, yu, yv
-    # useful FLOP per cell of a training step: forward + data gradients of
-    # layers 5..1 + weight gradients of all layers
-    train_flop = (2 * 27 * (4 * 32 + 4 * 32 * 32 + 32 * 2) + 2 * 27 * (2 * 32 + 4 * 32 * 32)
-                  + 2 * 27 * (4 * 32 + 4 * 32 * 32 + 32 * 2)) * args.surr_batch * 128 ** 3
+    train_flop = surrogate.TRAIN_FLOP_PER_CELL * args.surr_batch * 128 ** 3
     losses, t_train = surrogate.train(net, pool, iters=args.surr_iters, lr=1e-3, batch=args.surr_batch,
                                       warmup=100)
     ev = surrogate.evaluate(net, pool, pairs=8)

@@ -378,6 +378,22 @@ int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k,
                           int64_t t, int cur, int64_t nsteps, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Checking aid: guard bands around the library's own allocations          */
+/* ---------------------------------------------------------------------- */
+/* Out-of-bounds writes are caught without a sanitizer.  After
+ * gs_set_alloc_guard(G) (G a multiple of 256; 0 turns it off; process-wide)
+ * every device buffer a batch or a surrogate allocates from then on sits
+ * between two G-byte guard bands of 0xFF bytes (a NaN pattern for FP32,
+ * FP64 and bfloat16), and starts filled with 0xFF itself.
+ * gs_batch_guard_check / gs_surr_guard_check synchronise the object's stream
+ * and count the guard bytes of its buffers that no longer hold 0xFF
+ * (*bad = 0: nothing was written outside a buffer).  The surrogate's checked
+ * run allocates two temporary fields per call that are not covered. */
+int gs_set_alloc_guard(size_t bytes);
+int gs_batch_guard_check(gs_batch* b, int64_t* bad);
+int gs_surr_guard_check(gs_surr* s, int64_t* bad);
+
+/* ---------------------------------------------------------------------- */
 /* Measurement aid (not in the paper)                                      */
 /* ---------------------------------------------------------------------- */
 /* FP64 fused multiply-adds per second this GPU sustains (independent chains

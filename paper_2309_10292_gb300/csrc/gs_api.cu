@@ -4,6 +4,9 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <map>
+#include <mutex>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -33,6 +36,71 @@ int cuda_fail(cudaError_t e, const char* what)
 }
 
 int elem_size(int dtype) { return dtype == GS_F32 ? 4 : 8; }
+
+namespace {
+std::mutex g_guard_mutex;
+size_t g_guard_bytes = 0;
+struct GuardRec {
+    char* base;
+    size_t bytes, guard;
+};
+std::map<const void*, GuardRec> g_guarded;
+}  // namespace
+
+cudaError_t guarded_malloc(void** p, size_t bytes)
+{
+    size_t g;
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mutex);
+        g = g_guard_bytes;
+    }
+    if (g == 0) return cudaMalloc(p, bytes);
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes + 2 * g);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemset(base, 0xFF, bytes + 2 * g)) != cudaSuccess) {
+        cudaFree(base);
+        return e;
+    }
+    *p = base + g;
+    std::lock_guard<std::mutex> lk(g_guard_mutex);
+    g_guarded[*p] = GuardRec{base, bytes, g};
+    return cudaSuccess;
+}
+
+void guarded_free(void* p)
+{
+    if (!p) return;
+    char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mutex);
+        auto it = g_guarded.find(p);
+        if (it != g_guarded.end()) {
+            base = it->second.base;
+            g_guarded.erase(it);
+        }
+    }
+    cudaFree(base ? (void*)base : p);
+}
+
+int64_t guarded_check(const void* p)
+{
+    GuardRec r{};
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mutex);
+        auto it = g_guarded.find(p);
+        if (it == g_guarded.end()) return 0;
+        r = it->second;
+    }
+    std::vector<unsigned char> h(r.guard);
+    int64_t bad = 0;
+    for (int side = 0; side < 2; ++side) {
+        const char* src = side == 0 ? r.base : r.base + r.guard + r.bytes;
+        if (cudaMemcpy(h.data(), src, r.guard, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+        for (unsigned char c : h) bad += c != 0xFF;
+    }
+    return bad;
+}
 
 int num_sms()
 {
@@ -718,3 +786,11 @@ int gs_noise_field(uint64_t seed, int64_t t, int64_t n, int dtype, void* dev_out
 }
 
 }  // extern "C"
+
+extern "C" int gs_set_alloc_guard(size_t bytes)
+{
+    if (bytes % 256) return fail(GS_EINVAL, "guard bytes=%zu must be a multiple of 256", bytes);
+    std::lock_guard<std::mutex> lk(g_guard_mutex);
+    g_guard_bytes = bytes;
+    return GS_OK;
+}

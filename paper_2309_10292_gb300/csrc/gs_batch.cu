@@ -404,8 +404,8 @@ static int upload_items(gs_batch* b, const std::vector<int4>& items)
 {
     if ((int)items.size() > b->items_cap) {
         int4* d = nullptr;
-        GS_CUDA_TRY(cudaMalloc(&d, sizeof(int4) * items.size()));
-        cudaFree(b->d_items);
+        GS_CUDA_TRY(guarded_malloc((void**)&d, sizeof(int4) * items.size()));
+        guarded_free(b->d_items);
         b->d_items = d;
         b->items_cap = (int)items.size();
     }
@@ -527,11 +527,11 @@ int gs_batch_destroy(gs_batch* b)
 {
     if (!b) return GS_OK;
     drop_graphs(b);
-    if (b->arena) cudaFree(b->arena);
-    if (b->d_inst) cudaFree(b->d_inst);
-    if (b->d_items) cudaFree(b->d_items);
-    if (b->d_maps) cudaFree(b->d_maps);
-    if (b->d_ctrl) cudaFree(b->d_ctrl);
+    guarded_free(b->arena);
+    guarded_free(b->d_inst);
+    guarded_free(b->d_items);
+    guarded_free(b->d_maps);
+    guarded_free(b->d_ctrl);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return GS_OK;
@@ -604,10 +604,10 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
     int rc = GS_OK;
     cudaError_t e;
     b->arena_bytes = (size_t)off * esz;
-    if ((e = cudaMalloc(&b->arena, (size_t)off * esz)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_inst, sizeof(BInst) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * (size_t)n * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_ctrl, sizeof(BCtrl))) != cudaSuccess ||
+    if ((e = guarded_malloc((void**)&b->arena, (size_t)off * esz)) != cudaSuccess ||
+        (e = guarded_malloc((void**)&b->d_inst, sizeof(BInst) * n)) != cudaSuccess ||
+        (e = guarded_malloc((void**)&b->d_maps, sizeof(CUtensorMap) * (size_t)n * 8)) != cudaSuccess ||
+        (e = guarded_malloc((void**)&b->d_ctrl, sizeof(BCtrl))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
         rc = cuda_fail(e, "allocating the batch");
         gs_batch_destroy(b);
@@ -888,6 +888,21 @@ int gs_batch_set_plan(gs_batch* b, int tile_z, int stages)
     b->tz = tile_z;
     b->stages = stages;
     drop_graphs(b);
+    return GS_OK;
+}
+
+int gs_batch_guard_check(gs_batch* b, int64_t* bad)
+{
+    if (!b || !bad) return fail(GS_EINVAL, "NULL argument");
+    GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    int64_t n = 0;
+    for (const void* p : {(const void*)b->arena, (const void*)b->d_inst, (const void*)b->d_items, (const void*)b->d_maps,
+                          (const void*)b->d_ctrl}) {
+        const int64_t r = guarded_check(p);
+        if (r < 0) return fail(GS_ECUDA, "reading a guard band failed");
+        n += r;
+    }
+    *bad = n;
     return GS_OK;
 }
 

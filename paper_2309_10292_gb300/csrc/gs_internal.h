@@ -30,6 +30,15 @@ int cuda_fail(cudaError_t e, const char* what);
 int elem_size(int dtype);
 int num_sms();
 
+// Library-owned device allocations that honour the guard-band checking aid
+// (gs_set_alloc_guard): with a guard of G bytes the buffer sits between two
+// G-byte bands of 0xFF bytes (and its own bytes start as 0xFF too).
+cudaError_t guarded_malloc(void** p, size_t bytes);
+void guarded_free(void* p);
+// guard bytes of p that no longer hold 0xFF (0 for an unguarded buffer);
+// -1 if the check itself failed
+int64_t guarded_check(const void* p);
+
 // Tensor-map encoder obtained from the driver at first use.
 CUresult encode_tiled_3d(CUtensorMap* map, int dtype, void* base, int L, int box_x, int box_y);
 // channels-last bf16 activations [planes][L][L][C] (planes = N * L): boxes of

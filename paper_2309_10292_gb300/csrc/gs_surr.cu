@@ -1903,17 +1903,17 @@ int surr_valid_L(int L)
 
 void free_ws(gs_surr* s)
 {
-    cudaFree(s->x0);
-    for (auto& p : s->h) { cudaFree(p); p = nullptr; }
-    for (auto& p : s->z) { cudaFree(p); p = nullptr; }
-    cudaFree(s->gh);
-    cudaFree(s->gz[0]);
-    cudaFree(s->gz[1]);
-    cudaFree(s->gd);
-    cudaFree(s->ou);
-    cudaFree(s->ov);
-    cudaFree(s->fk);
-    cudaFree(s->wpart);
+    guarded_free(s->x0);
+    for (auto& p : s->h) { guarded_free(p); p = nullptr; }
+    for (auto& p : s->z) { guarded_free(p); p = nullptr; }
+    guarded_free(s->gh);
+    guarded_free(s->gz[0]);
+    guarded_free(s->gz[1]);
+    guarded_free(s->gd);
+    guarded_free(s->ou);
+    guarded_free(s->ov);
+    guarded_free(s->fk);
+    guarded_free(s->wpart);
     s->wpart = nullptr;
     s->x0 = nullptr; s->gh = nullptr; s->gz[0] = s->gz[1] = nullptr; s->gd = nullptr;
     s->ou = s->ov = nullptr; s->fk = nullptr;
@@ -1926,7 +1926,7 @@ int ensure_ws(gs_surr* s, int N, int L, bool train)
     free_ws(s);
     const size_t cells = (size_t)N * L * L * L;
     cudaError_t e;
-#define ALLOC(p, bytes) if ((e = cudaMalloc(&(p), (bytes))) != cudaSuccess) { free_ws(s); return cuda_fail(e, "surrogate workspace"); }
+#define ALLOC(p, bytes) if ((e = guarded_malloc((void**)&(p), (bytes))) != cudaSuccess) { free_ws(s); return cuda_fail(e, "surrogate workspace"); }
     ALLOC(s->x0, cells * 16 * sizeof(bf16));
     ALLOC(s->fk, (size_t)N * 2 * sizeof(float));
     const int nh = train ? 5 : 2;
@@ -2317,21 +2317,21 @@ int gs_surr_destroy(gs_surr* s)
 {
     if (!s) return GS_OK;
     free_ws(s);
-    cudaFree(s->params);
-    cudaFree(s->grads);
-    cudaFree(s->m);
-    cudaFree(s->v);
+    guarded_free(s->params);
+    guarded_free(s->grads);
+    guarded_free(s->m);
+    guarded_free(s->v);
     for (int l = 0; l < kSurrLayers; ++l) {
-        cudaFree(s->wf[l]);
-        cudaFree(s->wd[l]);
-        cudaFree(s->wt[l]);
-        cudaFree(s->wdt[l]);
+        guarded_free(s->wf[l]);
+        guarded_free(s->wd[l]);
+        guarded_free(s->wt[l]);
+        guarded_free(s->wdt[l]);
     }
-    cudaFree(s->wt0x);
-    cudaFree(s->d_err);
-    cudaFree(s->d_loss);
-    cudaFree(s->d_max);
-    cudaFree(s->d_ss);
+    guarded_free(s->wt0x);
+    guarded_free(s->d_err);
+    guarded_free(s->d_loss);
+    guarded_free(s->d_max);
+    guarded_free(s->d_ss);
     delete s;
     return GS_OK;
 }
@@ -2351,24 +2351,24 @@ int gs_surr_create(gs_surr** out)
     }
     s->np = off;
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&s->params, off * 4)) != cudaSuccess || (e = cudaMalloc(&s->grads, off * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&s->m, off * 4)) != cudaSuccess || (e = cudaMalloc(&s->v, off * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_loss, sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_max, sizeof(unsigned))) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_ss, sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(s->d_err, 0, sizeof(int))) != cudaSuccess) {
+    if ((e = guarded_malloc((void**)&s->params, off * 4)) != cudaSuccess || (e = guarded_malloc((void**)&s->grads, off * 4)) != cudaSuccess ||
+        (e = guarded_malloc((void**)&s->m, off * 4)) != cudaSuccess || (e = guarded_malloc((void**)&s->v, off * 4)) != cudaSuccess ||
+        (e = guarded_malloc((void**)&s->d_loss, sizeof(double))) != cudaSuccess ||
+        (e = guarded_malloc((void**)&s->d_max, sizeof(unsigned))) != cudaSuccess ||
+        (e = guarded_malloc((void**)&s->d_ss, sizeof(double))) != cudaSuccess ||
+        (e = guarded_malloc((void**)&s->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(s->d_err, 0, sizeof(int))) != cudaSuccess) {
         int rc = cuda_fail(e, "surrogate allocation");
         gs_surr_destroy(s);
         return rc;
     }
     for (int l = 0; l < kSurrLayers && e == cudaSuccess; ++l) {
-        e = cudaMalloc(&s->wf[l], (size_t)27 * kCoutP[l] * kCinP[l] * sizeof(bf16));
+        e = guarded_malloc((void**)&s->wf[l], (size_t)27 * kCoutP[l] * kCinP[l] * sizeof(bf16));
         if (e == cudaSuccess)
-            e = cudaMalloc(&s->wt[l], (l == 5 ? (size_t)6 * 3 * 2 * 2 * 48 * 8 : (size_t)27 * kCinP[l] * 32) * sizeof(bf16));
-        if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wd[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
-        if (e == cudaSuccess && l >= 1) e = cudaMalloc(&s->wdt[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
+            e = guarded_malloc((void**)&s->wt[l], (l == 5 ? (size_t)6 * 3 * 2 * 2 * 48 * 8 : (size_t)27 * kCinP[l] * 32) * sizeof(bf16));
+        if (e == cudaSuccess && l >= 1) e = guarded_malloc((void**)&s->wd[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
+        if (e == cudaSuccess && l >= 1) e = guarded_malloc((void**)&s->wdt[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
     }
-    if (e == cudaSuccess) e = cudaMalloc(&s->wt0x, (size_t)9 * kCinP[0] * 32 * sizeof(bf16));
+    if (e == cudaSuccess) e = guarded_malloc((void**)&s->wt0x, (size_t)9 * kCinP[0] * 32 * sizeof(bf16));
     if (e != cudaSuccess || (e = cudaMemset(s->params, 0, off * 4)) != cudaSuccess ||
         (e = cudaMemset(s->m, 0, off * 4)) != cudaSuccess || (e = cudaMemset(s->v, 0, off * 4)) != cudaSuccess) {
         int rc = cuda_fail(e, "surrogate allocation");
@@ -2622,6 +2622,31 @@ int gs_surr_run(gs_surr* s, gs_sim* sim, double F, double k, int64_t nsteps, int
     s->stream = saved_stream;
     if (rep) *rep = r;
     return rc;
+}
+
+int gs_surr_guard_check(gs_surr* s, int64_t* bad)
+{
+    if (!s || !bad) return fail(GS_EINVAL, "NULL argument");
+    GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    std::vector<const void*> bufs = {s->params, s->grads, s->m, s->v, s->wt0x, s->d_err, s->d_loss, s->d_max, s->d_ss,
+                                     s->x0, s->gh, s->gz[0], s->gz[1], s->gd, s->ou, s->ov, s->fk, s->wpart};
+    for (int l = 0; l < kSurrLayers; ++l) {
+        bufs.push_back(s->wf[l]);
+        bufs.push_back(s->wd[l]);
+        bufs.push_back(s->wt[l]);
+        bufs.push_back(s->wdt[l]);
+        bufs.push_back(s->h[l]);
+        if (l < kSurrLayers - 1) bufs.push_back(s->z[l]);
+    }
+    int64_t n = 0;
+    for (const void* p : bufs) {
+        if (!p) continue;
+        const int64_t r = guarded_check(p);
+        if (r < 0) return fail(GS_ECUDA, "reading a guard band failed");
+        n += r;
+    }
+    *bad = n;
+    return GS_OK;
 }
 
 int gs_surr_set_backend(gs_surr* s, int backend)

@@ -132,6 +132,9 @@ _SIGS = {
     "gs_surr_destroy": [_vp],
     "gs_batch_step_noalloc": [_i, _vp, _vp, _vp, _d, _d, _d, _d, _u64, _i, _vp, _i64, _i, _i64, _vp],
     "gs_measure_fp64_fma": [_vp, ctypes.POINTER(_d)],
+    "gs_set_alloc_guard": [_sz],
+    "gs_batch_guard_check": [_vp, ctypes.POINTER(_i64)],
+    "gs_surr_guard_check": [_vp, ctypes.POINTER(_i64)],
     "gs_slab_create_on": [_i, _i, _i, _i, _d, _d, _d, _d, _d, _d, _u64, _i, _vp, _vp, _vp, _vp, _pp],
     "gs_slab_set_stream": [_vp, _vp],
     "gs_slab_init": [_vp],
@@ -777,6 +780,22 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def gs_set_alloc_guard(nbytes: int):
+    _check(lib().gs_set_alloc_guard(int(nbytes)), "gs_set_alloc_guard")
+
+
+def gs_batch_guard_check(b) -> int:
+    n = _i64()
+    _check(lib().gs_batch_guard_check(b, ctypes.byref(n)), "gs_batch_guard_check")
+    return n.value
+
+
+def gs_surr_guard_check(s) -> int:
+    n = _i64()
+    _check(lib().gs_surr_guard_check(s, ctypes.byref(n)), "gs_surr_guard_check")
+    return n.value
 
 
 def gs_measure_fp64_fma(stream=None) -> float:

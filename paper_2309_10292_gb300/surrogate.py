@@ -138,12 +138,50 @@ def time_forward(L: int = 256, reps: int = 5, backend: str = "tcgen05", seed: in
     return {"L": L, "backend": backend, "ms": ms, "tflops": flop / ms / 1e9}
 
 
+# useful FLOP per cell of one training step: the forward pass, the data
+# gradients of layers 5..1 and the weight gradients of all six layers
+TRAIN_FLOP_PER_CELL = (2 * 27 * (4 * 32 + 4 * 32 * 32 + 32 * 2) + 2 * 27 * (2 * 32 + 4 * 32 * 32)
+                       + 2 * 27 * (4 * 32 + 4 * 32 * 32 + 32 * 2))
+
+
+def time_train_step(L: int = 128, N: int = 1, reps: int = 10, backend: str = "tcgen05", seed: int = 0) -> dict:
+    """Time one training step (forward, every gradient, Adam) on N random
+    L^3 pairs after three untimed steps; returns ms per step and useful TFLOP/s."""
+    import torch
+    be = {"auto": gs.GS_SURR_AUTO, "mma": gs.GS_SURR_MMA, "tcgen05": gs.GS_SURR_TCGEN05}[backend]
+    s = gs.Surrogate(inputs.surrogate_init_params(seed=seed, last_scale=0.1))
+    gs.gs_surr_set_backend(s.handle, be)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    u, v, tu, tv = (torch.rand((N, L, L, L), device="cuda", generator=g) * (1.0 if i % 2 == 0 else 0.5)
+                    for i in range(4))
+    F, k = [0.03] * N, [0.05] * N
+    for _ in range(3):
+        s.train_step(u, v, F, k, tu, tv, 1e-5)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        s.train_step(u, v, F, k, tu, tv, 1e-5)
+    b.record(st)
+    gs.gs_surr_sync(s.handle)
+    ms = a.elapsed_time(b) / reps
+    s.close()
+    return {"L": L, "N": N, "backend": backend, "ms_per_step": ms,
+            "tflops": TRAIN_FLOP_PER_CELL * N * L ** 3 / ms / 1e9}
+
+
 if __name__ == "__main__":
     import argparse
     import json
-    ap = argparse.ArgumentParser(description="time the surrogate's forward pass")
+    ap = argparse.ArgumentParser(description="time the surrogate's forward pass or one training step")
     ap.add_argument("--L", type=int, default=256)
+    ap.add_argument("--N", type=int, default=1, help="grids per training step (--train)")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--train", action="store_true", help="time a training step instead of the forward pass")
     ap.add_argument("--backend", default="tcgen05", choices=["auto", "mma", "tcgen05"])
     args = ap.parse_args()
-    print(json.dumps(time_forward(args.L, args.reps, args.backend)))
+    if args.train:
+        print(json.dumps(time_train_step(args.L, args.N, args.reps, args.backend)))
+    else:
+        print(json.dumps(time_forward(args.L, args.reps, args.backend)))

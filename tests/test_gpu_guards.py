@@ -129,3 +129,89 @@ def test_batch_noalloc_stays_inside_its_instances(dtype):
         got = arena[offs[i][2]:offs[i][2] + L ** 3].cpu().numpy().reshape(L, L, L)
         np.testing.assert_array_equal(got, ref.read(i)[0])
     ref.close()
+
+
+# ---------------------------------------------------------------------------
+# Buffers the library allocates itself (gs_set_alloc_guard): the batch's
+# arena and tables, every surrogate buffer
+# ---------------------------------------------------------------------------
+class _LibraryGuards:
+    def __enter__(self):
+        gs.gs_set_alloc_guard(GUARD)
+        return self
+
+    def __exit__(self, *exc):
+        gs.gs_set_alloc_guard(0)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_step_stays_inside_its_arena(dtype):
+    torch = need_cuda()
+    v4 = dtype == "f32"
+    Ls = [8, 12 if v4 else 6, 32, 48, 4 if v4 else 2, 64, 128, 96]
+    F = list(np.linspace(0.01, 0.06, len(Ls)))
+    k = list(np.linspace(0.07, 0.04, len(Ls)))
+    prm = dict(Du=0.2, Dv=0.1, dt=1.0, noise=0.1, seed=3, dtype=dtype)
+    ref = gs.GrayScottBatch(Ls, F, k, **prm)
+    with _LibraryGuards():
+        b = gs.GrayScottBatch(Ls, F, k, **prm)
+    try:
+        assert gs.gs_batch_guard_check(b.handle) == 0
+        for n in (3, 4):
+            b.step(n)
+            ref.step(n)
+            assert gs.gs_batch_guard_check(b.handle) == 0
+        for i in range(len(Ls)):
+            for got, want in zip(b.read(i), ref.read(i)):
+                np.testing.assert_array_equal(got, want)
+    finally:
+        b.close()
+        ref.close()
+
+
+def _guarded_pair(torch, shape):
+    # two FP32 output fields between guard bands (caller-owned outputs)
+    n = int(np.prod(shape))
+    g = GUARD // 4
+    field = -(-n // 64) * 64
+    raw = torch.empty(g + 2 * (field + g), dtype=torch.int32, device="cuda")
+    raw.fill_(POISON["f32"])
+    outs = [raw[g + i * (field + g):g + i * (field + g) + n].view(torch.float32).view(shape) for i in range(2)]
+    guards = [(0, g)] + [(g + i * (field + g) + n, g + (i + 1) * (field + g)) for i in range(2)]
+    return raw, outs, guards
+
+
+@pytest.mark.parametrize("L,backend", [(32, gs.GS_SURR_MMA), (128, gs.GS_SURR_TCGEN05),
+                                       (128, gs.GS_SURR_MMA), (256, gs.GS_SURR_TCGEN05)])
+def test_surrogate_buffers_stay_inside(L, backend):
+    torch = need_cuda()
+    from paper_2309_10292_gb300 import inputs
+    params = inputs.surrogate_init_params(seed=3, last_scale=0.3)
+    g = torch.Generator(device="cuda").manual_seed(L)
+    u = torch.rand((1, L, L, L), device="cuda", generator=g)
+    v = torch.rand((1, L, L, L), device="cuda", generator=g) * 0.5
+    with _LibraryGuards():
+        s = gs.Surrogate(params)
+    ref = gs.Surrogate(params)
+    try:
+        for net in (s, ref):
+            gs.gs_surr_set_backend(net.handle, backend)
+        raw, (uo, vo), guards = _guarded_pair(torch, (1, L, L, L))
+        gs.gs_surr_forward(s.handle, 1, L, u, v, [0.03], [0.05], uo, vo)
+        ru, rv = ref.forward(u, v, [0.03], [0.05])
+        assert gs.gs_surr_guard_check(s.handle) == 0
+        _check_guards(raw, guards, "f32")
+        assert torch.equal(uo, ru) and torch.equal(vo, rv)
+        if L <= 128:  # one training step: every gradient buffer
+            with _LibraryGuards():  # the training workspace is allocated now
+                ls = s.train_step(u, v, [0.03], [0.05], ru, rv, 1e-4)
+            lr_ = ref.train_step(u, v, [0.03], [0.05], ru, rv, 1e-4)
+            assert gs.gs_surr_guard_check(s.handle) == 0
+            # the loss and (on the mma.sync path) the weight gradients are summed
+            # with atomics, in no fixed order
+            assert ls == pytest.approx(lr_, rel=1e-9)
+            np.testing.assert_allclose(gs.gs_surr_get_params(s.handle), gs.gs_surr_get_params(ref.handle),
+                                       rtol=1e-5, atol=1e-8)
+    finally:
+        s.close()
+        ref.close()
