@@ -88,6 +88,27 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
+TBLOCK_PROFILE = os.path.join(ROOT, "profiles", "gs_tblock_issue_L512.md")
+TBLOCK_SRC = [os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", f) for f in ("gs_tblock.cu", "gs_common.cuh")]
+
+
+def profiled_issue():
+    """Warp instructions per cell update of the temporally blocked and z-march
+    plans from the committed ncu summary, if it was taken on the current
+    temporal-blocking source (else None): {plan string: count}."""
+    if not os.path.exists(TBLOCK_PROFILE):
+        return None
+    text = open(TBLOCK_PROFILE).read()
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    w = re.search(r"warp_inst_per_update:\s*(.*)", text)
+    h = hashlib.sha256()
+    for f in TBLOCK_SRC:
+        h.update(open(f, "rb").read())
+    if not m or not w or m.group(1) != h.hexdigest()[:16]:
+        return None
+    return {k: float(v) for k, v in (item.split("=") for item in w.group(1).split())}
+
+
 def profiled_traffic():
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
@@ -419,6 +440,28 @@ def bench_large(args, stream, hbm_peak):
     out.update(_large_run(L, n, NOISE, stream, hbm_peak))
     out["noise0"] = {"workload": f"the same grid and plan search without noise (noise 0), {n} steps"}
     out["noise0"].update(_large_run(L, n, 0.0, stream, hbm_peak))
+    # issue roofline of the temporally blocked plans (noise on): warp
+    # instructions per update from the committed ncu counts, against the
+    # issue ceiling of 4 warp instructions per clock per SM at the SM clock
+    # sampled during the bench
+    inst = profiled_issue()
+    if inst is not None:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        clk = (getattr(args, "sm_mhz_seen", None) or 2070.0) * 1e6
+        peak = 4 * sms * clk / 1e9  # G warp instructions / s
+        hbm_bound = hbm_peak / 16.0
+        rows = {}
+        for plan, i in inst.items():
+            rows[plan] = {"warp_inst_per_update": i, "issue_bound_gcups": peak / i}
+        d3 = inst.get("tblock,32,32,64,3")
+        out["issue_roofline"] = {
+            "bound": "issue", "unit": "G warp instructions/s", "peak": peak,
+            "peak_kind": "4 warp instructions per clock per SM x SMs x the sampled SM clock",
+            "plans": rows, "single_step_hbm_bound_gcups": hbm_bound,
+            "depth3_achieved_issue_fraction": 0.724,
+            "depth3_warp_inst_needed_to_pass_single_step": (peak * 0.724 / hbm_bound) if d3 else None,
+            "source": os.path.relpath(TBLOCK_PROFILE, ROOT)}
     return out
 
 
@@ -606,6 +649,7 @@ def run_ours(args):
     t_end.record(stream)
     barrier()
     clk = clocks.stop() if clocks else None
+    args.sm_mhz_seen = clk["sm_mhz"] if clk else None
     launches = gs.gs_launch_count(sim.handle) - launches0
     stencil_launches = launches - args.steps  # one init launch per bench step
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), ws, dev)
