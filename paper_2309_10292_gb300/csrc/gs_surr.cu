@@ -97,15 +97,15 @@ struct ConvArgs {
     int N, L;
     const bf16* res;    // EPI_HIDDEN: residual h_in [..][32]
     bf16* out;          // EPI_FIRST / EPI_HIDDEN: h_out [..][32]
-    bf16* zout;         // forward: pre-activation z [..][32] (or null)
+    uint32_t* zmask;    // forward (training): ReLU mask, bit c = (pre-activation c > 0), one word a cell (or null)
     const float* su;    // EPI_LAST: state in, u and v planes [N][L^3]
     const float* sv;
     float* ou;          // EPI_LAST: state out
     float* ov;
     float* gh;          // EPI_DGRAD: residual-path gradient [..][32], fp32, in / out
     int gh_acc;         // EPI_DGRAD: 1 -> gh += acc, 0 -> gh = acc
-    const bf16* zprev;  // EPI_DGRAD: z of the layer below (ReLU mask) or null
-    bf16* gz;           // EPI_DGRAD: gz = gh * (zprev > 0)
+    const uint32_t* mprev;  // EPI_DGRAD: ReLU mask words of the layer below
+    bf16* gz;           // EPI_DGRAD: gz = gh * mask
 };
 
 // Work item: (n, z, y-group of 4 rows, x segment).
@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) gs_conv_kernel(const ConvArgs
             for (int hh = 0; hh < 2; ++hh) {
                 const int x = x0 + wseg + mt * 16 + g + hh * 8;
                 const size_t cell = (size_t)n * L3 + ((size_t)z * L + y) * L + x;
+                uint32_t bits = 0;  // this thread's channels of the cell's ReLU mask
+                uint32_t mw = 0;
+                if constexpr (EPI == EPI_DGRAD) mw = a.gz ? a.mprev[cell] : 0u;
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt) {
                     const int ch = nt * 8 + 2 * t;
@@ -220,7 +223,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) gs_conv_kernel(const ConvArgs
                     if constexpr (EPI == EPI_FIRST || EPI == EPI_HIDDEN) {
                         v0 += a.bias[ch];
                         v1 += a.bias[ch + 1];
-                        if (a.zout) *reinterpret_cast<__nv_bfloat162*>(a.zout + cell * 32 + ch) = __floats2bfloat162_rn(v0, v1);
+                        bits |= (v0 > 0.f ? 1u : 0u) << ch;
+                        bits |= (v1 > 0.f ? 1u : 0u) << (ch + 1);
                         float h0 = fmaxf(v0, 0.f), h1 = fmaxf(v1, 0.f);
                         if constexpr (EPI == EPI_HIDDEN) {
                             const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(a.res + cell * 32 + ch);
@@ -242,12 +246,17 @@ __global__ void __launch_bounds__(kConvThreads, 1) gs_conv_kernel(const ConvArgs
                         gp[0] = v0;
                         gp[1] = v1;
                         if (a.gz) {
-                            const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162*>(a.zprev + cell * 32 + ch);
-                            const float m0 = __bfloat162float(zz.x) > 0.f ? v0 : 0.f;
-                            const float m1 = __bfloat162float(zz.y) > 0.f ? v1 : 0.f;
+                            const float m0 = (mw >> ch) & 1u ? v0 : 0.f;
+                            const float m1 = (mw >> (ch + 1)) & 1u ? v1 : 0.f;
                             *reinterpret_cast<__nv_bfloat162*>(a.gz + cell * 32 + ch) = __floats2bfloat162_rn(m0, m1);
                         }
                     }
+                }
+                if constexpr (EPI == EPI_FIRST || EPI == EPI_HIDDEN) {
+                    // the four threads of a quad hold the cell's 32 channels
+                    bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
+                    bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
+                    if (a.zmask && t == 0) a.zmask[cell] = bits;
                 }
             }
         }
@@ -618,17 +627,18 @@ struct ConvTcArgs {
     int N, L;
     const bf16* res;    // unused (the residual comes from the centre slab)
     bf16* out;
-    bf16* zout;
+    uint32_t* zmask;    // training: ReLU mask words (bit c = pre-activation c > 0), or null
     const float* su;
     const float* sv;
     float* ou;
     float* ov;
     // EPI_DGRAD (data gradient: the convolution of gz_l with the tap-flipped,
     // transposed weights of layer l): gh = acc (+ gh when gh_acc), fp32
-    // [..][32]; gz = bf16(gh * (zprev > 0)) for the layer below, [..][32]
+    // [..][32]; gz = bf16(gh * mask) for the layer below, [..][32], with the
+    // mask words the layer below's forward pass stored
     float* gh;
     int gh_acc;
-    const bf16* zprev;
+    const uint32_t* mprev;
     bf16* gz;
     int* err;
     uint64_t timeout_ns;
@@ -1149,12 +1159,12 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
         constexpr int NRES = EPI == EPI_HIDDEN ? NT / 8 : 1;
         uint4 rv[EROWS][NRES];
         float sres[EROWS][2];
-        // EPI_DGRAD: the layer below's pre-activation (bf16, 4 x 16 bytes a
-        // cell) one item ahead; the incoming residual-path gradient (fp32)
-        // is loaded in the epilogue itself (registers)
+        // EPI_DGRAD: the layer below's ReLU mask word one item ahead; the
+        // incoming residual-path gradient (fp32) is loaded in the epilogue
+        // itself (registers)
         constexpr bool DG = EPI == EPI_DGRAD;
         static_assert(!DG || NT == 32, "the data gradient has 32 output channels");
-        uint4 pz[DG ? EROWS : 1][DG ? 4 : 1];
+        uint32_t pm[DG ? EROWS : 1];
         auto cell_of = [&](const Unit& u, int q, int r) -> size_t {
             return (size_t)u.n * L3 + ((size_t)(u.z0 + q) * L + (u.y0 + r)) * L + (u.x0 + x_in_seg);
         };
@@ -1170,8 +1180,7 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                     sres[rr][0] = a.su[cell];
                     sres[rr][1] = a.sv[cell];
                 } else if constexpr (DG) {
-#pragma unroll
-                    for (int j = 0; j < 4; j += 2) gs_ld_v8(a.zprev + cell * 32 + j * 8, pz[rr][j], pz[rr][j + 1]);
+                    pm[rr] = a.mprev[cell];
                 }
             }
         };
@@ -1208,15 +1217,15 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
 #pragma unroll
                     for (int j = 0; j < 8; j += 2) gs_st_v8(a.gh + cell * 32 + j * 4, gout[j], gout[j + 1]);
                     uint4 zo[4];
+                    const uint32_t mw = pm[rr];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const __nv_bfloat162* zb = reinterpret_cast<const __nv_bfloat162*>(&pz[rr][j]);
                         __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&zo[j]);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int c = j * 8 + 2 * e;
-                            const float m0 = __bfloat162float(zb[e].x) > 0.f ? acc[c] : 0.f;
-                            const float m1 = __bfloat162float(zb[e].y) > 0.f ? acc[c + 1] : 0.f;
+                            const float m0 = (mw >> c) & 1u ? acc[c] : 0.f;
+                            const float m1 = (mw >> (c + 1)) & 1u ? acc[c + 1] : 0.f;
                             ob[e] = __floats2bfloat162_rn(m0, m1);
                         }
                     }
@@ -1224,7 +1233,9 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                     for (int j = 0; j < 4; j += 2) gs_st_v8(a.gz + cell * 32 + j * 8, zo[j], zo[j + 1]);
                 } else if constexpr (EPI != EPI_LAST) {  // (the last layer drains in its own loop below)
                     static_assert(NT % 16 == 0, "the epilogue stores 16 channels (32 bytes) at a time");
-                    uint4 ho[NT / 8], zo[NT / 8];
+                    static_assert(NT <= 32, "one mask word a cell");
+                    uint4 ho[NT / 8];
+                    uint32_t bits = 0;
 #pragma unroll
                     for (int j = 0; j < NT / 8; ++j) {
                         float h[8], zv[8];
@@ -1232,6 +1243,7 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                         for (int e = 0; e < 8; ++e) {
                             zv[e] = acc[j * 8 + e] + bias_r[j * 8 + e];
                             h[e] = fmaxf(zv[e], 0.f);
+                            bits |= (zv[e] > 0.f ? 1u : 0u) << (j * 8 + e);
                         }
                         if constexpr (EPI == EPI_HIDDEN) {
                             const __nv_bfloat162* rb = reinterpret_cast<const __nv_bfloat162*>(&rv[rr][j]);
@@ -1242,19 +1254,13 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                             }
                         }
                         __nv_bfloat162* hb = reinterpret_cast<__nv_bfloat162*>(&ho[j]);
-                        __nv_bfloat162* zb = reinterpret_cast<__nv_bfloat162*>(&zo[j]);
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            hb[e] = __floats2bfloat162_rn(h[2 * e], h[2 * e + 1]);
-                            zb[e] = __floats2bfloat162_rn(zv[2 * e], zv[2 * e + 1]);
-                        }
+                        for (int e = 0; e < 4; ++e) hb[e] = __floats2bfloat162_rn(h[2 * e], h[2 * e + 1]);
                     }
                     // 32-byte stores: each writes a whole sector of the cell's 64 bytes
 #pragma unroll
-                    for (int j = 0; j < NT / 8; j += 2) {
-                        gs_st_v8(a.out + cell * 32 + j * 8, ho[j], ho[j + 1]);
-                        if (a.zout) gs_st_v8(a.zout + cell * 32 + j * 8, zo[j], zo[j + 1]);
-                    }
+                    for (int j = 0; j < NT / 8; j += 2) gs_st_v8(a.out + cell * 32 + j * 8, ho[j], ho[j + 1]);
+                    if (a.zmask) a.zmask[cell] = bits;
                 }
             }
         };
@@ -1872,7 +1878,7 @@ struct gs_surr {
     bool train_ws = false;
     bf16* x0 = nullptr;
     bf16* h[kSurrLayers] = {};  // h[1..5] (training) / h[1], h[2] ping-pong (inference)
-    bf16* z[kSurrLayers - 1] = {};
+    uint32_t* zm[kSurrLayers - 1] = {};  // training: ReLU mask words of layers 0..4
     float* gh = nullptr;
     bf16* gz[2] = {};
     bf16* gd = nullptr;
@@ -1905,7 +1911,7 @@ void free_ws(gs_surr* s)
 {
     guarded_free(s->x0);
     for (auto& p : s->h) { guarded_free(p); p = nullptr; }
-    for (auto& p : s->z) { guarded_free(p); p = nullptr; }
+    for (auto& p : s->zm) { guarded_free(p); p = nullptr; }
     guarded_free(s->gh);
     guarded_free(s->gz[0]);
     guarded_free(s->gz[1]);
@@ -1932,7 +1938,7 @@ int ensure_ws(gs_surr* s, int N, int L, bool train)
     const int nh = train ? 5 : 2;
     for (int l = 1; l <= nh; ++l) ALLOC(s->h[l], cells * 32 * sizeof(bf16));
     if (train) {
-        for (int l = 0; l < 5; ++l) ALLOC(s->z[l], cells * 32 * sizeof(bf16));
+        for (int l = 0; l < 5; ++l) ALLOC(s->zm[l], cells * sizeof(uint32_t));
         ALLOC(s->gh, cells * 32 * sizeof(float));
         ALLOC(s->gz[0], cells * 32 * sizeof(bf16));
         ALLOC(s->gz[1], cells * 32 * sizeof(bf16));
@@ -2114,14 +2120,14 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
         t.w = xtaps ? s->wt0x : s->wt[0];
         t.bias = s->params + s->boff[0];
         t.out = s->h[1];
-        t.zout = train ? s->z[0] : nullptr;
+        t.zmask = train ? s->zm[0] : nullptr;
         if ((rc = xtaps ? tc_launch<16, 32, EPI_FIRST, true>(s, t) : tc_launch<16, 32, EPI_FIRST>(s, t))) return rc;
         for (int l = 1; l <= 4; ++l) {
             t.in = train ? s->h[l] : s->h[1 + ((l - 1) & 1)];
             t.out = train ? s->h[l + 1] : s->h[1 + (l & 1)];
             t.w = s->wt[l];
             t.bias = s->params + s->boff[l];
-            t.zout = train ? s->z[l] : nullptr;
+            t.zmask = train ? s->zm[l] : nullptr;
             if ((rc = tc_launch<32, 32, EPI_HIDDEN>(s, t))) return rc;
         }
         ConvTcArgs b{};
@@ -2144,7 +2150,7 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
     a.w = s->wf[0];
     a.bias = s->params + s->boff[0];
     a.out = s->h[1];
-    a.zout = train ? s->z[0] : nullptr;
+    a.zmask = train ? s->zm[0] : nullptr;
     if ((rc = conv_launch<16, 32, EPI_FIRST>(s, a))) return rc;
     // layers 1..4
     for (int l = 1; l <= 4; ++l) {
@@ -2155,7 +2161,7 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
         a.w = s->wf[l];
         a.bias = s->params + s->boff[l];
         a.out = hout;
-        a.zout = train ? s->z[l] : nullptr;
+        a.zmask = train ? s->zm[l] : nullptr;
         if ((rc = conv_launch<32, 32, EPI_HIDDEN>(s, a))) return rc;
     }
     // layer 5: state update
@@ -2215,7 +2221,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
             t.w = s->wdt[l];
             t.gh = s->gh;
             t.gh_acc = gh_acc;
-            t.zprev = s->z[l - 1];
+            t.mprev = s->zm[l - 1];
             t.gz = gz;
             return l == 5 ? tc_launch<16, 32, EPI_DGRAD>(s, t) : tc_launch<32, 32, EPI_DGRAD>(s, t);
         }
@@ -2226,7 +2232,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
         d.w = s->wd[l];
         d.gh = s->gh;
         d.gh_acc = gh_acc;
-        d.zprev = s->z[l - 1];
+        d.mprev = s->zm[l - 1];
         d.gz = gz;
         int r = l == 5 ? conv_launch<16, 32, EPI_DGRAD>(s, d) : conv_launch<32, 32, EPI_DGRAD>(s, d);
         if (r) return r;
@@ -2636,7 +2642,7 @@ int gs_surr_guard_check(gs_surr* s, int64_t* bad)
         bufs.push_back(s->wt[l]);
         bufs.push_back(s->wdt[l]);
         bufs.push_back(s->h[l]);
-        if (l < kSurrLayers - 1) bufs.push_back(s->z[l]);
+        if (l < kSurrLayers - 1) bufs.push_back(s->zm[l]);
     }
     int64_t n = 0;
     for (const void* p : bufs) {
