@@ -285,11 +285,11 @@ def surrogate_backward(cache, dout: np.ndarray, *, emulate_bf16: bool = False, r
 
     Chain rule through the network of surrogate_forward: for the residual
     layers h_{l+1} = h_l + relu(z_l), dL/dh_l = dL/dh_{l+1} + conv_l^T(dz_l)
-    with dz_l = dL/dh_{l+1} * [z_l > 0].  With emulate_bf16 the two kinds of
-    back-propagated values the GPU stores in bfloat16 are rounded where it
-    rounds them: dL/dout (its storage has the first layer's 16-channel
-    format) and every dz_l; the residual-path sums dL/dh_l stay unrounded
-    (FP32 on the GPU).  With return_dh the list [dL/dh_1, ..., dL/dh_5] is
+    with dz_l = dL/dh_{l+1} * [z_l > 0].  With emulate_bf16 the values the
+    GPU stores in bfloat16 are rounded where it rounds them: dL/dout (its
+    storage has the first layer's 16-channel format) and every residual-path
+    sum dL/dh_l; dz_l, a masked copy of a stored dL/dh_{l+1}, is then
+    bfloat16 already.  With return_dh the list [dL/dh_1, ..., dL/dh_5] is
     returned as well.
     """
     hs, zs, ws = cache["hs"], cache["zs"], cache["ws"]
@@ -298,15 +298,15 @@ def surrogate_backward(cache, dout: np.ndarray, *, emulate_bf16: bool = False, r
     dout = _q(dout, emulate_bf16)
     dw, db = conv3d_bwd_weight(hs[5], dout)
     grads[5] = (dw, db)
-    dh = conv3d_bwd_data(dout, ws[5])
+    dh = _q(conv3d_bwd_data(dout, ws[5]), emulate_bf16)
     dhs[5] = dh
     for l in range(4, 0, -1):
-        dz = _q(dh * (zs[l] > 0.0), emulate_bf16)
+        dz = dh * (zs[l] > 0.0)
         dw, db = conv3d_bwd_weight(hs[l], dz)
         grads[l] = (dw, db)
-        dh = dh + conv3d_bwd_data(dz, ws[l])
+        dh = _q(dh + conv3d_bwd_data(dz, ws[l]), emulate_bf16)
         dhs[l] = dh
-    dz = _q(dh * (zs[0] > 0.0), emulate_bf16)
+    dz = dh * (zs[0] > 0.0)
     dw, db = conv3d_bwd_weight(hs[0], dz)
     grads[0] = (dw, db)
     if return_dh:

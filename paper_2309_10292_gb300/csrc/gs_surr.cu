@@ -102,7 +102,7 @@ struct ConvArgs {
     const float* sv;
     float* ou;          // EPI_LAST: state out
     float* ov;
-    float* gh;          // EPI_DGRAD: residual-path gradient [..][32], fp32, in / out
+    bf16* gh;           // EPI_DGRAD: residual-path gradient [..][32], bf16, in / out
     int gh_acc;         // EPI_DGRAD: 1 -> gh += acc, 0 -> gh = acc
     const uint32_t* mprev;  // EPI_DGRAD: ReLU mask words of the layer below
     bf16* gz;           // EPI_DGRAD: gz = gh * mask
@@ -238,17 +238,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) gs_conv_kernel(const ConvArgs
                             a.ov[cell] = a.sv[cell] + (v1 + a.bias[1]);
                         }
                     } else {  // EPI_DGRAD
-                        float* gp = a.gh + cell * 32 + ch;
+                        __nv_bfloat162* gp = reinterpret_cast<__nv_bfloat162*>(a.gh + cell * 32 + ch);
                         if (a.gh_acc) {
-                            v0 += gp[0];
-                            v1 += gp[1];
+                            const __nv_bfloat162 old = *gp;
+                            v0 = __bfloat162float(old.x) + v0;
+                            v1 = __bfloat162float(old.y) + v1;
                         }
-                        gp[0] = v0;
-                        gp[1] = v1;
+                        const __nv_bfloat162 gn = __floats2bfloat162_rn(v0, v1);
+                        *gp = gn;
                         if (a.gz) {
-                            const float m0 = (mw >> ch) & 1u ? v0 : 0.f;
-                            const float m1 = (mw >> (ch + 1)) & 1u ? v1 : 0.f;
-                            *reinterpret_cast<__nv_bfloat162*>(a.gz + cell * 32 + ch) = __floats2bfloat162_rn(m0, m1);
+                            __nv_bfloat162 m = gn;
+                            if (!((mw >> ch) & 1u)) m.x = __float2bfloat16_rn(0.f);
+                            if (!((mw >> (ch + 1)) & 1u)) m.y = __float2bfloat16_rn(0.f);
+                            *reinterpret_cast<__nv_bfloat162*>(a.gz + cell * 32 + ch) = m;
                         }
                     }
                 }
@@ -527,6 +529,12 @@ __global__ void gs_bias_grad_kernel(const bf16* __restrict__ g, long long cells,
     if (threadIdx.x < cout) atomicAdd(db + threadIdx.x, part[threadIdx.x]);
 }
 
+__global__ void gs_bf16_to_f32_kernel(const bf16* __restrict__ a, long long n, float* __restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(a[i]);
+}
+
 // Adam (Kingma & Ba 2015, Algorithm 1) on fp32 master parameters.
 __global__ void gs_adam_kernel(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m,
                                float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
@@ -633,10 +641,10 @@ struct ConvTcArgs {
     float* ou;
     float* ov;
     // EPI_DGRAD (data gradient: the convolution of gz_l with the tap-flipped,
-    // transposed weights of layer l): gh = acc (+ gh when gh_acc), fp32
-    // [..][32]; gz = bf16(gh * mask) for the layer below, [..][32], with the
-    // mask words the layer below's forward pass stored
-    float* gh;
+    // transposed weights of layer l): gh = bf16(acc (+ gh when gh_acc)),
+    // [..][32]; gz = gh * mask for the layer below, [..][32], with the mask
+    // words the layer below's forward pass stored
+    bf16* gh;
     int gh_acc;
     const uint32_t* mprev;
     bf16* gz;
@@ -1185,16 +1193,16 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
             }
         };
         auto epilogue = [&](int set, const Unit& u, int q) {
-            // EPI_DGRAD: the incoming gh of all this warp's rows, issued before the
-            // first TMEM load so their latencies overlap
-            uint4 gin[DG ? EROWS : 1][DG ? 8 : 1];
+            // EPI_DGRAD: the incoming gh (bf16) of all this warp's rows, issued
+            // before the first TMEM load so their latencies overlap
+            uint4 gin[DG ? EROWS : 1][DG ? 4 : 1];
             if constexpr (DG) {
                 if (a.gh_acc) {
 #pragma unroll
                     for (int rr = 0; rr < EROWS; ++rr) {
                         const size_t cell = cell_of(u, q, r0 + rr);
 #pragma unroll
-                        for (int j = 0; j < 8; j += 2) gs_ld_v8(a.gh + cell * 32 + j * 4, gin[rr][j], gin[rr][j + 1]);
+                        for (int j = 0; j < 4; j += 2) gs_ld_v8(a.gh + cell * 32 + j * 8, gin[rr][j], gin[rr][j + 1]);
                     }
                 }
             }
@@ -1205,30 +1213,30 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
                 float acc[NT];
                 tc_ld<NT>(lane_base + (uint32_t)(set * ACC_COLS + r * NT), acc);
                 if constexpr (DG) {
-                    if (a.gh_acc) {
-                        const float* go = reinterpret_cast<const float*>(&gin[rr][0]);
-#pragma unroll
-                        for (int j = 0; j < NT; ++j) acc[j] += go[j];
-                    }
-                    uint4 gout[8];
-                    float* gf = reinterpret_cast<float*>(&gout[0]);
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) gf[j] = acc[j];
-#pragma unroll
-                    for (int j = 0; j < 8; j += 2) gs_st_v8(a.gh + cell * 32 + j * 4, gout[j], gout[j + 1]);
-                    uint4 zo[4];
+                    // gh = bf16(gh + acc); gz = gh * mask (exact in bf16)
+                    uint4 gout[4], zo[4];
                     const uint32_t mw = pm[rr];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
+                        const __nv_bfloat162* gi = reinterpret_cast<const __nv_bfloat162*>(&gin[rr][j]);
+                        __nv_bfloat162* go = reinterpret_cast<__nv_bfloat162*>(&gout[j]);
                         __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&zo[j]);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int c = j * 8 + 2 * e;
-                            const float m0 = (mw >> c) & 1u ? acc[c] : 0.f;
-                            const float m1 = (mw >> (c + 1)) & 1u ? acc[c + 1] : 0.f;
-                            ob[e] = __floats2bfloat162_rn(m0, m1);
+                            float g0 = acc[c], g1 = acc[c + 1];
+                            if (a.gh_acc) {
+                                g0 = __bfloat162float(gi[e].x) + g0;
+                                g1 = __bfloat162float(gi[e].y) + g1;
+                            }
+                            go[e] = __floats2bfloat162_rn(g0, g1);
+                            const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+                            ob[e].x = (mw >> c) & 1u ? go[e].x : zero;
+                            ob[e].y = (mw >> (c + 1)) & 1u ? go[e].y : zero;
                         }
                     }
+#pragma unroll
+                    for (int j = 0; j < 4; j += 2) gs_st_v8(a.gh + cell * 32 + j * 8, gout[j], gout[j + 1]);
 #pragma unroll
                     for (int j = 0; j < 4; j += 2) gs_st_v8(a.gz + cell * 32 + j * 8, zo[j], zo[j + 1]);
                 } else if constexpr (EPI != EPI_LAST) {  // (the last layer drains in its own loop below)
@@ -1879,7 +1887,7 @@ struct gs_surr {
     bf16* x0 = nullptr;
     bf16* h[kSurrLayers] = {};  // h[1..5] (training) / h[1], h[2] ping-pong (inference)
     uint32_t* zm[kSurrLayers - 1] = {};  // training: ReLU mask words of layers 0..4
-    float* gh = nullptr;
+    bf16* gh = nullptr;  // training: the residual-path gradient dL/dh_l, bf16 [cells][32]
     bf16* gz[2] = {};
     bf16* gd = nullptr;
     float* ou = nullptr;
@@ -1939,7 +1947,7 @@ int ensure_ws(gs_surr* s, int N, int L, bool train)
     for (int l = 1; l <= nh; ++l) ALLOC(s->h[l], cells * 32 * sizeof(bf16));
     if (train) {
         for (int l = 0; l < 5; ++l) ALLOC(s->zm[l], cells * sizeof(uint32_t));
-        ALLOC(s->gh, cells * 32 * sizeof(float));
+        ALLOC(s->gh, cells * 32 * sizeof(bf16));
         ALLOC(s->gz[0], cells * 32 * sizeof(bf16));
         ALLOC(s->gz[1], cells * 32 * sizeof(bf16));
         ALLOC(s->gd, cells * 16 * sizeof(bf16));
@@ -2178,14 +2186,14 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
     return conv_launch<32, 8, EPI_LAST>(s, b);
 }
 
-// checking aid: copy the residual-path gradient gh = dL/dh_l (fp32) into
-// slot l - 1 of the caller's trace array
+// checking aid: copy the residual-path gradient gh = dL/dh_l (bf16) as FP32
+// into slot l - 1 of the caller's trace array
 int trace_dh(gs_surr* s, int l, long long cells)
 {
     if (!s->trace_dh) return GS_OK;
-    const size_t n = (size_t)cells * 32;
-    GS_CUDA_TRY(cudaMemcpyAsync(s->trace_dh + (size_t)(l - 1) * n, s->gh, n * sizeof(float), cudaMemcpyDeviceToDevice,
-                                s->stream));
+    const long long n = cells * 32;
+    gs_bf16_to_f32_kernel<<<grid1d(n, 256), 256, 0, s->stream>>>(s->gh, n, s->trace_dh + (size_t)(l - 1) * n);
+    GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
 
