@@ -460,9 +460,13 @@ __global__ void gs_wprep_kernel(const float* __restrict__ w, int cin, int cout, 
 // loss = sum (out - tgt)^2 / count;  gd[cell][0..1] = 2 (out - tgt) / count, rest 0;
 // db[0..1] += sum over cells of the stored (bf16) gd[cell][0..1] (the last
 // layer's bias gradient; db may be null)
+//
+// With L > 0 the stored gradient is x-tap packed for the tensor-core path:
+// channels 2 d + c (d < 3) hold channel c of the x neighbour x + d - 1
+// (periodic in each row of L cells), the rest 0; db stays the cells' own sums.
 __global__ void gs_mse_kernel(const float* __restrict__ ou, const float* __restrict__ ov, const float* __restrict__ tu,
                               const float* __restrict__ tv, long long total, double inv_count, bf16* __restrict__ gd,
-                              double* __restrict__ loss, float* __restrict__ db)
+                              double* __restrict__ loss, float* __restrict__ db, int L)
 {
     // FP32 arithmetic per cell (GB300's FP64 pipe is narrow); 2 / count is a
     // power of two whenever the cell count is, and the per-thread partial
@@ -479,7 +483,21 @@ __global__ void gs_mse_kernel(const float* __restrict__ ou, const float* __restr
         su += __bfloat162float(c01.x);
         sv += __bfloat162float(c01.y);
         uint4 first = zero;
-        first.x = *reinterpret_cast<const uint32_t*>(&c01);
+        if (L > 0) {
+            const int x = (int)(i % L);
+            const long long row = i - x;
+            const long long il = row + (x == 0 ? L - 1 : x - 1), ir = row + (x == L - 1 ? 0 : x + 1);
+            __nv_bfloat162 l01, r01;
+            l01.x = __float2bfloat16_rn((ou[il] - tu[il]) * scale);
+            l01.y = __float2bfloat16_rn((ov[il] - tv[il]) * scale);
+            r01.x = __float2bfloat16_rn((ou[ir] - tu[ir]) * scale);
+            r01.y = __float2bfloat16_rn((ov[ir] - tv[ir]) * scale);
+            first.x = *reinterpret_cast<const uint32_t*>(&l01);
+            first.y = *reinterpret_cast<const uint32_t*>(&c01);
+            first.z = *reinterpret_cast<const uint32_t*>(&r01);
+        } else {
+            first.x = *reinterpret_cast<const uint32_t*>(&c01);
+        }
         gs_st_v8(gd + i * 16, first, zero);  // 32 bytes: the whole cell
     }
     double local = lf;
@@ -1414,10 +1432,20 @@ GS_HD uint32_t tc_idesc_mn(int n)
            ((uint32_t)(128 >> 4) << 24);
 }
 
-template <int HC, int GC>
+// XTS (x-tap packed operands; one MMA per K step covers the three dx taps):
+//   0  none;
+//   1  A is the first layer's packed input: channel 4 d + c of cell x holds
+//      channel c of cell x + d - 1 (d < 3), so M row 16 j + 4 d + c is
+//      (dy = j - 1, dx = d - 1, ci = c);
+//   2  B is the last layer's packed dL/dout: channel 2 d + c of cell x holds
+//      channel c of cell x + d - 1, so N column 2 d + c pairs input cell x
+//      with gradient cell x + d - 1, i.e. dx = 1 - d.
+template <int HC, int GC, int XTS>
 __global__ void __launch_bounds__(kWgTcThreads, 1) gs_wgrad_tc_kernel(const __grid_constant__ WgTcArgs a)
 {
     static_assert((HC == 32 || HC == 16) && (GC == 32 || GC == 16), "16 or 32 channels");
+    static_assert(XTS == 0 || (XTS == 1 && HC == 16) || (XTS == 2 && GC == 16), "x-tap packing of a 16-channel operand");
+    constexpr int NDX = XTS ? 1 : 3;  // dx column blocks in TMEM (one when a packed operand carries dx)
     constexpr int MB = 128 / HC;                          // M blocks (slab rows) per MMA
     constexpr uint32_t HROWB = kTcRowCells * HC * 2;     // bytes of one input-slab row
     constexpr uint32_t HSLAB = (kWgRows + 2) * HROWB;
@@ -1425,7 +1453,7 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) gs_wgrad_tc_kernel(const __gr
     constexpr uint32_t GSLOT = kWgRows * GROWB;
     constexpr uint32_t HLAY = HC == 32 ? 4u : 6u, GLAY = GC == 32 ? 4u : 6u;
     constexpr uint32_t HATOM = HC == 32 ? 512u : 256u, GATOM = GC == 32 ? 512u : 256u;
-    constexpr uint32_t ACOLS = 9 * GC;                    // accumulator columns (3 dx x 3 dz x GC)
+    constexpr uint32_t ACOLS = NDX * 3 * GC;              // accumulator columns (dx blocks x 3 dz x GC)
     constexpr uint32_t TMEM_COLS = ACOLS <= 256 ? 256 : 512;
     constexpr int MMAW = 4, PRODW = 5;
     // blocks j >= 3 of the last slab read up to MB - 3 rows past it: the
@@ -1607,12 +1635,14 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) gs_wgrad_tc_kernel(const __gr
                     const uint32_t arow = hbase + hs * HSLAB + i * HROWB;
                     const uint32_t brow = gbase + gslot * GSLOT + i * GROWB;
 #pragma unroll
-                    for (int dxi = 0; dxi < 3; ++dxi) {
-                        const uint32_t dcol = tmem + (uint32_t)(dxi * 3 * GC + b_lo * GC);
+                    for (int dxc = 0; dxc < NDX; ++dxc) {
+                        // with a packed operand the input cell is not shifted (dx in the channels)
+                        const int shift = XTS ? 0 : dxc - 1;
+                        const uint32_t dcol = tmem + (uint32_t)(dxc * 3 * GC + b_lo * GC);
 #pragma unroll
                         for (int ks = 0; ks < kTcCells / 16; ++ks) {
                             // output cell x0 + 16 ks + k reads input cell x0 + 16 ks + k + dx
-                            const uint64_t ad = tc_desc_lay(arow + (uint32_t)(kTcRowX0 + 16 * ks + dxi - 1) * HC * 2,
+                            const uint64_t ad = tc_desc_lay(arow + (uint32_t)(kTcRowX0 + 16 * ks + shift) * HC * 2,
                                                             HROWB, 8 * HC * 2, HLAY);
                             const uint64_t bd = tc_desc_lay(brow + (uint32_t)(16 * ks) * GC * 2, GSLOT, 8 * GC * 2, GLAY);
                             tc_mma_if(leader, dcol, ad, bd, idesc, 1u);
@@ -1679,15 +1709,17 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) gs_wgrad_tc_kernel(const __gr
             // TMEM lane m = 32 warp + lane is M row m: block j = m / HC (dy = j - 1), channel ci = m % HC
             const int m = warp * 32 + lane;
             const int j = m / HC, ci = m % HC;
+            float* const part = a.part + (size_t)blockIdx.x * (27 * HC * GC + GC);
 #pragma unroll 1
-            for (int dxi = 0; dxi < 3; ++dxi)
+            for (int dxc = 0; dxc < NDX; ++dxc)
 #pragma unroll 1
                 for (int b = 0; b < 3; ++b) {
                     float v[GC];
-                    tc_ld<GC>(lane_base + (uint32_t)(dxi * 3 * GC + b * GC), v);
-                    if (j <= 2) {
-                        const int tap = 9 * (2 - b) + 3 * j + dxi;  // dz = 1 - b, dy = j - 1, dx = dxi - 1
-                        float* dst = a.part + (size_t)blockIdx.x * (27 * HC * GC + GC) + ((size_t)tap * HC + ci) * GC;
+                    tc_ld<GC>(lane_base + (uint32_t)(dxc * 3 * GC + b * GC), v);
+                    if (j > 2) continue;
+                    if constexpr (XTS == 0) {
+                        const int tap = 9 * (2 - b) + 3 * j + dxc;  // dz = 1 - b, dy = j - 1, dx = dxc - 1
+                        float* dst = part + ((size_t)tap * HC + ci) * GC;
 #pragma unroll
                         for (int e = 0; e < GC; e += 8) {
                             uint4 lo, hi;
@@ -1700,6 +1732,22 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) gs_wgrad_tc_kernel(const __gr
                             hi.z = __float_as_uint(v[e + 6]);
                             hi.w = __float_as_uint(v[e + 7]);
                             gs_st_v8(dst + e, lo, hi);
+                        }
+                    } else if constexpr (XTS == 1) {
+                        // packed input channel ci = 4 d + c: dx = d - 1, input channel c
+                        const int d = ci / 4, c = ci % 4;
+                        if (d < 3) {
+                            float* dst = part + ((size_t)(9 * (2 - b) + 3 * j + d) * HC + c) * GC;
+#pragma unroll
+                            for (int e = 0; e < GC; ++e) dst[e] = v[e];
+                        }
+                    } else {
+                        // packed gradient column 2 d + co: dx = 1 - d, output channel co
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            float* dst = part + ((size_t)(9 * (2 - b) + 3 * j + (2 - d)) * HC + ci) * GC;
+                            dst[0] = v[2 * d];
+                            dst[1] = v[2 * d + 1];
                         }
                     }
                 }
@@ -1716,8 +1764,16 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) gs_wgrad_tc_kernel(const __gr
                 s1 += dbs[g * NPAIR + tid][1];
             }
             float* dst = a.part + (size_t)blockIdx.x * (27 * HC * GC + GC) + 27 * HC * GC;
-            dst[2 * tid] = s0;
-            dst[2 * tid + 1] = s1;
+            if constexpr (XTS == 2) {
+                // the packed dL/dout holds each cell's own values in channels 2, 3 (d = 1)
+                if (tid == 1) {
+                    dst[0] = s0;
+                    dst[1] = s1;
+                }
+            } else {
+                dst[2 * tid] = s0;
+                dst[2 * tid + 1] = s1;
+            }
         }
     }
     tc_fence_before();
@@ -1814,6 +1870,28 @@ __global__ void gs_wprep_tc_dgrad_kernel(const float* __restrict__ w, int cin, i
     }
 }
 
+// the last layer's data-gradient weights for x-tap packed dL/dout (channels
+// 2 d + c hold channel c of cell x + d - 1): [3 dz][2 chunks][3 nt][8], K
+// index k = 2 d + c (k < 6), the three dy taps side by side along N
+__global__ void gs_wprep_tc_dgrad_xtaps_kernel(const float* __restrict__ w, int cin, int cout, int nt,
+                                               bf16* __restrict__ wt)
+{
+    const int nn = 3 * nt;
+    const int total = 3 * 2 * nn * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i % 8;
+        const int n = (i / 8) % nn;
+        const int j = (i / (8 * nn)) % 2;
+        const int dzi = i / (8 * nn * 2);
+        const int kx = j * 8 + e, d = kx / 2, co = kx % 2;
+        const int dyi = 2 - n / nt;
+        const int ci = n % nt;
+        const int tap = dzi * 9 + dyi * 3 + d;
+        const float val = (kx < 6 && ci < cin && co < cout) ? w[((size_t)(26 - tap) * cin + ci) * cout + co] : 0.f;
+        wt[i] = __float2bfloat16_rn(val);
+    }
+}
+
 // the last layer's weights for its dz-stacked schedule (EPI_LAST in
 // gs_conv_tc_kernel): [6 slab rows][3 dx][2 K steps][2 chunks][48][8], row
 // n = 16 b + 2 r + co (2 r + co < 8, the rest zero): block b feeds output
@@ -1878,6 +1956,7 @@ struct gs_surr {
     bf16* wt[kSurrLayers] = {};  // tcgen05 B layout [3 dz][3 dx][CINP/8][3 NT][8]
     bf16* wt0x = nullptr;        // the first layer's for x-tap packed input [3 dz][2][3 NT][8]
     bf16* wdt[kSurrLayers] = {}; // tcgen05 B layout of the data gradient (layers 1..5)
+    bf16* wdt5x = nullptr;       // the last layer's, for x-tap packed dL/dout [3 dz][2][3 NT][8]
     bool wdirty = true;
     int backend = 0;             // 0 auto (tcgen05 when L % 128 == 0), 1 mma.sync, 2 tcgen05
     int* d_err = nullptr;
@@ -2000,7 +2079,7 @@ int wgrad_launch(gs_surr* s, WgArgs a)
 
 // weight and bias gradients on the tensor cores: h (HC channels), g (GC
 // channels) -> dw [27][cin][cout], db [cout] (overwritten)
-template <int HC, int GC>
+template <int HC, int GC, int XTS>
 int wgrad_tc_launch(gs_surr* s, int N, int L, const bf16* h, const bf16* g, int cin, int cout, float* dw, float* db)
 {
     constexpr uint32_t HSLAB = (kWgRows + 2) * kTcRowCells * HC * 2;
@@ -2014,7 +2093,7 @@ int wgrad_tc_launch(gs_surr* s, int N, int L, const bf16* h, const bf16* g, int 
         encode_act_4d(&a.map_hhalo, h, HC, L, (long long)N * L, HC, 8, HC == 32 ? 64 : 32) != CUDA_SUCCESS ||
         encode_act_4d(&a.map_g, g, GC, L, (long long)N * L, GC, kTcCells, GC == 32 ? 64 : 32) != CUDA_SUCCESS)
         return fail(GS_ECUDA, "cuTensorMapEncodeTiled failed for the weight-gradient maps");
-    auto k = gs_wgrad_tc_kernel<HC, GC>;
+    auto k = gs_wgrad_tc_kernel<HC, GC, XTS>;
     GS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWgTcThreads, smem));
@@ -2089,6 +2168,9 @@ int prep_weights(gs_surr* s)
     }
     gs_wprep_tc_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[0], kChan[0], kChan[1], 32, s->wt0x);
     GS_CUDA_TRY(cudaGetLastError());
+    gs_wprep_tc_dgrad_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[5], kChan[5], kChan[6], 32, s->wdt5x);
+    s->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
     s->wdirty = false;
     return GS_OK;
@@ -2113,9 +2195,10 @@ int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo,
     const long long cells = (long long)N * L * L * L;
     const bool tc = s->backend != 1 && L % kTcCells == 0;
     if (s->backend == 2 && !tc) return fail(GS_EINVAL, "the tcgen05 path needs L %% 128 == 0 (L=%d)", L);
-    // inference on the tensor cores packs the x taps into the first layer's
-    // input; training keeps the plain layout, which its weight gradient reads
-    const bool xtaps = tc && !train;
+    // the tensor-core path packs the x taps into the first layer's input
+    // (its weight gradient reads the packed form too); mma.sync keeps the
+    // plain layout
+    const bool xtaps = tc;
     gs_pack_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(u, v, s->fk, s->x0, (long long)L * L * L, N, L,
                                                               xtaps ? 1 : 0);
     GS_CUDA_TRY(cudaGetLastError());
@@ -2207,7 +2290,8 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     GS_CUDA_TRY(cudaMemsetAsync(s->grads, 0, s->np * sizeof(float), s->stream));
     GS_CUDA_TRY(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
     gs_mse_kernel<<<grid1d(cells, 256), 256, 0, s->stream>>>(s->ou, s->ov, tu, tv, cells, 1.0 / (2.0 * cells), s->gd,
-                                                            s->d_loss, tc ? nullptr : s->grads + s->boff[5]);
+                                                            s->d_loss, tc ? nullptr : s->grads + s->boff[5],
+                                                            tc ? L : 0);
     GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
     int rc;
@@ -2231,7 +2315,11 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
             t.gh_acc = gh_acc;
             t.mprev = s->zm[l - 1];
             t.gz = gz;
-            return l == 5 ? tc_launch<16, 32, EPI_DGRAD>(s, t) : tc_launch<32, 32, EPI_DGRAD>(s, t);
+            if (l == 5) {
+                t.w = s->wdt5x;  // dL/dout is x-tap packed on this path
+                return tc_launch<16, 32, EPI_DGRAD, true>(s, t);
+            }
+            return tc_launch<32, 32, EPI_DGRAD>(s, t);
         }
         ConvArgs d{};
         d.N = N;
@@ -2256,7 +2344,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     w.cin = 32;
     w.cout = 2;
     w.dw = s->grads + s->woff[5];
-    if ((rc = tc ? wgrad_tc_launch<32, 16>(s, N, L, s->h[5], s->gd, 32, 2, w.dw, s->grads + s->boff[5]) : wgrad_launch<32, 8>(s, w))) return rc;
+    if ((rc = tc ? wgrad_tc_launch<32, 16, 2>(s, N, L, s->h[5], s->gd, 32, 2, w.dw, s->grads + s->boff[5]) : wgrad_launch<32, 8>(s, w))) return rc;
     if ((rc = dgrad(5, s->gd, 0, s->gz[0]))) return rc;
     if ((rc = trace_dh(s, 5, cells))) return rc;
     int cur = 0;
@@ -2267,7 +2355,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
         w.cin = 32;
         w.cout = 32;
         w.dw = s->grads + s->woff[l];
-        if ((rc = tc ? wgrad_tc_launch<32, 32>(s, N, L, s->h[l], s->gz[cur], 32, 32, w.dw, s->grads + s->boff[l]) : wgrad_launch<32, 32>(s, w)))
+        if ((rc = tc ? wgrad_tc_launch<32, 32, 0>(s, N, L, s->h[l], s->gz[cur], 32, 32, w.dw, s->grads + s->boff[l]) : wgrad_launch<32, 32>(s, w)))
             return rc;
         if ((rc = dgrad(l, s->gz[cur], 1, s->gz[cur ^ 1]))) return rc;
         if ((rc = trace_dh(s, l, cells))) return rc;
@@ -2280,7 +2368,7 @@ int backward(gs_surr* s, int N, int L, const float* tu, const float* tv, double*
     w.cin = 4;
     w.cout = 32;
     w.dw = s->grads + s->woff[0];
-    if ((rc = tc ? wgrad_tc_launch<16, 32>(s, N, L, s->x0, s->gz[cur], 4, 32, w.dw, s->grads + s->boff[0]) : wgrad_launch<16, 32>(s, w)))
+    if ((rc = tc ? wgrad_tc_launch<16, 32, 1>(s, N, L, s->x0, s->gz[cur], 4, 32, w.dw, s->grads + s->boff[0]) : wgrad_launch<16, 32>(s, w)))
         return rc;
     if (loss) GS_CUDA_TRY(cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     return gs_surr_sync(s);
@@ -2342,6 +2430,7 @@ int gs_surr_destroy(gs_surr* s)
         guarded_free(s->wdt[l]);
     }
     guarded_free(s->wt0x);
+    guarded_free(s->wdt5x);
     guarded_free(s->d_err);
     guarded_free(s->d_loss);
     guarded_free(s->d_max);
@@ -2383,6 +2472,7 @@ int gs_surr_create(gs_surr** out)
         if (e == cudaSuccess && l >= 1) e = guarded_malloc((void**)&s->wdt[l], (size_t)27 * 32 * (l == 5 ? 16 : 32) * sizeof(bf16));
     }
     if (e == cudaSuccess) e = guarded_malloc((void**)&s->wt0x, (size_t)9 * kCinP[0] * 32 * sizeof(bf16));
+    if (e == cudaSuccess) e = guarded_malloc((void**)&s->wdt5x, (size_t)9 * 16 * 32 * sizeof(bf16));
     if (e != cudaSuccess || (e = cudaMemset(s->params, 0, off * 4)) != cudaSuccess ||
         (e = cudaMemset(s->m, 0, off * 4)) != cudaSuccess || (e = cudaMemset(s->v, 0, off * 4)) != cudaSuccess) {
         int rc = cuda_fail(e, "surrogate allocation");
@@ -2642,7 +2732,7 @@ int gs_surr_guard_check(gs_surr* s, int64_t* bad)
 {
     if (!s || !bad) return fail(GS_EINVAL, "NULL argument");
     GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    std::vector<const void*> bufs = {s->params, s->grads, s->m, s->v, s->wt0x, s->d_err, s->d_loss, s->d_max, s->d_ss,
+    std::vector<const void*> bufs = {s->params, s->grads, s->m, s->v, s->wt0x, s->wdt5x, s->d_err, s->d_loss, s->d_max, s->d_ss,
                                      s->x0, s->gh, s->gz[0], s->gz[1], s->gd, s->ou, s->ov, s->fk, s->wpart};
     for (int l = 0; l < kSurrLayers; ++l) {
         bufs.push_back(s->wf[l]);
