@@ -1957,7 +1957,7 @@ struct gs_surr {
     bf16* wt0x = nullptr;        // the first layer's for x-tap packed input [3 dz][2][3 NT][8]
     bf16* wdt[kSurrLayers] = {}; // tcgen05 B layout of the data gradient (layers 1..5)
     bf16* wdt5x = nullptr;       // the last layer's, for x-tap packed dL/dout [3 dz][2][3 NT][8]
-    bool wdirty = true;
+    unsigned wdirty = 3;        // bit 0: mma.sync weight layouts stale, bit 1: tcgen05 layouts stale
     int backend = 0;             // 0 auto (tcgen05 when L % 128 == 0), 1 mma.sync, 2 tcgen05
     int* d_err = nullptr;
     // workspace
@@ -2144,35 +2144,40 @@ int tc_launch(gs_surr* s, ConvTcArgs a)
 
 int grid1d(long long n, int block) { return (int)std::max<long long>(1, std::min<long long>((n + block - 1) / block, 8LL * num_sms())); }
 
-int prep_weights(gs_surr* s)
+// bf16 weight layouts of the path about to run (mma.sync: forward and data
+// gradient; tcgen05: forward, x-tap first layer, data gradient, x-tap last
+// layer), redone after the parameters change
+int prep_weights(gs_surr* s, bool tc)
 {
-    if (!s->wdirty) return GS_OK;
+    const unsigned need = tc ? 2u : 1u;
+    if (!(s->wdirty & need)) return GS_OK;
     for (int l = 0; l < kSurrLayers; ++l) {
         const int cin = kChan[l], cout = kChan[l + 1];
-        const int dk = l == 5 ? 16 : 32;
-        gs_wprep_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, s->wf[l], kCoutP[l], kCinP[l],
-                                                  l >= 1 ? s->wd[l] : nullptr, dk);
-        GS_CUDA_TRY(cudaGetLastError());
-        if (l == 5)
+        if (!tc) {
+            gs_wprep_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, s->wf[l], kCoutP[l],
+                                                      kCinP[l], l >= 1 ? s->wd[l] : nullptr, l == 5 ? 16 : 32);
+        } else if (l == 5) {
             gs_wprep_tc_last_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, s->wt[l]);
-        else
-            gs_wprep_tc_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, kCinP[l], 32, s->wt[l]);
+        } else {
+            if (l >= 1)
+                gs_wprep_tc_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, kCinP[l], 32,
+                                                             s->wt[l]);
+            if (l >= 1)
+                gs_wprep_tc_dgrad_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, 32, 32,
+                                                                   s->wdt[l]);
+        }
+        GS_CUDA_TRY(cudaGetLastError());
+        s->launches += (tc && l >= 1 && l <= 4) ? 2 : (tc && l == 0 ? 0 : 1);
+    }
+    if (tc) {
+        gs_wprep_tc_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[0], kChan[0], kChan[1], 32, s->wt0x);
+        GS_CUDA_TRY(cudaGetLastError());
+        gs_wprep_tc_dgrad_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[5], kChan[5], kChan[6], 32,
+                                                                  s->wdt5x);
         GS_CUDA_TRY(cudaGetLastError());
         s->launches += 2;
-        if (l >= 1) {
-            gs_wprep_tc_dgrad_kernel<<<64, 256, 0, s->stream>>>(s->params + s->woff[l], cin, cout, l == 5 ? 16 : 32, 32,
-                                                               s->wdt[l]);
-            GS_CUDA_TRY(cudaGetLastError());
-            s->launches += 1;
-        }
     }
-    gs_wprep_tc_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[0], kChan[0], kChan[1], 32, s->wt0x);
-    GS_CUDA_TRY(cudaGetLastError());
-    gs_wprep_tc_dgrad_xtaps_kernel<<<16, 256, 0, s->stream>>>(s->params + s->woff[5], kChan[5], kChan[6], 32, s->wdt5x);
-    s->launches += 1;
-    GS_CUDA_TRY(cudaGetLastError());
-    s->launches += 1;
-    s->wdirty = false;
+    s->wdirty &= ~need;
     return GS_OK;
 }
 
@@ -2190,10 +2195,10 @@ int upload_fk(gs_surr* s, int N, const double* F, const double* k)
 // forward pass; train: keep h1..h5 and z0..z4, write (ou, ov); else ping-pong
 int forward(gs_surr* s, int N, int L, const float* u, const float* v, float* uo, float* vo, bool train)
 {
-    int rc = prep_weights(s);
-    if (rc) return rc;
     const long long cells = (long long)N * L * L * L;
     const bool tc = s->backend != 1 && L % kTcCells == 0;
+    int rc = prep_weights(s, tc);
+    if (rc) return rc;
     if (s->backend == 2 && !tc) return fail(GS_EINVAL, "the tcgen05 path needs L %% 128 == 0 (L=%d)", L);
     // the tensor-core path packs the x taps into the first layer's input
     // (its weight gradient reads the packed form too); mma.sync keeps the
@@ -2499,7 +2504,7 @@ int gs_surr_set_params(gs_surr* s, const float* host, size_t count)
     GS_CUDA_TRY(cudaMemsetAsync(s->v, 0, count * 4, s->stream));
     GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->adam_t = 0;
-    s->wdirty = true;
+    s->wdirty = 3;
     return GS_OK;
 }
 
@@ -2616,7 +2621,7 @@ int gs_surr_adam(gs_surr* s, double lr, double beta1, double beta2, double eps)
                                                                          (float)beta2, (float)eps, c1, c2);
     GS_CUDA_TRY(cudaGetLastError());
     s->launches += 1;
-    s->wdirty = true;
+    s->wdirty = 3;
     return GS_OK;
 }
 
