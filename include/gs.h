@@ -64,14 +64,21 @@ enum {
 };
 
 /* Arithmetic of FP64 fields (gs_set_arith).  GB300's FP64 pipe is narrow
- * (about 2 FP64 FMAs per clock per SM): GS_ARITH_DS keeps the fields in FP64
- * but computes each step in double-single arithmetic (pairs of floats,
- * about 48 significant bits, error-free transformations on the FP32 pipe;
- * values below 2^-126 flush to zero), which matches the FP64 oracle within
- * its 1e-10 tolerance. */
+ * (about 2 FP64 FMAs per clock per SM), so two other arithmetics keep the
+ * fields in FP64 but compute each step elsewhere:
+ *   GS_ARITH_DS  double-single (pairs of floats, about 48 significant bits,
+ *                error-free transformations on the FP32 pipe; values below
+ *                2^-126 flush to zero);
+ *   GS_ARITH_FX  64-bit fixed point with 52 fractional bits on the integer
+ *                pipes: the neighbour sums and sum - 6u are exact, only the
+ *                products round (to 2^-53); requires |u|, |v| < 1024 (a
+ *                value outside is reported by the next gs_sync / gs_read as
+ *                GS_EINVAL).
+ * Both match the FP64 oracle within its 1e-10 tolerance. */
 enum {
     GS_ARITH_IEEE = 0, /* the dtype's own IEEE arithmetic (default)         */
-    GS_ARITH_DS = 1    /* FP64 fields only: double-single arithmetic        */
+    GS_ARITH_DS = 1,   /* FP64 fields only: double-single arithmetic        */
+    GS_ARITH_FX = 2    /* FP64 fields only: 64-bit fixed-point arithmetic   */
 };
 
 /* Boundary of the single-grid simulations (gs_set_boundary, gs_single_create). */
@@ -232,8 +239,9 @@ int gs_destroy(gs_sim* sim);
 int gs_set_boundary(gs_sim* sim, int boundary);
 int gs_get_boundary(gs_sim* sim, int* boundary);
 
-/* Arithmetic mode (GS_ARITH_IEEE or GS_ARITH_DS; GS_EINVAL for GS_ARITH_DS on
- * an FP32 simulation).  Applies to the plain and z-marching kernels. */
+/* Arithmetic mode (GS_ARITH_IEEE, GS_ARITH_DS or GS_ARITH_FX; GS_EINVAL for
+ * the last two on an FP32 simulation).  Applies to the plain and z-marching
+ * kernels. */
 int gs_set_arith(gs_sim* sim, int arith);
 int gs_get_arith(gs_sim* sim, int* arith);
 

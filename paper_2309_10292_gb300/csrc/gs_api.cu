@@ -345,7 +345,7 @@ int gs_step(gs_sim* s, int64_t n)
                                s->t, s->d_err, s->timeout_ns, s->fault, s->stream);
         } else {
             rc = launch_naive(s->dtype, s->L, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1],
-                              s->p, s->t, s->stream);
+                              s->p, s->t, s->d_err, s->stream);
         }
         if (rc) return rc;
         s->launches += 1;
@@ -377,6 +377,12 @@ int gs_sync(gs_sim* s)
     GS_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     if (err == GS_DERR_TIMEOUT) return fail(GS_ETIMEOUT, "a device-side wait timed out");
+    if (err == GS_DERR_RANGE) {
+        // reported once: the steps since the last check met a value outside
+        // the fixed-point range (the fields are unreliable from there on)
+        GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+        return fail(GS_EINVAL, "a field value left the fixed-point range (|u|, |v| < 1024) of GS_ARITH_FX");
+    }
     if (err) return fail(GS_ECUDA, "device error code %d", err);
     return GS_OK;
 }
@@ -636,7 +642,7 @@ static int plan_key(gs_sim* s, char* key, size_t n)
     for (; i < sizeof(pr.name) && pr.name[i]; ++i) name[i] = (pr.name[i] == ' ' || pr.name[i] == '/') ? '_' : pr.name[i];
     name[i] = 0;
     snprintf(key, n, "%s/sm%d%d/L%d/%s/%s/%s/%s", name, pr.major, pr.minor, s->L, s->dtype == GS_F32 ? "f32" : "f64",
-             s->p.arith == GS_ARITH_DS ? "ds" : "ieee", s->boundary == GS_BOUNDARY_HELD ? "held" : "periodic",
+             s->p.arith == GS_ARITH_DS ? "ds" : (s->p.arith == GS_ARITH_FX ? "fx" : "ieee"), s->boundary == GS_BOUNDARY_HELD ? "held" : "periodic",
              s->p.noise != 0.0 ? "noise" : "still");
     return GS_OK;
 }
@@ -718,10 +724,10 @@ int gs_set_boundary(gs_sim* s, int boundary)
 int gs_set_arith(gs_sim* s, int arith)
 {
     if (!s) return fail(GS_EINVAL, "sim is NULL");
-    if (arith != GS_ARITH_IEEE && arith != GS_ARITH_DS)
-        return fail(GS_EINVAL, "arith=%d must be GS_ARITH_IEEE or GS_ARITH_DS", arith);
-    if (arith == GS_ARITH_DS && s->dtype != GS_F64)
-        return fail(GS_EINVAL, "double-single arithmetic applies to FP64 fields only");
+    if (arith != GS_ARITH_IEEE && arith != GS_ARITH_DS && arith != GS_ARITH_FX)
+        return fail(GS_EINVAL, "arith=%d must be GS_ARITH_IEEE, GS_ARITH_DS or GS_ARITH_FX", arith);
+    if (arith != GS_ARITH_IEEE && s->dtype != GS_F64)
+        return fail(GS_EINVAL, "double-single and fixed-point arithmetic apply to FP64 fields only");
     s->p.arith = arith;
     return GS_OK;
 }

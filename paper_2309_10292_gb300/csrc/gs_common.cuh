@@ -17,7 +17,7 @@
 #define GS_D __device__ __forceinline__
 
 // device error codes written to the object's error word
-enum : int { GS_DERR_NONE = 0, GS_DERR_TIMEOUT = 1, GS_DERR_BADARG = 2 };
+enum : int { GS_DERR_NONE = 0, GS_DERR_TIMEOUT = 1, GS_DERR_BADARG = 2, GS_DERR_RANGE = 3 };
 
 // ---------------------------------------------------------------------------
 // Noise: r(seed, t, c) in (-1, 1), exact in float and double.

@@ -53,7 +53,7 @@ CUresult encode_act_4d(CUtensorMap* map, const void* base, int C, int L, long lo
 int launch_init(int dtype, int L, void* u, void* v, cudaStream_t s);
 int launch_noise_field(int dtype, uint64_t seed, int64_t t, int64_t n, void* out, cudaStream_t s);
 int launch_naive(int dtype, int L, const void* u, const void* v, void* un, void* vn,
-                 const Params& p, int64_t t, cudaStream_t s);
+                 const Params& p, int64_t t, int* err, cudaStream_t s);
 
 // Three tensor maps per field for the z-marching kernels (main tile, one
 // halo row, one halo column block), for the two fields u, v.

@@ -23,6 +23,7 @@
 
 #include "gs_common.cuh"
 #include "gs_ds.cuh"
+#include "gs_fx.cuh"
 #include "gs_internal.h"
 
 namespace gs {
@@ -64,11 +65,13 @@ static GsCoef<T> make_coef(const Params& p)
     return gs_make_coef<T>(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
 }
 
-template <typename T, bool NOISE, bool DS>
+// AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed point)
+template <typename T, bool NOISE, int AR>
 __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, const T* __restrict__ v,
                                                        T* __restrict__ un, T* __restrict__ vn, int L,
-                                                       GsCoef<T> c, GsCoefDS cds, GsKeys k)
+                                                       GsCoef<T> c, GsCoefDS cds, GsCoefFX cfx, GsKeys k, int* err)
 {
+    constexpr bool DS = AR == 1;
     const int64_t n = (int64_t)L * L * L;
     const int64_t LL = (int64_t)L * L;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -98,6 +101,25 @@ __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, 
             gs_update_ds<NOISE>(cds, uc, vc, su, sv, rn, a, b);
             un[i] = ds_to_double(a);
             vn[i] = ds_to_double(b);
+        } else if constexpr (AR == 2) {
+            // FP64 fields in fixed point (gs_fx.cuh)
+            bool o[14];
+            const long long uc = fx_from_double(u[i], o[0]), vc = fx_from_double(v[i], o[1]);
+            const long long su = fx_from_double(u[ixm], o[2]) + fx_from_double(u[ixp], o[3]) +
+                                 fx_from_double(u[iym], o[4]) + fx_from_double(u[iyp], o[5]) +
+                                 fx_from_double(u[izm], o[6]) + fx_from_double(u[izp], o[7]);
+            const long long sv = fx_from_double(v[ixm], o[8]) + fx_from_double(v[ixp], o[9]) +
+                                 fx_from_double(v[iym], o[10]) + fx_from_double(v[iyp], o[11]) +
+                                 fx_from_double(v[izm], o[12]) + fx_from_double(v[izp], o[13]);
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < 14; ++q) any |= o[q];
+            if (any) gs_report(err, GS_DERR_RANGE);
+            const int32_t rn = NOISE ? gs_noise_num((uint32_t)i, k) : 0;
+            long long a, b;
+            gs_update_fx<NOISE>(cfx, uc, vc, su, sv, rn, a, b);
+            un[i] = fx_to_double(a);
+            vn[i] = fx_to_double(b);
         } else {
             const T uc = u[i], vc = v[i];
             const T su = gs_nsum(u[ixm], u[ixp], u[iym], u[iyp], u[izm], u[izp]);
@@ -146,38 +168,42 @@ int launch_noise_field(int dtype, uint64_t seed, int64_t t, int64_t n, void* out
 
 template <typename T>
 static int naive_t(int L, const void* u, const void* v, void* un, void* vn, const Params& p,
-                   int64_t t, cudaStream_t s)
+                   int64_t t, int* err, cudaStream_t s)
 {
     const int64_t n = (int64_t)L * L * L;
     const int g = grid_for(n, 256);
     GsCoef<T> c = make_coef<T>(p);
     const GsCoefDS cds = gs_make_coef_ds(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
+    const GsCoefFX cfx = gs_make_coef_fx(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     GsKeys k = gs_step_keys(p.seed, t);
+    const bool nz = p.noise != 0.0;
+    const T* cu = (const T*)u;
+    const T* cv = (const T*)v;
     bool launched = false;
     if constexpr (std::is_same<T, double>::value) {
         if (p.arith == GS_ARITH_DS) {
-            if (p.noise != 0.0)
-                gs_naive_kernel<T, true, true><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
-            else
-                gs_naive_kernel<T, false, true><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
+            if (nz) gs_naive_kernel<T, true, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
+            else gs_naive_kernel<T, false, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
+            launched = true;
+        } else if (p.arith == GS_ARITH_FX) {
+            if (nz) gs_naive_kernel<T, true, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
+            else gs_naive_kernel<T, false, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
             launched = true;
         }
     }
     if (!launched) {
-        if (p.noise != 0.0)
-            gs_naive_kernel<T, true, false><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
-        else
-            gs_naive_kernel<T, false, false><<<g, 256, 0, s>>>((const T*)u, (const T*)v, (T*)un, (T*)vn, L, c, cds, k);
+        if (nz) gs_naive_kernel<T, true, 0><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
+        else gs_naive_kernel<T, false, 0><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
     }
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
 
 int launch_naive(int dtype, int L, const void* u, const void* v, void* un, void* vn,
-                 const Params& p, int64_t t, cudaStream_t s)
+                 const Params& p, int64_t t, int* err, cudaStream_t s)
 {
-    return dtype == GS_F32 ? naive_t<float>(L, u, v, un, vn, p, t, s)
-                           : naive_t<double>(L, u, v, un, vn, p, t, s);
+    return dtype == GS_F32 ? naive_t<float>(L, u, v, un, vn, p, t, err, s)
+                           : naive_t<double>(L, u, v, un, vn, p, t, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -224,6 +250,7 @@ struct ZArgs {
     ZLayout lay;
     GsCoef<T> c;
     GsCoefDS cds;            // the same coefficients as double-single pairs (DS kernels)
+    GsCoefFX cfx;            // and in fixed point (FX kernels)
     GsKeys keys;
     int* err;
     uint64_t timeout_ns;
@@ -273,21 +300,25 @@ GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
     }
 }
 
-template <typename T, bool NOISE, bool DS>
+// AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed
+// point); the last two convert every staged plane in place once (CONV)
+template <typename T, bool NOISE, int AR>
 __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
 {
+    constexpr bool DS = AR == 1;
+    constexpr bool CONV = AR != 0;
     constexpr int V = GsVec<T>::N;
     using VT = typename GsVec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
-    // full / empty per stage; with DS also `conv`: one arrival per consumer
+    // full / empty per stage; with CONV also `conv`: one arrival per consumer
     // warp once its part of the stage has been converted in place
-    __shared__ __align__(8) uint64_t bars[(DS ? 3 : 2) * 8];
+    __shared__ __align__(8) uint64_t bars[(CONV ? 3 : 2) * 8];
     __shared__ volatile int abort_flag;
 
     const int S = a.stages;
     uint64_t* full = bars;
     uint64_t* empty = bars + S;
-    uint64_t* conv = bars + 2 * S;  // DS only
+    uint64_t* conv = bars + 2 * S;  // CONV only
     const int nxv = a.tx / V;
     const int ncons = nxv * a.ty;
     const int cons_threads = (ncons + 31) & ~31;
@@ -300,7 +331,7 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         for (int s = 0; s < S; ++s) {
             gs_mbar_init(&full[s], 1);
             gs_mbar_init(&empty[s], cons_warps);
-            if constexpr (DS) gs_mbar_init(&conv[s], cons_warps);
+            if constexpr (CONV) gs_mbar_init(&conv[s], cons_warps);
         }
         abort_flag = 0;
         gs_fence_mbar_init();
@@ -370,9 +401,9 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         if (++cs == S) { cs = 0; cph ^= 1u; }
     };
     auto release = [&](int s) {
-        // DS: the in-place conversion wrote the stage; order those writes
+        // CONV: the in-place conversion wrote the stage; order those writes
         // before the copy engine's next fill of it
-        if constexpr (DS) gs_fence_proxy_async();
+        if constexpr (CONV) gs_fence_proxy_async();
         __syncwarp();
         if (lane == 0) gs_mbar_arrive(&empty[s]);
     };
@@ -407,16 +438,26 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         const int oxr = has_r ? moff + V : a.lay.right_off + rr * V;
         int64_t gidx = (int64_t)z0 * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
 
-        // DS: convert this thread's cells of stage s, and the halo entries only
-        // it reads, to packed double-single pairs in place, then announce it;
-        // every FP64 value is converted once per pass instead of at each use
+        // CONV: convert this thread's cells of stage s, and the halo entries
+        // only it reads, to packed double-single pairs (DS) or fixed-point
+        // values (FX) in place, then announce it; every FP64 value is
+        // converted once per pass instead of at each use
         auto convert_stage = [&](int s) {
-            if constexpr (DS) {
+            if constexpr (CONV) {
+                bool ovf = false;
                 if (active) {
 #pragma unroll
                     for (int f = 0; f < 2; ++f) {
                         T* bf = ring + s * stage_elems + f * a.lay.field_elems;
-                        auto cvt = [&](int off) { bf[off] = ds_pack(ds_from_double(bf[off])); };
+                        auto cvt = [&](int off) {
+                            if constexpr (DS) {
+                                bf[off] = ds_pack(ds_from_double(bf[off]));
+                            } else {
+                                bool o;
+                                bf[off] = fx_pack(fx_from_double(bf[off], o));
+                                ovf |= o;
+                            }
+                        };
 #pragma unroll
                         for (int e = 0; e < V; ++e) {
                             cvt(moff + e);
@@ -426,6 +467,9 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                         if (xv == 0) cvt(oxl);
                         if (!has_r) cvt(oxr);
                     }
+                }
+                if constexpr (AR == 2) {
+                    if (__any_sync(0xffffffffu, ovf) && lane == 0) gs_report(a.err, GS_DERR_RANGE);
                 }
                 __syncwarp();
                 if (lane == 0) gs_mbar_arrive(&conv[s]);
@@ -450,7 +494,7 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
             const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
             const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
             const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
-            if constexpr (DS) {
+            if constexpr (CONV) {
                 // every warp's part of the centre stage is converted
                 if (!gs_mbar_wait(&conv[sc], scp, a.timeout_ns)) {
                     gs_report(a.err, GS_DERR_TIMEOUT);
@@ -474,6 +518,9 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                 if constexpr (DS)
                     gs_update_group_ds<NOISE>(a.cds, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
                                               xlv, xrv, outu, outv, GsFromPacked());
+                else if constexpr (AR == 2)
+                    gs_update_group_fx<NOISE>(a.cfx, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
+                                              xlv, xrv, outu, outv);
                 else
                     gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
                                               xlv, xrv, outu, outv);
@@ -559,7 +606,7 @@ int zmarch_encode(int dtype, int L, const ZPlan& pl, void* u, void* v, ZMaps* ma
     return GS_OK;
 }
 
-template <typename T, bool NOISE, bool DS>
+template <typename T, bool NOISE, int AR>
 static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
                            const Params& p, int64_t t, int* d_err, uint64_t timeout_ns,
                            int stall, cudaStream_t s)
@@ -580,6 +627,7 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     a.lay = make_layout(sizeof(T), V, pl.tx, pl.ty);
     a.c = make_coef<T>(p);
     a.cds = gs_make_coef_ds(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
+    a.cfx = gs_make_coef_fx(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     a.keys = gs_step_keys(p.seed, t);
     a.err = d_err;
     a.timeout_ns = timeout_ns;
@@ -587,7 +635,7 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     const int ncons = (pl.tx / V) * pl.ty;
     const int threads = ((ncons + 31) & ~31) + 32;
     const size_t smem = (size_t)a.lay.stage_bytes * pl.stages;
-    auto kern = gs_zmarch_kernel<T, NOISE, DS>;
+    auto kern = gs_zmarch_kernel<T, NOISE, AR>;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -604,13 +652,16 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
 {
     const bool noise = p.noise != 0.0;
     if (dtype == GS_F32)
-        return noise ? zmarch_launch_t<float, true, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                     : zmarch_launch_t<float, false, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+        return noise ? zmarch_launch_t<float, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                     : zmarch_launch_t<float, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
     if (p.arith == GS_ARITH_DS)
-        return noise ? zmarch_launch_t<double, true, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                     : zmarch_launch_t<double, false, true>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
-    return noise ? zmarch_launch_t<double, true, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                 : zmarch_launch_t<double, false, false>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+        return noise ? zmarch_launch_t<double, true, 1>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                     : zmarch_launch_t<double, false, 1>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+    if (p.arith == GS_ARITH_FX)
+        return noise ? zmarch_launch_t<double, true, 2>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                     : zmarch_launch_t<double, false, 2>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+    return noise ? zmarch_launch_t<double, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+                 : zmarch_launch_t<double, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
 }
 
 }  // namespace gs

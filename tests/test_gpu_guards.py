@@ -49,6 +49,8 @@ CASES = [
     (40, "f32", gs.GS_KERNEL_ZMARCH, (32, 16, 16), 0, None, None),
     (40, "f64", gs.GS_KERNEL_ZMARCH, (16, 6, 7), 0, None, None),
     (40, "f64", gs.GS_KERNEL_ZMARCH, (32, 16, 16), 0, gs.GS_ARITH_DS, None),
+    (40, "f64", gs.GS_KERNEL_ZMARCH, (16, 6, 7), 0, gs.GS_ARITH_FX, None),
+    (17, "f64", gs.GS_KERNEL_NAIVE, (0, 0, 0), 0, gs.GS_ARITH_FX, None),
     (48, "f32", gs.GS_KERNEL_TBLOCK, (16, 16, 16), 2, None, None),
     (48, "f32", gs.GS_KERNEL_TBLOCK, (16, 16, 24), 3, None, None),
     (48, "f32", gs.GS_KERNEL_TBLOCK, (16, 8, 48), 5, None, None),

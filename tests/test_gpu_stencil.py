@@ -324,23 +324,29 @@ def test_autotune_restores_state_and_keeps_fastest_plan(dtype):
 
 
 # ---------------------------------------------------------------------------
-# FP64 fields in double-single arithmetic (GS_ARITH_DS)
+# FP64 fields in double-single (GS_ARITH_DS) and fixed-point (GS_ARITH_FX)
+# arithmetic
 # ---------------------------------------------------------------------------
-def make_ds(L, kernel=None, tiles=(0, 0, 0), **kw):
+ARITHS = [gs.GS_ARITH_DS, gs.GS_ARITH_FX]
+ARITH_IDS = ["ds", "fx"]
+
+
+def make_ar(arith, L, kernel=None, tiles=(0, 0, 0), **kw):
     sim = make(L, "f64", kernel, tiles, **kw)
-    sim.arith = gs.GS_ARITH_DS
+    sim.arith = arith
     return sim
 
 
 # partial tiles in x and y (the z-march kernel converts each staged plane in
 # place, its own cells and the halo entries each thread alone reads)
+@pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
 @pytest.mark.parametrize("tiles", [(32, 16, 16), (16, 6, 7), (8, 4, 40), (40, 1, 3)])
-def test_ds_zmarch_partial_tiles_bitwise_equal_plain(tiles):
+def test_conv_arith_zmarch_partial_tiles_bitwise_equal_plain(arith, tiles):
     L, n = 40, 12
     prm = dict(PAPER, noise=0.1, seed=11)
     u0, v0 = inputs.random_fields(L, seed=5, lo=0.0, hi=1.0)
-    a = make_ds(L, gs.GS_KERNEL_NAIVE, **prm)
-    b = make_ds(L, gs.GS_KERNEL_ZMARCH, tiles, **prm)
+    a = make_ar(arith, L, gs.GS_KERNEL_NAIVE, **prm)
+    b = make_ar(arith, L, gs.GS_KERNEL_ZMARCH, tiles, **prm)
     for s in (a, b):
         s.write(u0, v0)
         s.step(n)
@@ -352,39 +358,45 @@ def test_ds_zmarch_partial_tiles_bitwise_equal_plain(tiles):
     assert max(maxabs(ub, uo), maxabs(vb, vo)) <= TOL["f64"]
 
 
+@pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
 @pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
-def test_ds_config1_parity(kernel):
+def test_conv_arith_config1_parity(arith, kernel):
     L, n = 64, 100
     u0, v0 = oracle.init(L)
     uo, vo = oracle.step(u0, v0, n, **PAPER, noise=0.0, seed=0)
-    sim = make_ds(L, kernel, noise=0.0, seed=0)
-    assert sim.arith == gs.GS_ARITH_DS
+    sim = make_ar(arith, L, kernel, noise=0.0, seed=0)
+    assert sim.arith == arith
     sim.step(n)
     u, v = sim.read()
     err = max(maxabs(u, uo), maxabs(v, vo))
-    print(f"double-single config 1: max-abs error vs oracle {err:.3e}")
+    print(f"arith {arith} config 1: max-abs error vs oracle {err:.3e}")
     assert err <= TOL["f64"]
 
 
+@pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
 @pytest.mark.parametrize("L", [48, 17, 5, 2])
-def test_ds_random_state_parity_with_noise(L):
+def test_conv_arith_random_state_parity_with_noise(arith, L):
+    # dt = 0.5: the products du dt are taken (dt = 1 skips them)
     prm = dict(Du=0.2, Dv=0.1, F=0.035, k=0.06, dt=0.5, noise=0.1, seed=77)
     u0, v0 = inputs.random_fields(L, seed=600 + L, lo=0.0, hi=1.0)
     sim = gs.GrayScott(L, dtype="f64", **prm)
-    sim.arith = gs.GS_ARITH_DS
+    sim.arith = arith
     sim.write(u0, v0)
     sim.t = 7
     sim.step(40)
     u, v = sim.read()
     uo, vo = oracle.step(u0, v0, 40, t0=7, **prm)
-    assert max(maxabs(u, uo), maxabs(v, vo)) <= TOL["f64"]
+    err = max(maxabs(u, uo), maxabs(v, vo))
+    print(f"arith {arith} L={L}: max-abs error vs oracle {err:.3e}")
+    assert err <= TOL["f64"]
 
 
-def test_ds_kernels_bitwise_equal_and_close_to_ieee():
+@pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
+def test_conv_arith_kernels_bitwise_equal_and_close_to_ieee(arith):
     L, n = 64, 60
     prm = dict(PAPER, noise=0.1, seed=3)
-    a = make_ds(L, gs.GS_KERNEL_NAIVE, **prm)
-    b = make_ds(L, gs.GS_KERNEL_ZMARCH, **prm)
+    a = make_ar(arith, L, gs.GS_KERNEL_NAIVE, **prm)
+    b = make_ar(arith, L, gs.GS_KERNEL_ZMARCH, **prm)
     c = make(L, "f64", gs.GS_KERNEL_ZMARCH, **prm)
     for s in (a, b, c):
         s.step(n)
@@ -394,14 +406,15 @@ def test_ds_kernels_bitwise_equal_and_close_to_ieee():
     np.testing.assert_array_equal(ua, ub)
     np.testing.assert_array_equal(va, vb)
     d = max(maxabs(ua, uc), maxabs(va, vc))
-    print(f"double-single vs IEEE FP64 after {n} steps: {d:.3e}")
+    print(f"arith {arith} vs IEEE FP64 after {n} steps: {d:.3e}")
     assert 0 < d <= 1e-11
 
 
-def test_ds_full_size_sampled_cells():
+@pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
+def test_conv_arith_full_size_sampled_cells(arith):
     L, n, m = 512, 16, 2
     prm = dict(PAPER, noise=0.1, seed=42)
-    sim = make_ds(L, **prm)
+    sim = make_ar(arith, L, **prm)
     sim.step(n)
     for c in [(L // 2, L // 2, L // 2), (0, 0, 0), (L - 1, 5, L // 2)]:
         uo, vo = oracle.window(L, c, m, n, **prm)
@@ -413,14 +426,34 @@ def test_ds_full_size_sampled_cells():
     sim.close()
 
 
-def test_ds_only_for_fp64_fields():
+def test_conv_arith_only_for_fp64_fields():
     s32 = make(16, "f32")
-    with pytest.raises(gs.GsError) as e:
-        s32.arith = gs.GS_ARITH_DS
-    assert e.value.status == gs.GS_EINVAL and s32.arith == gs.GS_ARITH_IEEE
+    for ar in ARITHS:
+        with pytest.raises(gs.GsError) as e:
+            s32.arith = ar
+        assert e.value.status == gs.GS_EINVAL and s32.arith == gs.GS_ARITH_IEEE
     s64 = make(16, "f64")
     with pytest.raises(gs.GsError):
         s64.arith = 5
+
+
+@pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
+def test_fx_reports_values_outside_its_range(kernel):
+    # |u| >= 1024 cannot be held in the fixed-point format: the next check
+    # reports it once, and the object stays usable
+    L = 16
+    sim = make_ar(gs.GS_ARITH_FX, L, kernel, noise=0.0, seed=0)
+    u0, v0 = inputs.random_fields(L, seed=3, lo=0.0, hi=1.0)
+    u0[3, 4, 5] = 2048.0
+    sim.write(u0, v0)
+    sim.step(1)
+    with pytest.raises(gs.GsError) as e:
+        sim.sync()
+    assert e.value.status == gs.GS_EINVAL and "fixed-point range" in str(e.value)
+    sim.init()
+    sim.step(2)
+    sim.sync()
+    sim.close()
 
 
 # ---------------------------------------------------------------------------
