@@ -1186,7 +1186,7 @@ __global__ void __launch_bounds__(tc_threads(EPI, XT), 1) gs_conv_tc_kernel(cons
         uint4 rv[EROWS][NRES];
         float sres[EROWS][2];
         // EPI_DGRAD: the layer below's ReLU mask word one item ahead; the
-        // incoming residual-path gradient (fp32) is loaded in the epilogue
+        // incoming residual-path gradient (bf16) is loaded in the epilogue
         // itself (registers)
         constexpr bool DG = EPI == EPI_DGRAD;
         static_assert(!DG || NT == 32, "the data gradient has 32 output channels");
