@@ -278,6 +278,7 @@ def bench_batched(args, stream, hbm_peak):
                 for i in (0, 7, 128, 255))
     c.close()
     b.close()
+    noise0 = bench_batched_noise0(Ls, F, k, base, cells, max(12, nsteps // 2), stream)
     g_pers = cells * nsteps / t_pers / 1e9
     g_seq = cells * nseq / t_seq / 1e9
     return {"workload": f"256 instances, L_i uniform on {{32,48,64,96,128}} ({cells} cells), "
@@ -289,7 +290,42 @@ def bench_batched(args, stream, hbm_peak):
             "speedup_vs_sequential": g_pers / g_seq,
             "bitwise_equal_to_sequential": bool(equal),
             "persistent_grid": info["grid"], "work_items_per_step": info["items"], "plan": plan,
-            "cooperative_attribute": info["cooperative"], "graph_launches": 1}
+            "cooperative_attribute": info["cooperative"], "graph_launches": 1, "noise0": noise0}
+
+
+def bench_batched_noise0(Ls, F, k, base, cells, nsteps, stream):
+    """The same 256 instances without noise (no counter hash per cell
+    update), where the temporally blocked form can pay: the autotuner's plan
+    (depth included) against the best one-step-per-pass plan of a short
+    sweep, both timed over the same steps."""
+    import torch
+
+    from paper_2309_10292_gb300 import gs
+    b = gs.GrayScottBatch(Ls, F, k, noise=0.0, seed=SEED, dtype="f32", **base)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed():
+        b.init()
+        b.step(nsteps)  # capture + warm-up
+        b.sync()
+        b.init()
+        ev[0].record(stream)
+        b.step(nsteps)
+        ev[1].record(stream)
+        b.sync()
+        return cells * nsteps / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e9
+
+    plan = b.autotune(steps_per_trial=24)
+    tuned = timed()
+    one = {}
+    b.set_depth(1)
+    for tz in (16, 32):
+        gs.gs_batch_set_plan(b.handle, tz, 8)
+        one[tz] = timed()
+    b.close()
+    return {"plan": plan, "value": tuned, "unit": "GCUPS", "steps": nsteps,
+            "depth1_value": max(one.values()), "depth1_by_tile_z": one,
+            "note": "noise 0: the same instances without the counter hash; value = the tuned plan"}
 
 
 def bench_snapshot(args, stream):

@@ -298,7 +298,11 @@ int gs_batch_init(gs_batch* b);
 
 /* Advance every instance n steps with ONE launch of a persistent kernel
  * (captured once per distinct n as a CUDA graph: barrier-counter reset +
- * kernel).  Between steps all CTAs meet at a bounded grid barrier.
+ * kernel).  Between steps all CTAs meet at a bounded grid barrier.  At a
+ * blocking depth D > 1 (gs_batch_set_depth) the graph holds the temporally
+ * blocked kernel for n / D passes of D steps (one grid barrier per pass)
+ * and, when D does not divide n, the single-step kernel for the remaining
+ * n mod D steps.  Every depth and plan gives bitwise-equal fields.
  * Asynchronous; failures surface at gs_batch_sync / gs_batch_read. */
 int gs_batch_step(gs_batch* b, int64_t n);
 
@@ -319,7 +323,8 @@ int gs_batch_set_step(gs_batch* b, int64_t t);
 int gs_batch_sync(gs_batch* b);
 
 /* Failure injection (see gs_set_fault): mode 1 = the TMA producer issues no
- * copies; mode 2 = CTA 0 never arrives at the grid barrier, so every other
+ * copies (single-step kernel; the blocked kernel has no producer); mode 2 =
+ * CTA 0 never arrives at the grid barrier (either kernel), so every other
  * CTA's bounded barrier wait expires.  mode 0 restores normal operation and
  * clears the recorded error. */
 int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns);
@@ -329,20 +334,36 @@ int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns);
  * drops the captured graphs. */
 int gs_batch_set_plan(gs_batch* b, int tile_z, int stages);
 
-/* Autotuner of the batched launch (not in the paper): time every z-chunk in
- * {16, 32, 64} x ring depth in {4, 6, 8} that fits (steps_per_trial steps
- * each, after one untimed run of the same length that captures the graph;
- * CUDA events on the batch's stream), restore every instance's fields and
- * the step counter exactly (the arena is copied to a temporary device buffer
- * for the duration), and keep the fastest plan.  *best_tile_z,
- * *best_stages, *best_us (may be NULL) receive it and its time per step.
- * GS_EINVAL for a NULL batch or steps_per_trial < 1.  Synchronous. */
-int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* best_stages, double* best_us);
+/* Temporal-blocking depth of the batched launch (not in the paper; the
+ * spec workload asks for it): D = 1 (default) runs one step per pass
+ * over HBM; D = 2..4 (FP32 batches only) fuses D steps per pass.  The blocked
+ * kernel cuts instance i into full-row tiles of ty_i rows, ty_i the largest
+ * divisor of L[i] with (L[i] / 4) * (ty_i + 2D) <= 512, by the z-chunk of
+ * gs_batch_set_plan, and recomputes a halo of D - s rows at level s (none in
+ * x: the rows are whole).  GS_EINVAL for D outside [1, 4], an FP64 batch at
+ * D > 1, or an instance with no such tile (L[i] > 224 at D = 4).
+ * Synchronous; drops the captured graphs. */
+int gs_batch_set_depth(gs_batch* b, int depth);
 
-/* Launch shape of the persistent kernel (CTAs, work items per step, whether
- * the cooperative launch attribute was accepted) and the number of kernel
- * launches issued so far. */
-int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t* launches);
+/* Autotuner of the batched launch (not in the paper): time every plan of
+ * the single-step kernel (z-chunk in {16, 32, 64} x TMA ring depth in
+ * {4, 6, 8} that fits) and, for FP32 batches, of the blocked kernel (depth
+ * 2, 3, 4 that fits x z-chunk in {16, 32, 64, 128}; the halo planes a pass
+ * recomputes favour long chunks), each for steps_per_trial steps
+ * rounded up to a multiple of 12 (so every depth runs whole passes), after
+ * one untimed run of the same length that captures the graph; CUDA events
+ * on the batch's stream.  Restores every instance's fields and the step
+ * counter exactly (the arena is copied to a temporary device buffer for the
+ * duration) and keeps the fastest plan.  *best_tile_z, *best_stages, *best_us
+ * and *best_depth (each may be NULL) receive it and its time per step.
+ * GS_EINVAL for a NULL batch or steps_per_trial < 1.  Synchronous. */
+int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* best_stages, double* best_us,
+                      int* best_depth);
+
+/* Launch shape of the persistent kernel at the current depth (CTAs, work
+ * items per pass, whether the cooperative launch attribute was accepted),
+ * the number of kernel launches issued so far, and the blocking depth. */
+int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t* launches, int* depth);
 
 int gs_batch_destroy(gs_batch* b);
 

@@ -30,6 +30,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "gs_common.cuh"
@@ -324,6 +325,237 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Temporally blocked batch (FP32, D = 2..4 steps per pass over HBM).
+//
+// The schedule is the single-grid gs_tblock_kernel's (level s = 1..D applies
+// step t + s - 1 to plane j = p + 1 - 2 (s - 1) at iteration p, register
+// FIFOs for the z neighbours, a 3-plane shared ring per level for the y
+// neighbours, one barrier per iteration), on the batch's full-row tiles: a
+// work item is ty_i rows of instance i by a z-chunk, and its region is the
+// whole row (the x wrap is an index wrap in shared memory, so no cell is
+// recomputed in x) by ty_i + 2D rows (the y halo shrinks by one row per
+// level).  ty_i is the largest divisor of L_i with (L_i / 4) (ty_i + 2D)
+// groups fitting the 512 threads, one group of 4 cells per thread.  Each
+// thread stages its own group with 16-byte cp.async copies into a 5-plane
+// ring.  All CTAs meet at the grid barrier after each pass (D steps).
+// ---------------------------------------------------------------------------
+constexpr int kBtbThreads = 512;
+constexpr int kBtbStages = 5;
+constexpr int kBtbMaxDepth = 4;
+
+// rows per tile of the blocked form for edge L and depth D (0: no tile fits)
+static int btb_rows(int L, int D)
+{
+    const int G = L / 4;
+    for (int ty = L; ty >= 1; --ty)
+        if (L % ty == 0 && G * (ty + 2 * D) <= kBtbThreads) return ty;
+    return 0;
+}
+
+// floats per field and plane of the blocked form's shared-memory planes
+static int btb_plane_elems(const std::vector<int>& L, int D)
+{
+    int pe = 0;
+    for (int l : L) pe = std::max(pe, (btb_rows(l, D) + 2 * D) * l);
+    return (pe + 31) / 32 * 32;
+}
+
+static size_t btb_smem_bytes(int pe, int D) { return (size_t)(2 * kBtbStages + 6 * (D - 1)) * pe * sizeof(float); }
+
+struct BtbArgs {
+    float* arena;
+    const BInst* inst;
+    const int* rows;    // ty_i of the blocked form, per instance
+    const int4* items;  // (instance, y0, z0, nz)
+    BCtrl* ctrl;
+    int nitems;
+    int pe;             // floats per field and plane of the shared-memory planes
+    long long npasses;
+    float Du6, Dv6, dt, noise24;
+    uint64_t timeout_ns;
+    int fault;          // 2: CTA 0 never arrives at the grid barrier
+};
+
+static GS_D void btb_cp16(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(gs_smem_addr(smem)), "l"(gmem) : "memory");
+}
+static GS_D void btb_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+static GS_D void btb_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <bool NOISE, int D>
+__global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __grid_constant__ BtbArgs a)
+{
+    constexpr int V = 4;
+    constexpr int S = kBtbStages;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ volatile int s_abort;
+    float* ring = reinterpret_cast<float*>(smem);
+    const int PE = a.pe;
+    float* lev = ring + (size_t)S * 2 * PE;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) s_abort = 0;
+    __syncthreads();
+    const long long t0 = a.ctrl->t;
+    const int cur0 = a.ctrl->cur;
+    long long pass = 0;
+    for (; pass < a.npasses; ++pass) {
+        const int in = (cur0 + (int)(pass & 1)) & 1, out = in ^ 1;
+        const long long tp = t0 + pass * D;
+        for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+            const int4 itm = a.items[item];
+            const BInst& I = a.inst[itm.x];
+            const int L = I.L, G = L / V, W = L;
+            const int ty = a.rows[itm.x];
+            const int H = ty + 2 * D;
+            const int y0 = itm.y, z0 = itm.z, nz = itm.w;
+            const bool real = tid < G * H;
+            const int gx = real ? tid % G : 0;
+            const int row = real ? tid / G : 0;
+            const uint32_t LL = (uint32_t)L * (uint32_t)L;
+            // this thread's group and its neighbours in shared memory: y
+            // clamped inside the region (clamped values feed unused cells
+            // only), x periodic within the row
+            const int o = row * W + gx * V;
+            const int oym = (row > 0 ? row - 1 : row) * W + gx * V;
+            const int oyp = (row < H - 1 ? row + 1 : row) * W + gx * V;
+            const bool lsh = gx > 0 && lane > 0;
+            const bool rsh = gx < G - 1 && lane < 31;
+            const int oxl = gx > 0 ? o - 1 : row * W + W - 1;
+            const int oxr = gx < G - 1 ? o + V : row * W;
+            bool act[D + 1];
+#pragma unroll
+            for (int s = 1; s <= D; ++s) act[s] = real && row >= s && row < H - s;
+            const bool store = real && row >= D && row < D + ty;
+            GsCoef<float> c;
+            c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise24 = a.noise24;
+            c.F = (float)I.F; c.Fk = (float)I.Fk;
+            const uint64_t seed = ((uint64_t)I.seed_hi << 32) | I.seed_lo;
+            GsKeys keys[D];
+            uint32_t kk2[D];
+#pragma unroll
+            for (int s = 0; s < D; ++s) {
+                keys[s] = gs_step_keys(seed, tp + s);
+                kk2[s] = gs_kk2(keys[s]);
+            }
+            const float* u = a.arena + I.off[in][0];
+            const float* v = a.arena + I.off[in][1];
+            float* un = a.arena + I.off[out][0];
+            float* vn = a.arena + I.off[out][1];
+            const int yg = (y0 - D + row + L) % L;
+            const uint32_t rowoff = (uint32_t)yg * (uint32_t)L + (uint32_t)(gx * V);
+            const int zlo = z0 - D;            // global z of local level-0 plane 0
+            const int nplanes = nz + 2 * D;    // level-0 planes z0-D .. z0+nz+D-1
+            const int niter = nz + 3 * D - 3;  // level D finishes local plane nz+D-1 at it = nz+3D-4
+
+            auto issue = [&](int jl) {
+                if (real && jl < nplanes) {
+                    int zq = zlo + jl;
+                    zq += zq < 0 ? L : 0;
+                    zq -= zq >= L ? L : 0;
+                    const size_t gidx = (size_t)zq * LL + rowoff;
+                    float* st = ring + (size_t)(jl % S) * 2 * PE;
+                    btb_cp16(st + o, u + gidx);
+                    btb_cp16(st + PE + o, v + gidx);
+                }
+                btb_commit();
+            };
+#pragma unroll
+            for (int jl = 0; jl < S - 1; ++jl) issue(jl);
+            btb_wait<S - 4>();  // planes 0, 1, 2 complete
+            __syncthreads();
+
+            float fu[D][3][4], fv[D][3][4];
+            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + o), fu[0][1]);
+            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + PE + o), fv[0][1]);
+            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + 2 * PE + o), fu[0][2]);
+            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + 3 * PE + o), fv[0][2]);
+
+            auto iteration = [&](const int it, auto full_tag) {
+                constexpr bool FULL = decltype(full_tag)::value;
+                issue(it + S - 1);
+                const int zb = zlo + it + 1;  // global z of level 1's plane, unwrapped
+#pragma unroll
+                for (int s = D; s >= 1; --s) {
+                    const int j = it + 1 - 2 * (s - 1);
+                    if (s == 1) {
+                        const float* nb = ring + (size_t)((it + 2) % S) * 2 * PE;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            fu[0][0][e] = fu[0][1][e]; fu[0][1][e] = fu[0][2][e];
+                            fv[0][0][e] = fv[0][1][e]; fv[0][1][e] = fv[0][2][e];
+                        }
+                        gs_unpack<float>(*reinterpret_cast<const float4*>(nb + o), fu[0][2]);
+                        gs_unpack<float>(*reinterpret_cast<const float4*>(nb + PE + o), fv[0][2]);
+                    }
+                    const float* cb = s == 1 ? ring + (size_t)(j % S) * 2 * PE
+                                             : lev + ((size_t)(s - 2) * 3 + (size_t)(j % 3)) * 2 * PE;
+                    const float(&cu)[4] = fu[s - 1][1];
+                    const float(&cv)[4] = fv[s - 1][1];
+                    float xlu = __shfl_up_sync(0xffffffffu, cu[3], 1);
+                    float xlv = __shfl_up_sync(0xffffffffu, cv[3], 1);
+                    float xru = __shfl_down_sync(0xffffffffu, cu[0], 1);
+                    float xrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
+                    if (!FULL && !(j >= s && j <= nz + 2 * D - 1 - s)) continue;
+                    float ou[4] = {0.f, 0.f, 0.f, 0.f}, ov[4] = {0.f, 0.f, 0.f, 0.f};
+                    int zq = zb - 2 * (s - 1);
+                    zq += zq < 0 ? L : 0;
+                    zq -= zq >= L ? L : 0;
+                    if (FULL || act[s]) {
+                        if (!lsh) { xlu = cb[oxl]; xlv = cb[PE + oxl]; }
+                        if (!rsh) { xru = cb[oxr]; xrv = cb[PE + oxr]; }
+                        float ymu[4], ypu[4], ymv[4], ypv[4];
+                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + oym), ymu);
+                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + oyp), ypu);
+                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + PE + oym), ymv);
+                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + PE + oyp), ypv);
+                        const uint32_t g = (uint32_t)zq * LL + rowoff;
+                        const uint32_t pre = NOISE ? gs_group_pre(g, keys[s - 1]) : 0u;
+                        gs_update_group<float, NOISE>(c, pre, kk2[s - 1], cu, cv, fu[s - 1][0], fv[s - 1][0],
+                                                      fu[s - 1][2], fv[s - 1][2], ymu, ypu, ymv, ypv, xlu, xru,
+                                                      xlv, xrv, ou, ov);
+                        if (s < D) {
+                            float* wb = lev + ((size_t)(s - 1) * 3 + (size_t)(j % 3)) * 2 * PE;
+                            *reinterpret_cast<float4*>(wb + o) = gs_pack<float>(ou);
+                            *reinterpret_cast<float4*>(wb + PE + o) = gs_pack<float>(ov);
+                        } else if (store) {
+                            *reinterpret_cast<float4*>(un + (size_t)zq * LL + rowoff) = gs_pack<float>(ou);
+                            *reinterpret_cast<float4*>(vn + (size_t)zq * LL + rowoff) = gs_pack<float>(ov);
+                        }
+                    }
+                    if (s < D) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            fu[s][0][e] = fu[s][1][e]; fu[s][1][e] = fu[s][2][e]; fu[s][2][e] = ou[e];
+                            fv[s][0][e] = fv[s][1][e]; fv[s][1][e] = fv[s][2][e]; fv[s][2][e] = ov[e];
+                        }
+                    }
+                }
+                btb_wait<S - 4>();  // planes up to it + 3 complete
+                __syncthreads();
+            };
+            const int steady_end = nz + 2 * D - 2;  // every level in range for it in [3D-3, nz+2D-3]
+            int it = 0;
+            for (; it < 3 * D - 3; ++it) iteration(it, std::false_type{});
+#pragma unroll 3
+            for (; it < steady_end; ++it) iteration(it, std::true_type{});
+            for (; it < niter; ++it) iteration(it, std::false_type{});
+            btb_wait<0>();
+            __syncthreads();
+        }
+        const bool skip = a.fault == 2 && blockIdx.x == 0;
+        if (!batch_grid_sync(a.ctrl, (unsigned)((unsigned long long)(pass + 1) * gridDim.x), a.timeout_ns, skip,
+                             &s_abort))
+            break;
+    }
+    if (blockIdx.x == 0 && tid == 0 && pass == a.npasses) {
+        a.ctrl->t = t0 + a.npasses * D;
+        a.ctrl->cur = (cur0 + (int)(a.npasses & 1)) & 1;
+    }
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -358,6 +590,13 @@ struct gs_batch {
     uint64_t timeout_ns = 2000000000ull;
     int fault = 0;
     bool cooperative = true;
+    // temporally blocked form (depth > 1, FP32): rows per tile per instance,
+    // its own work-item table (cut for its own grid) and plane stride
+    int depth = 1;
+    int* d_tb_rows = nullptr;
+    std::vector<int4> tb_base_items;
+    int4* d_tb_items = nullptr;
+    int tb_items_cap = 0, tb_nitems = 0, tb_items_grid = -1, tb_pe = 0, tb_grid = 0;
 };
 
 // the work items of instances [0, n): (instance, y0, z0, nz), instance by
@@ -414,6 +653,51 @@ static int upload_items(gs_batch* b, const std::vector<int4>& items)
     return GS_OK;
 }
 
+// upload the blocked form's work-item table (growing its device buffer if needed)
+static int upload_tb_items(gs_batch* b, const std::vector<int4>& items)
+{
+    if ((int)items.size() > b->tb_items_cap) {
+        int4* d = nullptr;
+        GS_CUDA_TRY(guarded_malloc((void**)&d, sizeof(int4) * items.size()));
+        guarded_free(b->d_tb_items);
+        b->d_tb_items = d;
+        b->tb_items_cap = (int)items.size();
+    }
+    GS_CUDA_TRY(cudaMemcpy(b->d_tb_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    b->tb_nitems = (int)items.size();
+    return GS_OK;
+}
+
+// (Re)build the blocked form's tables for depth D and the current z-chunk:
+// rows per tile per instance, base work items (instance by instance, y tiles
+// fastest), plane stride.  GS_EINVAL when some instance has no tile that fits.
+static int build_tb_tables(gs_batch* b, int D)
+{
+    std::vector<int> rows(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        rows[i] = btb_rows(b->L[i], D);
+        if (rows[i] < 1)
+            return fail(GS_EINVAL, "depth %d: instance %d (L=%d) has no blocked tile within %d threads", D, i,
+                        b->L[i], kBtbThreads);
+    }
+    b->tb_base_items.clear();
+    for (int i = 0; i < b->n; ++i) {
+        const int L = b->L[i], nty = L / rows[i], ntz = (L + b->tz - 1) / b->tz;
+        for (int j = 0; j < nty * ntz; ++j) {
+            const int y0 = (j % nty) * rows[i], z0 = (j / nty) * b->tz;
+            b->tb_base_items.push_back(make_int4(i, y0, z0, std::min(b->tz, L - z0)));
+        }
+    }
+    GS_CUDA_TRY(cudaStreamSynchronize(b->stream));  // no launch still reads the old tables
+    if (!b->d_tb_rows) GS_CUDA_TRY(guarded_malloc((void**)&b->d_tb_rows, sizeof(int) * b->n));
+    GS_CUDA_TRY(cudaMemcpy(b->d_tb_rows, rows.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
+    const int rc = upload_tb_items(b, b->tb_base_items);
+    if (rc) return rc;
+    b->tb_pe = btb_plane_elems(b->L, D);
+    b->tb_items_grid = -1;
+    return GS_OK;
+}
+
 static int batch_upload_ctrl(gs_batch* b)
 {
     BCtrl h{};
@@ -434,10 +718,11 @@ static void drop_graphs(gs_batch* b)
     b->graphs.clear();
 }
 
+// Arguments, grid and (for a new grid) the tail-split item table of the
+// single-step kernel for an n-step run.  Runs before a capture begins.
 template <typename T, bool NOISE>
-static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
+static int plain_prepare(gs_batch* b, int64_t n, BArgs<T>& a, size_t& smem)
 {
-    BArgs<T> a;
     a.arena = (T*)b->arena;
     a.inst = b->d_inst;
     a.maps = b->d_maps;
@@ -455,7 +740,7 @@ static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
     a.noise24 = c.noise24;
     a.timeout_ns = b->timeout_ns;
     a.fault = b->fault;
-    const size_t smem = (size_t)2 * b->field_elems * sizeof(T) * b->stages;
+    smem = (size_t)2 * b->field_elems * sizeof(T) * b->stages;
     auto kern = gs_batch_kernel<T, NOISE>;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -475,21 +760,98 @@ static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
     b->grid = grid;
     a.items = b->d_items;
     a.nitems = b->nitems;
+    return GS_OK;
+}
+
+// The same for the temporally blocked kernel (npasses passes of D steps).
+template <bool NOISE, int D>
+static int tb_prepare(gs_batch* b, int64_t npasses, BtbArgs& a, size_t& smem)
+{
+    a.arena = (float*)b->arena;
+    a.inst = b->d_inst;
+    a.rows = b->d_tb_rows;
+    a.ctrl = b->d_ctrl;
+    a.pe = b->tb_pe;
+    a.npasses = npasses;
+    GsCoef<float> c = gs_make_coef<float>(b->Du, b->Dv, 0.0, 0.0, b->dt, b->noise);
+    a.Du6 = c.Du6;
+    a.Dv6 = c.Dv6;
+    a.dt = c.dt;
+    a.noise24 = c.noise24;
+    a.timeout_ns = b->timeout_ns;
+    a.fault = b->fault;
+    smem = btb_smem_bytes(b->tb_pe, D);
+    auto kern = gs_batch_tb_kernel<NOISE, D>;
+    GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBtbThreads, smem));
+    if (per_sm < 1) return fail(GS_EINVAL, "blocked batch kernel does not fit on an SM");
+    const int grid = std::min(per_sm * num_sms(), (int)b->tb_base_items.size());
+    if (b->tb_items_grid != grid) {
+        std::vector<int4> items;
+        split_tail(b->tb_base_items, grid, items);
+        GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+        const int rc = upload_tb_items(b, items);
+        if (rc) return rc;
+        b->tb_items_grid = grid;
+        drop_graphs(b);
+    }
+    b->tb_grid = grid;
+    a.items = b->d_tb_items;
+    a.nitems = b->tb_nitems;
+    return GS_OK;
+}
+
+// one persistent launch inside a capture: barrier counter reset + kernel
+template <typename K, typename A>
+static cudaError_t capture_persistent(gs_batch* b, K kern, const A& args, int grid, int threads, size_t smem)
+{
+    cudaError_t e = cudaMemsetAsync(&b->d_ctrl->bar, 0, sizeof(unsigned), b->cap);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = b->cap;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = b->cooperative ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args);
+}
+
+// An n-step run as one graph: n / D blocked passes (D > 1), then the
+// remaining steps on the single-step kernel (which reads the step counter
+// and buffer set the blocked kernel leaves in the control block).
+template <typename T, bool NOISE, int D>
+static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
+{
+    const int64_t npasses = D > 1 ? n / D : 0;
+    const int64_t rem = n - npasses * D;
+    BArgs<T> pa{};
+    size_t psmem = 0;
+    BtbArgs ta{};
+    size_t tsmem = 0;
+    if constexpr (D > 1) {
+        if (npasses) {
+            const int rc = tb_prepare<NOISE, D>(b, npasses, ta, tsmem);
+            if (rc) return rc;
+        }
+    }
+    if (rem) {
+        const int rc = plain_prepare<T, NOISE>(b, rem, pa, psmem);
+        if (rc) return rc;
+    }
     for (int attempt = 0; attempt < 2; ++attempt) {
         cudaGraph_t g = nullptr;
         GS_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = cudaMemsetAsync(&b->d_ctrl->bar, 0, sizeof(unsigned), b->cap);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(b->grid);
-        cfg.blockDim = dim3(kBatchThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = b->cap;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = b->cooperative ? 1 : 0;
-        cudaError_t e2 = e1 == cudaSuccess ? cudaLaunchKernelEx(&cfg, kern, a) : e1;
+        cudaError_t e2 = cudaSuccess;
+        if constexpr (D > 1) {
+            if (npasses) e2 = capture_persistent(b, gs_batch_tb_kernel<NOISE, D>, ta, b->tb_grid, kBtbThreads, tsmem);
+        }
+        if (e2 == cudaSuccess && rem)
+            e2 = capture_persistent(b, gs_batch_kernel<T, NOISE>, pa, b->grid, kBatchThreads, psmem);
         cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
         cudaError_t e4 = cudaErrorUnknown;
         if (e2 == cudaSuccess && e3 == cudaSuccess) e4 = cudaGraphInstantiate(exec, g, 0);
@@ -500,7 +862,7 @@ static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
             cudaError_t e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
             return cuda_fail(e, "capturing the batched persistent launch");
         }
-        b->cooperative = false;  // retry without the cooperative attribute (grid is sized to be co-resident)
+        b->cooperative = false;  // retry without the cooperative attribute (grids are sized to be co-resident)
     }
     return fail(GS_ECUDA, "capturing the batched persistent launch failed");
 }
@@ -508,9 +870,21 @@ static int batch_capture_t(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
 static int batch_capture(gs_batch* b, int64_t n, cudaGraphExec_t* exec)
 {
     const bool noise = b->noise != 0.0;
-    if (b->dtype == GS_F32)
-        return noise ? batch_capture_t<float, true>(b, n, exec) : batch_capture_t<float, false>(b, n, exec);
-    return noise ? batch_capture_t<double, true>(b, n, exec) : batch_capture_t<double, false>(b, n, exec);
+    if (b->dtype != GS_F32)
+        return noise ? batch_capture_t<double, true, 1>(b, n, exec) : batch_capture_t<double, false, 1>(b, n, exec);
+    switch (b->depth) {
+    case 2: return noise ? batch_capture_t<float, true, 2>(b, n, exec) : batch_capture_t<float, false, 2>(b, n, exec);
+    case 3: return noise ? batch_capture_t<float, true, 3>(b, n, exec) : batch_capture_t<float, false, 3>(b, n, exec);
+    case 4: return noise ? batch_capture_t<float, true, 4>(b, n, exec) : batch_capture_t<float, false, 4>(b, n, exec);
+    default: return noise ? batch_capture_t<float, true, 1>(b, n, exec) : batch_capture_t<float, false, 1>(b, n, exec);
+    }
+}
+
+// buffer flips of an n-step run: one per blocked pass, one per single step
+static int batch_flips(const gs_batch* b, int64_t n)
+{
+    const int64_t passes = b->depth > 1 ? n / b->depth : 0;
+    return (int)((passes + (n - passes * b->depth)) & 1);
 }
 
 static int batch_check_inst(gs_batch* b, int i, int field)
@@ -532,6 +906,8 @@ int gs_batch_destroy(gs_batch* b)
     guarded_free(b->d_items);
     guarded_free(b->d_maps);
     guarded_free(b->d_ctrl);
+    guarded_free(b->d_tb_rows);
+    guarded_free(b->d_tb_items);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return GS_OK;
@@ -702,7 +1078,7 @@ int gs_batch_step(gs_batch* b, int64_t n)
     GS_CUDA_TRY(cudaGraphLaunch(exec, b->stream));
     b->launches += 1;
     b->t += n;
-    b->cur = (b->cur + (int)(n & 1)) & 1;
+    b->cur = (b->cur + batch_flips(b, n)) & 1;
     return GS_OK;
 }
 
@@ -730,11 +1106,14 @@ int gs_batch_step_sequential(gs_batch* b, int64_t n)
     return GS_OK;
 }
 
-int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* best_stages, double* best_us)
+int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* best_stages, double* best_us,
+                      int* best_depth)
 {
     if (!b) return fail(GS_EINVAL, "batch is NULL");
     if (steps_per_trial < 1) return fail(GS_EINVAL, "steps_per_trial must be >= 1");
-    const int tz0 = b->tz, st0 = b->stages;
+    // whole passes at every depth: the trial length is a multiple of 12
+    const int trial = (steps_per_trial + 11) / 12 * 12;
+    const int tz0 = b->tz, st0 = b->stages, d0 = b->depth;
     const int64_t t0 = b->t;
     const int cur0 = b->cur;
     void* saved = nullptr;
@@ -746,29 +1125,36 @@ int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* b
         rc = cuda_fail(e, "batch autotune set-up");
     if (!rc && (e = cudaMemcpyAsync(saved, b->arena, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess)
         rc = cuda_fail(e, "batch autotune save");
-    int win_tz = tz0, win_st = st0;
+    int win_tz = tz0, win_st = st0, win_d = d0;
     double win_us = -1.0;
-    for (int tz : {16, 32, 64}) {
-        for (int st : {4, 6, 8}) {
-            if (rc) break;
-            if (gs_batch_set_plan(b, tz, st) != GS_OK) continue;  // a ring that does not fit
-            int r = gs_batch_step(b, steps_per_trial);            // captures the graph, warms up
-            if (!r) r = gs_batch_sync(b);
-            if (!r && (e = cudaEventRecord(e0, b->stream)) != cudaSuccess) r = cuda_fail(e, "event");
-            if (!r) r = gs_batch_step(b, steps_per_trial);
-            if (!r && (e = cudaEventRecord(e1, b->stream)) != cudaSuccess) r = cuda_fail(e, "event");
-            if (!r) r = gs_batch_sync(b);
-            float ms = 0.f;
-            if (!r && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) r = cuda_fail(e, "event");
-            if (r) {
-                rc = r;
-                break;
-            }
-            const double us = 1e3 * ms / steps_per_trial;
-            if (win_us < 0 || us < win_us) {
-                win_us = us;
-                win_tz = tz;
-                win_st = st;
+    for (int depth = 1; depth <= kBtbMaxDepth && !rc; ++depth) {
+        if (depth > 1 && b->dtype != GS_F32) break;
+        for (int tz : {16, 32, 64, 128}) {
+            for (int st : {4, 6, 8}) {
+                if (rc) break;
+                if (depth == 1 && tz > 64) continue;  // one step per pass: longer chunks only lengthen the tail
+                if (depth > 1 && st != 4) continue;   // the blocked form has no TMA ring
+                if (gs_batch_set_plan(b, tz, st) != GS_OK) continue;  // a ring that does not fit
+                if (gs_batch_set_depth(b, depth) != GS_OK) continue;  // no blocked tile for some instance
+                int r = gs_batch_step(b, trial);                      // captures the graph, warms up
+                if (!r) r = gs_batch_sync(b);
+                if (!r && (e = cudaEventRecord(e0, b->stream)) != cudaSuccess) r = cuda_fail(e, "event");
+                if (!r) r = gs_batch_step(b, trial);
+                if (!r && (e = cudaEventRecord(e1, b->stream)) != cudaSuccess) r = cuda_fail(e, "event");
+                if (!r) r = gs_batch_sync(b);
+                float ms = 0.f;
+                if (!r && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) r = cuda_fail(e, "event");
+                if (r) {
+                    rc = r;
+                    break;
+                }
+                const double us = 1e3 * ms / trial;
+                if (win_us < 0 || us < win_us) {
+                    win_us = us;
+                    win_tz = tz;
+                    win_st = depth > 1 ? st0 : st;
+                    win_d = depth;
+                }
             }
         }
     }
@@ -783,12 +1169,14 @@ int gs_batch_autotune(gs_batch* b, int steps_per_trial, int* best_tile_z, int* b
     b->t = t0;
     b->cur = cur0;
     b->ctrl_dirty = true;
-    const int rc2 = rc ? gs_batch_set_plan(b, tz0, st0) : gs_batch_set_plan(b, win_tz, win_st);
+    int rc2 = rc ? gs_batch_set_plan(b, tz0, st0) : gs_batch_set_plan(b, win_tz, win_st);
+    if (!rc2) rc2 = gs_batch_set_depth(b, rc ? d0 : win_d);
     if (rc) return rc;
     if (rc2) return rc2;
     if (best_tile_z) *best_tile_z = win_tz;
     if (best_stages) *best_stages = win_st;
     if (best_us) *best_us = win_us;
+    if (best_depth) *best_depth = win_d;
     return GS_OK;
 }
 
@@ -888,6 +1276,21 @@ int gs_batch_set_plan(gs_batch* b, int tile_z, int stages)
     b->tz = tile_z;
     b->stages = stages;
     drop_graphs(b);
+    if (b->depth > 1) return build_tb_tables(b, b->depth);  // the blocked items follow the z-chunk
+    return GS_OK;
+}
+
+int gs_batch_set_depth(gs_batch* b, int depth)
+{
+    if (!b) return fail(GS_EINVAL, "batch is NULL");
+    if (depth < 1 || depth > kBtbMaxDepth) return fail(GS_EINVAL, "depth=%d must be in [1, %d]", depth, kBtbMaxDepth);
+    if (depth > 1 && b->dtype != GS_F32) return fail(GS_EINVAL, "the temporally blocked batch is FP32 only");
+    if (depth > 1) {
+        const int rc = build_tb_tables(b, depth);
+        if (rc) return rc;
+    }
+    b->depth = depth;
+    drop_graphs(b);
     return GS_OK;
 }
 
@@ -897,7 +1300,7 @@ int gs_batch_guard_check(gs_batch* b, int64_t* bad)
     GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
     int64_t n = 0;
     for (const void* p : {(const void*)b->arena, (const void*)b->d_inst, (const void*)b->d_items, (const void*)b->d_maps,
-                          (const void*)b->d_ctrl}) {
+                          (const void*)b->d_ctrl, (const void*)b->d_tb_rows, (const void*)b->d_tb_items}) {
         const int64_t r = guarded_check(p);
         if (r < 0) return fail(GS_ECUDA, "reading a guard band failed");
         n += r;
@@ -906,11 +1309,12 @@ int gs_batch_guard_check(gs_batch* b, int64_t* bad)
     return GS_OK;
 }
 
-int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t* launches)
+int gs_batch_info(gs_batch* b, int* grid, int* items, int* cooperative, int64_t* launches, int* depth)
 {
     if (!b) return fail(GS_EINVAL, "batch is NULL");
-    if (grid) *grid = b->grid;
-    if (items) *items = b->nitems;
+    if (depth) *depth = b->depth;
+    if (grid) *grid = b->depth > 1 ? b->tb_grid : b->grid;
+    if (items) *items = b->depth > 1 ? b->tb_nitems : b->nitems;
     if (cooperative) *cooperative = b->cooperative ? 1 : 0;
     if (launches) *launches = b->launches;
     return GS_OK;

@@ -63,7 +63,8 @@ _SIGS = {
     "gs_sync": [_vp],
     "gs_set_plan_full": [_vp, _vp],
     "gs_autotune": [_vp, _i, _vp, _i, ctypes.POINTER(_i), _vp],
-    "gs_batch_autotune": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)],
+    "gs_batch_autotune": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(_i)],
     "gs_read_async": [_vp, _i, _vp, _sz],
     "gs_write_async": [_vp, _i, _vp, _sz],
     "gs_autotune_cached": [_vp, _i, ctypes.c_char_p, _vp, ctypes.POINTER(_i)],
@@ -105,8 +106,9 @@ _SIGS = {
     "gs_batch_sync": [_vp],
     "gs_batch_set_fault": [_vp, _i, _u64],
     "gs_batch_set_plan": [_vp, _i, _i],
+    "gs_batch_set_depth": [_vp, _i],
     "gs_batch_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
-                      ctypes.POINTER(_i64)],
+                      ctypes.POINTER(_i64), ctypes.POINTER(_i)],
     "gs_batch_destroy": [_vp],
     "gs_get_stream": [_vp, _pp],
     "gs_sim_shape": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)],
@@ -322,11 +324,12 @@ def gs_autotune_cached(sim, path: str, steps_per_trial: int = 12):
 
 
 def gs_batch_autotune(b, steps_per_trial: int = 20) -> dict:
-    """Tune the batched launch's z-chunk and ring depth; returns the kept plan."""
-    tz, st, us = _i(), _i(), ctypes.c_double()
-    _check(lib().gs_batch_autotune(b, steps_per_trial, ctypes.byref(tz), ctypes.byref(st), ctypes.byref(us)),
-           "gs_batch_autotune")
-    return {"tile_z": tz.value, "stages": st.value, "us_per_step": us.value}
+    """Tune the batched launch's z-chunk, ring depth and temporal-blocking
+    depth; returns the kept plan."""
+    tz, st, us, d = _i(), _i(), ctypes.c_double(), _i()
+    _check(lib().gs_batch_autotune(b, steps_per_trial, ctypes.byref(tz), ctypes.byref(st), ctypes.byref(us),
+                                   ctypes.byref(d)), "gs_batch_autotune")
+    return {"tile_z": tz.value, "stages": st.value, "depth": d.value, "us_per_step": us.value}
 
 
 def gs_read_async(sim, field: int, dst):
@@ -532,11 +535,16 @@ def gs_batch_set_plan(b, tile_z: int, stages: int):
     _check(lib().gs_batch_set_plan(b, tile_z, stages), "gs_batch_set_plan")
 
 
+def gs_batch_set_depth(b, depth: int):
+    _check(lib().gs_batch_set_depth(b, depth), "gs_batch_set_depth")
+
+
 def gs_batch_info(b) -> dict:
-    g, it, co, la = _i(), _i(), _i(), _i64()
-    _check(lib().gs_batch_info(b, ctypes.byref(g), ctypes.byref(it), ctypes.byref(co), ctypes.byref(la)),
-           "gs_batch_info")
-    return {"grid": g.value, "items": it.value, "cooperative": bool(co.value), "launches": la.value}
+    g, it, co, la, d = _i(), _i(), _i(), _i64(), _i()
+    _check(lib().gs_batch_info(b, ctypes.byref(g), ctypes.byref(it), ctypes.byref(co), ctypes.byref(la),
+                               ctypes.byref(d)), "gs_batch_info")
+    return {"grid": g.value, "items": it.value, "cooperative": bool(co.value), "launches": la.value,
+            "depth": d.value}
 
 
 def gs_batch_destroy(b):
@@ -971,6 +979,10 @@ class GrayScottBatch:
 
     def sync(self):
         gs_batch_sync(self.handle)
+
+    def set_depth(self, depth: int):
+        """Temporal-blocking depth of the persistent launch (1 = one step per pass)."""
+        gs_batch_set_depth(self.handle, depth)
 
     def autotune(self, steps_per_trial: int = 20) -> dict:
         """Pick the batched launch's z-chunk and ring depth (state left unchanged)."""

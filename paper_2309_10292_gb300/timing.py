@@ -4,7 +4,12 @@ second, CUDA events on the grid's stream), e.g.
     python -m paper_2309_10292_gb300.timing --L 256 --dtype f64 --arith ds \
         --plan zmarch,128,8,32 --steps 6
 
-prints one JSON line with the plan and the rate.  All compute runs in libgs.
+prints one JSON line with the plan and the rate; with --batch it times the
+batched workload instead (256 instances, L_i on {32, 48, 64, 96, 128}), e.g.
+
+    python -m paper_2309_10292_gb300.timing --batch --depth 2 --tile-z 64 --steps 6
+
+All compute runs in libgs.
 """
 from __future__ import annotations
 
@@ -26,7 +31,13 @@ def main(argv=None):
     ap.add_argument("--plan", default="", help="kernel,tile_x,tile_y,tile_z[,depth[,stages]]; empty: autotune")
     ap.add_argument("--steps", type=int, default=100, help="timed steps")
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", action="store_true", help="time the 256-instance batched launch")
+    ap.add_argument("--depth", type=int, default=1, help="--batch: temporal-blocking depth")
+    ap.add_argument("--tile-z", type=int, default=32, help="--batch: z-chunk per work item")
+    ap.add_argument("--stages", type=int, default=8, help="--batch: TMA ring depth (depth 1)")
     a = ap.parse_args(argv)
+    if a.batch:
+        return time_batch(a)
     sim = gs.GrayScott(a.L, Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0, noise=a.noise, seed=42, dtype=a.dtype)
     if a.arith in ("ds", "fx"):
         sim.arith = gs.GS_ARITH_DS if a.arith == "ds" else gs.GS_ARITH_FX
@@ -51,6 +62,31 @@ def main(argv=None):
     out = {"L": a.L, "dtype": a.dtype, "arith": a.arith, "noise": a.noise, "plan": sim.plan,
            "steps": a.steps, "ms": ms, "gcups": a.L ** 3 * a.steps / (ms / 1e3) / 1e9}
     sim.close()
+    print(json.dumps(out))
+
+
+def time_batch(a):
+    import torch
+
+    from paper_2309_10292_gb300 import gs, inputs
+    Ls, F, k = inputs.batch_instances(256, seed=0)
+    b = gs.GrayScottBatch(Ls, F, k, Du=0.2, Dv=0.1, dt=1.0, noise=a.noise, seed=42, dtype="f32")
+    gs.gs_batch_set_plan(b.handle, a.tile_z, a.stages)
+    b.set_depth(a.depth)
+    b.step(a.steps)  # capture + warm-up with the timed step count
+    b.sync()
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    b.step(a.steps)
+    t1.record(stream)
+    b.sync()
+    ms = t0.elapsed_time(t1)
+    cells = sum(L ** 3 for L in Ls)
+    out = {"batch": len(Ls), "cells": cells, "noise": a.noise, "depth": a.depth, "tile_z": a.tile_z,
+           "steps": a.steps, "ms": ms, "gcups": cells * a.steps / (ms / 1e3) / 1e9, "info": b.info}
+    b.close()
     print(json.dumps(out))
 
 

@@ -187,7 +187,7 @@ def test_batch_autotune_keeps_state_and_results():
     b.step(3)
     before = [a.read(i) for i in range(len(Ls))]
     plan = a.autotune(steps_per_trial=4)
-    assert plan["tile_z"] in (16, 32, 64) and plan["stages"] in (4, 6, 8) and plan["us_per_step"] > 0
+    assert plan["tile_z"] in (16, 32, 64, 128) and plan["stages"] in (4, 6, 8) and plan["us_per_step"] > 0
     assert a.t == 3
     for i in range(len(Ls)):
         np.testing.assert_array_equal(a.read(i)[0], before[i][0])

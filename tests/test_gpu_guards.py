@@ -171,6 +171,33 @@ def test_batch_step_stays_inside_its_arena(dtype):
         ref.close()
 
 
+@pytest.mark.parametrize("depth", [2, 4])
+def test_blocked_batch_stays_inside_its_arena(depth):
+    # the temporally blocked kernel: its cp.async staging and 16-byte stores
+    # stay inside each instance's fields; its tables sit between guard bands
+    need_cuda()
+    Ls = [8, 12, 32, 48, 4, 64, 128, 96]
+    F = list(np.linspace(0.01, 0.06, len(Ls)))
+    k = list(np.linspace(0.07, 0.04, len(Ls)))
+    prm = dict(Du=0.2, Dv=0.1, dt=1.0, noise=0.1, seed=3, dtype="f32")
+    ref = gs.GrayScottBatch(Ls, F, k, **prm)
+    with _LibraryGuards():
+        b = gs.GrayScottBatch(Ls, F, k, **prm)
+        b.set_depth(depth)
+    try:
+        assert gs.gs_batch_guard_check(b.handle) == 0
+        for n in (2 * depth, depth + 1):
+            b.step(n)
+            ref.step(n)
+            assert gs.gs_batch_guard_check(b.handle) == 0
+        for i in range(len(Ls)):
+            for got, want in zip(b.read(i), ref.read(i)):
+                np.testing.assert_array_equal(got, want)
+    finally:
+        b.close()
+        ref.close()
+
+
 def _guarded_pair(torch, shape):
     # two FP32 output fields between guard bands (caller-owned outputs)
     n = int(np.prod(shape))
