@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
 // ring.  All CTAs meet at the grid barrier after each pass (D steps).
 // ---------------------------------------------------------------------------
 constexpr int kBtbThreads = 512;
-constexpr int kBtbStages = 5;
+constexpr int kBtbStages = 5;  // level-0 ring (7 planes measured no faster)
 constexpr int kBtbMaxDepth = 4;
 
 // rows per tile of the blocked form for edge L and depth D (0: no tile fits)
@@ -425,9 +425,15 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
             const bool rsh = gx < G - 1 && lane < 31;
             const int oxl = gx > 0 ? o - 1 : row * W + W - 1;
             const int oxr = gx < G - 1 ? o + V : row * W;
-            bool act[D + 1];
+            bool act[D + 1], wact[D + 1];
 #pragma unroll
-            for (int s = 1; s <= D; ++s) act[s] = real && row >= s && row < H - s;
+            for (int s = 1; s <= D; ++s) {
+                act[s] = real && row >= s && row < H - s;
+                // warp-uniform: some lane of this warp needs level s (the
+                // region's halo rows and the threads beyond it skip whole
+                // warps; within a warp every lane computes, branch-free)
+                wact[s] = __any_sync(0xffffffffu, act[s]);
+            }
             const bool store = real && row >= D && row < D + ty;
             GsCoef<float> c;
             c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise24 = a.noise24;
@@ -464,7 +470,7 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
             };
 #pragma unroll
             for (int jl = 0; jl < S - 1; ++jl) issue(jl);
-            btb_wait<S - 4>();  // planes 0, 1, 2 complete
+            btb_wait<S - 4>();  // planes 0, 1, 2 complete (S - 4 newer ones pending)
             __syncthreads();
 
             float fu[D][3][4], fv[D][3][4];
@@ -480,6 +486,9 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
 #pragma unroll
                 for (int s = D; s >= 1; --s) {
                     const int j = it + 1 - 2 * (s - 1);
+                    // a warp with no lane at level s leaves it (and its FIFO
+                    // and level plane, which no active lane reads) alone
+                    if (!wact[s]) continue;
                     if (s == 1) {
                         const float* nb = ring + (size_t)((it + 2) % S) * 2 * PE;
 #pragma unroll
@@ -533,7 +542,7 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
                         }
                     }
                 }
-                btb_wait<S - 4>();  // planes up to it + 3 complete
+                btb_wait<S - 4>();  // planes up to it + 3 complete (it + 4 .. it + S - 1 pending)
                 __syncthreads();
             };
             const int steady_end = nz + 2 * D - 2;  // every level in range for it in [3D-3, nz+2D-3]
