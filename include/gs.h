@@ -64,7 +64,7 @@ enum {
 };
 
 /* Arithmetic of FP64 fields (gs_set_arith).  GB300's FP64 pipe is narrow
- * (about 2 FP64 FMAs per clock per SM), so two other arithmetics keep the
+ * (about 2 FP64 FMAs per clock per SM), so three other arithmetics keep the
  * fields in FP64 but compute each step elsewhere:
  *   GS_ARITH_DS  double-single (pairs of floats, about 48 significant bits,
  *                error-free transformations on the FP32 pipe; values below
@@ -73,12 +73,17 @@ enum {
  *                pipes: the neighbour sums and sum - 6u are exact, only the
  *                products round (to 2^-53); requires |u|, |v| < 1024 (a
  *                value outside is reported by the next gs_sync / gs_read as
- *                GS_EINVAL).
- * Both match the FP64 oracle within its 1e-10 tolerance. */
+ *                GS_EINVAL);
+ *   GS_ARITH_FXF 32-bit fixed point (2^-22 units) with an FP32 remainder:
+ *                exact integer neighbour sums and sum - 6u, float-pair
+ *                products (about 47 significant bits, as double-single);
+ *                requires |u|, |v| < 4 (reported as for GS_ARITH_FX).
+ * All three match the FP64 oracle within its 1e-10 tolerance. */
 enum {
     GS_ARITH_IEEE = 0, /* the dtype's own IEEE arithmetic (default)         */
     GS_ARITH_DS = 1,   /* FP64 fields only: double-single arithmetic        */
-    GS_ARITH_FX = 2    /* FP64 fields only: 64-bit fixed-point arithmetic   */
+    GS_ARITH_FX = 2,   /* FP64 fields only: 64-bit fixed-point arithmetic   */
+    GS_ARITH_FXF = 3   /* FP64 fields only: fixed point + float remainder   */
 };
 
 /* Boundary of the single-grid simulations (gs_set_boundary, gs_single_create). */
@@ -239,9 +244,9 @@ int gs_destroy(gs_sim* sim);
 int gs_set_boundary(gs_sim* sim, int boundary);
 int gs_get_boundary(gs_sim* sim, int* boundary);
 
-/* Arithmetic mode (GS_ARITH_IEEE, GS_ARITH_DS or GS_ARITH_FX; GS_EINVAL for
- * the last two on an FP32 simulation).  Applies to the plain and z-marching
- * kernels. */
+/* Arithmetic mode (GS_ARITH_IEEE, GS_ARITH_DS, GS_ARITH_FX or GS_ARITH_FXF;
+ * GS_EINVAL for the last three on an FP32 simulation).  Applies to the plain
+ * and z-marching kernels. */
 int gs_set_arith(gs_sim* sim, int arith);
 int gs_get_arith(gs_sim* sim, int* arith);
 

@@ -336,16 +336,23 @@ int gs_step(gs_sim* s, int64_t n)
             s->t += D;
         }
     }
+    const int64_t first = i;
     for (; i < n; ++i) {
         const int in = s->cur, outs = 1 - s->cur;
+        // GS_ARITH_FXF keeps the fields as packed (X, l) pairs between the
+        // steps of this call (periodic grids): the first step reads FP64, the
+        // last writes FP64
+        Params p = s->p;
+        if (p.arith == GS_ARITH_FXF && s->boundary == GS_BOUNDARY_PERIODIC)
+            p.fxf_io = (i > first ? 1 : 0) | (i + 1 < n ? 2 : 0);
         int rc;
         if (s->kernel != GS_KERNEL_NAIVE) {
             if (!s->maps_ok) return fail(GS_ESTATE, "tensor maps not encoded");
-            rc = launch_zmarch(s->dtype, s->L, s->zp, s->maps[in], s->buf[outs][0], s->buf[outs][1], s->p,
-                               s->t, s->d_err, s->timeout_ns, s->fault, s->stream);
+            rc = launch_zmarch(s->dtype, s->L, s->zp, s->maps[in], s->buf[outs][0], s->buf[outs][1], p, s->t,
+                               s->d_err, s->timeout_ns, s->fault, s->stream);
         } else {
-            rc = launch_naive(s->dtype, s->L, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1],
-                              s->p, s->t, s->d_err, s->stream);
+            rc = launch_naive(s->dtype, s->L, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1], p,
+                              s->t, s->d_err, s->stream);
         }
         if (rc) return rc;
         s->launches += 1;
@@ -381,7 +388,8 @@ int gs_sync(gs_sim* s)
         // reported once: the steps since the last check met a value outside
         // the fixed-point range (the fields are unreliable from there on)
         GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
-        return fail(GS_EINVAL, "a field value left the fixed-point range (|u|, |v| < 1024) of GS_ARITH_FX");
+        return fail(GS_EINVAL, "a field value left the fixed-point range (|u|, |v| < %s) of %s",
+                    s->p.arith == GS_ARITH_FXF ? "4" : "1024", s->p.arith == GS_ARITH_FXF ? "GS_ARITH_FXF" : "GS_ARITH_FX");
     }
     if (err) return fail(GS_ECUDA, "device error code %d", err);
     return GS_OK;
@@ -642,7 +650,8 @@ static int plan_key(gs_sim* s, char* key, size_t n)
     for (; i < sizeof(pr.name) && pr.name[i]; ++i) name[i] = (pr.name[i] == ' ' || pr.name[i] == '/') ? '_' : pr.name[i];
     name[i] = 0;
     snprintf(key, n, "%s/sm%d%d/L%d/%s/%s/%s/%s", name, pr.major, pr.minor, s->L, s->dtype == GS_F32 ? "f32" : "f64",
-             s->p.arith == GS_ARITH_DS ? "ds" : (s->p.arith == GS_ARITH_FX ? "fx" : "ieee"), s->boundary == GS_BOUNDARY_HELD ? "held" : "periodic",
+             s->p.arith == GS_ARITH_DS ? "ds" : s->p.arith == GS_ARITH_FX ? "fx" : s->p.arith == GS_ARITH_FXF ? "fxf" : "ieee",
+             s->boundary == GS_BOUNDARY_HELD ? "held" : "periodic",
              s->p.noise != 0.0 ? "noise" : "still");
     return GS_OK;
 }
@@ -724,8 +733,8 @@ int gs_set_boundary(gs_sim* s, int boundary)
 int gs_set_arith(gs_sim* s, int arith)
 {
     if (!s) return fail(GS_EINVAL, "sim is NULL");
-    if (arith != GS_ARITH_IEEE && arith != GS_ARITH_DS && arith != GS_ARITH_FX)
-        return fail(GS_EINVAL, "arith=%d must be GS_ARITH_IEEE, GS_ARITH_DS or GS_ARITH_FX", arith);
+    if (arith != GS_ARITH_IEEE && arith != GS_ARITH_DS && arith != GS_ARITH_FX && arith != GS_ARITH_FXF)
+        return fail(GS_EINVAL, "arith=%d must be GS_ARITH_IEEE, GS_ARITH_DS, GS_ARITH_FX or GS_ARITH_FXF", arith);
     if (arith != GS_ARITH_IEEE && s->dtype != GS_F64)
         return fail(GS_EINVAL, "double-single and fixed-point arithmetic apply to FP64 fields only");
     s->p.arith = arith;

@@ -147,12 +147,16 @@ static std::string provenance_json(const gs_sim* s)
     char buf[1024];
     std::snprintf(buf, sizeof buf,
                   "{\"format\": \"gs-snapshot\", \"version\": 1, \"L\": %d, \"dtype\": \"%s\", "
-                  "\"layout\": \"[z][y][x], x fastest, little-endian\", \"boundary\": \"periodic\", "
+                  "\"layout\": \"[z][y][x], x fastest, little-endian\", \"boundary\": \"%s\", "
                   "\"Du\": %.17g, \"Dv\": %.17g, \"F\": %.17g, \"k\": %.17g, \"dt\": %.17g, \"noise\": %.17g, "
                   "\"seed\": %llu, \"arithmetic\": \"%s\", \"variables\": [\"U\", \"V\"], "
                   "\"record\": \"GSREC001, int64 step, float64 Umin Umax Vmin Vmax, U, V\"}",
-                  s->L, s->dtype == GS_F32 ? "f32" : "f64", s->p.Du, s->p.Dv, s->p.F, s->p.k, s->p.dt, s->p.noise,
-                  (unsigned long long)s->p.seed, s->p.arith == GS_ARITH_DS ? "double-single" : "ieee");
+                  s->L, s->dtype == GS_F32 ? "f32" : "f64", s->boundary == GS_BOUNDARY_HELD ? "held" : "periodic",
+                  s->p.Du, s->p.Dv, s->p.F, s->p.k, s->p.dt, s->p.noise, (unsigned long long)s->p.seed,
+                  s->p.arith == GS_ARITH_DS    ? "double-single"
+                  : s->p.arith == GS_ARITH_FX  ? "fixed-point"
+                  : s->p.arith == GS_ARITH_FXF ? "fixed-point-remainder"
+                                               : "ieee");
     return buf;
 }
 

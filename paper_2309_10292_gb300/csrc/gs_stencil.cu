@@ -24,6 +24,7 @@
 #include "gs_common.cuh"
 #include "gs_ds.cuh"
 #include "gs_fx.cuh"
+#include "gs_fxf.cuh"
 #include "gs_internal.h"
 
 namespace gs {
@@ -65,11 +66,14 @@ static GsCoef<T> make_coef(const Params& p)
     return gs_make_coef<T>(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
 }
 
-// AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed point)
+// AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed
+// point, 3-6: fixed point with a float remainder, 3 + (input packed) +
+// 2 (output packed))
 template <typename T, bool NOISE, int AR>
 __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, const T* __restrict__ v,
                                                        T* __restrict__ un, T* __restrict__ vn, int L,
-                                                       GsCoef<T> c, GsCoefDS cds, GsCoefFX cfx, GsKeys k, int* err)
+                                                       GsCoef<T> c, GsCoefDS cds, GsCoefFX cfx, GsCoefFXF cfxf,
+                                                       GsKeys k, int* err)
 {
     constexpr bool DS = AR == 1;
     const int64_t n = (int64_t)L * L * L;
@@ -120,6 +124,32 @@ __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, 
             gs_update_fx<NOISE>(cfx, uc, vc, su, sv, rn, a, b);
             un[i] = fx_to_double(a);
             vn[i] = fx_to_double(b);
+        } else if constexpr (AR >= 3) {
+            // FP64 fields in fixed point with a float remainder (gs_fxf.cuh);
+            // inputs and outputs FP64 or packed pairs
+            constexpr bool IN_PACKED = (AR - 3) & 1, OUT_PACKED = (AR - 3) & 2;
+            bool any = false;
+            auto get = [&](double x) -> GsFxf {
+                if constexpr (IN_PACKED) {
+                    return fxf_unpack(x);
+                } else {
+                    bool o;
+                    const GsFxf r = fxf_from_double(x, o);
+                    any |= o;
+                    return r;
+                }
+            };
+            const GsFxf uc = get(u[i]), vc = get(v[i]);
+            int32_t SU, SV;
+            float SLU, SLV;
+            fxf_nsum(get(u[ixm]), get(u[ixp]), get(u[iym]), get(u[iyp]), get(u[izm]), get(u[izp]), SU, SLU);
+            fxf_nsum(get(v[ixm]), get(v[ixp]), get(v[iym]), get(v[iyp]), get(v[izm]), get(v[izp]), SV, SLV);
+            const int32_t rn = NOISE ? gs_noise_num((uint32_t)i, k) : 0;
+            GsFxf a, b;
+            gs_update_fxf<NOISE>(cfxf, uc, vc, SU, SLU, SV, SLV, rn, a, b, any);
+            if (any) gs_report(err, GS_DERR_RANGE);
+            un[i] = OUT_PACKED ? fxf_pack(a) : fxf_to_double(a);
+            vn[i] = OUT_PACKED ? fxf_pack(b) : fxf_to_double(b);
         } else {
             const T uc = u[i], vc = v[i];
             const T su = gs_nsum(u[ixm], u[ixp], u[iym], u[iyp], u[izm], u[izp]);
@@ -175,6 +205,7 @@ static int naive_t(int L, const void* u, const void* v, void* un, void* vn, cons
     GsCoef<T> c = make_coef<T>(p);
     const GsCoefDS cds = gs_make_coef_ds(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     const GsCoefFX cfx = gs_make_coef_fx(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
+    const GsCoefFXF cfxf = gs_make_coef_fxf(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     GsKeys k = gs_step_keys(p.seed, t);
     const bool nz = p.noise != 0.0;
     const T* cu = (const T*)u;
@@ -182,18 +213,30 @@ static int naive_t(int L, const void* u, const void* v, void* un, void* vn, cons
     bool launched = false;
     if constexpr (std::is_same<T, double>::value) {
         if (p.arith == GS_ARITH_DS) {
-            if (nz) gs_naive_kernel<T, true, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
-            else gs_naive_kernel<T, false, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
+            if (nz) gs_naive_kernel<T, true, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
+            else gs_naive_kernel<T, false, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
             launched = true;
         } else if (p.arith == GS_ARITH_FX) {
-            if (nz) gs_naive_kernel<T, true, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
-            else gs_naive_kernel<T, false, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
+            if (nz) gs_naive_kernel<T, true, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
+            else gs_naive_kernel<T, false, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
+            launched = true;
+        } else if (p.arith == GS_ARITH_FXF) {
+#define GS_NAIVE_FXF(AR)                                                                                      \
+    (nz ? gs_naive_kernel<T, true, AR><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err) \
+        : gs_naive_kernel<T, false, AR><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err))
+            switch (p.fxf_io & 3) {
+            case 0: GS_NAIVE_FXF(3); break;
+            case 1: GS_NAIVE_FXF(4); break;
+            case 2: GS_NAIVE_FXF(5); break;
+            default: GS_NAIVE_FXF(6); break;
+            }
+#undef GS_NAIVE_FXF
             launched = true;
         }
     }
     if (!launched) {
-        if (nz) gs_naive_kernel<T, true, 0><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
-        else gs_naive_kernel<T, false, 0><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, k, err);
+        if (nz) gs_naive_kernel<T, true, 0><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
+        else gs_naive_kernel<T, false, 0><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
     }
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -251,6 +294,7 @@ struct ZArgs {
     GsCoef<T> c;
     GsCoefDS cds;            // the same coefficients as double-single pairs (DS kernels)
     GsCoefFX cfx;            // and in fixed point (FX kernels)
+    GsCoefFXF cfxf;          // and as float pairs for the fixed point with a remainder (FXF kernels)
     GsKeys keys;
     int* err;
     uint64_t timeout_ns;
@@ -301,12 +345,15 @@ GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
 }
 
 // AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed
-// point); the last two convert every staged plane in place once (CONV)
+// point, 3-6: fixed point with a float remainder, 3 + (input packed) +
+// 2 (output packed)); the ones that read FP64 values into another
+// arithmetic convert every staged plane in place once (CONV)
 template <typename T, bool NOISE, int AR>
 __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
 {
     constexpr bool DS = AR == 1;
-    constexpr bool CONV = AR != 0;
+    constexpr bool FXF = AR >= 3;
+    constexpr bool CONV = AR == 1 || AR == 2 || AR == 3 || AR == 5;
     constexpr int V = GsVec<T>::N;
     using VT = typename GsVec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -439,9 +486,9 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
         int64_t gidx = (int64_t)z0 * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
 
         // CONV: convert this thread's cells of stage s, and the halo entries
-        // only it reads, to packed double-single pairs (DS) or fixed-point
-        // values (FX) in place, then announce it; every FP64 value is
-        // converted once per pass instead of at each use
+        // only it reads, to packed double-single pairs (DS), fixed-point
+        // values (FX) or fixed-point pairs (FXF) in place, then announce it;
+        // every FP64 value is converted once per pass instead of at each use
         auto convert_stage = [&](int s) {
             if constexpr (CONV) {
                 bool ovf = false;
@@ -452,9 +499,13 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                         auto cvt = [&](int off) {
                             if constexpr (DS) {
                                 bf[off] = ds_pack(ds_from_double(bf[off]));
-                            } else {
+                            } else if constexpr (AR == 2) {
                                 bool o;
                                 bf[off] = fx_pack(fx_from_double(bf[off], o));
+                                ovf |= o;
+                            } else {
+                                bool o;
+                                bf[off] = fxf_pack(fxf_from_double(bf[off], o));
                                 ovf |= o;
                             }
                         };
@@ -468,9 +519,10 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                         if (!has_r) cvt(oxr);
                     }
                 }
-                if constexpr (AR == 2) {
+                if constexpr (AR >= 2) {
                     if (__any_sync(0xffffffffu, ovf) && lane == 0) gs_report(a.err, GS_DERR_RANGE);
                 }
+                (void)ovf;
                 __syncwarp();
                 if (lane == 0) gs_mbar_arrive(&conv[s]);
             }
@@ -521,6 +573,12 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
                 else if constexpr (AR == 2)
                     gs_update_group_fx<NOISE>(a.cfx, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
                                               xlv, xrv, outu, outv);
+                else if constexpr (FXF) {
+                    bool ovf = false;
+                    gs_update_group_fxf<NOISE, (AR - 3 & 2) != 0>(a.cfxf, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu,
+                                                                    ymv, ypv, xlu, xru, xlv, xrv, outu, outv, ovf);
+                    if (ovf) gs_report(a.err, GS_DERR_RANGE);
+                }
                 else
                     gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
                                               xlv, xrv, outu, outv);
@@ -628,6 +686,7 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     a.c = make_coef<T>(p);
     a.cds = gs_make_coef_ds(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     a.cfx = gs_make_coef_fx(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
+    a.cfxf = gs_make_coef_fxf(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     a.keys = gs_step_keys(p.seed, t);
     a.err = d_err;
     a.timeout_ns = timeout_ns;
@@ -660,6 +719,18 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
     if (p.arith == GS_ARITH_FX)
         return noise ? zmarch_launch_t<double, true, 2>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
                      : zmarch_launch_t<double, false, 2>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+    if (p.arith == GS_ARITH_FXF) {
+#define GS_ZMARCH_FXF(AR)                                                                               \
+    return noise ? zmarch_launch_t<double, true, AR>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s) \
+                 : zmarch_launch_t<double, false, AR>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+        switch (p.fxf_io & 3) {
+        case 0: GS_ZMARCH_FXF(3);
+        case 1: GS_ZMARCH_FXF(4);
+        case 2: GS_ZMARCH_FXF(5);
+        default: GS_ZMARCH_FXF(6);
+        }
+#undef GS_ZMARCH_FXF
+    }
     return noise ? zmarch_launch_t<double, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
                  : zmarch_launch_t<double, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
 }

@@ -371,7 +371,7 @@ def gs_noise_field(seed, t, n, dtype, dev_out, stream=None):
 
 
 GS_BOUNDARY_PERIODIC, GS_BOUNDARY_HELD = 0, 1
-GS_ARITH_IEEE, GS_ARITH_DS, GS_ARITH_FX = 0, 1, 2
+GS_ARITH_IEEE, GS_ARITH_DS, GS_ARITH_FX, GS_ARITH_FXF = 0, 1, 2, 3
 
 
 def gs_set_arith(sim, arith: int):
@@ -1037,8 +1037,9 @@ class GrayScott:
 
     @property
     def arith(self) -> int:
-        """GS_ARITH_IEEE, GS_ARITH_DS (FP64 fields in double-single arithmetic) or
-        GS_ARITH_FX (FP64 fields in 64-bit fixed-point arithmetic)."""
+        """GS_ARITH_IEEE, GS_ARITH_DS (FP64 fields in double-single arithmetic),
+        GS_ARITH_FX (FP64 fields in 64-bit fixed-point arithmetic) or
+        GS_ARITH_FXF (FP64 fields in 32-bit fixed point with a float remainder)."""
         return gs_get_arith(self.handle)
 
     @arith.setter

@@ -26,7 +26,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="time the Gray-Scott stencil on one grid")
     ap.add_argument("--L", type=int, default=512)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--arith", default="ieee", choices=["ieee", "ds", "fx"])
+    ap.add_argument("--arith", default="ieee", choices=["ieee", "ds", "fx", "fxf"])
     ap.add_argument("--noise", type=float, default=0.1)
     ap.add_argument("--plan", default="", help="kernel,tile_x,tile_y,tile_z[,depth[,stages]]; empty: autotune")
     ap.add_argument("--steps", type=int, default=100, help="timed steps")
@@ -39,8 +39,8 @@ def main(argv=None):
     if a.batch:
         return time_batch(a)
     sim = gs.GrayScott(a.L, Du=0.2, Dv=0.1, F=0.02, k=0.048, dt=1.0, noise=a.noise, seed=42, dtype=a.dtype)
-    if a.arith in ("ds", "fx"):
-        sim.arith = gs.GS_ARITH_DS if a.arith == "ds" else gs.GS_ARITH_FX
+    if a.arith != "ieee":
+        sim.arith = {"ds": gs.GS_ARITH_DS, "fx": gs.GS_ARITH_FX, "fxf": gs.GS_ARITH_FXF}[a.arith]
     if a.plan:
         f = a.plan.split(",")
         nums = [int(x) for x in f[1:]] + [0] * (5 - len(f[1:]))

@@ -324,11 +324,11 @@ def test_autotune_restores_state_and_keeps_fastest_plan(dtype):
 
 
 # ---------------------------------------------------------------------------
-# FP64 fields in double-single (GS_ARITH_DS) and fixed-point (GS_ARITH_FX)
-# arithmetic
+# FP64 fields in double-single (GS_ARITH_DS), fixed-point (GS_ARITH_FX) and
+# fixed-point-with-remainder (GS_ARITH_FXF) arithmetic
 # ---------------------------------------------------------------------------
-ARITHS = [gs.GS_ARITH_DS, gs.GS_ARITH_FX]
-ARITH_IDS = ["ds", "fx"]
+ARITHS = [gs.GS_ARITH_DS, gs.GS_ARITH_FX, gs.GS_ARITH_FXF]
+ARITH_IDS = ["ds", "fx", "fxf"]
 
 
 def make_ar(arith, L, kernel=None, tiles=(0, 0, 0), **kw):
@@ -426,6 +426,40 @@ def test_conv_arith_full_size_sampled_cells(arith):
     sim.close()
 
 
+@pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
+def test_fxf_packed_between_the_steps_of_a_call(kernel):
+    # GS_ARITH_FXF keeps the fields as packed pairs between the steps of one
+    # gs_step call and rounds them to FP64 only at its end: n steps in one
+    # call and in n calls differ by those roundings, and both match the oracle
+    L, n = 32, 30
+    prm = dict(PAPER, noise=0.1, seed=21)
+    u0, v0 = inputs.random_fields(L, seed=8, lo=0.0, hi=1.0)
+    one = make_ar(gs.GS_ARITH_FXF, L, kernel, **prm)
+    many = make_ar(gs.GS_ARITH_FXF, L, kernel, **prm)
+    for s in (one, many):
+        s.write(u0, v0)
+    one.step(n)
+    for _ in range(n):
+        many.step(1)
+    assert one.t == many.t == n
+    u1, v1 = one.read()
+    un, vn = many.read()
+    uo, vo = oracle.step(u0, v0, n, **prm)
+    e1 = max(maxabs(u1, uo), maxabs(v1, vo))
+    en = max(maxabs(un, uo), maxabs(vn, vo))
+    d = max(maxabs(u1, un), maxabs(v1, vn))
+    print(f"FXF {n} steps: one call {e1:.3e}, {n} calls {en:.3e} from the oracle; apart {d:.3e}")
+    assert e1 <= TOL["f64"] and en <= TOL["f64"] and d <= 1e-11
+    # a second call continues from FP64 fields exactly as a fresh object would
+    fresh = make_ar(gs.GS_ARITH_FXF, L, kernel, **prm)
+    fresh.write(u1, v1)
+    fresh.t = n
+    one.step(5)
+    fresh.step(5)
+    np.testing.assert_array_equal(one.read()[0], fresh.read()[0])
+    np.testing.assert_array_equal(one.read()[1], fresh.read()[1])
+
+
 def test_conv_arith_only_for_fp64_fields():
     s32 = make(16, "f32")
     for ar in ARITHS:
@@ -438,13 +472,15 @@ def test_conv_arith_only_for_fp64_fields():
 
 
 @pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
-def test_fx_reports_values_outside_its_range(kernel):
-    # |u| >= 1024 cannot be held in the fixed-point format: the next check
-    # reports it once, and the object stays usable
+@pytest.mark.parametrize("arith,bad", [(gs.GS_ARITH_FX, 2048.0), (gs.GS_ARITH_FXF, 4.5), (gs.GS_ARITH_FXF, -4.0)],
+                         ids=["fx", "fxf", "fxf-neg"])
+def test_fixed_point_reports_values_outside_its_range(kernel, arith, bad):
+    # |u| >= 1024 (FX) or >= 4 (FXF) cannot be held in the fixed-point
+    # format: the next check reports it once, and the object stays usable
     L = 16
-    sim = make_ar(gs.GS_ARITH_FX, L, kernel, noise=0.0, seed=0)
+    sim = make_ar(arith, L, kernel, noise=0.0, seed=0)
     u0, v0 = inputs.random_fields(L, seed=3, lo=0.0, hi=1.0)
-    u0[3, 4, 5] = 2048.0
+    u0[3, 4, 5] = bad
     sim.write(u0, v0)
     sim.step(1)
     with pytest.raises(gs.GsError) as e:
