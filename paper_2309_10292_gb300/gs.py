@@ -985,7 +985,7 @@ class GrayScottBatch:
         gs_batch_set_depth(self.handle, depth)
 
     def autotune(self, steps_per_trial: int = 20) -> dict:
-        """Pick the batched launch's z-chunk and ring depth (state left unchanged)."""
+        """Pick the batched launch's z-chunk, ring depth and temporal-blocking depth (state left unchanged)."""
         return gs_batch_autotune(self.handle, steps_per_trial)
 
     @property
