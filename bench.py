@@ -89,7 +89,7 @@ def kernel_digest() -> str:
 
 
 TBLOCK_PROFILE = os.path.join(ROOT, "profiles", "gs_tblock_issue_L512.md")
-TBLOCK_SRC = [os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", f) for f in ("gs_tblock.cu", "gs_common.cuh")]
+TBLOCK_SRC = [os.path.join(ROOT, "paper_2309_10292_gb300", "csrc", f) for f in ("gs_tblock.cu", "gs_tblock.cuh", "gs_common.cuh")]
 
 
 def profiled_issue():

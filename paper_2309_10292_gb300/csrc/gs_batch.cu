@@ -35,6 +35,7 @@
 
 #include "gs_common.cuh"
 #include "gs_internal.h"
+#include "gs_tblock.cuh"
 
 namespace gs {
 
@@ -328,20 +329,16 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
 // ---------------------------------------------------------------------------
 // Temporally blocked batch (FP32, D = 2..4 steps per pass over HBM).
 //
-// The schedule is the single-grid gs_tblock_kernel's (level s = 1..D applies
-// step t + s - 1 to plane j = p + 1 - 2 (s - 1) at iteration p, register
-// FIFOs for the z neighbours, a 3-plane shared ring per level for the y
-// neighbours, one barrier per iteration), on the batch's full-row tiles: a
-// work item is ty_i rows of instance i by a z-chunk, and its region is the
-// whole row (the x wrap is an index wrap in shared memory, so no cell is
-// recomputed in x) by ty_i + 2D rows (the y halo shrinks by one row per
-// level).  ty_i is the largest divisor of L_i with (L_i / 4) (ty_i + 2D)
-// groups fitting the 512 threads, one group of 4 cells per thread.  Each
-// thread stages its own group with 16-byte cp.async copies into a 5-plane
-// ring.  All CTAs meet at the grid barrier after each pass (D steps).
+// The single-grid kernel's schedule (tb_item, gs_tblock.cuh) on the batch's
+// full-row tiles: a work item is ty_i rows of instance i by a z-chunk, and
+// its region is the whole row (the x wrap is an index wrap in shared memory,
+// so no cell is recomputed in x) by ty_i + 2D rows (the y halo shrinks by
+// one row per level).  ty_i is the largest divisor of L_i with
+// (L_i / 4) (ty_i + 2D) groups fitting the 512 threads, one group of 4 cells
+// per thread.  All CTAs meet at the grid barrier after each pass (D steps).
 // ---------------------------------------------------------------------------
 constexpr int kBtbThreads = 512;
-constexpr int kBtbStages = 5;  // level-0 ring (7 planes measured no faster)
+constexpr int kBtbStages = kTbStages;  // level-0 ring (7 planes measured no faster)
 constexpr int kBtbMaxDepth = 4;
 
 // rows per tile of the blocked form for edge L and depth D (0: no tile fits)
@@ -377,24 +374,15 @@ struct BtbArgs {
     int fault;          // 2: CTA 0 never arrives at the grid barrier
 };
 
-static GS_D void btb_cp16(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(gs_smem_addr(smem)), "l"(gmem) : "memory");
-}
-static GS_D void btb_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-static GS_D void btb_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 template <bool NOISE, int D>
 __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __grid_constant__ BtbArgs a)
 {
     constexpr int V = 4;
-    constexpr int S = kBtbStages;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ volatile int s_abort;
     float* ring = reinterpret_cast<float*>(smem);
     const int PE = a.pe;
-    float* lev = ring + (size_t)S * 2 * PE;
+    float* lev = ring + (size_t)kBtbStages * 2 * PE;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) s_abort = 0;
     __syncthreads();
@@ -410,31 +398,25 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
             const int L = I.L, G = L / V, W = L;
             const int ty = a.rows[itm.x];
             const int H = ty + 2 * D;
-            const int y0 = itm.y, z0 = itm.z, nz = itm.w;
-            const bool real = tid < G * H;
-            const int gx = real ? tid % G : 0;
-            const int row = real ? tid / G : 0;
-            const uint32_t LL = (uint32_t)L * (uint32_t)L;
-            // this thread's group and its neighbours in shared memory: y
-            // clamped inside the region (clamped values feed unused cells
-            // only), x periodic within the row
-            const int o = row * W + gx * V;
-            const int oym = (row > 0 ? row - 1 : row) * W + gx * V;
-            const int oyp = (row < H - 1 ? row + 1 : row) * W + gx * V;
-            const bool lsh = gx > 0 && lane > 0;
-            const bool rsh = gx < G - 1 && lane < 31;
-            const int oxl = gx > 0 ? o - 1 : row * W + W - 1;
-            const int oxr = gx < G - 1 ? o + V : row * W;
-            bool act[D + 1], wact[D + 1];
+            // this thread's place in the item's region: x periodic within the
+            // row, y clamped inside the region
+            TbThread<D> th;
+            th.real = tid < G * H;
+            const int gx = th.real ? tid % G : 0;
+            const int row = th.real ? tid / G : 0;
+            th.o = row * W + gx * V;
+            th.oym = (row > 0 ? row - 1 : row) * W + gx * V;
+            th.oyp = (row < H - 1 ? row + 1 : row) * W + gx * V;
+            th.lsh = gx > 0 && lane > 0;
+            th.rsh = gx < G - 1 && lane < 31;
+            th.oxl = gx > 0 ? th.o - 1 : row * W + W - 1;
+            th.oxr = gx < G - 1 ? th.o + V : row * W;
 #pragma unroll
             for (int s = 1; s <= D; ++s) {
-                act[s] = real && row >= s && row < H - s;
-                // warp-uniform: some lane of this warp needs level s (the
-                // region's halo rows and the threads beyond it skip whole
-                // warps; within a warp every lane computes, branch-free)
-                wact[s] = __any_sync(0xffffffffu, act[s]);
+                th.act[s] = th.real && row >= s && row < H - s;
+                th.wact[s] = __any_sync(0xffffffffu, th.act[s]);
             }
-            const bool store = real && row >= D && row < D + ty;
+            th.store = th.real && row >= D && row < D + ty;
             GsCoef<float> c;
             c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise24 = a.noise24;
             c.F = (float)I.F; c.Fk = (float)I.Fk;
@@ -446,113 +428,10 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
                 keys[s] = gs_step_keys(seed, tp + s);
                 kk2[s] = gs_kk2(keys[s]);
             }
-            const float* u = a.arena + I.off[in][0];
-            const float* v = a.arena + I.off[in][1];
-            float* un = a.arena + I.off[out][0];
-            float* vn = a.arena + I.off[out][1];
-            const int yg = (y0 - D + row + L) % L;
-            const uint32_t rowoff = (uint32_t)yg * (uint32_t)L + (uint32_t)(gx * V);
-            const int zlo = z0 - D;            // global z of local level-0 plane 0
-            const int nplanes = nz + 2 * D;    // level-0 planes z0-D .. z0+nz+D-1
-            const int niter = nz + 3 * D - 3;  // level D finishes local plane nz+D-1 at it = nz+3D-4
-
-            auto issue = [&](int jl) {
-                if (real && jl < nplanes) {
-                    int zq = zlo + jl;
-                    zq += zq < 0 ? L : 0;
-                    zq -= zq >= L ? L : 0;
-                    const size_t gidx = (size_t)zq * LL + rowoff;
-                    float* st = ring + (size_t)(jl % S) * 2 * PE;
-                    btb_cp16(st + o, u + gidx);
-                    btb_cp16(st + PE + o, v + gidx);
-                }
-                btb_commit();
-            };
-#pragma unroll
-            for (int jl = 0; jl < S - 1; ++jl) issue(jl);
-            btb_wait<S - 4>();  // planes 0, 1, 2 complete (S - 4 newer ones pending)
-            __syncthreads();
-
-            float fu[D][3][4], fv[D][3][4];
-            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + o), fu[0][1]);
-            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + PE + o), fv[0][1]);
-            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + 2 * PE + o), fu[0][2]);
-            gs_unpack<float>(*reinterpret_cast<const float4*>(ring + 3 * PE + o), fv[0][2]);
-
-            auto iteration = [&](const int it, auto full_tag) {
-                constexpr bool FULL = decltype(full_tag)::value;
-                issue(it + S - 1);
-                const int zb = zlo + it + 1;  // global z of level 1's plane, unwrapped
-#pragma unroll
-                for (int s = D; s >= 1; --s) {
-                    const int j = it + 1 - 2 * (s - 1);
-                    // a warp with no lane at level s leaves it (and its FIFO
-                    // and level plane, which no active lane reads) alone
-                    if (!wact[s]) continue;
-                    if (s == 1) {
-                        const float* nb = ring + (size_t)((it + 2) % S) * 2 * PE;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            fu[0][0][e] = fu[0][1][e]; fu[0][1][e] = fu[0][2][e];
-                            fv[0][0][e] = fv[0][1][e]; fv[0][1][e] = fv[0][2][e];
-                        }
-                        gs_unpack<float>(*reinterpret_cast<const float4*>(nb + o), fu[0][2]);
-                        gs_unpack<float>(*reinterpret_cast<const float4*>(nb + PE + o), fv[0][2]);
-                    }
-                    const float* cb = s == 1 ? ring + (size_t)(j % S) * 2 * PE
-                                             : lev + ((size_t)(s - 2) * 3 + (size_t)(j % 3)) * 2 * PE;
-                    const float(&cu)[4] = fu[s - 1][1];
-                    const float(&cv)[4] = fv[s - 1][1];
-                    float xlu = __shfl_up_sync(0xffffffffu, cu[3], 1);
-                    float xlv = __shfl_up_sync(0xffffffffu, cv[3], 1);
-                    float xru = __shfl_down_sync(0xffffffffu, cu[0], 1);
-                    float xrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
-                    if (!FULL && !(j >= s && j <= nz + 2 * D - 1 - s)) continue;
-                    float ou[4] = {0.f, 0.f, 0.f, 0.f}, ov[4] = {0.f, 0.f, 0.f, 0.f};
-                    int zq = zb - 2 * (s - 1);
-                    zq += zq < 0 ? L : 0;
-                    zq -= zq >= L ? L : 0;
-                    if (FULL || act[s]) {
-                        if (!lsh) { xlu = cb[oxl]; xlv = cb[PE + oxl]; }
-                        if (!rsh) { xru = cb[oxr]; xrv = cb[PE + oxr]; }
-                        float ymu[4], ypu[4], ymv[4], ypv[4];
-                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + oym), ymu);
-                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + oyp), ypu);
-                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + PE + oym), ymv);
-                        gs_unpack<float>(*reinterpret_cast<const float4*>(cb + PE + oyp), ypv);
-                        const uint32_t g = (uint32_t)zq * LL + rowoff;
-                        const uint32_t pre = NOISE ? gs_group_pre(g, keys[s - 1]) : 0u;
-                        gs_update_group<float, NOISE>(c, pre, kk2[s - 1], cu, cv, fu[s - 1][0], fv[s - 1][0],
-                                                      fu[s - 1][2], fv[s - 1][2], ymu, ypu, ymv, ypv, xlu, xru,
-                                                      xlv, xrv, ou, ov);
-                        if (s < D) {
-                            float* wb = lev + ((size_t)(s - 1) * 3 + (size_t)(j % 3)) * 2 * PE;
-                            *reinterpret_cast<float4*>(wb + o) = gs_pack<float>(ou);
-                            *reinterpret_cast<float4*>(wb + PE + o) = gs_pack<float>(ov);
-                        } else if (store) {
-                            *reinterpret_cast<float4*>(un + (size_t)zq * LL + rowoff) = gs_pack<float>(ou);
-                            *reinterpret_cast<float4*>(vn + (size_t)zq * LL + rowoff) = gs_pack<float>(ov);
-                        }
-                    }
-                    if (s < D) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            fu[s][0][e] = fu[s][1][e]; fu[s][1][e] = fu[s][2][e]; fu[s][2][e] = ou[e];
-                            fv[s][0][e] = fv[s][1][e]; fv[s][1][e] = fv[s][2][e]; fv[s][2][e] = ov[e];
-                        }
-                    }
-                }
-                btb_wait<S - 4>();  // planes up to it + 3 complete (it + 4 .. it + S - 1 pending)
-                __syncthreads();
-            };
-            const int steady_end = nz + 2 * D - 2;  // every level in range for it in [3D-3, nz+2D-3]
-            int it = 0;
-            for (; it < 3 * D - 3; ++it) iteration(it, std::false_type{});
-#pragma unroll 3
-            for (; it < steady_end; ++it) iteration(it, std::true_type{});
-            for (; it < niter; ++it) iteration(it, std::false_type{});
-            btb_wait<0>();
-            __syncthreads();
+            const int yg = (itm.y - D + row + L) % L;
+            tb_item<NOISE, D, true>(a.arena + I.off[in][0], a.arena + I.off[in][1], a.arena + I.off[out][0],
+                              a.arena + I.off[out][1], L, (uint32_t)yg * (uint32_t)L + (uint32_t)(gx * V), itm.z,
+                              itm.w, c, keys, kk2, th, ring, lev, PE);
         }
         const bool skip = a.fault == 2 && blockIdx.x == 0;
         if (!batch_grid_sync(a.ctrl, (unsigned)((unsigned long long)(pass + 1) * gridDim.x), a.timeout_ns, skip,

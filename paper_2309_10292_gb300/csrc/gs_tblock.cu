@@ -1,24 +1,14 @@
 // Temporally blocked Gray-Scott stencil: D time steps per pass over HBM
 // (FP32).
 //
-// Each CTA owns an x-y tile of TX x TY cells and a z-chunk of TZ planes.  It
-// stages the tile plus a halo of HX = 4 cells in x and D rows in y (periodic
-// wrap by modular addressing) plane by plane into a shared-memory ring with
-// 16-byte cp.async copies, one group of 4 cells per thread.  Level s = 1..D
-// applies step t+s-1 (gs_update_group, the arithmetic of every other kernel)
-// to the region where level s-1 is valid, which shrinks by one cell per
-// level.  Level s computes plane j = p + 1 - 2 (s - 1) at iteration p (two
-// planes behind level s-1), so every input of every level was produced in an
-// earlier iteration: the levels of one iteration are independent (the
-// instruction-level parallelism that hides latency), levels run from the
-// top down and each reads its input FIFO before the level below pushes.  The
-// z-1 / z / z+1 values of a thread's own group come from per-level register
-// FIFOs, x neighbours from the adjacent lanes, and only the y neighbours
-// from shared memory (a 3-plane ring per level), so one __syncthreads per
-// iteration orders everything.  Level D writes the tile's interior to
-// HBM.  HBM traffic per cell and pass: one read and one write of u and v
-// (16 B) plus halo re-reads of neighbouring tiles (mostly L2 hits), for D
-// steps.
+// Each CTA owns an x-y tile of TX x TY cells and a z-chunk of TZ planes.  Its
+// region is the tile plus a halo of HX = 4 cells in x and D rows in y
+// (periodic wrap by modular addressing), one group of 4 cells per thread, and
+// tb_item (gs_tblock.cuh) stages, steps and stores it: level s applies step
+// t + s - 1 where level s-1 is valid, the region shrinking by one cell per
+// level in x and y.  HBM traffic per cell and pass: one read and one write of
+// u and v (16 B) plus halo re-reads of neighbouring tiles (mostly L2 hits),
+// for D steps.
 //
 // Requirements (checked by tblock_validate): L % TX == 0, L % TY == 0,
 // TX % 4 == 0, 2 <= D <= 8, at most 512 threads.  Depths 5-8 use the deep
@@ -29,10 +19,9 @@
 
 #include "gs_common.cuh"
 #include "gs_internal.h"
+#include "gs_tblock.cuh"
 
 namespace gs {
-
-constexpr int kTbStages = 5;  // level-0 ring depth (planes)
 
 struct TbArgs {
     const float* u;
@@ -48,14 +37,6 @@ struct TbArgs {
     GsKeys keys[8];       // step t + s - 1 for level s
 };
 
-GS_D void cp_async16(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(gs_smem_addr(smem)), "l"(gmem) : "memory");
-}
-GS_D void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-GS_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // Shared memory: level-0 ring of kTbStages planes, then for each level
 // 1..D-1 a ring of 3 planes; each plane holds u then v, H rows x W cells.
 template <bool NOISE, int D>
@@ -63,34 +44,32 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_kernel(const TbArgs a)
 {
     constexpr int V = 4;
     constexpr int HX = 4;
-    constexpr int S = kTbStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);
-    float* lev = ring + (size_t)S * 2 * a.plane_elems;
+    float* lev = ring + (size_t)kTbStages * 2 * a.plane_elems;
     const int tid = threadIdx.x, lane = tid & 31;
     const int G = a.G, W = a.W, H = a.H, L = a.L;
-    const int PE = a.plane_elems;
-    const bool real = tid < G * H;
-    const int gx = real ? tid % G : 0;
-    const int row = real ? tid / G : 0;
-    const uint32_t LL = (uint32_t)L * (uint32_t)L;
 
-    // shared-memory offsets of this thread's group and its y neighbours
-    // (clamped inside the region: clamped values only feed unused cells)
-    const int o = row * W + gx * V;
-    const int oym = (row > 0 ? row - 1 : row) * W + gx * V;
-    const int oyp = (row < H - 1 ? row + 1 : row) * W + gx * V;
+    // this thread's place in the region (the same for every tile)
+    TbThread<D> th;
+    th.real = tid < G * H;
+    const int gx = th.real ? tid % G : 0;
+    const int row = th.real ? tid / G : 0;
+    th.o = row * W + gx * V;
+    th.oym = (row > 0 ? row - 1 : row) * W + gx * V;
+    th.oyp = (row < H - 1 ? row + 1 : row) * W + gx * V;
     // x neighbours from the adjacent lanes when they hold this row's
-    // neighbouring groups, else from shared memory
-    const bool lsh = gx > 0 && lane > 0;
-    const bool rsh = gx < G - 1 && lane < 31;
-    const int oxl = gx > 0 ? o - 1 : o;
-    const int oxr = gx < G - 1 ? o + V : o + V - 1;
-    bool act[D + 1];
+    // neighbouring groups, else from shared memory (clamped inside the region)
+    th.lsh = gx > 0 && lane > 0;
+    th.rsh = gx < G - 1 && lane < 31;
+    th.oxl = gx > 0 ? th.o - 1 : th.o;
+    th.oxr = gx < G - 1 ? th.o + V : th.o + V - 1;
 #pragma unroll
-    for (int s = 1; s <= D; ++s)
-        act[s] = real && row >= s && row < H - s && gx * V + V > s && gx * V < W - s;
-    const bool store = real && row >= D && row < D + a.ty && gx * V >= HX && gx * V < HX + a.tx;
+    for (int s = 1; s <= D; ++s) {
+        th.act[s] = th.real && row >= s && row < H - s && gx * V + V > s && gx * V < W - s;
+        th.wact[s] = true;  // not used (rows of 10-18 groups rarely leave a whole warp idle)
+    }
+    th.store = th.real && row >= D && row < D + a.ty && gx * V >= HX && gx * V < HX + a.tx;
     uint32_t kk2[D];
 #pragma unroll
     for (int s = 0; s < D; ++s) kk2[s] = gs_kk2(a.keys[s]);
@@ -100,123 +79,10 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_kernel(const TbArgs a)
         const int tyi = (tile / a.ntx) % a.nty;
         const int tzi = tile / (a.ntx * a.nty);
         const int x0 = txi * a.tx, y0 = tyi * a.ty, z0 = tzi * a.tz;
-        const int nz = min(a.tz, L - z0);
         const int xg = (x0 - HX + gx * V + L) % L;
         const int yg = (y0 - D + row + L) % L;
-        const uint32_t rowoff = (uint32_t)yg * (uint32_t)L + (uint32_t)xg;
-        const int zlo = z0 - D;                 // global z of local level-0 plane 0
-        const int nplanes = nz + 2 * D;         // level-0 planes z0-D .. z0+nz+D-1
-        const int niter = nz + 3 * D - 3;       // level D finishes local plane nz+D-1 at it = nz+3D-4
-
-        auto issue = [&](int jl) {
-            if (real && jl < nplanes) {
-                int zq = zlo + jl;
-                zq += zq < 0 ? L : 0;
-                zq -= zq >= L ? L : 0;
-                const size_t gidx = (size_t)zq * LL + rowoff;
-                float* st = ring + (size_t)(jl % S) * 2 * PE;
-                cp_async16(st + o, a.u + gidx);
-                cp_async16(st + PE + o, a.v + gidx);
-            }
-            cp_async_commit();
-        };
-#pragma unroll
-        for (int jl = 0; jl < S - 1; ++jl) issue(jl);
-        cp_async_wait<S - 4>();  // planes 0, 1, 2 complete
-        __syncthreads();
-
-        // register FIFOs of this thread's group: level s planes (oldest, middle, newest)
-        float fu[D][3][4], fv[D][3][4];
-        gs_unpack<float>(*reinterpret_cast<const float4*>(ring + o), fu[0][1]);
-        gs_unpack<float>(*reinterpret_cast<const float4*>(ring + PE + o), fv[0][1]);
-        gs_unpack<float>(*reinterpret_cast<const float4*>(ring + 2 * PE + o), fu[0][2]);
-        gs_unpack<float>(*reinterpret_cast<const float4*>(ring + 3 * PE + o), fv[0][2]);
-
-        // One iteration: levels from the top down.  FULL (the steady state,
-        // every level in range) drops the range and activity tests, so the
-        // iteration is one straight-line block the compiler can interleave
-        // across levels: inactive threads compute values nobody reads (their
-        // shared-memory offsets are clamped inside the region) and only
-        // `store` guards the write to HBM.
-        auto iteration = [&](const int it, auto full_tag) {
-            constexpr bool FULL = decltype(full_tag)::value;
-            issue(it + S - 1);
-            const int zb = zlo + it + 1;  // global z of local plane it + 1 (level 1's plane), unwrapped
-#pragma unroll
-            for (int s = D; s >= 1; --s) {
-                // level s computes local plane j = it + 1 - 2 (s - 1) from level s-1 planes
-                // j-1, j, j+1: all produced in earlier iterations
-                const int j = it + 1 - 2 * (s - 1);
-                if (s == 1) {
-                    // level 0 "computes" by loading: push local plane it + 2 (complete)
-                    const float* nb = ring + (size_t)((it + 2) % S) * 2 * PE;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        fu[0][0][e] = fu[0][1][e]; fu[0][1][e] = fu[0][2][e];
-                        fv[0][0][e] = fv[0][1][e]; fv[0][1][e] = fv[0][2][e];
-                    }
-                    gs_unpack<float>(*reinterpret_cast<const float4*>(nb + o), fu[0][2]);
-                    gs_unpack<float>(*reinterpret_cast<const float4*>(nb + PE + o), fv[0][2]);
-                }
-                // centre plane of level s-1 (for y and x neighbours)
-                const float* cb = s == 1 ? ring + (size_t)(j % S) * 2 * PE
-                                         : lev + ((size_t)(s - 2) * 3 + (size_t)(j % 3)) * 2 * PE;
-                const float(&cu)[4] = fu[s - 1][1];
-                const float(&cv)[4] = fv[s - 1][1];
-                // x neighbours by shuffle (all lanes take part)
-                float xlu = __shfl_up_sync(0xffffffffu, cu[3], 1);
-                float xlv = __shfl_up_sync(0xffffffffu, cv[3], 1);
-                float xru = __shfl_down_sync(0xffffffffu, cu[0], 1);
-                float xrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
-                if (!FULL && !(j >= s && j <= nz + 2 * D - 1 - s)) continue;
-                float ou[4] = {0.f, 0.f, 0.f, 0.f}, ov[4] = {0.f, 0.f, 0.f, 0.f};
-                int zq = zb - 2 * (s - 1);
-                zq += zq < 0 ? L : 0;
-                zq -= zq >= L ? L : 0;
-                if (FULL || act[s]) {
-                    if (!lsh) { xlu = cb[oxl]; xlv = cb[PE + oxl]; }
-                    if (!rsh) { xru = cb[oxr]; xrv = cb[PE + oxr]; }
-                    float ymu[4], ypu[4], ymv[4], ypv[4];
-                    gs_unpack<float>(*reinterpret_cast<const float4*>(cb + oym), ymu);
-                    gs_unpack<float>(*reinterpret_cast<const float4*>(cb + oyp), ypu);
-                    gs_unpack<float>(*reinterpret_cast<const float4*>(cb + PE + oym), ymv);
-                    gs_unpack<float>(*reinterpret_cast<const float4*>(cb + PE + oyp), ypv);
-                    const uint32_t g = (uint32_t)zq * LL + rowoff;
-                    const uint32_t pre = NOISE ? gs_group_pre(g, a.keys[s - 1]) : 0u;
-                    gs_update_group<float, NOISE>(a.c, pre, kk2[s - 1], cu, cv, fu[s - 1][0], fv[s - 1][0],
-                                                  fu[s - 1][2], fv[s - 1][2], ymu, ypu, ymv, ypv, xlu, xru, xlv,
-                                                  xrv, ou, ov);
-                    if (s < D) {
-                        float* wb = lev + ((size_t)(s - 1) * 3 + (size_t)(j % 3)) * 2 * PE;
-                        *reinterpret_cast<float4*>(wb + o) = gs_pack<float>(ou);
-                        *reinterpret_cast<float4*>(wb + PE + o) = gs_pack<float>(ov);
-                    } else if (store) {
-                        *reinterpret_cast<float4*>(a.un + (size_t)zq * LL + rowoff) = gs_pack<float>(ou);
-                        *reinterpret_cast<float4*>(a.vn + (size_t)zq * LL + rowoff) = gs_pack<float>(ov);
-                    }
-                }
-                if (s < D) {
-                    // push level s plane j (values of inactive threads are never used)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        fu[s][0][e] = fu[s][1][e]; fu[s][1][e] = fu[s][2][e]; fu[s][2][e] = ou[e];
-                        fv[s][0][e] = fv[s][1][e]; fv[s][1][e] = fv[s][2][e]; fv[s][2][e] = ov[e];
-                    }
-                }
-            }
-            cp_async_wait<S - 4>();  // planes up to it + 3 complete
-            __syncthreads();
-        };
-        // every level is in range for it in [3D-3, nz+2D-3]
-        const int steady_end = nz + 2 * D - 2;
-        int it = 0;
-        for (; it < 3 * D - 3; ++it) iteration(it, std::false_type{});
-        // unrolled by 3: the FIFO rotation becomes register renaming
-#pragma unroll 3
-        for (; it < steady_end; ++it) iteration(it, std::true_type{});
-        for (; it < niter; ++it) iteration(it, std::false_type{});
-        cp_async_wait<0>();
-        __syncthreads();
+        tb_item<NOISE, D, false>(a.u, a.v, a.un, a.vn, L, (uint32_t)yg * (uint32_t)L + (uint32_t)xg, z0, min(a.tz, L - z0),
+                          a.c, a.keys, kk2, th, ring, lev, a.plane_elems);
     }
 }
 
@@ -285,14 +151,14 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_deep_kernel(const TbArgs a)
                 zq -= zq >= L ? L : 0;
                 const size_t gidx = (size_t)zq * LL + rowoff;
                 float* st = ring + (size_t)(jl % S) * 2 * PE;
-                cp_async16(st + o, a.u + gidx);
-                cp_async16(st + PE + o, a.v + gidx);
+                tb_cp16(st + o, a.u + gidx);
+                tb_cp16(st + PE + o, a.v + gidx);
             }
-            cp_async_commit();
+            tb_commit();
         };
 #pragma unroll
         for (int jl = 0; jl < S - 1; ++jl) issue(jl);
-        cp_async_wait<S - 4>();  // planes 0, 1, 2 complete
+        tb_wait<S - 4>();  // planes 0, 1, 2 complete
         __syncthreads();
 
         for (int it = 0; it < niter; ++it) {
@@ -344,10 +210,10 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_deep_kernel(const TbArgs a)
                     *reinterpret_cast<float4*>(a.vn + (size_t)zq * LL + rowoff) = gs_pack<float>(ov);
                 }
             }
-            cp_async_wait<S - 4>();  // planes up to it + 3 complete
+            tb_wait<S - 4>();  // planes up to it + 3 complete
             __syncthreads();
         }
-        cp_async_wait<0>();
+        tb_wait<0>();
         __syncthreads();
     }
 }
