@@ -339,9 +339,9 @@ int gs_batch_set_fault(gs_batch* b, int mode, uint64_t timeout_ns);
  * drops the captured graphs. */
 int gs_batch_set_plan(gs_batch* b, int tile_z, int stages);
 
-/* Temporal-blocking depth of the batched launch (not in the paper; the
- * spec workload asks for it): D = 1 (default) runs one step per pass
- * over HBM; D = 2..4 (FP32 batches only) fuses D steps per pass.  The blocked
+/* Temporal-blocking depth of the batched launch (not in the paper): D = 1
+ * (default) runs one step per pass over HBM; D = 2..4 (FP32 batches only)
+ * fuses D steps per pass.  The blocked
  * kernel cuts instance i into full-row tiles of ty_i rows, ty_i the largest
  * divisor of L[i] with (L[i] / 4) * (ty_i + 2D) <= 512, by the z-chunk of
  * gs_batch_set_plan, and recomputes a halo of D - s rows at level s (none in
