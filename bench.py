@@ -751,7 +751,11 @@ def run_ours(args):
     if rank == 0 and not args.no_fp64:
         # FP64 runs of the same workload (oracle-matching precision), shorter:
         # IEEE FP64 arithmetic, and double-single arithmetic on the FP32 pipe
+        ref64 = {}
+
         def fp64_rate(arith):
+            # GCUPS, and the max-abs difference of the final fields (5 + n64
+            # steps from the centred cube) from the IEEE FP64 run's
             s64 = gs.GrayScott(L, dtype="f64", noise=NOISE, seed=SEED, **PARAMS)
             s64.arith = arith
             if arith != gs.GS_ARITH_IEEE:
@@ -764,18 +768,25 @@ def run_ours(args):
             s64.step(n64)
             b.record(stream)
             torch.cuda.synchronize()
+            u, v = s64.tensors()
+            if arith == gs.GS_ARITH_IEEE:
+                ref64["u"], ref64["v"] = u.clone(), v.clone()
+                diff = 0.0
+            else:
+                diff = max(float((u - ref64["u"]).abs().max()), float((v - ref64["v"]).abs().max()))
             s64.close()
-            return cells * n64 / (a.elapsed_time(b) / 1e3) / 1e9
+            return cells * n64 / (a.elapsed_time(b) / 1e3) / 1e9, diff
 
         n64 = 100
         # the FP64 pipe's measured rate (FMAs per second), clocks sampled meanwhile
         csamp = Clocks(torch.cuda.current_device())
         fp64_ops = max(gs.gs_measure_fp64_fma(stream) for _ in range(6))
         fp64_clocks = csamp.stop()
-        g64 = fp64_rate(gs.GS_ARITH_IEEE)
-        g64ds = fp64_rate(gs.GS_ARITH_DS)
-        g64fx = fp64_rate(gs.GS_ARITH_FX)
-        g64fxf = fp64_rate(gs.GS_ARITH_FXF)
+        g64, _ = fp64_rate(gs.GS_ARITH_IEEE)
+        g64ds, d64ds = fp64_rate(gs.GS_ARITH_DS)
+        g64fx, d64fx = fp64_rate(gs.GS_ARITH_FX)
+        g64fxf, d64fxf = fp64_rate(gs.GS_ARITH_FXF)
+        ref64.clear()
         # precision: the FP32 result of the whole workload (the e2e run's
         # output) against the same run in IEEE FP64 on the GPU
         s64 = gs.GrayScott(L, dtype="f64", noise=NOISE, seed=SEED, **PARAMS)
@@ -799,16 +810,20 @@ def run_ours(args):
                                           "peak_clocks": fp64_clocks,
                                           "nominal_peak": 625.0},
                          "double_single": {"value": g64ds, "unit": "GCUPS", "hbm_frac": g64ds * 32.0 / hbm_peak,
+                                           "max_abs_vs_ieee_fp64": d64ds,
                                            "note": "FP64 fields, double-single arithmetic on the FP32 pipe "
                                                    "(within 1e-13 of the FP64 oracle)"},
                          "fixed_point": {"value": g64fx, "unit": "GCUPS", "hbm_frac": g64fx * 32.0 / hbm_peak,
+                                         "max_abs_vs_ieee_fp64": d64fx,
                                          "note": "FP64 fields, 64-bit fixed point on the integer pipes: exact "
                                                  "neighbour sums (within 1e-14 of the FP64 oracle)"},
                          "fixed_point_remainder": {"value": g64fxf, "unit": "GCUPS",
                                                    "hbm_frac": g64fxf * 32.0 / hbm_peak,
+                                                   "max_abs_vs_ieee_fp64": d64fxf,
                                                    "note": "FP64 fields, 32-bit fixed point with an FP32 "
                                                            "remainder: exact integer neighbour sums, float-pair "
-                                                           "products"}}
+                                                           "products (within 2e-13 of the FP64 oracle)"},
+                         "compared_after_steps": 5 + n64}
 
     if rank == 0 and not args.no_batch:
         extra["batched"] = bench_batched(args, stream, hbm_peak)
