@@ -554,7 +554,8 @@ int gs_autotune(gs_sim* s, int steps_per_trial, gs_plan* results, int max_result
     // candidate plans
     std::vector<gs_plan> cand;
     cand.push_back(gs_plan{GS_KERNEL_NAIVE, 0, 0, 0, 1, 0, 0.0});
-    const int zt[][2] = {{128, 8}, {256, 4}, {64, 16}, {128, 4}, {64, 8}, {256, 8}, {128, 16}, {32, 16}, {128, 10}};
+    const int zt[][2] = {{128, 8}, {256, 4}, {64, 16}, {128, 4}, {64, 8}, {256, 8}, {128, 16}, {32, 16}, {128, 10},
+                         {128, 12}, {256, 6}};
     for (auto& t : zt)
         for (int tz : {32, 64, 128})
             for (int st : {4, 6, 8}) cand.push_back(gs_plan{GS_KERNEL_ZMARCH, t[0], t[1], tz, 1, st, 0.0});

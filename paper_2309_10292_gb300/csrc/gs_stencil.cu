@@ -349,7 +349,7 @@ GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
 // 2 (output packed)); the ones that read FP64 values into another
 // arithmetic convert every staged plane in place once (CONV)
 template <typename T, bool NOISE, int AR>
-__global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
+GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
 {
     constexpr bool DS = AR == 1;
     constexpr bool FXF = AR >= 3;
@@ -621,6 +621,21 @@ __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs
     }
 }
 
+template <typename T, bool NOISE, int AR>
+__global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
+{
+    zmarch_body<T, NOISE, AR>(maps, a);
+}
+
+// The fixed point with a remainder, capped at 72 registers (which its
+// packed-step form needs anyway): 7 warps of 72 fit one SM sub-partition's
+// 16K registers, so tiles of up to 25 warps (128 x 12 cells) fit an SM.
+template <bool NOISE, int AR>
+__global__ void __maxnreg__(72) gs_zmarch_fxf_kernel(const __grid_constant__ ZMaps maps, const ZArgs<double> a)
+{
+    zmarch_body<double, NOISE, AR>(maps, a);
+}
+
 bool zmarch_supported(int dtype, int L)
 {
     const int V = dtype == GS_F32 ? 4 : 2;
@@ -694,7 +709,11 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     const int ncons = (pl.tx / V) * pl.ty;
     const int threads = ((ncons + 31) & ~31) + 32;
     const size_t smem = (size_t)a.lay.stage_bytes * pl.stages;
-    auto kern = gs_zmarch_kernel<T, NOISE, AR>;
+    void (*kern)(const ZMaps, const ZArgs<T>) = nullptr;
+    if constexpr (AR >= 3)
+        kern = gs_zmarch_fxf_kernel<NOISE, AR>;
+    else
+        kern = gs_zmarch_kernel<T, NOISE, AR>;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
