@@ -339,12 +339,12 @@ int gs_step(gs_sim* s, int64_t n)
     const int64_t first = i;
     for (; i < n; ++i) {
         const int in = s->cur, outs = 1 - s->cur;
-        // GS_ARITH_FXF keeps the fields as packed (X, l) pairs between the
-        // steps of this call (periodic grids): the first step reads FP64, the
-        // last writes FP64
+        // the FP64 arithmetics other than IEEE keep the fields in their own
+        // packed form between the steps of this call (periodic grids): the
+        // first step reads FP64, the last writes FP64
         Params p = s->p;
-        if (p.arith == GS_ARITH_FXF && s->boundary == GS_BOUNDARY_PERIODIC)
-            p.fxf_io = (i > first ? 1 : 0) | (i + 1 < n ? 2 : 0);
+        if (p.arith != GS_ARITH_IEEE && s->boundary == GS_BOUNDARY_PERIODIC)
+            p.io = (i > first ? 1 : 0) | (i + 1 < n ? 2 : 0);
         int rc;
         if (s->kernel != GS_KERNEL_NAIVE) {
             if (!s->maps_ok) return fail(GS_ESTATE, "tensor maps not encoded");

@@ -162,7 +162,8 @@ GS_D void gs_update_ds(const GsCoefDS& c, GsDS u, GsDS v, GsDS su, GsDS sv, floa
 
 // A double-single pair kept in the 8 bytes of a double (hi in the low word):
 // the z-marching kernel converts each staged plane in place once, so its
-// neighbours are read already converted.
+// neighbours are read already converted, and the steps inside one gs_step
+// call keep the fields in this form between steps.
 GS_D double ds_pack(GsDS a)
 {
     return __longlong_as_double(
@@ -184,8 +185,9 @@ struct GsFromPacked {
 
 // A 2-cell group of FP64 cells (the z-marching kernels' double2 groups);
 // `get` turns an input into a pair (conversion of an FP64 value, or a pair
-// packed by ds_pack): the arithmetic is the same either way.
-template <bool NOISE, typename Get = GsFromDouble>
+// packed by ds_pack): the arithmetic is the same either way.  PACK: write
+// the results as packed pairs (ds_pack) instead of FP64 values.
+template <bool NOISE, typename Get = GsFromDouble, bool PACK = false>
 GS_D void gs_update_group_ds(const GsCoefDS& c, uint32_t pre, uint32_t kk2, const double* cu, const double* cv,
                              const double* pu, const double* pv, const double* nu, const double* nv,
                              const double* ymu, const double* ypu, const double* ymv, const double* ypv,
@@ -208,7 +210,7 @@ GS_D void gs_update_group_ds(const GsCoefDS& c, uint32_t pre, uint32_t kk2, cons
         const float rn = NOISE ? (float)gs_group_num(pre, (uint32_t)e, kk2) : 0.0f;
         GsDS un, vn;
         gs_update_ds<NOISE>(c, u[e], v[e], su, sv, rn, un, vn);
-        ou[e] = ds_to_double(un);
-        ov[e] = ds_to_double(vn);
+        ou[e] = PACK ? ds_pack(un) : ds_to_double(un);
+        ov[e] = PACK ? ds_pack(vn) : ds_to_double(vn);
     }
 }

@@ -106,13 +106,14 @@ GS_D void gs_update_fx(const GsCoefFX& c, long long u, long long v, long long su
 }
 
 // A fixed-point value kept in the 8 bytes of a double (the z-marching
-// kernel converts each staged plane in place once).
+// kernel converts each staged plane in place once, and the steps inside one
+// gs_step call keep the fields in this form between steps).
 GS_D double fx_pack(long long X) { return __longlong_as_double(X); }
 GS_D long long fx_unpack(double d) { return (long long)__double_as_longlong(d); }
 
 // A 2-cell group of FP64 cells whose inputs are packed fixed-point values;
-// writes FP64 outputs.
-template <bool NOISE>
+// writes packed values (PACK) or FP64 outputs.
+template <bool NOISE, bool PACK = false>
 GS_D void gs_update_group_fx(const GsCoefFX& c, uint32_t pre, uint32_t kk2, const double* cu, const double* cv,
                              const double* pu, const double* pv, const double* nu, const double* nv,
                              const double* ymu, const double* ypu, const double* ymv, const double* ypv,
@@ -128,7 +129,7 @@ GS_D void gs_update_group_fx(const GsCoefFX& c, uint32_t pre, uint32_t kk2, cons
         const int32_t rn = NOISE ? gs_group_num(pre, (uint32_t)e, kk2) : 0;
         long long un, vn;
         gs_update_fx<NOISE>(c, u, v, su, sv, rn, un, vn);
-        ou[e] = fx_to_double(un);
-        ov[e] = fx_to_double(vn);
+        ou[e] = PACK ? fx_pack(un) : fx_to_double(un);
+        ov[e] = PACK ? fx_pack(vn) : fx_to_double(vn);
     }
 }

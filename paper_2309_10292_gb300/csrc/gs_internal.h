@@ -16,11 +16,11 @@ struct Params {
     double Du, Dv, F, k, dt, noise;
     uint64_t seed;
     int arith = GS_ARITH_IEEE;  // GS_ARITH_DS: FP64 fields in double-single arithmetic
-    // GS_ARITH_FXF only: bit 0 = the input fields hold packed (X, l) pairs
-    // instead of FP64 values, bit 1 = write packed pairs (the steps inside
-    // one gs_step call keep the fields packed; the call's first step reads
-    // FP64 and its last writes FP64)
-    int fxf_io = 0;
+    // FP64 fields in GS_ARITH_DS, _FX or _FXF: bit 0 = the input fields hold
+    // that arithmetic's packed values instead of FP64 values, bit 1 = write
+    // packed values (the steps inside one gs_step call keep the fields
+    // packed; the call's first step reads FP64 and its last writes FP64)
+    int io = 0;
 };
 
 // Thread-local error message + status helper.

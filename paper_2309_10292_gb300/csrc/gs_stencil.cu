@@ -67,15 +67,16 @@ static GsCoef<T> make_coef(const Params& p)
 }
 
 // AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed
-// point, 3-6: fixed point with a float remainder, 3 + (input packed) +
-// 2 (output packed))
-template <typename T, bool NOISE, int AR>
+// point, 3: fixed point with a float remainder).  IO (AR > 0): bit 0 = the
+// inputs hold that arithmetic's packed values (else FP64 values, converted
+// at use), bit 1 = write packed values (else FP64).
+template <typename T, bool NOISE, int AR, int IO = 0>
 __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, const T* __restrict__ v,
                                                        T* __restrict__ un, T* __restrict__ vn, int L,
                                                        GsCoef<T> c, GsCoefDS cds, GsCoefFX cfx, GsCoefFXF cfxf,
                                                        GsKeys k, int* err)
 {
-    constexpr bool DS = AR == 1;
+    constexpr bool IN_PACKED = (IO & 1) != 0, OUT_PACKED = (IO & 2) != 0;
     const int64_t n = (int64_t)L * L * L;
     const int64_t LL = (int64_t)L * L;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -93,41 +94,44 @@ __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, 
         const int64_t base = i - (int64_t)z * LL;
         const int64_t izm = base + (int64_t)(z == 0 ? L - 1 : z - 1) * LL;
         const int64_t izp = base + (int64_t)(z == L - 1 ? 0 : z + 1) * LL;
-        if constexpr (DS) {
+        if constexpr (AR == 1) {
             // FP64 fields in double-single arithmetic (gs_ds.cuh)
-            const GsDS uc = ds_from_double(u[i]), vc = ds_from_double(v[i]);
-            const GsDS su = ds_nsum(ds_from_double(u[ixm]), ds_from_double(u[ixp]), ds_from_double(u[iym]),
-                                    ds_from_double(u[iyp]), ds_from_double(u[izm]), ds_from_double(u[izp]));
-            const GsDS sv = ds_nsum(ds_from_double(v[ixm]), ds_from_double(v[ixp]), ds_from_double(v[iym]),
-                                    ds_from_double(v[iyp]), ds_from_double(v[izm]), ds_from_double(v[izp]));
+            auto get = [&](double x) -> GsDS {
+                if constexpr (IN_PACKED) return ds_unpack(x);
+                else return ds_from_double(x);
+            };
+            const GsDS uc = get(u[i]), vc = get(v[i]);
+            const GsDS su = ds_nsum(get(u[ixm]), get(u[ixp]), get(u[iym]), get(u[iyp]), get(u[izm]), get(u[izp]));
+            const GsDS sv = ds_nsum(get(v[ixm]), get(v[ixp]), get(v[iym]), get(v[iyp]), get(v[izm]), get(v[izp]));
             const float rn = NOISE ? (float)gs_noise_num((uint32_t)i, k) : 0.0f;
             GsDS a, b;
             gs_update_ds<NOISE>(cds, uc, vc, su, sv, rn, a, b);
-            un[i] = ds_to_double(a);
-            vn[i] = ds_to_double(b);
+            un[i] = OUT_PACKED ? ds_pack(a) : ds_to_double(a);
+            vn[i] = OUT_PACKED ? ds_pack(b) : ds_to_double(b);
         } else if constexpr (AR == 2) {
             // FP64 fields in fixed point (gs_fx.cuh)
-            bool o[14];
-            const long long uc = fx_from_double(u[i], o[0]), vc = fx_from_double(v[i], o[1]);
-            const long long su = fx_from_double(u[ixm], o[2]) + fx_from_double(u[ixp], o[3]) +
-                                 fx_from_double(u[iym], o[4]) + fx_from_double(u[iyp], o[5]) +
-                                 fx_from_double(u[izm], o[6]) + fx_from_double(u[izp], o[7]);
-            const long long sv = fx_from_double(v[ixm], o[8]) + fx_from_double(v[ixp], o[9]) +
-                                 fx_from_double(v[iym], o[10]) + fx_from_double(v[iyp], o[11]) +
-                                 fx_from_double(v[izm], o[12]) + fx_from_double(v[izp], o[13]);
             bool any = false;
-#pragma unroll
-            for (int q = 0; q < 14; ++q) any |= o[q];
+            auto get = [&](double x) -> long long {
+                if constexpr (IN_PACKED) {
+                    return fx_unpack(x);
+                } else {
+                    bool o;
+                    const long long r = fx_from_double(x, o);
+                    any |= o;
+                    return r;
+                }
+            };
+            const long long uc = get(u[i]), vc = get(v[i]);
+            const long long su = get(u[ixm]) + get(u[ixp]) + get(u[iym]) + get(u[iyp]) + get(u[izm]) + get(u[izp]);
+            const long long sv = get(v[ixm]) + get(v[ixp]) + get(v[iym]) + get(v[iyp]) + get(v[izm]) + get(v[izp]);
             if (any) gs_report(err, GS_DERR_RANGE);
             const int32_t rn = NOISE ? gs_noise_num((uint32_t)i, k) : 0;
             long long a, b;
             gs_update_fx<NOISE>(cfx, uc, vc, su, sv, rn, a, b);
-            un[i] = fx_to_double(a);
-            vn[i] = fx_to_double(b);
-        } else if constexpr (AR >= 3) {
-            // FP64 fields in fixed point with a float remainder (gs_fxf.cuh);
-            // inputs and outputs FP64 or packed pairs
-            constexpr bool IN_PACKED = (AR - 3) & 1, OUT_PACKED = (AR - 3) & 2;
+            un[i] = OUT_PACKED ? fx_pack(a) : fx_to_double(a);
+            vn[i] = OUT_PACKED ? fx_pack(b) : fx_to_double(b);
+        } else if constexpr (AR == 3) {
+            // FP64 fields in fixed point with a float remainder (gs_fxf.cuh)
             bool any = false;
             auto get = [&](double x) -> GsFxf {
                 if constexpr (IN_PACKED) {
@@ -212,25 +216,26 @@ static int naive_t(int L, const void* u, const void* v, void* un, void* vn, cons
     const T* cv = (const T*)v;
     bool launched = false;
     if constexpr (std::is_same<T, double>::value) {
-        if (p.arith == GS_ARITH_DS) {
-            if (nz) gs_naive_kernel<T, true, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
-            else gs_naive_kernel<T, false, 1><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
-            launched = true;
-        } else if (p.arith == GS_ARITH_FX) {
-            if (nz) gs_naive_kernel<T, true, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
-            else gs_naive_kernel<T, false, 2><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err);
-            launched = true;
-        } else if (p.arith == GS_ARITH_FXF) {
-#define GS_NAIVE_FXF(AR)                                                                                      \
-    (nz ? gs_naive_kernel<T, true, AR><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err) \
-        : gs_naive_kernel<T, false, AR><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err))
-            switch (p.fxf_io & 3) {
-            case 0: GS_NAIVE_FXF(3); break;
-            case 1: GS_NAIVE_FXF(4); break;
-            case 2: GS_NAIVE_FXF(5); break;
-            default: GS_NAIVE_FXF(6); break;
+        if (p.arith == GS_ARITH_DS || p.arith == GS_ARITH_FX || p.arith == GS_ARITH_FXF) {
+#define GS_NAIVE_AR(AR, IO)                                                                                       \
+    (nz ? gs_naive_kernel<T, true, AR, IO><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err) \
+        : gs_naive_kernel<T, false, AR, IO><<<g, 256, 0, s>>>(cu, cv, (T*)un, (T*)vn, L, c, cds, cfx, cfxf, k, err))
+#define GS_NAIVE_IO(AR)                      \
+    switch (p.io & 3) {                      \
+    case 0: GS_NAIVE_AR(AR, 0); break;       \
+    case 1: GS_NAIVE_AR(AR, 1); break;       \
+    case 2: GS_NAIVE_AR(AR, 2); break;       \
+    default: GS_NAIVE_AR(AR, 3); break;      \
+    }
+            if (p.arith == GS_ARITH_DS) {
+                GS_NAIVE_IO(1)
+            } else if (p.arith == GS_ARITH_FX) {
+                GS_NAIVE_IO(2)
+            } else {
+                GS_NAIVE_IO(3)
             }
-#undef GS_NAIVE_FXF
+#undef GS_NAIVE_IO
+#undef GS_NAIVE_AR
             launched = true;
         }
     }
@@ -345,15 +350,17 @@ GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
 }
 
 // AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed
-// point, 3-6: fixed point with a float remainder, 3 + (input packed) +
-// 2 (output packed)); the ones that read FP64 values into another
-// arithmetic convert every staged plane in place once (CONV)
-template <typename T, bool NOISE, int AR>
+// point, 3: fixed point with a float remainder).  IO (AR > 0): bit 0 = the
+// input fields hold that arithmetic's packed values, bit 1 = write packed
+// values.  The other arithmetics reading FP64 values convert every staged
+// plane in place once (CONV).
+template <typename T, bool NOISE, int AR, int IO = 0>
 GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
 {
     constexpr bool DS = AR == 1;
-    constexpr bool FXF = AR >= 3;
-    constexpr bool CONV = AR == 1 || AR == 2 || AR == 3 || AR == 5;
+    constexpr bool FXF = AR == 3;
+    constexpr bool CONV = AR != 0 && (IO & 1) == 0;
+    constexpr bool PACK = (IO & 2) != 0;
     constexpr int V = GsVec<T>::N;
     using VT = typename GsVec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -568,15 +575,15 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
                 if (r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
                 const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
                 if constexpr (DS)
-                    gs_update_group_ds<NOISE>(a.cds, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
-                                              xlv, xrv, outu, outv, GsFromPacked());
+                    gs_update_group_ds<NOISE, GsFromPacked, PACK>(a.cds, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu,
+                                                                  ymv, ypv, xlu, xru, xlv, xrv, outu, outv);
                 else if constexpr (AR == 2)
-                    gs_update_group_fx<NOISE>(a.cfx, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
-                                              xlv, xrv, outu, outv);
+                    gs_update_group_fx<NOISE, PACK>(a.cfx, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
+                                                    xru, xlv, xrv, outu, outv);
                 else if constexpr (FXF) {
                     bool ovf = false;
-                    gs_update_group_fxf<NOISE, (AR - 3 & 2) != 0>(a.cfxf, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu,
-                                                                    ymv, ypv, xlu, xru, xlv, xrv, outu, outv, ovf);
+                    gs_update_group_fxf<NOISE, PACK>(a.cfxf, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
+                                                     xru, xlv, xrv, outu, outv, ovf);
                     if (ovf) gs_report(a.err, GS_DERR_RANGE);
                 }
                 else
@@ -621,19 +628,19 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
     }
 }
 
-template <typename T, bool NOISE, int AR>
+template <typename T, bool NOISE, int AR, int IO>
 __global__ void gs_zmarch_kernel(const __grid_constant__ ZMaps maps, const ZArgs<T> a)
 {
-    zmarch_body<T, NOISE, AR>(maps, a);
+    zmarch_body<T, NOISE, AR, IO>(maps, a);
 }
 
 // The fixed point with a remainder, capped at 72 registers (which its
 // packed-step form needs anyway): 7 warps of 72 fit one SM sub-partition's
 // 16K registers, so tiles of up to 25 warps (128 x 12 cells) fit an SM.
-template <bool NOISE, int AR>
+template <bool NOISE, int IO>
 __global__ void __maxnreg__(72) gs_zmarch_fxf_kernel(const __grid_constant__ ZMaps maps, const ZArgs<double> a)
 {
-    zmarch_body<double, NOISE, AR>(maps, a);
+    zmarch_body<double, NOISE, 3, IO>(maps, a);
 }
 
 bool zmarch_supported(int dtype, int L)
@@ -679,7 +686,7 @@ int zmarch_encode(int dtype, int L, const ZPlan& pl, void* u, void* v, ZMaps* ma
     return GS_OK;
 }
 
-template <typename T, bool NOISE, int AR>
+template <typename T, bool NOISE, int AR, int IO = 0>
 static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
                            const Params& p, int64_t t, int* d_err, uint64_t timeout_ns,
                            int stall, cudaStream_t s)
@@ -710,10 +717,10 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     const int threads = ((ncons + 31) & ~31) + 32;
     const size_t smem = (size_t)a.lay.stage_bytes * pl.stages;
     void (*kern)(const ZMaps, const ZArgs<T>) = nullptr;
-    if constexpr (AR >= 3)
-        kern = gs_zmarch_fxf_kernel<NOISE, AR>;
+    if constexpr (AR == 3)
+        kern = gs_zmarch_fxf_kernel<NOISE, IO>;
     else
-        kern = gs_zmarch_kernel<T, NOISE, AR>;
+        kern = gs_zmarch_kernel<T, NOISE, AR, IO>;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -732,23 +739,22 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
     if (dtype == GS_F32)
         return noise ? zmarch_launch_t<float, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
                      : zmarch_launch_t<float, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
-    if (p.arith == GS_ARITH_DS)
-        return noise ? zmarch_launch_t<double, true, 1>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                     : zmarch_launch_t<double, false, 1>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
-    if (p.arith == GS_ARITH_FX)
-        return noise ? zmarch_launch_t<double, true, 2>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                     : zmarch_launch_t<double, false, 2>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
-    if (p.arith == GS_ARITH_FXF) {
-#define GS_ZMARCH_FXF(AR)                                                                               \
-    return noise ? zmarch_launch_t<double, true, AR>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s) \
-                 : zmarch_launch_t<double, false, AR>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-        switch (p.fxf_io & 3) {
-        case 0: GS_ZMARCH_FXF(3);
-        case 1: GS_ZMARCH_FXF(4);
-        case 2: GS_ZMARCH_FXF(5);
-        default: GS_ZMARCH_FXF(6);
-        }
-#undef GS_ZMARCH_FXF
+    if (p.arith == GS_ARITH_DS || p.arith == GS_ARITH_FX || p.arith == GS_ARITH_FXF) {
+#define GS_ZM(AR, IO)                                                                                            \
+    return noise ? zmarch_launch_t<double, true, AR, IO>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s) \
+                 : zmarch_launch_t<double, false, AR, IO>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+#define GS_ZM_IO(AR)          \
+    switch (p.io & 3) {       \
+    case 0: GS_ZM(AR, 0);     \
+    case 1: GS_ZM(AR, 1);     \
+    case 2: GS_ZM(AR, 2);     \
+    default: GS_ZM(AR, 3);    \
+    }
+        if (p.arith == GS_ARITH_DS) GS_ZM_IO(1)
+        if (p.arith == GS_ARITH_FX) GS_ZM_IO(2)
+        GS_ZM_IO(3)
+#undef GS_ZM_IO
+#undef GS_ZM
     }
     return noise ? zmarch_launch_t<double, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
                  : zmarch_launch_t<double, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);

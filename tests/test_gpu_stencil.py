@@ -426,16 +426,18 @@ def test_conv_arith_full_size_sampled_cells(arith):
     sim.close()
 
 
+@pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
 @pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
-def test_fxf_packed_between_the_steps_of_a_call(kernel):
-    # GS_ARITH_FXF keeps the fields as packed pairs between the steps of one
-    # gs_step call and rounds them to FP64 only at its end: n steps in one
-    # call and in n calls differ by those roundings, and both match the oracle
+def test_conv_arith_packed_between_the_steps_of_a_call(kernel, arith):
+    # the FP64 arithmetics other than IEEE keep the fields in their own packed
+    # form between the steps of one gs_step call and round them to FP64 only
+    # at its end: n steps in one call and in n calls differ by those
+    # roundings, and both match the oracle
     L, n = 32, 30
     prm = dict(PAPER, noise=0.1, seed=21)
     u0, v0 = inputs.random_fields(L, seed=8, lo=0.0, hi=1.0)
-    one = make_ar(gs.GS_ARITH_FXF, L, kernel, **prm)
-    many = make_ar(gs.GS_ARITH_FXF, L, kernel, **prm)
+    one = make_ar(arith, L, kernel, **prm)
+    many = make_ar(arith, L, kernel, **prm)
     for s in (one, many):
         s.write(u0, v0)
     one.step(n)
@@ -448,10 +450,10 @@ def test_fxf_packed_between_the_steps_of_a_call(kernel):
     e1 = max(maxabs(u1, uo), maxabs(v1, vo))
     en = max(maxabs(un, uo), maxabs(vn, vo))
     d = max(maxabs(u1, un), maxabs(v1, vn))
-    print(f"FXF {n} steps: one call {e1:.3e}, {n} calls {en:.3e} from the oracle; apart {d:.3e}")
+    print(f"arith {arith}, {n} steps: one call {e1:.3e}, {n} calls {en:.3e} from the oracle; apart {d:.3e}")
     assert e1 <= TOL["f64"] and en <= TOL["f64"] and d <= 1e-11
     # a second call continues from FP64 fields exactly as a fresh object would
-    fresh = make_ar(gs.GS_ARITH_FXF, L, kernel, **prm)
+    fresh = make_ar(arith, L, kernel, **prm)
     fresh.write(u1, v1)
     fresh.t = n
     one.step(5)
