@@ -643,6 +643,14 @@ __global__ void __maxnreg__(72) gs_zmarch_fxf_kernel(const __grid_constant__ ZMa
     zmarch_body<double, NOISE, 3, IO>(maps, a);
 }
 
+// The 64-bit fixed point, capped at 72 registers as well: its long 64-bit
+// multiply chains leave it latency-bound, and the cap lets 25-warp tiles fit.
+template <bool NOISE, int IO>
+__global__ void __maxnreg__(72) gs_zmarch_fx_kernel(const __grid_constant__ ZMaps maps, const ZArgs<double> a)
+{
+    zmarch_body<double, NOISE, 2, IO>(maps, a);
+}
+
 bool zmarch_supported(int dtype, int L)
 {
     const int V = dtype == GS_F32 ? 4 : 2;
@@ -719,6 +727,8 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     void (*kern)(const ZMaps, const ZArgs<T>) = nullptr;
     if constexpr (AR == 3)
         kern = gs_zmarch_fxf_kernel<NOISE, IO>;
+    else if constexpr (AR == 2)
+        kern = gs_zmarch_fx_kernel<NOISE, IO>;
     else
         kern = gs_zmarch_kernel<T, NOISE, AR, IO>;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
