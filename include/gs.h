@@ -133,7 +133,11 @@ int gs_init(gs_sim* sim);
 
 /* Advance n >= 0 steps (asynchronous on the object's stream).  Step t -> t+1
  * draws r(seed, t, cell).  The plan (gs_set_plan) chooses the kernel; all
- * kernels give bitwise-identical results. */
+ * kernels give bitwise-identical results.  FP64 fields in GS_ARITH_DS, _FX
+ * or _FXF (periodic grids) stay in that arithmetic's packed form between the
+ * steps of one call and are FP64 again when it ends, so n steps in one call
+ * and in several calls can differ at the level of the FP64 rounding
+ * (GS_ARITH_FX excepted: its packed values are exact doubles). */
 int gs_step(gs_sim* sim, int64_t n);
 
 /* Copy field (GS_U / GS_V) of the current state to host memory `dst`
