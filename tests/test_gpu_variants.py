@@ -43,6 +43,36 @@ def test_held_boundary_matches_oracle(dtype, kernel, L):
     sim.close()
 
 
+@pytest.mark.parametrize("arith", [gs.GS_ARITH_DS, gs.GS_ARITH_FX, gs.GS_ARITH_FXF], ids=["ds", "fx", "fxf"])
+@pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
+def test_held_boundary_in_the_other_fp64_arithmetics(arith, kernel):
+    # a held grid rounds to FP64 after every step (the faces are copied from
+    # the FP64 input), whatever the arithmetic: equal across kernels and to
+    # the oracle, and the faces untouched
+    need_cuda()
+    L = 24
+    prm = dict(PAPER, noise=0.1, seed=13)
+    u0, v0 = inputs.random_fields(L, seed=4, lo=0.0, hi=1.0)
+    sims = []
+    for kern in (gs.GS_KERNEL_NAIVE, kernel):
+        sim = gs.GrayScott(L, dtype="f64", **prm)
+        sim.arith = arith
+        sim.set_plan(kern)
+        sim.boundary = gs.GS_BOUNDARY_HELD
+        sim.write(u0, v0)
+        sim.step(30)
+        sims.append(sim)
+    (ua, va), (ub, vb) = sims[0].read(), sims[1].read()
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(va, vb)
+    uo, vo = oracle.step_held(u0, v0, 30, **prm)
+    assert maxabs(ua, uo) <= 1e-10 and maxabs(va, vo) <= 1e-10
+    f = faces(L)
+    np.testing.assert_array_equal(ua[f], u0[f])
+    for sim in sims:
+        sim.close()
+
+
 def test_held_boundary_kernels_bitwise_equal_and_config1():
     need_cuda()
     L = 64
