@@ -409,8 +409,9 @@ int gs_batch_destroy(gs_batch* b);
  * call holds a lock from building its tables until its stream has finished,
  * so calls from several host threads run one after the other (another
  * process has its own copy of the array).  Its work items are the plain
- * (instance, y tile, 32-plane z-chunk) table: unlike gs_batch_step it does
- * not cut the partial last round of items along z. */
+ * (instance, run of 256 * V cells of a plane, 32-plane z-chunk) table:
+ * unlike gs_batch_step it does not cut the partial last round of items
+ * along z. */
 int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k, double Du,
                           double Dv, double dt, double noise, uint64_t seed, int dtype, void* arena,
                           int64_t t, int cur, int64_t nsteps, void* stream);

@@ -1,21 +1,27 @@
 // Batched Gray-Scott: many independent periodic grids of different sizes
 // and (F, k) advanced together by one persistent kernel.
 //
-// Work decomposition.  Instance i (edge L_i, 4 <= L_i <= 256) is cut into
-// full-row tiles: all L_i cells of a row by ty_i = min(L_i, 256 * V / L_i)
-// rows, times a z-chunk of tz planes.  Every work item therefore holds about
-// the same number of cells, and because a tile spans whole rows the x wrap is
-// an index wrap inside shared memory (no x-halo copies).  Work items are
-// numbered instance by instance; CTA b takes items b, b + grid, ...  The
+// Work decomposition.  Each plane of instance i (edge L_i, 4 <= L_i <= 256)
+// is cut into runs of 256 V consecutive cells in row-major order (one group
+// of V cells per consumer thread), times a z-chunk of tz planes.  Every tile
+// but the last of a plane is therefore full whatever L_i is (row-shaped
+// tiles leave threads idle when L_i does not divide 256 V: 10 rows of 96 use
+// 960 of 1024 cells, and the tenth tile of a 96^2 plane only 6 rows).  A tile
+// is staged as the whole rows it touches, so the x wrap is an index wrap
+// inside shared memory (no x-halo copies).  Work items are numbered instance
+// by instance; CTA b takes items b, b + grid, ...  The
 // items of a partial last round are cut along z into up to four pieces, so
 // that round ends after a fraction of an item instead of a whole one.
+// Neighbouring z-chunks march in opposite directions, so the halo planes two
+// chunks share are read by both at about the same time (once from HBM, once
+// from L2).
 //
-// Per item a producer warp streams the planes z0-1 .. z0+nz with TMA (tile
-// box + two wrapped halo rows per field, per-instance tensor maps in global
-// memory) into a shared-memory ring; 256 consumer threads hold z-1/z/z+1 in
-// registers and store u', v' with 16-byte writes, exactly like the single
-// grid z-march kernel and with the same per-cell update, so results are
-// bitwise equal to running each instance alone.
+// Per item a producer warp streams the planes z0-1 .. z0+nz with TMA (a box
+// of the tile's rows + two wrapped halo rows per field, per-instance tensor
+// maps in global memory) into a shared-memory ring; 256 consumer threads
+// hold z-1/z/z+1 in registers and store u', v' with 16-byte writes, exactly
+// like the single grid z-march kernel and with the same per-cell update, so
+// results are bitwise equal to running each instance alone.
 //
 // Between steps all CTAs meet at a grid barrier in global memory (an
 // arrival counter, reset before every launch).  Every wait is bounded: on
@@ -62,7 +68,7 @@ template <typename T>
 struct BArgs {
     T* arena;
     const BInst* inst;
-    const int4* items;        // work item -> (instance, y0, z0, nz)
+    const int4* items;        // work item -> (instance, y0, z0, nz); nz < 0: march down |nz| planes
     const CUtensorMap* maps;  // [inst][set][field][kind]: kind 0 tile box, 1 halo row
     BCtrl* ctrl;
     int nitems, tz, stages;
@@ -71,6 +77,25 @@ struct BArgs {
     T Du6, Dv6, dt, noise24;
     uint64_t timeout_ns;
     int fault;  // 1: the producer issues no copies; 2: CTA 0 never arrives at the grid barrier
+};
+
+// What the consumers need of one work item, written to shared memory by the
+// producer thread before it releases the item's first plane (the release of
+// that mbarrier arrival orders it), so the consumers start an item without
+// waiting on the item and instance tables in global memory.  kBatchDescs
+// slots are reused round robin: the producer fills slot k + kBatchDescs only
+// after the consumers freed a stage issued kBatchDescs items later than item
+// k's first plane (an item has at least 3 planes and the ring at most 8
+// stages, so they read slot k long before).
+constexpr int kBatchDescs = 4;
+template <typename T>
+struct BDesc {
+    T* un;
+    T* vn;             // output fields of this step
+    T F, Fk;
+    GsKeys keys;       // noise keys of the instance and step
+    uint32_t kk2;
+    int L, c0, z0, nz;  // nz < 0: march down |nz| planes
 };
 
 GS_D bool wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t timeout_ns, volatile int* abort_flag)
@@ -126,14 +151,19 @@ GS_D bool batch_grid_sync(BCtrl* ctrl, unsigned target, uint64_t timeout_ns, boo
     return *s_abort == 0;
 }
 
+// Register cap (measured on GB300, FP32, noise on, 256 mixed grids): 76
+// registers runs 1.3 % faster than 80, 6 % faster than the 88-94 the
+// compiler takes under __launch_bounds__(288, 2), and without any bound it
+// settles on 72 with spills (10 % slower).  FP64 spills below about 90.
 template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_constant__ BArgs<T> a)
+__global__ void __maxnreg__(sizeof(T) == 4 ? 76 : 96) gs_batch_kernel(const __grid_constant__ BArgs<T> a)
 {
     constexpr int V = GsVec<T>::N;
     using VT = typename GsVec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[16];
     __shared__ volatile int s_abort;
+    __shared__ BDesc<T> s_desc[kBatchDescs];
 
     const int S = a.stages;
     uint64_t* full = bars;
@@ -161,6 +191,7 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
     int cs = 0;
     uint32_t cph = 0;
     uint32_t seq = 0;      // planes issued by the producer (for its drain)
+    uint32_t kl = 0;       // items taken by this CTA (descriptor slot kl % kBatchDescs)
     bool wrapped = false;  // producer: every stage used once
     auto advance = [&]() {
         if (++cs == S) { cs = 0; cph ^= 1u; wrapped = true; }
@@ -173,122 +204,166 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
             // ------------------------------ consumers ------------------------------
             // planes z-1, z, z+1 in three register sets rotated by renaming
             T qu[3][V], qv[3][V];
-            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x) {
-                const int4 it = a.items[item];
-                const int ii = it.x;
-                const BInst& I = a.inst[ii];
-                const int L = I.L, ty = I.ty, nxv = L / V;
-                const int y0 = it.y, z0 = it.z, nz = it.w;
-                const int nvy = min(ty, L - y0);
-                const int xv = tid % nxv, row = tid / nxv;
-                const bool active = row < nvy;
-                const int rr = row < ty ? row : 0;
-                const int moff = rr * L + xv * V;
-                const int rowbase = rr * L;
-                GsCoef<T> c;
-                c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise24 = a.noise24;
-                c.F = (T)I.F; c.Fk = (T)I.Fk;
-                const GsKeys keys = gs_step_keys(((uint64_t)I.seed_hi << 32) | I.seed_lo, t);
-                const uint32_t kk2 = gs_kk2(keys);
-                T* un = a.arena + I.off[out][0];
-                T* vn = a.arena + I.off[out][1];
-                const long long LL = (long long)L * L;
-                const int om = row > 0 ? moff - L : top_off + xv * V;
-                const int op = row + 1 < nvy ? moff + L : bot_off + xv * V;
-                const bool l_smem = xv == 0 || lane == 0;
-                const bool r_smem = xv == nxv - 1 || lane == 31;
-                const int oxl = xv > 0 ? moff - 1 : rowbase + L - 1;  // periodic in x
-                const int oxr = xv < nxv - 1 ? moff + V : rowbase;
-                long long g = (long long)z0 * LL + (long long)(y0 + row) * L + xv * V;
-
-                auto load = [&](T (&u)[V], T (&v)[V]) {
-                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + cs * stage_elems + moff), u);
-                    gs_unpack<T>(*reinterpret_cast<const VT*>(ring + cs * stage_elems + a.field_elems + moff), v);
-                };
-                int sc = 0;
-                // one plane: P, C, N are planes z-1, z, z+1 (N loaded here)
-                auto plane = [&](T (&pu)[V], T (&pv)[V], T (&cu)[V], T (&cv)[V], T (&nu)[V], T (&nv)[V]) -> bool {
-                    const int sn = cs;
-                    if (!wait_or_abort(&full[sn], cph, a.timeout_ns, &s_abort)) return false;
-                    load(nu, nv);
-                    const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
-                    const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
-                    const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
-                    const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
-                    if (active) {
-                        const T* bu = ring + sc * stage_elems;
-                        const T* bv = bu + a.field_elems;
-                        T ymu[V], ypu[V], ymv[V], ypv[V], ou[V], ov[V];
-                        gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
-                        gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
-                        gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
-                        gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
-                        T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
-                        if (l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
-                        if (r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
-                        const uint32_t pre = NOISE ? gs_group_pre((uint32_t)g, keys) : 0u;
-                        gs_update_group<T, NOISE>(c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
-                                                  xru, xlv, xrv, ou, ov);
-                        *reinterpret_cast<VT*>(un + g) = gs_pack<T>(ou);
-                        *reinterpret_cast<VT*>(vn + g) = gs_pack<T>(ov);
-                    }
-                    __syncwarp();
-                    if (lane == 0) gs_mbar_arrive(&empty[sc]);
-                    sc = sn;
-                    advance();
-                    g += LL;
-                    return true;
-                };
-
-                if (!wait_or_abort(&full[cs], cph, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
-                load(qu[0], qv[0]);
-                __syncwarp();
-                if (lane == 0) gs_mbar_arrive(&empty[cs]);
-                advance();
-                sc = cs;
-                if (!wait_or_abort(&full[cs], cph, a.timeout_ns, &s_abort)) { gs_report(&a.ctrl->err, GS_DERR_TIMEOUT); s_abort = 1; break; }
-                load(qu[1], qv[1]);
-                advance();
-                bool ok = true;
-                int zi = 0;
-                for (; ok && zi + 3 <= nz; zi += 3) {
-                    ok = plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2]) &&
-                         plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0]) &&
-                         plane(qu[2], qv[2], qu[0], qv[0], qu[1], qv[1]);
-                }
-                // remainder (each item reloads its first two planes into q0, q1)
-                if (ok && zi < nz) ok = plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2]);
-                if (ok && zi + 1 < nz) ok = plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0]);
-                if (!ok) {
+            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x, ++kl) {
+                // the item's first plane, and with it the item's descriptor
+                if (!wait_or_abort(&full[cs], cph, a.timeout_ns, &s_abort)) {
                     gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
                     s_abort = 1;
                     break;
                 }
-                __syncwarp();
-                if (lane == 0) gs_mbar_arrive(&empty[sc]);
+                const BDesc<T> d = s_desc[kl % kBatchDescs];
+                // One item, marching up (DESC false: planes z0, z0+1, ...) or
+                // down (DESC true, d.nz < 0: planes z0+nz-1, z0+nz-2, ...).
+                // Either way each cell sees z-1 as its lower and z+1 as its
+                // upper neighbour, so the update is the same to the bit.
+                // Returns false when a wait for a stage ran out.
+                auto run = [&](auto desc_tag) -> bool {
+                    constexpr bool DESC = decltype(desc_tag)::value;
+                    const int L = d.L;
+                    const int c0 = d.c0, z0 = d.z0, nz = DESC ? -d.nz : d.nz;
+                    // the tile: cells c0 .. c0 + C - 1 of each plane (row
+                    // major), staged as the whole rows ya .. yb (box rows from
+                    // ya; rows past yb are not used) plus halo rows ya - 1,
+                    // yb + 1.  This thread's group: cell c0 + V tid.
+                    const int C = min(kBatchConsumers * V, L * L - c0);
+                    const int ya = c0 / L, nrows = (c0 + C - 1) / L - ya + 1;
+                    const bool active = V * tid < C;
+                    const int q = (active ? V * tid : 0) + c0 - ya * L;  // offset from the box's first row
+                    const int row = q / L, x = q - row * L;
+                    const int moff = q;
+                    const int rowbase = row * L;
+                    GsCoef<T> c;
+                    c.Du6 = a.Du6; c.Dv6 = a.Dv6; c.dt = a.dt; c.noise24 = a.noise24;
+                    c.F = d.F; c.Fk = d.Fk;
+                    const GsKeys keys = d.keys;
+                    const uint32_t kk2 = d.kk2;
+                    T* un = d.un;
+                    T* vn = d.vn;
+                    const long long LL = (long long)L * L;
+                    const int om = row > 0 ? moff - L : top_off + x;
+                    const int op = row + 1 < nrows ? moff + L : bot_off + x;
+                    // x neighbours from the adjacent lanes within a row: the
+                    // tile's last active group always ends a row (a partial
+                    // tile is the last of its plane), so no active lane
+                    // reads an inactive one
+                    const bool l_smem = x == 0 || lane == 0;
+                    const bool r_smem = x + V == L || lane == 31;
+                    const int oxl = x > 0 ? moff - 1 : rowbase + L - 1;  // periodic in x
+                    const int oxr = x + V < L ? moff + V : rowbase;
+                    long long g = (long long)(DESC ? z0 + nz - 1 : z0) * LL + (long long)(ya * L + q);
+
+                    auto load = [&](T (&u)[V], T (&v)[V]) {
+                        gs_unpack<T>(*reinterpret_cast<const VT*>(ring + cs * stage_elems + moff), u);
+                        gs_unpack<T>(*reinterpret_cast<const VT*>(ring + cs * stage_elems + a.field_elems + moff), v);
+                    };
+                    int sc = 0;
+                    // one plane: P, C, N are the previous, current and next
+                    // planes of the march (N loaded here)
+                    auto plane = [&](T (&pu)[V], T (&pv)[V], T (&cu)[V], T (&cv)[V], T (&nu)[V],
+                                     T (&nv)[V]) -> bool {
+                        const int sn = cs;
+                        if (!wait_or_abort(&full[sn], cph, a.timeout_ns, &s_abort)) return false;
+                        load(nu, nv);
+                        const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
+                        const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
+                        const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
+                        const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
+                        if (active) {
+                            const T* bu = ring + sc * stage_elems;
+                            const T* bv = bu + a.field_elems;
+                            T ymu[V], ypu[V], ymv[V], ypv[V], ou[V], ov[V];
+                            gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
+                            gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
+                            gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
+                            gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
+                            T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
+                            if (l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
+                            if (r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
+                            const uint32_t pre = NOISE ? gs_group_pre((uint32_t)g, keys) : 0u;
+                            if constexpr (DESC)
+                                gs_update_group<T, NOISE>(c, pre, kk2, cu, cv, nu, nv, pu, pv, ymu, ypu, ymv, ypv,
+                                                          xlu, xru, xlv, xrv, ou, ov);
+                            else
+                                gs_update_group<T, NOISE>(c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv,
+                                                          xlu, xru, xlv, xrv, ou, ov);
+                            *reinterpret_cast<VT*>(un + g) = gs_pack<T>(ou);
+                            *reinterpret_cast<VT*>(vn + g) = gs_pack<T>(ov);
+                        }
+                        __syncwarp();
+                        if (lane == 0) gs_mbar_arrive(&empty[sc]);
+                        sc = sn;
+                        advance();
+                        g += DESC ? -LL : LL;
+                        return true;
+                    };
+
+                    load(qu[0], qv[0]);  // the first plane (waited for above)
+                    __syncwarp();
+                    if (lane == 0) gs_mbar_arrive(&empty[cs]);
+                    advance();
+                    sc = cs;
+                    if (!wait_or_abort(&full[cs], cph, a.timeout_ns, &s_abort)) return false;
+                    load(qu[1], qv[1]);
+                    advance();
+                    bool ok = true;
+                    int zi = 0;
+                    for (; ok && zi + 3 <= nz; zi += 3) {
+                        ok = plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2]) &&
+                             plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0]) &&
+                             plane(qu[2], qv[2], qu[0], qv[0], qu[1], qv[1]);
+                    }
+                    // remainder (each item reloads its first two planes into q0, q1)
+                    if (ok && zi < nz) ok = plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2]);
+                    if (ok && zi + 1 < nz) ok = plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0]);
+                    if (!ok) return false;
+                    __syncwarp();
+                    if (lane == 0) gs_mbar_arrive(&empty[sc]);
+                    return true;
+                };
+                if (!(d.nz < 0 ? run(std::true_type{}) : run(std::false_type{}))) {
+                    gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
             }
             gs_fence_proxy_async_global();  // this step's stores before the next step's TMA reads
         } else if (tid == kBatchConsumers && a.fault != 1) {
             // ------------------------------ producer -------------------------------
             gs_fence_proxy_async_global();  // the previous step's stores (acquired at the barrier)
-            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x) {
+            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x, ++kl) {
                 const int4 it = a.items[item];
                 const int ii = it.x;
                 const BInst& I = a.inst[ii];
+                const GsKeys keys = gs_step_keys(((uint64_t)I.seed_hi << 32) | I.seed_lo, t);
                 const int L = I.L, ty = I.ty;
-                const int y0 = it.y, z0 = it.z, nz = it.w;
-                const int nvy = min(ty, L - y0);
-                const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
+                const bool desc = it.w < 0;  // march down from the top plane
+                const int c0 = it.y, z0 = it.z, nz = desc ? -it.w : it.w;
+                const int C = min(kBatchConsumers * V, L * L - c0);
+                const int y0 = c0 / L, y1 = (c0 + C - 1) / L;  // rows of the tile
+                const int ytop = (y0 - 1 + L) % L, ybot = (y1 + 1) % L;
                 const uint32_t bytes = 2u * (uint32_t)(L * ty + 2 * L) * (uint32_t)sizeof(T);
                 const CUtensorMap* mu = a.maps + (((size_t)ii * 2 + in) * 2 + 0) * 2;
                 const CUtensorMap* mv = a.maps + (((size_t)ii * 2 + in) * 2 + 1) * 2;
                 bool failed = false;
-                int zp = (z0 - 1 + L) % L;
+                int zp = desc ? (z0 + nz) % L : (z0 - 1 + L) % L;
                 for (int j = 0; j < nz + 2; ++j) {
                     const int sl = cs;
                     if (wrapped && !wait_or_abort(&empty[sl], cph ^ 1u, a.timeout_ns, &s_abort)) {
                         failed = true;
                         break;
+                    }
+                    if (j == 0) {
+                        BDesc<T>& d = s_desc[kl % kBatchDescs];
+                        d.un = a.arena + I.off[out][0];
+                        d.vn = a.arena + I.off[out][1];
+                        d.F = (T)I.F;
+                        d.Fk = (T)I.Fk;
+                        d.keys = keys;
+                        d.kk2 = gs_kk2(keys);
+                        d.L = L;
+                        d.c0 = c0;
+                        d.z0 = z0;
+                        d.nz = it.w;
                     }
                     gs_mbar_arrive_expect_tx(&full[sl], bytes);
                     T* b = ring + sl * stage_elems;
@@ -301,7 +376,10 @@ __global__ void __launch_bounds__(kBatchThreads) gs_batch_kernel(const __grid_co
                     gs_tma_load_3d(b + bot_off, &mv[1], &full[sl], 0, ybot, zp);
                     ++seq;
                     advance();
-                    zp = zp + 1 == L ? 0 : zp + 1;
+                    if (desc)
+                        zp = zp == 0 ? L - 1 : zp - 1;
+                    else
+                        zp = zp + 1 == L ? 0 : zp + 1;
                 }
                 if (failed) {
                     gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
@@ -457,7 +535,7 @@ struct gs_batch {
     std::vector<BInst> h_inst;
     void* arena = nullptr;
     BInst* d_inst = nullptr;
-    std::vector<int4> base_items;           // (instance, y0, z0, nz) before the tail split
+    std::vector<int4> base_items;           // (instance, y0, z0, +-nz) before the tail split
     int4* d_items = nullptr;                // the table the kernel walks
     int items_cap = 0;                      // capacity of d_items
     int items_grid = -1;                    // grid the device table was cut for (-1: none yet)
@@ -487,16 +565,42 @@ struct gs_batch {
     int tb_items_cap = 0, tb_nitems = 0, tb_items_grid = -1, tb_pe = 0, tb_grid = 0;
 };
 
-// the work items of instances [0, n): (instance, y0, z0, nz), instance by
-// instance, y tiles fastest
-static void plain_items(const BInst* inst, int n, int tz, std::vector<int4>& out)
+// The work item of z-chunk zc of a single-step table: (instance, c0, z0,
+// +-nz), marching up the chunk for even zc and down it (nz stored negated)
+// for odd zc.  Adjacent chunks then meet at their shared halo planes at the
+// same time (both ends, or both starts, of items that run side by side), so
+// the second read of those planes finds them in L2 instead of HBM.
+static int4 march_item(int i, int y0, int z0, int nz, int zc)
+{
+    return make_int4(i, y0, z0, (zc & 1) ? -nz : nz);
+}
+
+// Tiles of the single-step kernel: runs of tile_cells = 256 V consecutive
+// cells of a plane in row-major order (one group of V cells per consumer
+// thread), so every tile but the last of a plane is full whatever L is.
+// A tile is staged as the whole rows it touches; run_box_rows is the most
+// rows any tile of an L^2 plane touches (the height of its TMA box).
+static int run_tiles(int L, int tile_cells) { return (L * L + tile_cells - 1) / tile_cells; }
+static int run_box_rows(int L, int tile_cells)
+{
+    int rows = 0;
+    for (int c0 = 0; c0 < L * L; c0 += tile_cells) {
+        const int C = std::min(tile_cells, L * L - c0);
+        rows = std::max(rows, (c0 + C - 1) / L - c0 / L + 1);
+    }
+    return rows;
+}
+
+// the work items of instances [0, n) for the single-step kernel, instance by
+// instance, tiles of a plane fastest: (instance, first cell, z0, +-nz)
+static void plain_items(const BInst* inst, int n, int tz, int tile_cells, std::vector<int4>& out)
 {
     out.clear();
     for (int i = 0; i < n; ++i) {
         const BInst& I = inst[i];
         for (int j = 0; j < I.nty * I.ntz; ++j) {
-            const int y0 = (j % I.nty) * I.ty, z0 = (j / I.nty) * tz;
-            out.push_back(make_int4(i, y0, z0, std::min(tz, I.L - z0)));
+            const int c0 = (j % I.nty) * tile_cells, zc = j / I.nty, z0 = zc * tz;
+            out.push_back(march_item(i, c0, z0, std::min(tz, I.L - z0), zc));
         }
     }
 }
@@ -506,7 +610,9 @@ static void plain_items(const BInst* inst, int n, int tz, std::vector<int4>& out
 // Cut each of those items along z into f = min(4, grid / rem) pieces (fewer
 // when it has fewer planes) appended after the full rounds, so the last
 // round lasts about 1/f of an item.  Every cell is still updated once.
-static void split_tail(const std::vector<int4>& base, int grid, std::vector<int4>& out)
+// Items with nz < 0 (single-step tables) march down; with `alternate` the
+// pieces of an item alternate their direction, as whole chunks do.
+static void split_tail(const std::vector<int4>& base, int grid, bool alternate, std::vector<int4>& out)
 {
     out = base;
     const int n = (int)base.size();
@@ -518,10 +624,13 @@ static void split_tail(const std::vector<int4>& base, int grid, std::vector<int4
     out.resize(n - rem);
     for (int q = n - rem; q < n; ++q) {
         const int4 it = base[q];
-        const int parts = std::min(f, it.w);
+        const bool desc = it.w < 0;
+        const int nz = desc ? -it.w : it.w;
+        const int parts = std::min(f, nz);
         for (int p = 0; p < parts; ++p) {
-            const int za = it.w * p / parts, zb = it.w * (p + 1) / parts;
-            out.push_back(make_int4(it.x, it.y, it.z + za, zb - za));
+            const int za = nz * p / parts, zb = nz * (p + 1) / parts;
+            const bool d = alternate ? desc != ((p & 1) != 0) : desc;
+            out.push_back(make_int4(it.x, it.y, it.z + za, d ? za - zb : zb - za));
         }
     }
 }
@@ -638,7 +747,7 @@ static int plain_prepare(gs_batch* b, int64_t n, BArgs<T>& a, size_t& smem)
     if (b->items_grid != grid) {
         // cut the partial last round for this grid (once per plan)
         std::vector<int4> items;
-        split_tail(b->base_items, grid, items);
+        split_tail(b->base_items, grid, true, items);
         GS_CUDA_TRY(cudaStreamSynchronize(b->stream));  // no launch still reads the old table
         const int rc = upload_items(b, items);
         if (rc) return rc;
@@ -677,7 +786,7 @@ static int tb_prepare(gs_batch* b, int64_t npasses, BtbArgs& a, size_t& smem)
     const int grid = std::min(per_sm * num_sms(), (int)b->tb_base_items.size());
     if (b->tb_items_grid != grid) {
         std::vector<int4> items;
-        split_tail(b->tb_base_items, grid, items);
+        split_tail(b->tb_base_items, grid, false, items);
         GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
         const int rc = upload_tb_items(b, items);
         if (rc) return rc;
@@ -832,11 +941,11 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
     b->L.assign(L, L + n);
     b->F.assign(F, F + n);
     b->k.assign(k, k + n);
-    // shared-memory layout: the tile box (at most 256 * V elements) then two halo rows
+    // shared-memory layout per stage and field: the tile box (the largest
+    // box of any instance, whole rows) then two halo rows, each 128-byte aligned
     const int a128 = 128 / esz;
-    b->main_elems = kBatchConsumers * V;
-    b->row_elems = (maxL + a128 - 1) / a128 * a128;
-    b->field_elems = b->main_elems + 2 * b->row_elems;
+    const int tile_cells = kBatchConsumers * V;
+    int box_elems = 0;
     // instance table, arena offsets, work items
     int nit = 0;
     long long off = 0;
@@ -844,8 +953,9 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
     for (int i = 0; i < n; ++i) {
         BInst I{};
         I.L = L[i];
-        I.ty = std::min(L[i], kBatchConsumers * V / L[i]);
-        I.nty = (L[i] + I.ty - 1) / I.ty;
+        I.ty = run_box_rows(L[i], tile_cells);
+        I.nty = run_tiles(L[i], tile_cells);
+        box_elems = std::max(box_elems, I.ty * L[i]);
         I.ntz = (L[i] + b->tz - 1) / b->tz;
         I.item0 = nit;
         I.nitems = I.nty * I.ntz;
@@ -863,7 +973,10 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
             }
         b->h_inst.push_back(I);
     }
-    plain_items(b->h_inst.data(), n, b->tz, b->base_items);
+    b->main_elems = (box_elems + a128 - 1) / a128 * a128;
+    b->row_elems = (maxL + a128 - 1) / a128 * a128;
+    b->field_elems = b->main_elems + 2 * b->row_elems;
+    plain_items(b->h_inst.data(), n, b->tz, tile_cells, b->base_items);
     b->nitems = (int)b->base_items.size();
     int rc = GS_OK;
     cudaError_t e;
@@ -1153,7 +1266,7 @@ int gs_batch_set_plan(gs_batch* b, int tile_z, int stages)
         I.nitems = I.nty * I.ntz;
         nit += I.nitems;
     }
-    plain_items(b->h_inst.data(), b->n, tile_z, b->base_items);
+    plain_items(b->h_inst.data(), b->n, tile_z, kBatchConsumers * (b->dtype == GS_F32 ? 4 : 2), b->base_items);
     GS_CUDA_TRY(cudaStreamSynchronize(b->stream));  // no launch still reads the old table
     {
         const int rc = upload_items(b, b->base_items);
@@ -1317,8 +1430,7 @@ extern "C" int gs_batch_step_noalloc(int n, const int* L, const double* F, const
             return fail(GS_EINVAL, "instance %d: L=%d must be a multiple of %d in [%d, 256]", i, L[i], V, V);
         if (!std::isfinite(F[i]) || !std::isfinite(k[i])) return fail(GS_EINVAL, "instance %d: F, k must be finite", i);
         maxL = std::max(maxL, L[i]);
-        const int ty = std::min(L[i], kBatchConsumers * V / L[i]);
-        items += (long long)((L[i] + ty - 1) / ty) * ((L[i] + 31) / 32);
+        items += (long long)run_tiles(L[i], kBatchConsumers * V) * ((L[i] + 31) / 32);
     }
     if (items > kNoAllocMaxItems)
         return fail(GS_EINVAL, "%lld work items: the allocation-free step takes at most %d", items, kNoAllocMaxItems);
@@ -1338,7 +1450,10 @@ extern "C" int gs_batch_step_noalloc(int n, const int* L, const double* F, const
 
     // same tables as gs_batch_create, built in static host staging
     const int a128 = 128 / esz;
-    const int main_elems = kBatchConsumers * V;
+    const int tile_cells = kBatchConsumers * V;
+    int box_elems = 0;
+    for (int i = 0; i < n; ++i) box_elems = std::max(box_elems, run_box_rows(L[i], tile_cells) * L[i]);
+    const int main_elems = (box_elems + a128 - 1) / a128 * a128;
     const int row_elems = (maxL + a128 - 1) / a128 * a128;
     const long long align = 256 / esz;
     long long off = 0;
@@ -1346,8 +1461,8 @@ extern "C" int gs_batch_step_noalloc(int n, const int* L, const double* F, const
     for (int i = 0; i < n; ++i) {
         BInst I{};
         I.L = L[i];
-        I.ty = std::min(L[i], kBatchConsumers * V / L[i]);
-        I.nty = (L[i] + I.ty - 1) / I.ty;
+        I.ty = run_box_rows(L[i], tile_cells);
+        I.nty = run_tiles(L[i], tile_cells);
         I.ntz = (L[i] + 31) / 32;
         I.item0 = nit;
         I.nitems = I.nty * I.ntz;
@@ -1363,8 +1478,8 @@ extern "C" int gs_batch_step_noalloc(int n, const int* L, const double* F, const
                 off += (cells + align - 1) / align * align;
             }
         for (int j = 0; j < I.nitems; ++j) {
-            const int y0 = (j % I.nty) * I.ty, z0 = (j / I.nty) * 32;
-            g_na_items[nit++] = make_int4(i, y0, z0, std::min(32, I.L - z0));
+            const int c0 = (j % I.nty) * tile_cells, zc = j / I.nty, z0 = zc * 32;
+            g_na_items[nit++] = march_item(i, c0, z0, std::min(32, I.L - z0), zc);
         }
         g_na_inst[i] = I;
         for (int s = 0; s < 2; ++s)
