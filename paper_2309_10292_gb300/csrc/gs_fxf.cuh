@@ -15,8 +15,9 @@
 // whole-unit part into X and the rest into l.  The storage grid is 2^-47
 // absolute for |l| <= 1/2, and the float-pair products carry about 47
 // significant bits, as double-single does: a step rounds at a few 1e-15,
-// far inside the 1e-10 tolerance of the FP64 workload after 100 steps.  Supported range: |u|, |v| < 4 (reported as GS_DERR_RANGE
-// otherwise), and |du|, |dv| < 32 per step.  The operation structure
+// far inside the 1e-10 tolerance of the FP64 workload after 100 steps.
+// Supported range: |u|, |v| < 4 (reported as GS_DERR_RANGE otherwise), and
+// |du|, |dv| < 32 per step.  The operation structure
 // follows gs_update term by term: u + dt (Du lap u - u v^2 + F (1 - u) +
 // n r), v + dt (Dv lap v + u v^2 - (F + k) v), with lap x = (sum - 6x) / 6
 // folded into Du / 6, Dv / 6.
@@ -83,8 +84,8 @@ GS_D GsFxf fxf_unpack(double d)
 struct GsCoefFXF {
     float a1, a2;  // Du / 6 dt 16
     float b1, b2;  // Dv / 6 dt 16
-    float f1, f2;  // F dt 16
-    float k1, k2;  // (F + k) dt 16
+    float f1, f2;  // (Du + F) dt 16
+    float k1, k2;  // (Dv + F + k) dt 16
     float n1, n2;  // noise dt 4: the noise term per numerator (r = num 2^-24, 2^22 units, 16)
     float t1, t2;  // dt (u v^2 is formed in real units)
     int32_t KF;    // F dt in sixteenths of a unit, rounded ...
@@ -103,8 +104,8 @@ inline GsCoefFXF gs_make_coef_fxf(double Du, double Dv, double F, double k, doub
     GsCoefFXF c;
     fxf_split_host(Du / 6.0 * dt * 16.0, c.a1, c.a2);
     fxf_split_host(Dv / 6.0 * dt * 16.0, c.b1, c.b2);
-    fxf_split_host(F * dt * 16.0, c.f1, c.f2);
-    fxf_split_host((F + k) * dt * 16.0, c.k1, c.k2);
+    fxf_split_host((Du + F) * dt * 16.0, c.f1, c.f2);
+    fxf_split_host((Dv + F + k) * dt * 16.0, c.k1, c.k2);
     fxf_split_host(noise * dt * 4.0, c.n1, c.n2);
     fxf_split_host(dt, c.t1, c.t2);
     const double fs = F * dt * 67108864.0;  // 2^26 sixteenths of a unit per 1
@@ -135,9 +136,14 @@ GS_D void fxf_grid(float p, float e, int32_t& K, float& r)
     r = __fadd_rn(__fsub_rn(p, __int2float_rn(K)), e);
 }
 
+// The range check of the results: each new X, biased by 2^24, is OR-ed into
+// one word (per thread, over as many cells as the caller likes); the word
+// reaches 2^25 exactly when some result has |x'| >= 4.
+GS_D bool fxf_range_bad(uint32_t rng) { return rng >= (1u << 25); }
+
 // x + (T + t) / 16 units, T an integer count and t a float rest (both in
-// sixteenths), renormalised to |l| <= 1/2
-GS_D GsFxf fxf_finish(GsFxf x, int32_t T, float t, bool& ovf)
+// sixteenths), renormalised to |l| <= 1/2; the new X joins the range word
+GS_D GsFxf fxf_finish(GsFxf x, int32_t T, float t, uint32_t& rng)
 {
     const int32_t Th = (T + 8) >> 4;  // whole units, rounded
     const float low = __int2float_rn(T - (Th << 4));
@@ -146,7 +152,7 @@ GS_D GsFxf fxf_finish(GsFxf x, int32_t T, float t, bool& ovf)
     GsFxf r;
     r.X = x.X + Th + K;
     r.l = __fsub_rn(l, __int2float_rn(K));
-    ovf |= (uint32_t)(r.X + (1 << 24)) >= (uint32_t)(1 << 25);  // |x'| >= 4
+    rng |= (uint32_t)(r.X + (1 << 24));
     return r;
 }
 
@@ -159,17 +165,19 @@ GS_D void fxf_nsum(GsFxf xm, GsFxf xp, GsFxf ym, GsFxf yp, GsFxf zm, GsFxf zp, i
 }
 
 // gs_update in this arithmetic.  S*, SL*: the neighbour sums (fxf_nsum);
-// rnum: the noise numerator (r = rnum / 2^24).
-template <bool NOISE>
+// rnum: the noise numerator (r = rnum / 2^24); rng: the range word
+// (fxf_range_bad).  DT: 0 reads c.dt_one at run time, 1 knows dt == 1, 2
+// knows dt != 1.
+template <bool NOISE, int DT = 0>
 GS_D void gs_update_fxf(const GsCoefFXF& c, GsFxf u, GsFxf v, int32_t SU, float SLU, int32_t SV, float SLV,
-                        int32_t rnum, GsFxf& un, GsFxf& vn, bool& ovf)
+                        int32_t rnum, GsFxf& un, GsFxf& vn, uint32_t& rng)
 {
-    // Laplacians (times 6) in units: sum - 6x exactly in integers, then as a
-    // float pair (the integer part rounded to a float, and what that lost)
-    const int32_t LU = SU - 6 * u.X, LV = SV - 6 * v.X;
-    const float luh = __int2float_rn(LU), lvh = __int2float_rn(LV);
-    const float lul = __fadd_rn(__fmaf_rn(-6.0f, u.l, SLU), __int2float_rn(LU - __float2int_rn(luh)));
-    const float lvl = __fadd_rn(__fmaf_rn(-6.0f, v.l, SLV), __int2float_rn(LV - __float2int_rn(lvh)));
+    // the neighbour sums in units as float pairs (the integer sum rounded to
+    // a float, and what that lost plus the rests' sum); Du lap u dt =
+    // Du / 6 S dt - Du u dt, the second part joining F u dt in one product
+    const float suh = __int2float_rn(SU), svh = __int2float_rn(SV);
+    const float sul = __fadd_rn(SLU, __int2float_rn(SU - __float2int_rn(suh)));
+    const float svl = __fadd_rn(SLV, __int2float_rn(SV - __float2int_rn(svh)));
     const float uh = __int2float_rn(u.X), vhu = __int2float_rn(v.X);
     // v in real units times 4, so that u (units) v^2 comes out in sixteenths
     const float vh = __fmul_rn(vhu, 4.0f * kFxfInvUnit), vl = __fmul_rn(v.l, 4.0f * kFxfInvUnit);
@@ -180,7 +188,7 @@ GS_D void gs_update_fxf(const GsCoefFXF& c, GsFxf u, GsFxf v, int32_t SU, float 
     float w2 = __fmaf_rn(vh, vh, -w1);
     w2 = __fmaf_rn(__fadd_rn(vh, vh), vl, w2);
     w2 = __fmaf_rn(vl, vl, w2);
-    if (!c.dt_one) {
+    if (DT == 2 || (DT == 0 && !c.dt_one)) {
         float p, e;
         fxf_mul(c.t1, c.t2, w1, w2, p, e);
         w1 = p;
@@ -190,10 +198,10 @@ GS_D void gs_update_fxf(const GsCoefFXF& c, GsFxf u, GsFxf v, int32_t SU, float 
     fxf_mul(w1, w2, uh, u.l, q1, q2);
     q2 = __fmaf_rn(w2, u.l, q2);
     float pa, ea, pb, eb, pf, ef, pk, ek;
-    fxf_mul(c.a1, c.a2, luh, lul, pa, ea);   // Du lap u dt
-    fxf_mul(c.b1, c.b2, lvh, lvl, pb, eb);   // Dv lap v dt
-    fxf_mul(c.f1, c.f2, uh, u.l, pf, ef);    // F u dt
-    fxf_mul(c.k1, c.k2, vhu, v.l, pk, ek);   // (F + k) v dt
+    fxf_mul(c.a1, c.a2, suh, sul, pa, ea);   // Du / 6 S_u dt
+    fxf_mul(c.b1, c.b2, svh, svl, pb, eb);   // Dv / 6 S_v dt
+    fxf_mul(c.f1, c.f2, uh, u.l, pf, ef);    // (Du + F) u dt
+    fxf_mul(c.k1, c.k2, vhu, v.l, pk, ek);   // (Dv + F + k) v dt
     int32_t Ka, Kb, Kq, Kf, Kk;
     float ra, rb, rq, rf, rk;
     fxf_grid(pa, ea, Ka, ra);
@@ -201,7 +209,8 @@ GS_D void gs_update_fxf(const GsCoefFXF& c, GsFxf u, GsFxf v, int32_t SU, float 
     fxf_grid(q1, q2, Kq, rq);
     fxf_grid(pf, ef, Kf, rf);
     fxf_grid(pk, ek, Kk, rk);
-    // du dt = Du lap u - u v^2 + F (1 - u) + n r;  dv dt = Dv lap v + u v^2 - (F + k) v
+    // du dt = Du / 6 S_u - (Du + F) u - u v^2 + F + n r   (= Du lap u - u v^2 + F (1 - u) + n r)
+    // dv dt = Dv / 6 S_v - (Dv + F + k) v + u v^2         (= Dv lap v + u v^2 - (F + k) v)
     int32_t Tu = Ka - Kq + c.KF - Kf;
     float tu = __fsub_rn(__fadd_rn(__fsub_rn(ra, rq), c.rF), rf);
     if (NOISE) {
@@ -217,17 +226,17 @@ GS_D void gs_update_fxf(const GsCoefFXF& c, GsFxf u, GsFxf v, int32_t SU, float 
     }
     const int32_t Tv = Kb + Kq - Kk;
     const float tv = __fsub_rn(__fadd_rn(rb, rq), rk);
-    un = fxf_finish(u, Tu, tu, ovf);
-    vn = fxf_finish(v, Tv, tv, ovf);
+    un = fxf_finish(u, Tu, tu, rng);
+    vn = fxf_finish(v, Tv, tv, rng);
 }
 
 // A 2-cell group of cells whose inputs are packed pairs (fxf_pack); writes
 // packed pairs (PACK) or FP64 values.
-template <bool NOISE, bool PACK>
+template <bool NOISE, bool PACK, int DT>
 GS_D void gs_update_group_fxf(const GsCoefFXF& c, uint32_t pre, uint32_t kk2, const double* cu, const double* cv,
                               const double* pu, const double* pv, const double* nu, const double* nv,
                               const double* ymu, const double* ypu, const double* ymv, const double* ypv,
-                              double xlu, double xru, double xlv, double xrv, double* ou, double* ov, bool& ovf)
+                              double xlu, double xru, double xlv, double xrv, double* ou, double* ov, uint32_t& rng)
 {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -240,7 +249,7 @@ GS_D void gs_update_group_fxf(const GsCoefFXF& c, uint32_t pre, uint32_t kk2, co
                  fxf_unpack(ypv[e]), fxf_unpack(pv[e]), fxf_unpack(nv[e]), SV, SLV);
         const int32_t rn = NOISE ? gs_group_num(pre, (uint32_t)e, kk2) : 0;
         GsFxf a, b;
-        gs_update_fxf<NOISE>(c, u, v, SU, SLU, SV, SLV, rn, a, b, ovf);
+        gs_update_fxf<NOISE, DT>(c, u, v, SU, SLU, SV, SLV, rn, a, b, rng);
         ou[e] = PACK ? fxf_pack(a) : fxf_to_double(a);
         ov[e] = PACK ? fxf_pack(b) : fxf_to_double(b);
     }

@@ -150,8 +150,9 @@ __global__ void __launch_bounds__(256) gs_naive_kernel(const T* __restrict__ u, 
             fxf_nsum(get(v[ixm]), get(v[ixp]), get(v[iym]), get(v[iyp]), get(v[izm]), get(v[izp]), SV, SLV);
             const int32_t rn = NOISE ? gs_noise_num((uint32_t)i, k) : 0;
             GsFxf a, b;
-            gs_update_fxf<NOISE>(cfxf, uc, vc, SU, SLU, SV, SLV, rn, a, b, any);
-            if (any) gs_report(err, GS_DERR_RANGE);
+            uint32_t rng = 0;
+            gs_update_fxf<NOISE>(cfxf, uc, vc, SU, SLU, SV, SLV, rn, a, b, rng);
+            if (any || fxf_range_bad(rng)) gs_report(err, GS_DERR_RANGE);
             un[i] = OUT_PACKED ? fxf_pack(a) : fxf_to_double(a);
             vn[i] = OUT_PACKED ? fxf_pack(b) : fxf_to_double(b);
         } else {
@@ -352,8 +353,9 @@ GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
 // AR: the arithmetic of FP64 fields (0: IEEE, 1: double-single, 2: fixed
 // point, 3: fixed point with a float remainder).  IO (AR > 0): bit 0 = the
 // input fields hold that arithmetic's packed values, bit 1 = write packed
-// values.  The other arithmetics reading FP64 values convert every staged
-// plane in place once (CONV).
+// values; AR = 3: bit 2 = dt is 1 (its (v^2) dt product is skipped at
+// compile time).  The other arithmetics reading FP64 values convert every
+// staged plane in place once (CONV).
 template <typename T, bool NOISE, int AR, int IO = 0>
 GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
 {
@@ -361,6 +363,7 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
     constexpr bool FXF = AR == 3;
     constexpr bool CONV = AR != 0 && (IO & 1) == 0;
     constexpr bool PACK = (IO & 2) != 0;
+    constexpr int FXF_DT = (IO & 4) != 0 ? 1 : 2;
     constexpr int V = GsVec<T>::N;
     using VT = typename GsVec<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -471,6 +474,7 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
     // planes z-1, z, z+1 of this thread's group in three register sets that
     // rotate by renaming (the loop below is unrolled by 3)
     T qu[3][V], qv[3][V];
+    bool range_bad = false;  // FXF: some result out of range (reported once, at the end)
     int wk = 0;
     ZSeg sg;
     while (zmarch_next_seg(wk, a, sg)) {
@@ -549,10 +553,17 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
             if (!wait_full()) return false;
             convert_stage(cs);
             load_centre(nu, nv);
-            const T shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
-            const T shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
-            const T shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
-            const T shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
+            // x neighbours of the group's end cells from the adjacent lanes;
+            // the FP64 arithmetics on the FP32 and integer pipes read them all
+            // from shared memory instead (four loads issue fewer instructions
+            // than eight 32-bit shuffles and the edge lanes' loads)
+            T shlu{}, shlv{}, shru{}, shrv{};
+            if constexpr (AR == 0) {
+                shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
+                shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
+                shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
+                shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
+            }
             if constexpr (CONV) {
                 // every warp's part of the centre stage is converted
                 if (!gs_mbar_wait(&conv[sc], scp, a.timeout_ns)) {
@@ -571,8 +582,8 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
                 gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
                 T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
-                if (l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
-                if (r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
+                if (AR != 0 || l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
+                if (AR != 0 || r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
                 const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
                 if constexpr (DS)
                     gs_update_group_ds<NOISE, GsFromPacked, PACK>(a.cds, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu,
@@ -581,10 +592,10 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
                     gs_update_group_fx<NOISE, PACK>(a.cfx, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
                                                     xru, xlv, xrv, outu, outv);
                 else if constexpr (FXF) {
-                    bool ovf = false;
-                    gs_update_group_fxf<NOISE, PACK>(a.cfxf, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
-                                                     xru, xlv, xrv, outu, outv, ovf);
-                    if (ovf) gs_report(a.err, GS_DERR_RANGE);
+                    uint32_t rng = 0;
+                    gs_update_group_fxf<NOISE, PACK, FXF_DT>(a.cfxf, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv,
+                                                             ypv, xlu, xru, xlv, xrv, outu, outv, rng);
+                    range_bad |= fxf_range_bad(rng);
                 }
                 else
                     gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
@@ -626,6 +637,7 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
         release(sc);  // plane z0 + nz (only its centre was used)
         if (abort_flag) return;
     }
+    if (range_bad) gs_report(a.err, GS_DERR_RANGE);
 }
 
 template <typename T, bool NOISE, int AR, int IO>
@@ -762,7 +774,16 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
     }
         if (p.arith == GS_ARITH_DS) GS_ZM_IO(1)
         if (p.arith == GS_ARITH_FX) GS_ZM_IO(2)
-        GS_ZM_IO(3)
+        switch ((p.io & 3) | (p.dt == 1.0 ? 4 : 0)) {
+        case 0: GS_ZM(3, 0);
+        case 1: GS_ZM(3, 1);
+        case 2: GS_ZM(3, 2);
+        case 3: GS_ZM(3, 3);
+        case 4: GS_ZM(3, 4);
+        case 5: GS_ZM(3, 5);
+        case 6: GS_ZM(3, 6);
+        default: GS_ZM(3, 7);
+        }
 #undef GS_ZM_IO
 #undef GS_ZM
     }
