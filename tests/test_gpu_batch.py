@@ -118,6 +118,35 @@ def test_batch_full_config_sampled():
     b.close()
 
 
+def test_batch_tail_split_alternating_pieces_bitwise():
+    """Enough work items that the partial last round is cut along z: 40 grids
+    of 128^3 are 2560 items (16 runs of 1024 cells x 4 z-chunks each), so a
+    304-CTA launch has 128 items left for its last round and cuts each in
+    two, the halves marching in opposite directions.  Instances whose items
+    are cut, and one that is not, evolve bit for bit like single grids."""
+    need_cuda()
+    n, L = 40, 128
+    F = list(np.linspace(0.02, 0.05, n))
+    k = list(np.linspace(0.05, 0.065, n))
+    b = gs.GrayScottBatch([L] * n, F, k, noise=0.1, seed=9, dtype="f32", **BASE)
+    b.step(3)
+    info = b.info
+    base = n * (L * L // 1024) * (L // 32)
+    rem = base % info["grid"]
+    if base > info["grid"] and rem and info["grid"] // rem >= 2:
+        f = min(4, info["grid"] // rem)
+        assert info["items"] == base - rem + rem * f  # the tail was cut
+    for i in (0, n - 2, n - 1):
+        s = gs.GrayScott(L, F=F[i], k=k[i], noise=0.1, seed=9 + i, dtype="f32", **BASE)
+        s.step(3)
+        us, vs = s.read()
+        ub, vb = b.read(i)
+        np.testing.assert_array_equal(ub, us)
+        np.testing.assert_array_equal(vb, vs)
+        s.close()
+    b.close()
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_batch_bounded_waits_report_timeout(mode):
     # mode 1: the producer issues no copies; mode 2: CTA 0 never arrives at the

@@ -494,6 +494,26 @@ def test_fixed_point_reports_values_outside_its_range(kernel, arith, bad):
     sim.close()
 
 
+@pytest.mark.parametrize("kernel", [gs.GS_KERNEL_NAIVE, gs.GS_KERNEL_ZMARCH])
+def test_fxf_reports_results_outside_its_range(kernel):
+    # inputs inside the range (a plane of u = 3.9) that one step pushes
+    # past 4 (the oracle's step from the same fields reaches |u| 4.09 and
+    # |v| 4.75): the check of the step's results reports it
+    L = 16
+    sim = make_ar(gs.GS_ARITH_FXF, L, kernel, noise=0.5, seed=4)
+    u0, v0 = inputs.random_fields(L, seed=8, lo=0.0, hi=1.0)
+    u0[3, :, :] = 3.9
+    sim.write(u0, v0)
+    sim.step(1)
+    with pytest.raises(gs.GsError) as e:
+        sim.sync()
+    assert e.value.status == gs.GS_EINVAL and "fixed-point range" in str(e.value)
+    sim.init()
+    sim.step(2)
+    sim.sync()
+    sim.close()
+
+
 # ---------------------------------------------------------------------------
 # Plan cache (gs_autotune_cached)
 # ---------------------------------------------------------------------------
