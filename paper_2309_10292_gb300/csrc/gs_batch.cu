@@ -9,12 +9,13 @@
 // 960 of 1024 cells, and the tenth tile of a 96^2 plane only 6 rows).  A tile
 // is staged as the whole rows it touches, so the x wrap is an index wrap
 // inside shared memory (no x-halo copies).  Work items are numbered instance
-// by instance; CTA b takes items b, b + grid, ...  The
-// items of a partial last round are cut along z into up to four pieces, so
-// that round ends after a fraction of an item instead of a whole one.
-// Neighbouring z-chunks march in opposite directions, so the halo planes two
-// chunks share are read by both at about the same time (once from HBM, once
-// from L2).
+// by instance, and the CTAs take them in that order from a ticket counter
+// (each CTA's next item is the next free one, so a step ends within a
+// fraction of an item on every CTA; the last grid / 2 items are cut along z
+// into four pieces for the same reason).  Neighbouring z-chunks march in
+// opposite directions, so the halo planes two chunks share are read by both
+// at about the same time (once from HBM, once from L2).  The allocation-free
+// step keeps the static order instead: CTA b takes items b, b + grid, ...
 //
 // Per item a producer warp streams the planes z0-1 .. z0+nz with TMA (a box
 // of the tile's rows + two wrapped halo rows per field, per-instance tensor
@@ -57,12 +58,14 @@ struct BInst {
 };
 
 struct BCtrl {
-    long long t;   // step counter of the current state
-    int cur;       // buffer set holding the current state
-    unsigned bar;  // grid barrier arrivals (reset before every launch)
-    int err;       // device error word
-    int pad[3];
+    long long t;    // step counter of the current state
+    int cur;        // buffer set holding the current state
+    unsigned bar;   // grid barrier arrivals (reset before every launch) ...
+    unsigned next;  // ... and the work-item tickets of a dynamic launch (with it)
+    int err;        // device error word
+    int pad[2];
 };
+static_assert(offsetof(BCtrl, next) == offsetof(BCtrl, bar) + sizeof(unsigned), "bar and next reset together");
 
 template <typename T>
 struct BArgs {
@@ -76,7 +79,8 @@ struct BArgs {
     long long nsteps;
     T Du6, Dv6, dt, noise24;
     uint64_t timeout_ns;
-    int fault;  // 1: the producer issues no copies; 2: CTA 0 never arrives at the grid barrier
+    int fault;    // 1: the producer issues no copies; 2: CTA 0 never arrives at the grid barrier
+    int dynamic;  // 1: CTAs take items in table order from a ticket counter; 0: CTA b takes b, b + grid, ...
 };
 
 // What the consumers need of one work item, written to shared memory by the
@@ -85,8 +89,10 @@ struct BArgs {
 // waiting on the item and instance tables in global memory.  kBatchDescs
 // slots are reused round robin: the producer fills slot k + kBatchDescs only
 // after the consumers freed a stage issued kBatchDescs items later than item
-// k's first plane (an item has at least 3 planes and the ring at most 8
-// stages, so they read slot k long before).
+// k's first plane (an item has at least 3 planes, the end-of-step marker one,
+// and the ring at most 8 stages, so they read slot k long before).  A
+// descriptor with nz == 0 marks the end of the CTA's items for the step; it
+// travels through one ring stage (a plain arrival, no copy).
 constexpr int kBatchDescs = 4;
 template <typename T>
 struct BDesc {
@@ -204,14 +210,22 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 76 : 96) gs_batch_kernel(const __gr
             // ------------------------------ consumers ------------------------------
             // planes z-1, z, z+1 in three register sets rotated by renaming
             T qu[3][V], qv[3][V];
-            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x, ++kl) {
-                // the item's first plane, and with it the item's descriptor
+            for (;;) {
+                // the next item's first plane, and with it its descriptor
                 if (!wait_or_abort(&full[cs], cph, a.timeout_ns, &s_abort)) {
                     gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
                     s_abort = 1;
                     break;
                 }
                 const BDesc<T> d = s_desc[kl % kBatchDescs];
+                ++kl;
+                if (d.nz == 0) {
+                    // no more items for this CTA in this step
+                    __syncwarp();
+                    if (lane == 0) gs_mbar_arrive(&empty[cs]);
+                    advance();
+                    break;
+                }
                 // One item, marching up (DESC false: planes z0, z0+1, ...) or
                 // down (DESC true, d.nz < 0: planes z0+nz-1, z0+nz-2, ...).
                 // Either way each cell sees z-1 as its lower and z+1 as its
@@ -330,8 +344,34 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 76 : 96) gs_batch_kernel(const __gr
         } else if (tid == kBatchConsumers && a.fault != 1) {
             // ------------------------------ producer -------------------------------
             gs_fence_proxy_async_global();  // the previous step's stores (acquired at the barrier)
-            for (int item = blockIdx.x; item < a.nitems && !s_abort; item += gridDim.x, ++kl) {
+            // the step's tickets: nitems items and one failed draw per CTA, so
+            // step s of the launch draws base .. base + nitems + grid - 1
+            const unsigned base = (unsigned)((unsigned long long)s * (unsigned)(a.nitems + gridDim.x));
+            int k = 0;
+            auto draw = [&]() -> int {
+                return a.dynamic ? (int)(atomicAdd(&a.ctrl->next, 1u) - base) : blockIdx.x + (k++) * gridDim.x;
+            };
+            int item = draw();  // the next ticket is drawn one item ahead (its latency hides behind the copies)
+            for (;;) {
+                if (item >= a.nitems || s_abort) {
+                    // end of this CTA's items: the marker through one stage
+                    const int sl = cs;
+                    if (s_abort || (wrapped && !wait_or_abort(&empty[sl], cph ^ 1u, a.timeout_ns, &s_abort))) {
+                        if (!s_abort) {
+                            gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
+                            s_abort = 1;
+                        }
+                        break;
+                    }
+                    s_desc[kl % kBatchDescs].nz = 0;
+                    gs_mbar_arrive(&full[sl]);
+                    ++kl;
+                    ++seq;
+                    advance();
+                    break;
+                }
                 const int4 it = a.items[item];
+                item = draw();
                 const int ii = it.x;
                 const BInst& I = a.inst[ii];
                 const GsKeys keys = gs_step_keys(((uint64_t)I.seed_hi << 32) | I.seed_lo, t);
@@ -381,6 +421,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 76 : 96) gs_batch_kernel(const __gr
                     else
                         zp = zp + 1 == L ? 0 : zp + 1;
                 }
+                ++kl;
                 if (failed) {
                     gs_report(&a.ctrl->err, GS_DERR_TIMEOUT);
                     s_abort = 1;
@@ -610,9 +651,8 @@ static void plain_items(const BInst* inst, int n, int tz, int tile_cells, std::v
 // Cut each of those items along z into f = min(4, grid / rem) pieces (fewer
 // when it has fewer planes) appended after the full rounds, so the last
 // round lasts about 1/f of an item.  Every cell is still updated once.
-// Items with nz < 0 (single-step tables) march down; with `alternate` the
-// pieces of an item alternate their direction, as whole chunks do.
-static void split_tail(const std::vector<int4>& base, int grid, bool alternate, std::vector<int4>& out)
+// (The temporally blocked kernel's items, all marching up.)
+static void split_tail(const std::vector<int4>& base, int grid, std::vector<int4>& out)
 {
     out = base;
     const int n = (int)base.size();
@@ -624,12 +664,32 @@ static void split_tail(const std::vector<int4>& base, int grid, bool alternate, 
     out.resize(n - rem);
     for (int q = n - rem; q < n; ++q) {
         const int4 it = base[q];
+        const int parts = std::min(f, it.w);
+        for (int p = 0; p < parts; ++p) {
+            const int za = it.w * p / parts, zb = it.w * (p + 1) / parts;
+            out.push_back(make_int4(it.x, it.y, it.z + za, zb - za));
+        }
+    }
+}
+
+// For a launch whose CTAs take items from a ticket counter in table order:
+// cut the last m items along z into up to f pieces each (alternating their
+// direction), so the last items taken are short and the CTAs finish a step
+// within a fraction of an item of one another.  Every cell is still updated
+// once.
+static void split_last(const std::vector<int4>& base, int m, int f, std::vector<int4>& out)
+{
+    const int n = (int)base.size();
+    m = std::min(std::max(m, 0), n);
+    out.assign(base.begin(), base.end() - m);
+    for (int q = n - m; q < n; ++q) {
+        const int4 it = base[q];
         const bool desc = it.w < 0;
         const int nz = desc ? -it.w : it.w;
         const int parts = std::min(f, nz);
         for (int p = 0; p < parts; ++p) {
             const int za = nz * p / parts, zb = nz * (p + 1) / parts;
-            const bool d = alternate ? desc != ((p & 1) != 0) : desc;
+            const bool d = desc != ((p & 1) != 0);
             out.push_back(make_int4(it.x, it.y, it.z + za, d ? za - zb : zb - za));
         }
     }
@@ -737,6 +797,7 @@ static int plain_prepare(gs_batch* b, int64_t n, BArgs<T>& a, size_t& smem)
     a.noise24 = c.noise24;
     a.timeout_ns = b->timeout_ns;
     a.fault = b->fault;
+    a.dynamic = 1;
     smem = (size_t)2 * b->field_elems * sizeof(T) * b->stages;
     auto kern = gs_batch_kernel<T, NOISE>;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -745,9 +806,9 @@ static int plain_prepare(gs_batch* b, int64_t n, BArgs<T>& a, size_t& smem)
     if (per_sm < 1) return fail(GS_EINVAL, "batch kernel does not fit on an SM");
     const int grid = std::min(per_sm * num_sms(), (int)b->base_items.size());
     if (b->items_grid != grid) {
-        // cut the partial last round for this grid (once per plan)
+        // cut the last items for this grid (once per plan)
         std::vector<int4> items;
-        split_tail(b->base_items, grid, true, items);
+        split_last(b->base_items, grid / 2, 4, items);
         GS_CUDA_TRY(cudaStreamSynchronize(b->stream));  // no launch still reads the old table
         const int rc = upload_items(b, items);
         if (rc) return rc;
@@ -786,7 +847,7 @@ static int tb_prepare(gs_batch* b, int64_t npasses, BtbArgs& a, size_t& smem)
     const int grid = std::min(per_sm * num_sms(), (int)b->tb_base_items.size());
     if (b->tb_items_grid != grid) {
         std::vector<int4> items;
-        split_tail(b->tb_base_items, grid, false, items);
+        split_tail(b->tb_base_items, grid, items);
         GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
         const int rc = upload_tb_items(b, items);
         if (rc) return rc;
@@ -799,11 +860,11 @@ static int tb_prepare(gs_batch* b, int64_t npasses, BtbArgs& a, size_t& smem)
     return GS_OK;
 }
 
-// one persistent launch inside a capture: barrier counter reset + kernel
+// one persistent launch inside a capture: barrier and ticket counters reset + kernel
 template <typename K, typename A>
 static cudaError_t capture_persistent(gs_batch* b, K kern, const A& args, int grid, int threads, size_t smem)
 {
-    cudaError_t e = cudaMemsetAsync(&b->d_ctrl->bar, 0, sizeof(unsigned), b->cap);
+    cudaError_t e = cudaMemsetAsync(&b->d_ctrl->bar, 0, 2 * sizeof(unsigned), b->cap);  // bar and next
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1382,6 +1443,7 @@ static int noalloc_launch_t(char* scratch, void* arena, int n, int nitems, int m
     a.noise24 = c.noise24;
     a.timeout_ns = 2000000000ull;
     a.fault = 0;
+    a.dynamic = 0;
     (void)n;
     const size_t smem = (size_t)2 * a.field_elems * sizeof(T) * a.stages;
     auto kern = gs_batch_kernel<T, NOISE>;

@@ -119,11 +119,11 @@ def test_batch_full_config_sampled():
 
 
 def test_batch_tail_split_alternating_pieces_bitwise():
-    """Enough work items that the partial last round is cut along z: 40 grids
-    of 128^3 are 2560 items (16 runs of 1024 cells x 4 z-chunks each), so a
-    304-CTA launch has 128 items left for its last round and cuts each in
-    two, the halves marching in opposite directions.  Instances whose items
-    are cut, and one that is not, evolve bit for bit like single grids."""
+    """The last grid / 2 work items of a launch are cut along z into four
+    pieces that march in alternating directions: 40 grids of 128^3 are 2560
+    items (16 runs of 1024 cells x 4 z-chunks each), the last 152 of a
+    304-CTA launch become 608 pieces.  Instances whose items are cut, and one
+    that is not, evolve bit for bit like single grids."""
     need_cuda()
     n, L = 40, 128
     F = list(np.linspace(0.02, 0.05, n))
@@ -132,10 +132,8 @@ def test_batch_tail_split_alternating_pieces_bitwise():
     b.step(3)
     info = b.info
     base = n * (L * L // 1024) * (L // 32)
-    rem = base % info["grid"]
-    if base > info["grid"] and rem and info["grid"] // rem >= 2:
-        f = min(4, info["grid"] // rem)
-        assert info["items"] == base - rem + rem * f  # the tail was cut
+    m = min(info["grid"] // 2, base)
+    assert info["items"] == base - m + 4 * m  # the last items were cut
     for i in (0, n - 2, n - 1):
         s = gs.GrayScott(L, F=F[i], k=k[i], noise=0.1, seed=9 + i, dtype="f32", **BASE)
         s.step(3)
