@@ -214,8 +214,9 @@ static int check_common(int L, double Du, double Dv, double F, double k, double 
 
 static int finish_create(gs_sim* s, gs_sim** out)
 {
-    GS_CUDA_TRY(cudaMalloc(&s->d_err, sizeof(int)));
-    GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+    // the device error word, a pad word and the z-march kernel's two ticket words
+    GS_CUDA_TRY(cudaMalloc(&s->d_err, 4 * sizeof(int)));
+    GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4 * sizeof(int), s->stream));
     int rc = default_plan(s);
     if (!rc) rc = encode_maps(s);
     if (!rc) rc = launch_init(s->dtype, s->L, s->buf[0][0], s->buf[0][1], s->stream);
@@ -313,7 +314,7 @@ int gs_init(gs_sim* s)
     if (!s) return fail(GS_EINVAL, "sim is NULL");
     s->cur = 0;
     s->t = 0;
-    GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+    GS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4 * sizeof(int), s->stream));  // error word and tickets
     int rc = launch_init(s->dtype, s->L, s->buf[0][0], s->buf[0][1], s->stream);
     if (!rc) s->launches += 1;
     return rc;
@@ -349,7 +350,7 @@ int gs_step(gs_sim* s, int64_t n)
         if (s->kernel != GS_KERNEL_NAIVE) {
             if (!s->maps_ok) return fail(GS_ESTATE, "tensor maps not encoded");
             rc = launch_zmarch(s->dtype, s->L, s->zp, s->maps[in], s->buf[outs][0], s->buf[outs][1], p, s->t,
-                               s->d_err, s->timeout_ns, s->fault, s->stream);
+                               s->d_err, s->timeout_ns, s->fault, (unsigned*)(s->d_err + 2), s->stream);
         } else {
             rc = launch_naive(s->dtype, s->L, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1], p,
                               s->t, s->d_err, s->stream);

@@ -1157,7 +1157,7 @@ int gs_batch_step_sequential(gs_batch* b, int64_t n)
             int rc = launch_zmarch(b->dtype, I.L, b->zplan[i], b->zmaps[in][i],
                                    (char*)b->arena + (size_t)I.off[out][0] * esz,
                                    (char*)b->arena + (size_t)I.off[out][1] * esz, p, b->t, &b->d_ctrl->err,
-                                   b->timeout_ns, 0, b->stream);
+                                   b->timeout_ns, 0, nullptr, b->stream);
             if (rc) return rc;
             b->launches += 1;
         }

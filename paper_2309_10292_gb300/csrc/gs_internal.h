@@ -75,9 +75,12 @@ struct ZPlan {
 bool zmarch_supported(int dtype, int L);
 int zmarch_validate(int dtype, int L, const ZPlan& pl);
 int zmarch_encode(int dtype, int L, const ZPlan& pl, void* u, void* v, ZMaps* maps);
+// tickets: two zeroed words of device memory the launch leaves zeroed (the
+// CTAs take work units from it as they become free), or null for a static
+// round robin
 int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
                   const Params& p, int64_t t, int* d_err, uint64_t timeout_ns, int stall,
-                  cudaStream_t s);
+                  unsigned* tickets, cudaStream_t s);
 
 // Held outer layer (gs_variants.cu): copy the six faces of the input state
 // over the output state (iv/ov may be NULL for one field).
@@ -104,7 +107,7 @@ struct gs_sim {
     int cur = 0;       // set holding the current state
     int64_t t = 0;     // step counter
     cudaStream_t stream = nullptr;
-    int* d_err = nullptr;
+    int* d_err = nullptr;  // 4 words: the error word, a pad word, the z-march kernel's two ticket words
     int kernel = GS_KERNEL_NAIVE;
     ZPlan zp{128, 8, 32, 4, 1};   // z-march plan (also runs the steps a blocked pass leaves over)
     ZPlan tp{64, 16, 64, 5, 2};   // temporal-blocking plan (kernel GS_KERNEL_TBLOCK)

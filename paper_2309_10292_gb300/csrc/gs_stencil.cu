@@ -305,18 +305,51 @@ struct ZArgs {
     int* err;
     uint64_t timeout_ns;
     int stall;               // failure injection: the producer issues nothing
+    unsigned* tickets;       // [next ticket, CTAs done] (zeroed between launches), or null: round robin
+    int alternate;           // odd z-chunks march down
 };
 
 // Work of the persistent CTAs: tiles in the order x fastest, then y, then
-// z-chunk, round-robin over the CTAs (all CTAs work on neighbouring tiles of
-// the same z-chunk at a time, so the tiles' halo rows are L2 hits).  The
-// partial last round is split along z so that every CTA gets a share: each
-// of its `rem` tiles becomes s = G / rem pieces (G = CTAs) of about nz / s
-// planes, and no CTA idles while others finish whole tiles.
+// z-chunk (the CTAs work on neighbouring tiles of the same z-chunk at a time,
+// so the tiles' halo rows are L2 hits).  In the memory-bound IEEE kernels
+// (ZArgs::alternate) odd z-chunks march down (nz < 0: planes z0 + nz - 1
+// down to z0), so two neighbouring chunks read the halo planes they share at
+// about the same time, the second read from L2.  The FP64 arithmetics on the
+// FP32 and integer pipes are bound by instruction issue: they march up only,
+// and keep one copy of their long per-plane code (both directions at once
+// measured 1 % slower), and take tiles round robin (the counter measured
+// 0.5 % slower there).
+//
+// With a ticket counter (ZArgs::tickets) the CTAs take work units in that
+// order as they become free: units are the tiles, the last G / 2 of them
+// (G = CTAs) cut along z into four pieces (alternating direction), so every
+// CTA ends the launch within a fraction of a tile of the others.  Without
+// one (the batch's per-instance baseline) CTA c takes tiles c, c + G, ...,
+// and the partial last round is cut along z so that every CTA gets a share:
+// each of its `rem` tiles becomes s = G / rem pieces of about nz / s planes.
 struct ZSeg {
-    int x0, y0, z0, nz;
+    int x0, y0, z0, nz;  // nz < 0: march down |nz| planes
 };
 
+// the segment `part` of `parts` of tile `tile` (false when it is empty)
+template <typename T>
+GS_D bool zmarch_piece(int tile, int part, int parts, const ZArgs<T>& a, ZSeg& g)
+{
+    const int txi = tile % a.ntx;
+    const int tyi = (tile / a.ntx) % a.nty;
+    const int tzi = tile / (a.ntx * a.nty);
+    const int z0 = tzi * a.tz;
+    const int nz = min(a.tz, a.L - z0);
+    const int lo = nz * part / parts, hi = nz * (part + 1) / parts;
+    if (hi <= lo) return false;  // more pieces than planes: this one is empty
+    g.x0 = txi * a.tx;
+    g.y0 = tyi * a.ty;
+    g.z0 = z0 + lo;
+    g.nz = a.alternate && ((tzi + part) & 1) ? lo - hi : hi - lo;
+    return true;
+}
+
+// round robin: the next segment of CTA blockIdx.x (k counts its draws)
 template <typename T>
 GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
 {
@@ -335,18 +368,26 @@ GS_D bool zmarch_next_seg(int& k, const ZArgs<T>& a, ZSeg& g)
             return false;
         }
         ++k;
-        const int txi = tile % a.ntx;
-        const int tyi = (tile / a.ntx) % a.nty;
-        const int tzi = tile / (a.ntx * a.nty);
-        const int z0 = tzi * a.tz;
-        const int nz = min(a.tz, a.L - z0);
-        const int lo = nz * part / parts, hi = nz * (part + 1) / parts;
-        if (hi <= lo) continue;  // more pieces than planes: this one is empty
-        g.x0 = txi * a.tx;
-        g.y0 = tyi * a.ty;
-        g.z0 = z0 + lo;
-        g.nz = hi - lo;
-        return true;
+        if (zmarch_piece(tile, part, parts, a, g)) return true;
+    }
+}
+
+// ticket counter: the segment of the next free work unit (false: none left)
+template <typename T>
+GS_D bool zmarch_unit_seg(unsigned* tickets, const ZArgs<T>& a, ZSeg& g)
+{
+    const int m = min(a.ntiles, (int)gridDim.x / 2);
+    const int whole = a.ntiles - m;
+    for (;;) {
+        const int u = (int)atomicAdd(&tickets[0], 1u);
+        if (u < whole) {
+            if (zmarch_piece(u, 0, 1, a, g)) return true;
+        } else if (u < whole + 4 * m) {
+            const int v = u - whole;
+            if (zmarch_piece(whole + v / 4, v % 4, 4, a, g)) return true;
+        } else {
+            return false;
+        }
     }
 }
 
@@ -371,6 +412,13 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
     // warp once its part of the stage has been converted in place
     __shared__ __align__(8) uint64_t bars[(CONV ? 3 : 2) * 8];
     __shared__ volatile int abort_flag;
+    // the segments the producer hands to the consumers, in order, through
+    // four slots: (x0, y0, z0, +-nz), nz == 0 after the last.  The producer
+    // writes a slot before it releases the segment's first plane (that
+    // mbarrier arrival orders it) and reuses it four segments later, at
+    // least 12 planes on, when the consumers have read it long before (the
+    // ring holds at most 8 stages)
+    __shared__ int4 s_seg[4];
 
     const int S = a.stages;
     uint64_t* full = bars;
@@ -397,50 +445,86 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
 
     if (tid >= cons_threads) {
         // ------------------------------ producer warp ------------------------------
-        if (tid != cons_threads || a.stall) return;
-        for (int f = 0; f < 2; ++f)
-            for (int m = 0; m < 3; ++m) gs_prefetch_tmap(&maps.m[f][m]);
+        if (tid != cons_threads) return;
         uint32_t seq = 0;           // planes issued (for the drain)
         int ps = 0;                 // stage of the next plane
         uint32_t pph = 0;           // its round's parity
         bool wrapped = false;       // every stage used once: wait for the consumers' release
-        int wk = 0;
-        ZSeg sg;
-        while (zmarch_next_seg(wk, a, sg)) {
-            const int x0 = sg.x0, y0 = sg.y0, z0 = sg.z0, nz = sg.nz;
-            const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0);
-            const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
-            const int xl = (x0 - V + L) % L, xr = (x0 + nvx) % L;
-            int zp = (z0 - 1 + L) % L;
-            for (int j = 0; j < nz + 2; ++j) {
-                if (wrapped) {
-                    if (!gs_mbar_wait(&empty[ps], pph ^ 1u, a.timeout_ns)) {
-                        gs_report(a.err, GS_DERR_TIMEOUT);
-                        abort_flag = 1;
-                        goto drain;
-                    }
+        // with a ticket counter: the last CTA to finish (after every CTA drew
+        // its last ticket; the fence orders this CTA's draws before its count)
+        // zeroes the counter for the next launch
+        auto finish = [&]() {
+            if (!a.tickets) return;
+            __threadfence();
+            if (atomicAdd(&a.tickets[1], 1u) == gridDim.x - 1) {
+                a.tickets[0] = 0;
+                a.tickets[1] = 0;
+            }
+        };
+        if (!a.stall) {
+            for (int f = 0; f < 2; ++f)
+                for (int m = 0; m < 3; ++m) gs_prefetch_tmap(&maps.m[f][m]);
+            int wk = 0, kd = 0;
+            ZSeg sg;
+            for (;;) {
+                const bool more = a.tickets ? zmarch_unit_seg(a.tickets, a, sg) : zmarch_next_seg(wk, a, sg);
+                // the stage of the segment's first plane (or of the end marker)
+                if (wrapped && !gs_mbar_wait(&empty[ps], pph ^ 1u, a.timeout_ns)) {
+                    gs_report(a.err, GS_DERR_TIMEOUT);
+                    abort_flag = 1;
+                    goto drain;
                 }
                 if (abort_flag) goto drain;
-                gs_mbar_arrive_expect_tx(&full[ps], a.lay.tx_bytes);
-                for (int f = 0; f < 2; ++f) {
-                    T* b = ring + (size_t)ps * (a.lay.stage_bytes / sizeof(T)) + f * a.lay.field_elems;
-                    gs_tma_load_3d(b + a.lay.main_off, &maps.m[f][0], &full[ps], x0, y0, zp);
-                    gs_tma_load_3d(b + a.lay.top_off, &maps.m[f][1], &full[ps], x0, ytop, zp);
-                    gs_tma_load_3d(b + a.lay.bot_off, &maps.m[f][1], &full[ps], x0, ybot, zp);
-                    gs_tma_load_3d(b + a.lay.left_off, &maps.m[f][2], &full[ps], xl, y0, zp);
-                    gs_tma_load_3d(b + a.lay.right_off, &maps.m[f][2], &full[ps], xr, y0, zp);
+                if (!more) {
+                    s_seg[kd & 3] = make_int4(0, 0, 0, 0);
+                    gs_mbar_arrive(&full[ps]);  // no copy: the phase completes here
+                    ++seq;
+                    if (++ps == S) { ps = 0; pph ^= 1u; wrapped = true; }
+                    break;
                 }
-                ++seq;
-                if (++ps == S) { ps = 0; pph ^= 1u; wrapped = true; }
-                zp = zp + 1 == L ? 0 : zp + 1;
+                s_seg[kd & 3] = make_int4(sg.x0, sg.y0, sg.z0, sg.nz);
+                ++kd;
+                const bool down = sg.nz < 0;
+                const int x0 = sg.x0, y0 = sg.y0, z0 = sg.z0, nz = down ? -sg.nz : sg.nz;
+                const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0);
+                const int ytop = (y0 - 1 + L) % L, ybot = (y0 + nvy) % L;
+                const int xl = (x0 - V + L) % L, xr = (x0 + nvx) % L;
+                int zp = down ? (z0 + nz) % L : (z0 - 1 + L) % L;
+                for (int j = 0; j < nz + 2; ++j) {
+                    if (j > 0 && wrapped) {
+                        if (!gs_mbar_wait(&empty[ps], pph ^ 1u, a.timeout_ns)) {
+                            gs_report(a.err, GS_DERR_TIMEOUT);
+                            abort_flag = 1;
+                            goto drain;
+                        }
+                    }
+                    if (abort_flag) goto drain;
+                    gs_mbar_arrive_expect_tx(&full[ps], a.lay.tx_bytes);
+                    for (int f = 0; f < 2; ++f) {
+                        T* b = ring + (size_t)ps * (a.lay.stage_bytes / sizeof(T)) + f * a.lay.field_elems;
+                        gs_tma_load_3d(b + a.lay.main_off, &maps.m[f][0], &full[ps], x0, y0, zp);
+                        gs_tma_load_3d(b + a.lay.top_off, &maps.m[f][1], &full[ps], x0, ytop, zp);
+                        gs_tma_load_3d(b + a.lay.bot_off, &maps.m[f][1], &full[ps], x0, ybot, zp);
+                        gs_tma_load_3d(b + a.lay.left_off, &maps.m[f][2], &full[ps], xl, y0, zp);
+                        gs_tma_load_3d(b + a.lay.right_off, &maps.m[f][2], &full[ps], xr, y0, zp);
+                    }
+                    ++seq;
+                    if (++ps == S) { ps = 0; pph ^= 1u; wrapped = true; }
+                    if (down)
+                        zp = zp == 0 ? L - 1 : zp - 1;
+                    else
+                        zp = zp + 1 == L ? 0 : zp + 1;
+                }
             }
         }
+        finish();
         return;
     drain:
         // let every copy this thread issued land before the CTA can exit
         // (fixed 2 s budget: copies in flight always complete within it)
         for (uint32_t q = (seq > (uint32_t)S ? seq - S : 0); q < seq; ++q)
             gs_mbar_wait(&full[q % S], (q / S) & 1, 2000000000ull);
+        finish();
         return;
     }
 
@@ -475,167 +559,192 @@ GS_D void zmarch_body(const ZMaps& maps, const ZArgs<T>& a)
     // rotate by renaming (the loop below is unrolled by 3)
     T qu[3][V], qv[3][V];
     bool range_bad = false;  // FXF: some result out of range (reported once, at the end)
-    int wk = 0;
-    ZSeg sg;
-    while (zmarch_next_seg(wk, a, sg)) {
-        const int x0 = sg.x0, y0 = sg.y0, z0 = sg.z0, nz = sg.nz;
-        const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0);
-        const bool active = row < nvy && xv * V < nvx;
-        const int rr = row < a.ty ? row : 0;  // padding threads read a valid address
-        const int moff = a.lay.main_off + rr * a.tx + xv * V;
-        // y neighbours (top / bottom halo rows at the tile's edges)
-        const int om = row > 0 ? a.lay.main_off + (row - 1) * a.tx + xv * V : a.lay.top_off + xv * V;
-        const int op = row + 1 < nvy ? a.lay.main_off + (row + 1) * a.tx + xv * V : a.lay.bot_off + xv * V;
-        // x neighbours of the group's end cells: from the adjacent lanes when
-        // they hold the same row's neighbouring groups (conflict-free), else
-        // from shared memory (halo columns, or a group in another warp)
-        const bool has_r = xv * V + V < nvx;
-        const bool l_smem = xv == 0 || lane == 0;
-        const bool r_smem = !has_r || lane == 31;
-        const int oxl = xv > 0 ? moff - 1 : a.lay.left_off + rr * V + (V - 1);
-        const int oxr = has_r ? moff + V : a.lay.right_off + rr * V;
-        int64_t gidx = (int64_t)z0 * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
+    int kd = 0;
+    for (;;) {
+        // the next segment's first plane, and with it its descriptor
+        if (!wait_full()) return;
+        const int4 dsc = s_seg[kd & 3];
+        ++kd;
+        if (dsc.w == 0) break;  // no segment left (nothing follows the marker's stage)
+        // one segment, marching up (planes z0, z0 + 1, ...) or down (DESC:
+        // z0 + nz - 1, z0 + nz - 2, ...); either way each cell takes z-1 as
+        // its lower and z+1 as its upper neighbour, so the update is the
+        // same to the bit
+        auto run = [&](auto desc_tag) -> bool {
+            constexpr bool DESC = decltype(desc_tag)::value;
+            const int x0 = dsc.x, y0 = dsc.y, z0 = dsc.z, nz = DESC ? -dsc.w : dsc.w;
+            const int nvx = min(a.tx, L - x0), nvy = min(a.ty, L - y0);
+            const bool active = row < nvy && xv * V < nvx;
+            const int rr = row < a.ty ? row : 0;  // padding threads read a valid address
+            const int moff = a.lay.main_off + rr * a.tx + xv * V;
+            // y neighbours (top / bottom halo rows at the tile's edges)
+            const int om = row > 0 ? a.lay.main_off + (row - 1) * a.tx + xv * V : a.lay.top_off + xv * V;
+            const int op = row + 1 < nvy ? a.lay.main_off + (row + 1) * a.tx + xv * V : a.lay.bot_off + xv * V;
+            // x neighbours of the group's end cells: from the adjacent lanes when
+            // they hold the same row's neighbouring groups (conflict-free), else
+            // from shared memory (halo columns, or a group in another warp)
+            const bool has_r = xv * V + V < nvx;
+            const bool l_smem = xv == 0 || lane == 0;
+            const bool r_smem = !has_r || lane == 31;
+            const int oxl = xv > 0 ? moff - 1 : a.lay.left_off + rr * V + (V - 1);
+            const int oxr = has_r ? moff + V : a.lay.right_off + rr * V;
+            int64_t gidx = (int64_t)(DESC ? z0 + nz - 1 : z0) * LL + (int64_t)(y0 + row) * L + x0 + xv * V;
 
-        // CONV: convert this thread's cells of stage s, and the halo entries
-        // only it reads, to packed double-single pairs (DS), fixed-point
-        // values (FX) or fixed-point pairs (FXF) in place, then announce it;
-        // every FP64 value is converted once per pass instead of at each use
-        auto convert_stage = [&](int s) {
-            if constexpr (CONV) {
-                bool ovf = false;
-                if (active) {
+            // CONV: convert this thread's cells of stage s, and the halo entries
+            // only it reads, to packed double-single pairs (DS), fixed-point
+            // values (FX) or fixed-point pairs (FXF) in place, then announce it;
+            // every FP64 value is converted once per pass instead of at each use
+            auto convert_stage = [&](int s) {
+                if constexpr (CONV) {
+                    bool ovf = false;
+                    if (active) {
 #pragma unroll
-                    for (int f = 0; f < 2; ++f) {
-                        T* bf = ring + s * stage_elems + f * a.lay.field_elems;
-                        auto cvt = [&](int off) {
-                            if constexpr (DS) {
-                                bf[off] = ds_pack(ds_from_double(bf[off]));
-                            } else if constexpr (AR == 2) {
-                                bool o;
-                                bf[off] = fx_pack(fx_from_double(bf[off], o));
-                                ovf |= o;
-                            } else {
-                                bool o;
-                                bf[off] = fxf_pack(fxf_from_double(bf[off], o));
-                                ovf |= o;
+                        for (int f = 0; f < 2; ++f) {
+                            T* bf = ring + s * stage_elems + f * a.lay.field_elems;
+                            auto cvt = [&](int off) {
+                                if constexpr (DS) {
+                                    bf[off] = ds_pack(ds_from_double(bf[off]));
+                                } else if constexpr (AR == 2) {
+                                    bool o;
+                                    bf[off] = fx_pack(fx_from_double(bf[off], o));
+                                    ovf |= o;
+                                } else {
+                                    bool o;
+                                    bf[off] = fxf_pack(fxf_from_double(bf[off], o));
+                                    ovf |= o;
+                                }
+                            };
+#pragma unroll
+                            for (int e = 0; e < V; ++e) {
+                                cvt(moff + e);
+                                if (row == 0) cvt(a.lay.top_off + xv * V + e);
+                                if (row + 1 == nvy) cvt(a.lay.bot_off + xv * V + e);
                             }
-                        };
-#pragma unroll
-                        for (int e = 0; e < V; ++e) {
-                            cvt(moff + e);
-                            if (row == 0) cvt(a.lay.top_off + xv * V + e);
-                            if (row + 1 == nvy) cvt(a.lay.bot_off + xv * V + e);
+                            if (xv == 0) cvt(oxl);
+                            if (!has_r) cvt(oxr);
                         }
-                        if (xv == 0) cvt(oxl);
-                        if (!has_r) cvt(oxr);
+                    }
+                    if constexpr (AR >= 2) {
+                        if (__any_sync(0xffffffffu, ovf) && lane == 0) gs_report(a.err, GS_DERR_RANGE);
+                    }
+                    (void)ovf;
+                    __syncwarp();
+                    if (lane == 0) gs_mbar_arrive(&conv[s]);
+                }
+            };
+            auto load_centre = [&](T (&u)[V], T (&v)[V]) {
+                const T* b = ring + cs * stage_elems;
+                gs_unpack<T>(*reinterpret_cast<const VT*>(b + moff), u);
+                gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + moff), v);
+            };
+            // one plane: P, C, N are planes z-1, z, z+1 (N is loaded here); the
+            // centre plane's stage is released afterwards
+            int sc = 0;
+            uint32_t scp = 0;  // the centre stage's round parity
+            auto plane = [&](T (&pu)[V], T (&pv)[V], T (&cu)[V], T (&cv)[V], T (&nu)[V], T (&nv)[V]) -> bool {
+                // z-1 and z+1 of the centre plane: P and N marching up, N and P down
+                auto pick = [&](T (&up)[V], T (&dn)[V]) -> T (&)[V] {
+                    if constexpr (DESC) return dn; else return up;
+                };
+                T (&zmu)[V] = pick(pu, nu);
+                T (&zmv)[V] = pick(pv, nv);
+                T (&zpu)[V] = pick(nu, pu);
+                T (&zpv)[V] = pick(nv, pv);
+                const int sn = cs;
+                const uint32_t snp = cph;
+                if (!wait_full()) return false;
+                convert_stage(cs);
+                load_centre(nu, nv);
+                // x neighbours of the group's end cells from the adjacent lanes;
+                // the FP64 arithmetics on the FP32 and integer pipes read them all
+                // from shared memory instead (four loads issue fewer instructions
+                // than eight 32-bit shuffles and the edge lanes' loads)
+                T shlu{}, shlv{}, shru{}, shrv{};
+                if constexpr (AR == 0) {
+                    shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
+                    shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
+                    shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
+                    shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
+                }
+                if constexpr (CONV) {
+                    // every warp's part of the centre stage is converted
+                    if (!gs_mbar_wait(&conv[sc], scp, a.timeout_ns)) {
+                        gs_report(a.err, GS_DERR_TIMEOUT);
+                        abort_flag = 1;
+                        return false;
                     }
                 }
-                if constexpr (AR >= 2) {
-                    if (__any_sync(0xffffffffu, ovf) && lane == 0) gs_report(a.err, GS_DERR_RANGE);
+                if (active) {
+                    T outu[V], outv[V];
+                    const T* bu = ring + sc * stage_elems;
+                    const T* bv = bu + a.lay.field_elems;
+                    T ymu[V], ypu[V], ymv[V], ypv[V];
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
+                    gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
+                    T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
+                    if (AR != 0 || l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
+                    if (AR != 0 || r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
+                    const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
+                    if constexpr (DS)
+                        gs_update_group_ds<NOISE, GsFromPacked, PACK>(a.cds, pre, kk2, cu, cv, zmu, zmv, zpu, zpv, ymu,
+                                                                      ypu, ymv, ypv, xlu, xru, xlv, xrv, outu, outv);
+                    else if constexpr (AR == 2)
+                        gs_update_group_fx<NOISE, PACK>(a.cfx, pre, kk2, cu, cv, zmu, zmv, zpu, zpv, ymu, ypu, ymv, ypv,
+                                                        xlu, xru, xlv, xrv, outu, outv);
+                    else if constexpr (FXF) {
+                        uint32_t rng = 0;
+                        gs_update_group_fxf<NOISE, PACK, FXF_DT>(a.cfxf, pre, kk2, cu, cv, zmu, zmv, zpu, zpv, ymu, ypu,
+                                                                 ymv, ypv, xlu, xru, xlv, xrv, outu, outv, rng);
+                        range_bad |= fxf_range_bad(rng);
+                    }
+                    else
+                        gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, zmu, zmv, zpu, zpv, ymu, ypu, ymv, ypv, xlu,
+                                                  xru, xlv, xrv, outu, outv);
+                    *reinterpret_cast<VT*>(a.un + gidx) = gs_pack<T>(outu);
+                    *reinterpret_cast<VT*>(a.vn + gidx) = gs_pack<T>(outv);
                 }
-                (void)ovf;
-                __syncwarp();
-                if (lane == 0) gs_mbar_arrive(&conv[s]);
-            }
-        };
-        auto load_centre = [&](T (&u)[V], T (&v)[V]) {
-            const T* b = ring + cs * stage_elems;
-            gs_unpack<T>(*reinterpret_cast<const VT*>(b + moff), u);
-            gs_unpack<T>(*reinterpret_cast<const VT*>(b + a.lay.field_elems + moff), v);
-        };
-        // one plane: P, C, N are planes z-1, z, z+1 (N is loaded here); the
-        // centre plane's stage is released afterwards
-        int sc = 0;
-        uint32_t scp = 0;  // the centre stage's round parity
-        auto plane = [&](T (&pu)[V], T (&pv)[V], T (&cu)[V], T (&cv)[V], T (&nu)[V], T (&nv)[V]) -> bool {
-            const int sn = cs;
-            const uint32_t snp = cph;
+                release(sc);
+                sc = sn;
+                scp = snp;
+                advance();
+                gidx += DESC ? -LL : LL;
+                return true;
+            };
+
+            // the plane before the first: centre values only (waited for above)
             if (!wait_full()) return false;
             convert_stage(cs);
-            load_centre(nu, nv);
-            // x neighbours of the group's end cells from the adjacent lanes;
-            // the FP64 arithmetics on the FP32 and integer pipes read them all
-            // from shared memory instead (four loads issue fewer instructions
-            // than eight 32-bit shuffles and the edge lanes' loads)
-            T shlu{}, shlv{}, shru{}, shrv{};
-            if constexpr (AR == 0) {
-                shlu = __shfl_up_sync(0xffffffffu, cu[V - 1], 1);
-                shlv = __shfl_up_sync(0xffffffffu, cv[V - 1], 1);
-                shru = __shfl_down_sync(0xffffffffu, cu[0], 1);
-                shrv = __shfl_down_sync(0xffffffffu, cv[0], 1);
-            }
-            if constexpr (CONV) {
-                // every warp's part of the centre stage is converted
-                if (!gs_mbar_wait(&conv[sc], scp, a.timeout_ns)) {
-                    gs_report(a.err, GS_DERR_TIMEOUT);
-                    abort_flag = 1;
-                    return false;
-                }
-            }
-            if (active) {
-                T outu[V], outv[V];
-                const T* bu = ring + sc * stage_elems;
-                const T* bv = bu + a.lay.field_elems;
-                T ymu[V], ypu[V], ymv[V], ypv[V];
-                gs_unpack<T>(*reinterpret_cast<const VT*>(bu + om), ymu);
-                gs_unpack<T>(*reinterpret_cast<const VT*>(bu + op), ypu);
-                gs_unpack<T>(*reinterpret_cast<const VT*>(bv + om), ymv);
-                gs_unpack<T>(*reinterpret_cast<const VT*>(bv + op), ypv);
-                T xlu = shlu, xlv = shlv, xru = shru, xrv = shrv;
-                if (AR != 0 || l_smem) { xlu = bu[oxl]; xlv = bv[oxl]; }
-                if (AR != 0 || r_smem) { xru = bu[oxr]; xrv = bv[oxr]; }
-                const uint32_t pre = NOISE ? gs_group_pre((uint32_t)gidx, a.keys) : 0u;
-                if constexpr (DS)
-                    gs_update_group_ds<NOISE, GsFromPacked, PACK>(a.cds, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu,
-                                                                  ymv, ypv, xlu, xru, xlv, xrv, outu, outv);
-                else if constexpr (AR == 2)
-                    gs_update_group_fx<NOISE, PACK>(a.cfx, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu,
-                                                    xru, xlv, xrv, outu, outv);
-                else if constexpr (FXF) {
-                    uint32_t rng = 0;
-                    gs_update_group_fxf<NOISE, PACK, FXF_DT>(a.cfxf, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv,
-                                                             ypv, xlu, xru, xlv, xrv, outu, outv, rng);
-                    range_bad |= fxf_range_bad(rng);
-                }
-                else
-                    gs_update_group<T, NOISE>(a.c, pre, kk2, cu, cv, pu, pv, nu, nv, ymu, ypu, ymv, ypv, xlu, xru,
-                                              xlv, xrv, outu, outv);
-                *reinterpret_cast<VT*>(a.un + gidx) = gs_pack<T>(outu);
-                *reinterpret_cast<VT*>(a.vn + gidx) = gs_pack<T>(outv);
-            }
-            release(sc);
-            sc = sn;
-            scp = snp;
+            load_centre(qu[0], qv[0]);
+            release(cs);
             advance();
-            gidx += LL;
-            return true;
+            // the first plane
+            sc = cs;
+            scp = cph;
+            if (!wait_full()) return false;
+            convert_stage(cs);
+            load_centre(qu[1], qv[1]);
+            advance();
+
+            int zi = 0;
+            for (; zi + 3 <= nz; zi += 3) {
+                if (!plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2])) return false;
+                if (!plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0])) return false;
+                if (!plane(qu[2], qv[2], qu[0], qv[0], qu[1], qv[1])) return false;
+            }
+            // remainder (each tile reloads planes z0 - 1 and z0 into q0, q1)
+            if (zi < nz && !plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2])) return false;
+            if (zi + 1 < nz && !plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0])) return false;
+            release(sc);  // the plane after the last (only its centre was used)
+            return !abort_flag;
         };
-
-        // plane z0 - 1: centre values only
-        if (!wait_full()) return;
-        convert_stage(cs);
-        load_centre(qu[0], qv[0]);
-        release(cs);
-        advance();
-        // plane z0
-        sc = cs;
-        scp = cph;
-        if (!wait_full()) return;
-        convert_stage(cs);
-        load_centre(qu[1], qv[1]);
-        advance();
-
-        int zi = 0;
-        for (; zi + 3 <= nz; zi += 3) {
-            if (!plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2])) return;
-            if (!plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0])) return;
-            if (!plane(qu[2], qv[2], qu[0], qv[0], qu[1], qv[1])) return;
-        }
-        // remainder (each tile reloads planes z0 - 1 and z0 into q0, q1)
-        if (zi < nz && !plane(qu[0], qv[0], qu[1], qv[1], qu[2], qv[2])) return;
-        if (zi + 1 < nz && !plane(qu[1], qv[1], qu[2], qv[2], qu[0], qv[0])) return;
-        release(sc);  // plane z0 + nz (only its centre was used)
-        if (abort_flag) return;
+        bool ok;
+        if constexpr (AR == 0)
+            ok = dsc.w < 0 ? run(std::true_type{}) : run(std::false_type{});
+        else
+            ok = run(std::false_type{});  // these march up only
+        if (!ok) return;
     }
     if (range_bad) gs_report(a.err, GS_DERR_RANGE);
 }
@@ -709,7 +818,7 @@ int zmarch_encode(int dtype, int L, const ZPlan& pl, void* u, void* v, ZMaps* ma
 template <typename T, bool NOISE, int AR, int IO = 0>
 static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
                            const Params& p, int64_t t, int* d_err, uint64_t timeout_ns,
-                           int stall, cudaStream_t s)
+                           int stall, unsigned* tickets, cudaStream_t s)
 {
     constexpr int V = GsVec<T>::N;
     ZArgs<T> a;
@@ -733,6 +842,8 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
     a.err = d_err;
     a.timeout_ns = timeout_ns;
     a.stall = stall;
+    a.tickets = AR == 0 ? tickets : nullptr;
+    a.alternate = AR == 0;
     const int ncons = (pl.tx / V) * pl.ty;
     const int threads = ((ncons + 31) & ~31) + 32;
     const size_t smem = (size_t)a.lay.stage_bytes * pl.stages;
@@ -755,16 +866,16 @@ static int zmarch_launch_t(int L, const ZPlan& pl, const ZMaps& maps, void* un, 
 
 int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un, void* vn,
                   const Params& p, int64_t t, int* d_err, uint64_t timeout_ns, int stall,
-                  cudaStream_t s)
+                  unsigned* tickets, cudaStream_t s)
 {
     const bool noise = p.noise != 0.0;
     if (dtype == GS_F32)
-        return noise ? zmarch_launch_t<float, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                     : zmarch_launch_t<float, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+        return noise ? zmarch_launch_t<float, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, tickets, s)
+                     : zmarch_launch_t<float, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, tickets, s);
     if (p.arith == GS_ARITH_DS || p.arith == GS_ARITH_FX || p.arith == GS_ARITH_FXF) {
 #define GS_ZM(AR, IO)                                                                                            \
-    return noise ? zmarch_launch_t<double, true, AR, IO>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s) \
-                 : zmarch_launch_t<double, false, AR, IO>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
+    return noise ? zmarch_launch_t<double, true, AR, IO>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, tickets, s) \
+                 : zmarch_launch_t<double, false, AR, IO>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, tickets, s)
 #define GS_ZM_IO(AR)          \
     switch (p.io & 3) {       \
     case 0: GS_ZM(AR, 0);     \
@@ -787,8 +898,8 @@ int launch_zmarch(int dtype, int L, const ZPlan& pl, const ZMaps& maps, void* un
 #undef GS_ZM_IO
 #undef GS_ZM
     }
-    return noise ? zmarch_launch_t<double, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s)
-                 : zmarch_launch_t<double, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, s);
+    return noise ? zmarch_launch_t<double, true, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, tickets, s)
+                 : zmarch_launch_t<double, false, 0>(L, pl, maps, un, vn, p, t, d_err, timeout_ns, stall, tickets, s);
 }
 
 }  // namespace gs
