@@ -50,7 +50,9 @@ constexpr int kBatchConsumers = 256;
 constexpr int kBatchThreads = kBatchConsumers + 32;
 
 struct BInst {
-    int L, ty, nty, ntz;
+    int L;
+    int ty;         // rows of a tile's TMA box (the most rows a 256 V-cell run touches)
+    int nty, ntz;   // tiles per plane, z-chunks
     int item0, nitems;
     uint32_t seed_lo, seed_hi;
     double F, Fk;
@@ -1051,7 +1053,7 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
         gs_batch_destroy(b);
         return rc;
     }
-    // tensor maps: persistent kernel (full-row boxes) and the sequential baseline (z-march plans)
+    // tensor maps: persistent kernel (boxes of the rows a tile touches) and the sequential baseline (z-march plans)
     std::vector<CUtensorMap> maps((size_t)n * 8);
     b->zplan.resize(n);
     b->zmaps[0].resize(n);
