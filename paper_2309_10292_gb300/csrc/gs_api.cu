@@ -330,7 +330,7 @@ int gs_step(gs_sim* s, int64_t n)
         for (; i + D <= n; i += D) {
             const int in = s->cur, outs = 1 - s->cur;
             int rc = launch_tblock(s->L, s->tp, s->buf[in][0], s->buf[in][1], s->buf[outs][0], s->buf[outs][1],
-                                   s->p, s->t, s->stream);
+                                   s->p, s->t, (unsigned*)(s->d_err + 2), s->stream);
             if (rc) return rc;
             s->launches += 1;
             s->cur = outs;

@@ -88,8 +88,9 @@ int launch_hold_faces(int dtype, int L, const void* iu, const void* iv, void* ou
 
 // Temporally blocked kernel (gs_tblock.cu): `depth` steps per pass, FP32.
 int tblock_validate(int dtype, int L, const ZPlan& pl);
+// tickets: as for launch_zmarch (the same two words serve both kernels)
 int launch_tblock(int L, const ZPlan& pl, const void* u, const void* v, void* un, void* vn, const Params& p,
-                  int64_t t, cudaStream_t s);
+                  int64_t t, unsigned* tickets, cudaStream_t s);
 
 }  // namespace gs
 

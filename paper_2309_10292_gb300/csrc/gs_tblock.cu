@@ -35,6 +35,40 @@ struct TbArgs {
     int plane_elems;      // H * W (one field of one plane)
     GsCoef<float> c;
     GsKeys keys[8];       // step t + s - 1 for level s
+    unsigned* tickets;    // [next ticket, CTAs done] (zeroed between launches), or null: round robin
+};
+
+// The tiles of a launch, in x, y, z order.  With a ticket counter each CTA
+// takes the next free tile when it finishes one: thread 0 draws one tile
+// ahead into a two-slot shared buffer (the barrier that ends every tile
+// orders the hand-off), and the last CTA to finish zeroes the counter for
+// the next launch.  Without one, CTA c takes tiles c, c + G, ...
+struct TbTiles {
+    const TbArgs& a;
+    int* slot;  // two shared-memory slots
+    int k = 0;
+    GS_D int draw() { return a.tickets ? (int)atomicAdd(&a.tickets[0], 1u) : (int)blockIdx.x + (k++) * (int)gridDim.x; }
+    GS_D void start()
+    {
+        if (threadIdx.x == 0) slot[0] = draw();
+        __syncthreads();
+    }
+    // tile n of this CTA (>= ntiles: none left); thread 0 draws tile n + 1
+    GS_D int get(int n)
+    {
+        const int tile = slot[n & 1];
+        if (threadIdx.x == 0 && tile < a.ntiles) slot[(n + 1) & 1] = draw();
+        return tile;
+    }
+    GS_D void finish()
+    {
+        if (threadIdx.x != 0 || !a.tickets) return;
+        __threadfence();
+        if (atomicAdd(&a.tickets[1], 1u) == gridDim.x - 1) {
+            a.tickets[0] = 0;
+            a.tickets[1] = 0;
+        }
+    }
 };
 
 // Shared memory: level-0 ring of kTbStages planes, then for each level
@@ -74,7 +108,12 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_kernel(const TbArgs a)
 #pragma unroll
     for (int s = 0; s < D; ++s) kk2[s] = gs_kk2(a.keys[s]);
 
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    __shared__ int s_tile[2];
+    TbTiles tiles{a, s_tile};
+    tiles.start();
+    for (int n = 0;; ++n) {
+        const int tile = tiles.get(n);
+        if (tile >= a.ntiles) break;
         const int txi = tile % a.ntx;
         const int tyi = (tile / a.ntx) % a.nty;
         const int tzi = tile / (a.ntx * a.nty);
@@ -84,6 +123,7 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_kernel(const TbArgs a)
         tb_item<NOISE, D, false>(a.u, a.v, a.un, a.vn, L, (uint32_t)yg * (uint32_t)L + (uint32_t)xg, z0, min(a.tz, L - z0),
                           a.c, a.keys, kk2, th, ring, lev, a.plane_elems);
     }
+    tiles.finish();
 }
 
 // ---------------------------------------------------------------------------
@@ -131,7 +171,12 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_deep_kernel(const TbArgs a)
 #pragma unroll
     for (int s = 0; s < D; ++s) kk2[s] = gs_kk2(a.keys[s]);
 
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    __shared__ int s_tile[2];
+    TbTiles tiles{a, s_tile};
+    tiles.start();
+    for (int n = 0;; ++n) {
+        const int tile = tiles.get(n);
+        if (tile >= a.ntiles) break;
         const int txi = tile % a.ntx;
         const int tyi = (tile / a.ntx) % a.nty;
         const int tzi = tile / (a.ntx * a.nty);
@@ -216,6 +261,7 @@ __global__ void __launch_bounds__(512, 1) gs_tblock_deep_kernel(const TbArgs a)
         tb_wait<0>();
         __syncthreads();
     }
+    tiles.finish();
 }
 
 static int tblock_halo_x(int depth) { return depth <= 4 ? 4 : kTbDeepHX; }
@@ -245,7 +291,7 @@ int tblock_validate(int dtype, int L, const ZPlan& pl)
 
 template <bool NOISE, int D>
 static int tblock_launch_t(int L, const ZPlan& pl, const void* u, const void* v, void* un, void* vn,
-                           const Params& p, int64_t t, cudaStream_t s)
+                           const Params& p, int64_t t, unsigned* tickets, cudaStream_t s)
 {
     TbArgs a;
     a.u = (const float*)u;
@@ -265,6 +311,7 @@ static int tblock_launch_t(int L, const ZPlan& pl, const void* u, const void* v,
     a.plane_elems = a.W * a.H;
     a.c = gs_make_coef<float>(p.Du, p.Dv, p.F, p.k, p.dt, p.noise);
     for (int i = 0; i < 8; ++i) a.keys[i] = gs_step_keys(p.seed, t + (i < D ? i : 0));
+    a.tickets = tickets;
     const int threads = (a.G * a.H + 31) & ~31;
     const size_t smem = tblock_smem(D, a.W, a.H);
     void (*kern)(const TbArgs) = nullptr;
@@ -283,11 +330,11 @@ static int tblock_launch_t(int L, const ZPlan& pl, const void* u, const void* v,
 }
 
 int launch_tblock(int L, const ZPlan& pl, const void* u, const void* v, void* un, void* vn, const Params& p,
-                  int64_t t, cudaStream_t s)
+                  int64_t t, unsigned* tickets, cudaStream_t s)
 {
     const bool nz = p.noise != 0.0;
 #define GS_TB_CASE(DD) \
-    case DD: return nz ? tblock_launch_t<true, DD>(L, pl, u, v, un, vn, p, t, s) : tblock_launch_t<false, DD>(L, pl, u, v, un, vn, p, t, s);
+    case DD: return nz ? tblock_launch_t<true, DD>(L, pl, u, v, un, vn, p, t, tickets, s) : tblock_launch_t<false, DD>(L, pl, u, v, un, vn, p, t, tickets, s);
     switch (pl.depth) {
         GS_TB_CASE(2)
         GS_TB_CASE(3)
