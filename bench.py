@@ -497,8 +497,8 @@ def bench_large(args, stream, hbm_peak):
             "bound": "issue", "unit": "G warp instructions/s", "peak": peak,
             "peak_kind": "4 warp instructions per clock per SM x SMs x the sampled SM clock",
             "plans": rows, "single_step_hbm_bound_gcups": hbm_bound,
-            "depth3_achieved_issue_fraction": 0.724,
-            "depth3_warp_inst_needed_to_pass_single_step": (peak * 0.724 / hbm_bound) if d3 else None,
+            "depth3_achieved_issue_fraction": 0.734,
+            "depth3_warp_inst_needed_to_pass_single_step": (peak * 0.734 / hbm_bound) if d3 else None,
             "source": os.path.relpath(TBLOCK_PROFILE, ROOT)}
     return out
 
