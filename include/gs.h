@@ -121,7 +121,9 @@ int gs_create_on(int L, double Du, double Dv, double F, double k, double dt, dou
                  void* stream, gs_sim** out);
 
 /* Use `stream` (a cudaStream_t, caller-owned, NULL = legacy default) for all
- * later device work of this object. */
+ * later device work of this object.  A different stream first waits for the
+ * work already issued on the old one (steps of one grid never overlap: they
+ * share its fields and its kernels' work-unit counter). */
 int gs_set_stream(gs_sim* sim, void* stream);
 
 /* The object's stream and grid: edge L and dtype. */
@@ -298,7 +300,8 @@ int gs_single_destroy(gs_single* s);
 int gs_batch_create(int n, const int* L, const double* F, const double* k, double Du, double Dv,
                     double dt, double noise, uint64_t seed, int dtype, gs_batch** out);
 
-/* Stream for later device work (caller-owned; NULL = legacy default). */
+/* Stream for later device work (caller-owned; NULL = legacy default).  A
+ * different stream first waits for the work already issued on the old one. */
 int gs_batch_set_stream(gs_batch* b, void* stream);
 
 /* Reset every instance to the centred cube and step 0; clears a recorded

@@ -290,6 +290,9 @@ int gs_create_on(int L, double Du, double Dv, double F, double k, double dt, dou
 int gs_set_stream(gs_sim* s, void* stream)
 {
     if (!s) return fail(GS_EINVAL, "sim is NULL");
+    // the work already issued finishes first: the next step's kernels must
+    // not overlap it (they share the fields and the work-unit counter)
+    if ((cudaStream_t)stream != s->stream) GS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->stream = (cudaStream_t)stream;
     return GS_OK;
 }

@@ -1100,6 +1100,9 @@ int gs_batch_create(int n, const int* L, const double* F, const double* k, doubl
 int gs_batch_set_stream(gs_batch* b, void* stream)
 {
     if (!b) return fail(GS_EINVAL, "batch is NULL");
+    // the work already issued finishes first: the next launch must not
+    // overlap it (they share the arena and the control block)
+    if ((cudaStream_t)stream != b->stream) GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->stream = (cudaStream_t)stream;
     return GS_OK;
 }
