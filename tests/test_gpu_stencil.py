@@ -224,6 +224,37 @@ def test_bounded_wait_timeout_reports_and_recovers():
     assert maxabs(u, uo) <= 1e-4 and maxabs(v, vo) <= 1e-4
 
 
+def test_grids_on_two_streams_step_at_the_same_time():
+    # each grid's z-march and blocked kernels draw work units from that grid's
+    # own counter, so two grids stepping at once on two streams leave each
+    # other's results bit for bit as when they step one after the other
+    import torch
+    L = 96
+    prm = dict(PAPER, noise=0.1, seed=5)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    grids = []
+    for st, plan in ((s1, (gs.GS_KERNEL_ZMARCH, 32, 4, 16)), (s2, (gs.GS_KERNEL_TBLOCK, 32, 8, 32, 2))):
+        g = gs.GrayScott(L, dtype="f32", stream=st, **prm)
+        g.set_plan(*plan)
+        grids.append(g)
+    for _ in range(8):
+        for g in grids:
+            g.step(4)
+    outs = [g.read() for g in grids]
+    refs = []
+    for plan in ((gs.GS_KERNEL_ZMARCH, 32, 4, 16), (gs.GS_KERNEL_TBLOCK, 32, 8, 32, 2)):
+        r = make(L, "f32", **prm)
+        r.set_plan(*plan)
+        r.step(32)
+        refs.append(r.read())
+        r.close()
+    for (u, v), (ur, vr) in zip(outs, refs):
+        np.testing.assert_array_equal(u, ur)
+        np.testing.assert_array_equal(v, vr)
+    for g in grids:
+        g.close()
+
+
 # ---------------------------------------------------------------------------
 # Temporal blocking: `depth` fused steps per HBM pass (FP32)
 # ---------------------------------------------------------------------------
