@@ -456,7 +456,9 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 76 : 96) gs_batch_kernel(const __gr
 // so no cell is recomputed in x) by ty_i + 2D rows (the y halo shrinks by
 // one row per level).  ty_i is the largest divisor of L_i with
 // (L_i / 4) (ty_i + 2D) groups fitting the 512 threads, one group of 4 cells
-// per thread.  All CTAs meet at the grid barrier after each pass (D steps).
+// per thread.  The CTAs take items from the ticket counter in table order
+// (the last grid / 2 cut in four along z), and all meet at the grid barrier
+// after each pass (D steps).
 // ---------------------------------------------------------------------------
 constexpr int kBtbThreads = 512;
 constexpr int kBtbStages = kTbStages;  // level-0 ring (7 planes measured no faster)
@@ -501,6 +503,7 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
     constexpr int V = 4;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ volatile int s_abort;
+    __shared__ int s_item[2];  // this CTA's current and next item (thread 0 draws one ahead)
     float* ring = reinterpret_cast<float*>(smem);
     const int PE = a.pe;
     float* lev = ring + (size_t)kBtbStages * 2 * PE;
@@ -513,7 +516,18 @@ __global__ void __launch_bounds__(kBtbThreads, 1) gs_batch_tb_kernel(const __gri
     for (; pass < a.npasses; ++pass) {
         const int in = (cur0 + (int)(pass & 1)) & 1, out = in ^ 1;
         const long long tp = t0 + pass * D;
-        for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        // items from the ticket counter in table order, as in the single-step
+        // kernel: every CTA draws one ticket past the pass's items, so pass p
+        // draws p (nitems + grid) .. p (nitems + grid) + nitems + grid - 1; the
+        // barrier that ends each item orders the hand-off of the next
+        const unsigned base = (unsigned)((unsigned long long)pass * (unsigned)(a.nitems + gridDim.x));
+        auto draw = [&]() -> int { return (int)(atomicAdd(&a.ctrl->next, 1u) - base); };
+        if (tid == 0) s_item[0] = draw();
+        __syncthreads();
+        for (int n = 0;; ++n) {
+            const int item = s_item[n & 1];
+            if (item >= a.nitems) break;
+            if (tid == 0) s_item[(n + 1) & 1] = draw();
             const int4 itm = a.items[item];
             const BInst& I = a.inst[itm.x];
             const int L = I.L, G = L / V, W = L;
@@ -648,38 +662,12 @@ static void plain_items(const BInst* inst, int n, int tz, int tile_cells, std::v
     }
 }
 
-// With `grid` CTAs taking items round robin, the last round holds
-// rem = n mod grid items and lasts a whole item for the CTAs that have one.
-// Cut each of those items along z into f = min(4, grid / rem) pieces (fewer
-// when it has fewer planes) appended after the full rounds, so the last
-// round lasts about 1/f of an item.  Every cell is still updated once.
-// (The temporally blocked kernel's items, all marching up.)
-static void split_tail(const std::vector<int4>& base, int grid, std::vector<int4>& out)
-{
-    out = base;
-    const int n = (int)base.size();
-    if (grid < 1 || n <= grid) return;
-    const int rem = n % grid;
-    if (rem == 0) return;
-    const int f = std::min(4, grid / rem);
-    if (f < 2) return;
-    out.resize(n - rem);
-    for (int q = n - rem; q < n; ++q) {
-        const int4 it = base[q];
-        const int parts = std::min(f, it.w);
-        for (int p = 0; p < parts; ++p) {
-            const int za = it.w * p / parts, zb = it.w * (p + 1) / parts;
-            out.push_back(make_int4(it.x, it.y, it.z + za, zb - za));
-        }
-    }
-}
-
 // For a launch whose CTAs take items from a ticket counter in table order:
-// cut the last m items along z into up to f pieces each (alternating their
-// direction), so the last items taken are short and the CTAs finish a step
-// within a fraction of an item of one another.  Every cell is still updated
-// once.
-static void split_last(const std::vector<int4>& base, int m, int f, std::vector<int4>& out)
+// cut the last m items along z into up to f pieces each (with `alternate`,
+// alternating their direction), so the last items taken are short and the
+// CTAs finish a step within a fraction of an item of one another.  Every
+// cell is still updated once.
+static void split_last(const std::vector<int4>& base, int m, int f, bool alternate, std::vector<int4>& out)
 {
     const int n = (int)base.size();
     m = std::min(std::max(m, 0), n);
@@ -691,7 +679,7 @@ static void split_last(const std::vector<int4>& base, int m, int f, std::vector<
         const int parts = std::min(f, nz);
         for (int p = 0; p < parts; ++p) {
             const int za = nz * p / parts, zb = nz * (p + 1) / parts;
-            const bool d = desc != ((p & 1) != 0);
+            const bool d = alternate ? desc != ((p & 1) != 0) : desc;
             out.push_back(make_int4(it.x, it.y, it.z + za, d ? za - zb : zb - za));
         }
     }
@@ -810,7 +798,7 @@ static int plain_prepare(gs_batch* b, int64_t n, BArgs<T>& a, size_t& smem)
     if (b->items_grid != grid) {
         // cut the last items for this grid (once per plan)
         std::vector<int4> items;
-        split_last(b->base_items, grid / 2, 4, items);
+        split_last(b->base_items, grid / 2, 4, true, items);
         GS_CUDA_TRY(cudaStreamSynchronize(b->stream));  // no launch still reads the old table
         const int rc = upload_items(b, items);
         if (rc) return rc;
@@ -849,7 +837,7 @@ static int tb_prepare(gs_batch* b, int64_t npasses, BtbArgs& a, size_t& smem)
     const int grid = std::min(per_sm * num_sms(), (int)b->tb_base_items.size());
     if (b->tb_items_grid != grid) {
         std::vector<int4> items;
-        split_tail(b->tb_base_items, grid, items);
+        split_last(b->tb_base_items, grid / 2, 4, false, items);  // the blocked item marches up only
         GS_CUDA_TRY(cudaStreamSynchronize(b->stream));
         const int rc = upload_tb_items(b, items);
         if (rc) return rc;
