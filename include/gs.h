@@ -75,9 +75,10 @@ enum {
  *                value outside is reported by the next gs_sync / gs_read as
  *                GS_EINVAL);
  *   GS_ARITH_FXF 32-bit fixed point (2^-22 units) with an FP32 remainder:
- *                exact integer neighbour sums and sum - 6u, float-pair
- *                products (about 47 significant bits, as double-single);
- *                requires |u|, |v| < 4 (reported as for GS_ARITH_FX).
+ *                exact integer neighbour sums, float-pair products of the
+ *                sums and the fields (Du lap u - F u taken as Du / 6 S -
+ *                (Du + F) u; a step rounds at a few 1e-15); requires
+ *                |u|, |v| < 4 (reported as for GS_ARITH_FX).
  * All three match the FP64 oracle within its 1e-10 tolerance. */
 enum {
     GS_ARITH_IEEE = 0, /* the dtype's own IEEE arithmetic (default)         */
@@ -309,8 +310,10 @@ int gs_batch_set_stream(gs_batch* b, void* stream);
 int gs_batch_init(gs_batch* b);
 
 /* Advance every instance n steps with ONE launch of a persistent kernel
- * (captured once per distinct n as a CUDA graph: barrier-counter reset +
- * kernel).  Between steps all CTAs meet at a bounded grid barrier.  At a
+ * (captured once per distinct n as a CUDA graph: reset of the barrier and
+ * work-item counters + kernel).  The CTAs take work items from the counter
+ * as they become free; between steps all CTAs meet at a bounded grid
+ * barrier.  At a
  * blocking depth D > 1 (gs_batch_set_depth) the graph holds the temporally
  * blocked kernel for n / D passes of D steps (one grid barrier per pass)
  * and, when D does not divide n, the single-step kernel for the remaining
@@ -412,9 +415,10 @@ int gs_batch_destroy(gs_batch* b);
  * call holds a lock from building its tables until its stream has finished,
  * so calls from several host threads run one after the other (another
  * process has its own copy of the array).  Its work items are the plain
- * (instance, run of 256 * V cells of a plane, 32-plane z-chunk) table:
- * unlike gs_batch_step it does not cut the partial last round of items
- * along z. */
+ * (instance, run of 256 * V cells of a plane, 32-plane z-chunk) table, taken
+ * round robin (CTA c takes items c, c + grid, ...): unlike gs_batch_step it
+ * neither draws items from a ticket counter nor cuts the last items along
+ * z. */
 int gs_batch_step_noalloc(int n, const int* L, const double* F, const double* k, double Du,
                           double Dv, double dt, double noise, uint64_t seed, int dtype, void* arena,
                           int64_t t, int cur, int64_t nsteps, void* stream);
